@@ -394,14 +394,15 @@ int orc_map(const uint8_t *bits, int n, int p0, int n_tx, int m, int64_t B, doub
 /* ------------------------------------------------------------------------- */
 /* AWGN (AWGN()([x, no]), Listing 1): y = x + sqrt(N0/2) g per real dimension.*/
 /* g by Box-Muller (Box & Muller 1958) on Philox stream 1: block q gives       */
-/* (x0,x1,x2,x3); u1 = ((x0>>8)+0.5) 2^-24, u2 = (x1>>8) 2^-24,                 */
+/* (x0,x1,x2,x3); u1 = ((x0>>9)+0.5) 2^-23 in (0,1), u2 = (x1>>8) 2^-24 in     */
+/* [0,1) -- both exact binary32 numbers, so every side draws the same pair --  */
 /* g[4q] = r cos(2 pi u2), g[4q+1] = r sin(2 pi u2) with r = sqrt(-2 ln u1),  */
 /* and likewise (x2,x3) -> g[4q+2], g[4q+3].  Complex symbol s takes          */
 /* (g[2s], g[2s+1]); real symbol s takes g[s].                                 */
 /* ------------------------------------------------------------------------- */
 void orc_gauss_pair(uint32_t a, uint32_t b, double *g0, double *g1)
 {
-    double u1 = ((double)(a >> 8) + 0.5) * (1.0 / 16777216.0);
+    double u1 = ((double)(a >> 9) + 0.5) * (1.0 / 8388608.0);
     double u2 = (double)(b >> 8) * (1.0 / 16777216.0);
     double r = sqrt(-2.0 * log(u1));
     double th = 2.0 * M_PI * u2;

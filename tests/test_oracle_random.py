@@ -102,8 +102,9 @@ def test_box_muller_distribution(orc):
 def test_box_muller_pair_values(orc):
     # u1 = 1/2, u2 = 0: r = sqrt(2 ln 2), angle 0
     g0, g1 = orc.gauss_pair(0x80000000 - 128, 0)
-    u1 = ((0x80000000 - 128) >> 8) + 0.5
-    u1 /= 2**24
+    u1 = ((0x80000000 - 128) >> 9) + 0.5
+    u1 /= 2**23
+    assert np.float32(u1) == u1  # the uniform is an exact binary32 number
     assert g0 == pytest.approx(np.sqrt(-2 * np.log(u1)), rel=1e-15)
     assert g1 == pytest.approx(0.0, abs=1e-15)
     # u2 = 1/4: angle pi/2
