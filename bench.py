@@ -1,0 +1,389 @@
+#!/usr/bin/env python3
+"""Throughput of the QC-LDPC Monte-Carlo hot path on GB300.
+
+Workload (BG1-shaped Z=384 full-size case): seeded BG1-shaped 46x68 base
+matrix, Z = 384 (n = 26112, k = 8448, the first 2Z systematic bits
+punctured, n_tx = 25344), 16-QAM Gray, AWGN at Eb/N0 = 2.0 dB, batch of 4096
+codewords, layered offset min-sum (beta 0.5), 20 iterations without early
+stop, FP16 messages with FP32 arithmetic.
+
+One step = one Monte-Carlo batch through the whole device path: Philox
+source + dual-diagonal encoder + Gray mapper + AWGN (sim_tx) -> APP demapper
+(demap_app) -> layered BP decoder (ldpc_bp_decode) -> error count
+(sim_count). Metric: decoded information Gbit/s = ranks x B x k / step time;
+edge-updates/s = ranks x B x E x iterations / step time.
+
+Timing: W warm-up steps, then K timed steps between barriers and device
+synchronisations, CUDA events on the launching stream, max over ranks.
+Every buffer (y 208 MB, LLRs 406 MB, messages 994 MB) is larger than L2,
+so no flush is needed.
+
+--impl reference times the CPU oracle (the reference arm of this repository:
+the paper ships no code) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "decoded info Gbit/s & edge-updates/s, 1 GB300, BG1 Z=384 20-iter; FP16 vs FP32 @ BER 1e-4"
+BG, Z, PUNCT, B, M, EBN0, ITERS, OFFSET, CLAMP = 1, 384, 2, 4096, 4, 2.0, 20, 0.5, 20.0
+SEED = 0x1DBC | (2 << 32)
+PROFILE = os.path.join(ROOT, "profiles", "decode_layered_minsum_f16_bg1_z384.md")
+
+
+def workload_config(batch=None):
+    batch = B if batch is None else batch
+    return {"workload": "BG1-shaped 46x68 seeded QC-LDPC (seed 1), Z=384, batch %d, 16-QAM, AWGN Eb/N0 %.1f dB, "
+                        "layered offset min-sum (0.5), 20 iterations, FP16 messages" % (batch, EBN0),
+            "code": "BG1-shaped 46x68, 316 blocks, Z=384, n=26112, k=8448, 2Z punctured",
+            "batch": batch, "modulation": "16-QAM", "ebn0_db": EBN0, "iters": ITERS, "msg": "fp16",
+            "l2": "inputs larger than L2 (y %d MB, LLR %d MB, messages %d MB): no flush"
+                  % (batch * 6336 * 8 >> 20, batch * 25344 * 4 >> 20, batch * 121344 * 2 >> 20)}
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class Clocks:
+    """Samples nvidia-smi SM clocks and throttle reasons during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index, self.proc, self.path = index, None, None
+
+    def start(self):
+        try:
+            self.path = f"/tmp/ldpcx_clocks_{os.getpid()}.csv"
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == 7:
+                rows.append(parts)
+        os.remove(self.path)
+        if not rows:
+            return None
+        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[3 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def profile_traffic():
+    """dram bytes per launch from the committed ncu summary, if the decoder source is unchanged since."""
+    try:
+        text = open(PROFILE).read()
+    except OSError:
+        return None, None
+    src = os.path.join(ROOT, "paper_2203_11854_gb300", "csrc", "decode.cu")
+    digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    vals = {}
+    for line in text.splitlines():
+        if ":" in line and line.strip().startswith("- "):
+            k, v = line.strip()[2:].split(":", 1)
+            vals[k.strip()] = v.strip().strip("`")
+    if vals.get("decode.cu sha256[:16]") != digest:
+        return None, vals.get("decode.cu sha256[:16]")
+    try:
+        return float(vals["dram bytes per codeword (full-launch scale)"]), digest
+    except (KeyError, ValueError):
+        return None, digest
+
+
+def cpu_baseline(seconds=12.0, ebn0=EBN0):
+    """The oracle as it stands (FP64, layered min-sum with the FP16 message store), whole chain, on all
+    host cores, for a bounded sample of codewords of the same workload."""
+    import oracle
+    code = oracle.Code(BG, Z, punct_cols=PUNCT)
+    cores = os.cpu_count() or 1
+    done, t_total, cw0 = 0, 0.0, 1 << 40
+    chunk = max(cores, 8)
+    while t_total < seconds and done < 20000:
+        t0 = time.perf_counter()
+        oracle.sim(code, seed=SEED, cw0=cw0 + done, B=chunk, ebn0_db=ebn0, m=M, demap_method=oracle.DEMAP_MAXLOG,
+                   algo=oracle.ALGO_MINSUM, iters=ITERS, prec=0, store=oracle.STORE_F16, offset=OFFSET,
+                   clamp=CLAMP, nthreads=cores)
+        t_total += time.perf_counter() - t0
+        done += chunk
+    k = code.k
+    return {"value": done * k / t_total / 1e9, "unit": "Gbit/s", "cores": cores, "kind": "oracle",
+            "sample": f"{done} codewords of the workload (FP64 oracle chain: source, GF(2) encoder, mapper, AWGN, "
+                      f"max-log demapper, layered min-sum with FP16 message store, 20 iterations), {t_total:.1f} s",
+            "codewords_per_s": done / t_total}
+
+
+def dist_setup(n_gpus):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world != n_gpus and world > 1:
+        raise SystemExit(f"--gpus {n_gpus} but WORLD_SIZE {world}")
+    return rank, world, local
+
+
+def run_reference(args):
+    rank, world, local = dist_setup(args.gpus)
+    if rank != 0:
+        return
+    import oracle
+    code = oracle.Code(BG, Z, punct_cols=PUNCT)
+    cores = os.cpu_count() or 1
+    per_step = max(cores, 8)
+    for i in range(args.warmup):
+        oracle.sim(code, seed=SEED, cw0=i * per_step, B=per_step, ebn0_db=EBN0, m=M,
+                   demap_method=oracle.DEMAP_MAXLOG, iters=ITERS, store=oracle.STORE_F16, nthreads=cores)
+    times = []
+    for i in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.sim(code, seed=SEED, cw0=(args.warmup + i) * per_step, B=per_step, ebn0_db=EBN0, m=M,
+                   demap_method=oracle.DEMAP_MAXLOG, iters=ITERS, store=oracle.STORE_F16, nthreads=cores)
+        times.append(time.perf_counter() - t0)
+    t = sum(times) / len(times)
+    value = per_step * code.k / t / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "Gbit/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(per_step),
+            "cpu_baseline": {"value": value, "unit": "Gbit/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{per_step} codewords per step of the workload through the FP64 oracle chain"},
+            "e2e": {"value": value, "unit": "Gbit/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_gpu(args):
+    import torch
+    rank, world, local = dist_setup(args.gpus)
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import paper_2203_11854_gb300 as lx
+    lx.load_library()
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    code = lx.qc_ldpc_build(BG, Z, punct_cols=PUNCT)
+    S = code.n_tx // M
+    kw = (code.k + 31) // 32
+    r = code.k / code.n_tx
+    n0 = torch.tensor([1.0 / (r * M * 10 ** (EBN0 / 10))], dtype=torch.float32, device=dev)
+    y = torch.empty((B, S, 2), dtype=torch.float32, device=dev)
+    info = torch.empty((B, kw), dtype=torch.int32, device=dev)
+    llr = torch.empty((B, code.n_tx), dtype=torch.float32, device=dev)
+    bits = torch.empty((B, kw), dtype=torch.int32, device=dev)
+    its = torch.empty((B,), dtype=torch.int32, device=dev)
+    counts = torch.zeros(5, dtype=torch.int64, device=dev)
+    dec = dict(algo=lx.LAYERED_MINSUM, iters=ITERS, msg_prec=lx.MSG_F16, offset=OFFSET, clamp=CLAMP)
+    ws = torch.empty(lx.ldpc_bp_workspace(code, B, **dec), dtype=torch.uint8, device=dev)
+    from paper_2203_11854_gb300 import multi
+    cw_base = multi.rank_cw_base(rank)  # disjoint codeword (Philox counter) ranges per rank
+
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+
+    def step(i, timed_decode=None):
+        lx.sim_tx(code, SEED, cw_base + i * B, B, M, n0, y_out=y, info_out=info, stream=stream)
+        lx.demap_app(y, n0, M, method=lx.DEMAP_MAXLOG, clamp=CLAMP, llr_out=llr, stream=stream)
+        if timed_decode is not None:
+            timed_decode[0].record(stream)
+        lx.ldpc_bp_decode(code, llr, **dec, llr_out=False, bits_out=bits, iters_out=its, ws=ws, stream=stream)
+        if timed_decode is not None:
+            timed_decode[1].record(stream)
+        lx.sim_count(info, bits, its, code.k, counts, stream=stream)
+
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    st, flags = lx.ldpcx_sync_status()
+    if st != 0:
+        raise SystemExit(f"device status after warm-up: {lx.ldpcx_status_str(st)}")
+    counts.zero_()
+
+    clocks = Clocks(local)
+    dec_ms = []
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    dec_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for i in range(args.steps):
+        starts[i].record(stream)
+        step(args.warmup + i, dec_ev[i])
+        ends[i].record(stream)
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    elapsed_ms = t_start.elapsed_time(t_end)
+    dec_ms = [a.elapsed_time(b) for a, b in dec_ev]
+    elapsed_ms = multi.max_time(elapsed_ms, device=dev)
+    c = counts.cpu().tolist()
+    ms_per_step = elapsed_ms / args.steps
+    value = world * B * code.k / (ms_per_step * 1e-3) / 1e9
+    edge_updates = world * B * code.edges * ITERS / (ms_per_step * 1e-3)
+
+    # decode-kernel roofline: algorithmic bytes per launch / mean decode launch time
+    s_msg = 2
+    alg_bytes = B * (code.edges * s_msg * 2 * (ITERS - 1) + 4 * code.n_tx + code.k / 8)
+    dec_mean = sum(dec_ms) / len(dec_ms)
+    pk, pk_kind = peaks()
+    achieved = alg_bytes / (dec_mean * 1e-3) / 1e9
+    traffic_cw, _ = profile_traffic()
+
+    result = None
+    if rank == 0:
+        variants = {}
+        if not args.quick:
+            variants = measure_variants(lx, code, llr, bits, its, stream, args, pk)
+        e2e = measure_e2e(lx, code, y, info, n0, dec, stream, args, dev)
+        cpu = None if (world > 1 or args.no_cpu) else cpu_baseline(args.cpu_seconds)
+        result = {
+            "metric": METRIC, "value": value, "unit": "Gbit/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "msg_dtype": "f16", "data": "synthetic",
+            "config": workload_config(),
+            "edge_updates_per_s": edge_updates,
+            "codewords_per_s": world * B / (ms_per_step * 1e-3),
+            "ber": c[1] / c[0] if c[0] else None, "bler": c[3] / c[2] if c[2] else None,
+            "decode_ms_per_launch": dec_mean,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                         "frac": achieved / pk["hbm_gbs"],
+                         "traffic": None if traffic_cw is None else traffic_cw * B,
+                         "kernel": "k_layered<20, min-sum, fp16>",
+                         "peak_kind": f"{pk_kind} HBM copy bandwidth",
+                         "algorithmic_bytes_per_launch": alg_bytes},
+            "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+            "gpu_launches": 4 * args.steps,
+            "variants": variants,
+        }
+        print(json.dumps(result), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return result
+
+
+def measure_variants(lx, code, llr, bits, its, stream, args, pk):
+    """Decode-kernel time of the other message formats and check-node rules on the same LLRs."""
+    import torch
+    out = {}
+    reps = max(3, min(args.steps, 10))
+    for name, algo, prec, s_msg in [("minsum_f32", lx.LAYERED_MINSUM, lx.MSG_F32, 4),
+                                    ("minsum_f16", lx.LAYERED_MINSUM, lx.MSG_F16, 2),
+                                    ("minsum_fix6", lx.LAYERED_MINSUM, lx.MSG_FIX6, 1),
+                                    ("spa_f32", lx.LAYERED_SPA, lx.MSG_F32, 4),
+                                    ("spa_f16", lx.LAYERED_SPA, lx.MSG_F16, 2)]:
+        dec = dict(algo=algo, iters=ITERS, msg_prec=prec, offset=OFFSET, clamp=CLAMP)
+        ws = torch.empty(lx.ldpc_bp_workspace(code, B, **dec), dtype=torch.uint8, device=llr.device)
+        for _ in range(2):
+            lx.ldpc_bp_decode(code, llr, **dec, bits_out=bits, iters_out=its, ws=ws, stream=stream)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        for _ in range(reps):
+            lx.ldpc_bp_decode(code, llr, **dec, bits_out=bits, iters_out=its, ws=ws, stream=stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / reps
+        alg = B * (code.edges * s_msg * 2 * (ITERS - 1) + 4 * code.n_tx + code.k / 8)
+        out[name] = {"decode_ms": ms, "gbps": B * code.k / (ms * 1e-3) / 1e9,
+                     "edge_updates_per_s": B * code.edges * ITERS / (ms * 1e-3),
+                     "hbm_frac": alg / (ms * 1e-3) / 1e9 / pk["hbm_gbs"]}
+        del ws
+    if "minsum_f32" in out and "minsum_f16" in out:
+        out["f16_over_f32"] = out["minsum_f32"]["decode_ms"] / out["minsum_f16"]["decode_ms"]
+    return out
+
+
+def measure_e2e(lx, code, y_dev, info_dev, n0, dec, stream, args, dev):
+    """The receiver through the public API from host memory: pinned y -> device, demap, decode, bits -> host."""
+    import torch
+    kw = (code.k + 31) // 32
+    y_host = y_dev.cpu().pin_memory()
+    bits_host = torch.empty((B, kw), dtype=torch.int32).pin_memory()
+    y_d = torch.empty_like(y_dev)
+    llr = torch.empty((B, code.n_tx), dtype=torch.float32, device=dev)
+    bits = torch.empty((B, kw), dtype=torch.int32, device=dev)
+    ws = torch.empty(lx.ldpc_bp_workspace(code, B, **dec), dtype=torch.uint8, device=dev)
+
+    def one():
+        y_d.copy_(y_host, non_blocking=True)
+        lx.demap_app(y_d, n0, M, method=lx.DEMAP_MAXLOG, clamp=CLAMP, llr_out=llr, stream=stream)
+        lx.ldpc_bp_decode(code, llr, **dec, bits_out=bits, iters_out=False, ws=ws, stream=stream)
+        bits_host.copy_(bits, non_blocking=True)
+
+    for _ in range(2):
+        one()
+    torch.cuda.synchronize()
+    reps = max(3, min(args.steps, 10))
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        one()
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / reps
+    return {"value": B * code.k / (ms * 1e-3) / 1e9, "unit": "Gbit/s",
+            "h2d_bytes_per_step": y_host.numel() * 4, "d2h_bytes_per_step": bits_host.numel() * 4,
+            "ms_per_step": ms, "path": "pinned host y -> demap_app -> ldpc_bp_decode -> host bits"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--quick", action="store_true", help="skip the per-variant decode timings")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--batch", type=int, default=B, help="codewords per step (4096 for the headline workload)")
+    args = ap.parse_args()
+    globals()["B"] = args.batch
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

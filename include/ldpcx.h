@@ -1,0 +1,276 @@
+/*
+ * ldpcx.h -- C ABI of the GB300 QC-LDPC Monte-Carlo library (libldpcx.so).
+ *
+ * The library implements the hot path of the link-level Monte-Carlo
+ * simulation shown as the "Hello, World!" chain of the Sionna white paper
+ * (arXiv 2203.11854, Listing 1): BinarySource -> LDPC5GEncoder -> Mapper ->
+ * AWGN -> Demapper("app") -> LDPC5GDecoder -> compute_ber, with the min-sum
+ * belief-propagation decoder written as a custom CUDA kernel (Sec. IV-A).
+ *
+ * Conventions shared by every entry point
+ *  - Every function returns an int status: LDPCX_OK (0) or a negative
+ *    LDPCX_E_* code. Argument errors are detected on the host before any
+ *    work is queued and leave all outputs untouched.
+ *  - Pointers documented as "device" must point to memory of the current CUDA
+ *    device (cudaMalloc / torch CUDA tensors). The caller owns every buffer;
+ *    the library only owns ldpcx_code_t objects and their internal tables.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream). Work is
+ *    queued asynchronously on it; results are ready once it is synchronised.
+ *  - Conditions only the GPU can see (a non-finite input, a bounded wait that
+ *    gave up) do not abort the kernel: they are latched in a device status
+ *    word and reported by ldpcx_sync_status().
+ *  - LLR convention: L = ln P(b=0 | y) / P(b=1 | y); hard decision b = 1 iff
+ *    L < 0. (Listing 2 of the paper feeds LLRs to a binary cross-entropy
+ *    "from logits", which is the opposite sign: logits = -L.)
+ *  - Bit vectors are packed little-endian in uint32 words: bit j of a
+ *    codeword's vector is bit (j mod 32) of word j/32; words per codeword =
+ *    ceil(bits / 32); unused high bits of the last word are zero.
+ */
+#ifndef LDPCX_H
+#define LDPCX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ status */
+#define LDPCX_OK 0
+#define LDPCX_E_INVAL (-1)       /* bad argument: null pointer, size or enum out of range */
+#define LDPCX_E_UNSUPPORTED (-2) /* valid request this build does not implement */
+#define LDPCX_E_NOMEM (-3)       /* host or device allocation failed */
+#define LDPCX_E_WORKSPACE (-4)   /* workspace missing, too small or misaligned */
+#define LDPCX_E_CUDA (-5)        /* a CUDA runtime call failed */
+#define LDPCX_E_NONFINITE (-6)   /* device-latched: a non-finite input was sanitised */
+#define LDPCX_E_TIMEOUT (-7)     /* device-latched: a bounded wait gave up */
+#define LDPCX_E_NODEVICE (-8)    /* no CUDA device is visible */
+
+/* Device status flags latched by kernels (ldpcx_sync_status). */
+#define LDPCX_FLAG_NONFINITE 1u  /* NaN input -> treated as 0; +-inf -> +-clamp */
+#define LDPCX_FLAG_TIMEOUT 2u
+
+/* Human-readable name of a status code; never NULL. */
+const char *ldpcx_status_str(int status);
+
+/* Synchronise `stream`, then return (in *flags) the OR of the device status
+ * flags latched since the previous call on this device, and clear them.
+ * Returns LDPCX_E_NONFINITE / LDPCX_E_TIMEOUT when a flag was set, LDPCX_OK
+ * otherwise. flags may be NULL. */
+int ldpcx_sync_status(void *stream, unsigned int *flags);
+
+/* ------------------------------------------------------------ code (a1) */
+/* A seeded quasi-cyclic LDPC code with the 5G-NR base-graph shape (the
+ * paper's "5G LDPC codes", Sec. III-B; LDPC5GEncoder in Listing 1). The 3GPP
+ * TS 38.212 shift tables are not used: the base matrix S (rows x cols, -1 =
+ * all-zero block, s >= 0 = identity cyclically shifted by s) is drawn from
+ * splitmix64(seed):
+ *   columns [0,Kb) systematic, [Kb,Kb+4) core parity, [Kb+4,cols) extension;
+ *   core parity blocks  row0 [1 0 - -]  row1 [0 0 0 -]  row2 [- - 0 0]
+ *                       row3 [1 - - 0]   (dual diagonal, rows sum to [I 0 0 0]);
+ *   extension row j: identity at column Kb+4+j;
+ *   support: core rows draw d_core distinct systematic columns, extension row
+ *   j draws d_ext(j) distinct columns of [0,Kb+4), each by a partial
+ *   Fisher-Yates shuffle (index i + next() mod (N - i)); then each drawn
+ *   block in row-major order gets shift next() mod Z.
+ *   bg_shape 1: Kb 22, 46 rows, 68 cols, d_core 16, d_ext 5 (j<33) / 4 -> 316 blocks.
+ *   bg_shape 2: Kb 10, 42 rows, 52 cols, d_core 8,  d_ext 4 (j<4)  / 3 -> 197 blocks.
+ * Block (r,c) with shift s joins check node r*Z+z to variable node
+ * c*Z + (z+s) mod Z. Codeword c = [u | p], u = the k = Kb*Z information bits.
+ * Transmission: the first punct_cols*Z systematic bits are not sent; the
+ * n_tx bits at positions [punct_cols*Z, punct_cols*Z + n_tx) are sent.
+ * rows_kept < rows keeps the first rows_kept rows and Kb+rows_kept columns
+ * (rate by extension truncation). */
+typedef struct ldpcx_code *ldpcx_code_t;
+
+typedef struct {
+    int bg_shape;   /* 1 or 2 */
+    int Z;          /* lifting size, 2..384 */
+    uint64_t seed;  /* splitmix64 seed of the support and the shifts */
+    int rows_kept;  /* 4..rows, or 0 = all rows */
+    int punct_cols; /* 0..Kb systematic columns not transmitted (5G uses 2) */
+    int n_tx;       /* transmitted bits; 0 = every bit after the punctured ones */
+} ldpcx_code_params;
+
+typedef struct {
+    int Z, rows, cols, kb;   /* base matrix shape */
+    int nnz;                 /* nonzero base blocks (= weight classes) */
+    int max_row_deg;         /* largest check-node degree */
+    int n, k, n_tx, p0;      /* codeword, info and transmitted bits; p0 = first transmitted position */
+    int64_t edges;           /* nnz * Z */
+} ldpcx_code_info;
+
+/* Build the code on the host (no device work; device tables are uploaded on
+ * first use on the then-current device). *out is owned by the caller until
+ * qc_ldpc_free. Errors: LDPCX_E_INVAL for a bad shape or null pointer. */
+int qc_ldpc_build(const ldpcx_code_params *params, ldpcx_code_t *out);
+/* Release the code and its device tables. NULL is accepted. The code must not
+ * be in use by queued work. */
+int qc_ldpc_free(ldpcx_code_t code);
+/* Sizes of the code. */
+int qc_ldpc_info(ldpcx_code_t code, ldpcx_code_info *info);
+/* Copy the base matrix (row-major int16, -1 = zero block) into host memory
+ * S_out of `capacity` entries (>= rows*cols, else LDPCX_E_INVAL). */
+int qc_ldpc_base(ldpcx_code_t code, int16_t *S_out, int capacity);
+
+/* ------------------------------------------------ transmitter (a2 .. a5) */
+/* Monte-Carlo transmitter for codewords cw0 .. cw0+B-1 (BinarySource,
+ * LDPC5GEncoder, Mapper, AWGN of Listing 1), all on the device:
+ *  - info bit j of codeword w = bit (j mod 32) of output word (j mod 128)/32
+ *    of Philox4x32-10 (Salmon et al., SC'11) with key (seed lo32, seed hi32)
+ *    and counter (j/128, w lo32, w hi32, 0);
+ *  - systematic encoding by the dual-diagonal recursion of the core followed
+ *    by the extension parities;
+ *  - Gray square QAM per dimension: bits b0,b2,.. -> I and b1,b3,.. -> Q, level
+ *    (1-2a0)(2^(h-1) - (1-2a1)(2^(h-2) - ...)) scaled to unit average energy;
+ *    m = 1 is BPSK x = 1-2b on a real channel;
+ *  - AWGN y = x + sqrt(N0/2) g per real dimension, g by Box-Muller from
+ *    Philox block q = (index of the Gaussian)/4 on stream 1: u1 = ((a>>9)+0.5)
+ *    2^-23, u2 = (b>>8) 2^-24 from words (a,b) = (x0,x1) or (x2,x3),
+ *    g = sqrt(-2 ln u1) (cos 2 pi u2, sin 2 pi u2); complex symbol s uses
+ *    Gaussians 2s, 2s+1; real symbol s uses Gaussian s.
+ * no: device float, N0 of codeword b at no[b * no_stride] (stride 0 or 1).
+ * y_out (device): m = 1 -> [B][n_tx] float; else [B][n_tx/m][2] float (re, im).
+ * info_out (device, or NULL): [B][ceil(k/32)] packed information bits.
+ * m in {1,2,4,6,8} and n_tx divisible by m, else LDPCX_E_INVAL. */
+int sim_tx(ldpcx_code_t code, uint64_t seed, uint64_t cw0, int64_t B, int m,
+           const float *no, int64_t no_stride, float *y_out, uint32_t *info_out, void *stream);
+
+/* ----------------------------------------------------------- demap (a6) */
+/* APP demapper (Demapper("app"), Listing 1) for Gray square QAM on AWGN:
+ *   L_i = ln sum_{x: b_i(x)=0} exp(-|y-x|^2/N0) - ln sum_{x: b_i(x)=1} exp(...)
+ * computed per I/Q dimension (exact for Gray square QAM on a circular AWGN
+ * channel: the other dimension's factor cancels). method LDPCX_DEMAP_EXACT
+ * uses log-sum-exp, LDPCX_DEMAP_MAXLOG the largest term. The result is
+ * clamped to [-clamp, clamp]. A non-finite y gives L = 0 and latches
+ * LDPCX_FLAG_NONFINITE.
+ * y (device): m = 1 -> [B][syms] float; else [B][syms][2] float (re, im).
+ * no (device): N0 of codeword b at no[b * no_stride] (stride 0 or 1).
+ * llr_out (device): [B][syms*m] float, bit i of symbol s at s*m + i. */
+#define LDPCX_DEMAP_EXACT 0
+#define LDPCX_DEMAP_MAXLOG 1
+int demap_app(const float *y, const float *no, int64_t no_stride, int64_t B, int64_t syms_per_cw,
+              int m, int method, float clamp, float *llr_out, void *stream);
+
+/* ------------------------------------------------ BP decoding (a7 .. a10) */
+/* Belief-propagation decoding (LDPC5GDecoder, "BP decoder and variants",
+ * Sec. III-B; min-sum BP as the custom CUDA op of Sec. IV-A). Messages
+ * R = check-to-variable; for the variable-to-check inputs T_i of a check:
+ *  offset min-sum: R_j = sgn_j s max(m_j - offset, 0), m_j = second smallest
+ *    |T| at the first index of the smallest, the smallest elsewhere,
+ *    s = prod_i sgn(T_i), sgn(x) = -1 iff x < 0;
+ *  sum-product: R_j = sgn_j s phi(sum_{i!=j} phi(|T_i|)),
+ *    phi(x) = -ln tanh(x/2), each phi argument clamped to [phi(clamp), clamp];
+ *  |R| <= clamp; then R is rounded to the message format (FP32 as is; FP16
+ *  round-to-nearest-even; FIX6: 6-bit fixed point with step 0.5, RNE,
+ *  saturated to +-31 steps) and the rounded value is stored and used.
+ * Layered schedule: layer = base row in ascending order, each check node
+ *  T_j = APP_v - R_j(old), CN rule, APP_v = T_j + R_j(new).
+ * Flooding schedule: T_j = w[t][blk] (APP_v(old) - R_j(old)) with w = 1 when
+ *  weights == NULL; APP_v(new) = L_v + sum of the new R over v's checks,
+ *  added in ascending base-row order.
+ * Channel LLRs are clamped to +-clamp (NaN -> 0, latching NONFINITE);
+ * punctured / untransmitted positions start at 0; APP is not clamped.
+ * Early stop: after each full iteration the hard decisions are checked
+ * against every parity check; a codeword stops at the first iteration whose
+ * syndrome is zero. Iteration count = full iterations run (1..iters).
+ * Arithmetic is binary32 in the order above (no fused multiply-add), so
+ * min-sum results are reproducible bit for bit. */
+#define LDPCX_LAYERED_MINSUM 0
+#define LDPCX_LAYERED_SPA 1
+#define LDPCX_FLOOD_MINSUM 2
+#define LDPCX_FLOOD_SPA 3
+#define LDPCX_MSG_F32 0
+#define LDPCX_MSG_F16 1
+#define LDPCX_MSG_FIX6 2 /* min-sum only */
+
+typedef struct {
+    int algo;             /* LDPCX_LAYERED_MINSUM .. LDPCX_FLOOD_SPA */
+    int iters;            /* 1..1000 */
+    int msg_prec;         /* LDPCX_MSG_* */
+    int early_stop;       /* 0 or 1 */
+    float offset;         /* min-sum offset beta >= 0 (0.5 for the 5G workloads) */
+    float clamp;          /* > 0; 20 for the 5G workloads */
+    const float *weights; /* flooding only: device [iters][nnz] per-iteration per-base-block
+                             weights (block index = row-major order of the base matrix), or NULL */
+} ldpcx_decode_opts;
+
+/* Workspace in bytes that ldpc_bp_decode needs for B codewords (message
+ * storage: B * round_up(edges, 64) messages of the chosen format). */
+int ldpc_bp_workspace(ldpcx_code_t code, int64_t B, const ldpcx_decode_opts *opts, size_t *ws_bytes);
+
+/* Decode B codewords.
+ * llr_ch   (device) [B][n_tx] float channel LLRs of the transmitted positions.
+ * llr_out  (device, or NULL) [B][n] float final APP LLRs.
+ * bits_out (device, or NULL) [B][ceil(k/32)] packed hard decisions of the k
+ *          information positions (punctured ones included).
+ * iters_out(device, or NULL) [B] int32 iterations run.
+ * ws       (device) >= ldpc_bp_workspace bytes, 256-byte aligned; contents
+ *          on entry are ignored and on exit undefined.
+ * Pure function of its inputs: the same call gives the same outputs. */
+int ldpc_bp_decode(ldpcx_code_t code, const float *llr_ch, int64_t B, const ldpcx_decode_opts *opts,
+                   float *llr_out, uint32_t *bits_out, int32_t *iters_out,
+                   void *ws, size_t ws_bytes, void *stream);
+
+/* Decoder tuning knobs (process-wide; read at each launch; the autotuner's
+ * search space). LDPCX_TUNE_L2_PREFETCH: layered decoders prefetch into L2 the
+ * message span of the layer this many layers ahead (0 = off, 0..16, default 3).
+ * Knobs change speed only, never results. */
+#define LDPCX_TUNE_L2_PREFETCH 1
+int ldpcx_tune_set(int key, int value);
+int ldpcx_tune_get(int key, int *value);
+
+/* ------------------------------------------------------ error count (a10) */
+/* compute_ber of Listing 1: for each codeword, bit errors = popcount over
+ * the k information bits of ref XOR hat; block error = any bit error.
+ * counts (device int64[5]) accumulates {info bits, bit errors, blocks,
+ * block errors, sum of iters} (iters may be NULL: the last term is then 0).
+ * ref, hat: device [B][ceil(k/32)] packed bits. */
+int sim_count(const uint32_t *ref, const uint32_t *hat, const int32_t *iters, int64_t B, int k,
+              int64_t *counts, void *stream);
+
+/* -------------------------------------------------- Monte-Carlo run (a13) */
+/* A BER/BLER sweep over Eb/N0 points (the loop around Listing 1): for each
+ * point, batches of `batch` codewords run sim_tx -> demap_app -> ldpc_bp_decode
+ * -> sim_count on the device; codeword indices continue across batches and
+ * points from cw0, so every draw is reproducible. N0 = 1/(r m 10^(EbN0/10)),
+ * r = k/n_tx. A point ends after max_batches batches or once it has
+ * min_bit_errors bit errors (checked between batches when > 0); the sweep
+ * ends early after a point whose BER is below stop_ber (> 0). With
+ * use_graph, one batch is captured once as a CUDA graph and replayed.
+ * The sweep synchronises `stream` first and then runs on a private stream of
+ * its own; it returns after all its work has finished. */
+typedef struct {
+    ldpcx_code_t code;
+    int m;                  /* bits per symbol: 1, 2, 4, 6, 8 */
+    int demap_method;       /* LDPCX_DEMAP_* */
+    float demap_clamp;      /* demapper LLR clamp */
+    ldpcx_decode_opts dec;  /* decoder options (weights not allowed) */
+    uint64_t seed;          /* Philox key */
+    uint64_t cw0;           /* first codeword index */
+    int64_t batch;          /* codewords per batch, >= 1 */
+    int64_t max_batches;    /* batches per point, >= 1 */
+    int64_t min_bit_errors; /* 0 = always run max_batches */
+    const double *ebn0_db;  /* host [n_snr] */
+    int n_snr;
+    double stop_ber;        /* 0 = never stop early */
+    int use_graph;          /* capture and replay one batch as a CUDA graph */
+} ldpcx_sim_config;
+
+typedef struct {
+    int64_t bits, bit_errors, blocks, block_errors, iter_sum;
+} ldpcx_sim_counts;
+
+/* Workspace bytes sim_run needs for cfg (batch buffers + decoder messages). */
+int sim_workspace(const ldpcx_sim_config *cfg, size_t *ws_bytes);
+/* Run the sweep. out: host [n_snr] counts (points not run are zero);
+ * *points_run = points executed. Synchronises `stream` once per batch check
+ * and once per point. ws: device, >= sim_workspace bytes, 256-byte aligned. */
+int sim_run(const ldpcx_sim_config *cfg, ldpcx_sim_counts *out, int *points_run,
+            void *ws, size_t ws_bytes, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LDPCX_H */

@@ -1,0 +1,335 @@
+"""GB300 QC-LDPC Monte-Carlo hot path: thin Python binding of libldpcx.so.
+
+Every function here has the name of the C entry point it calls (see
+``include/ldpcx.h``) and only marshals arguments: torch CUDA tensors supply
+device memory and the current stream supplies ``stream``. All computation
+runs in the CUDA kernels of ``csrc/``; there is no CPU fallback: when the
+library is missing or no GPU is present, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+from . import _build
+
+__all__ = [
+    "LdpcxError", "Code", "ldpcx_status_str", "ldpcx_sync_status", "qc_ldpc_build", "qc_ldpc_free",
+    "qc_ldpc_info", "qc_ldpc_base", "sim_tx", "demap_app", "ldpc_bp_workspace", "ldpc_bp_decode",
+    "sim_count", "sim_workspace", "sim_run", "library_path", "load_library", "ldpcx_tune_set", "ldpcx_tune_get",
+    "LAYERED_MINSUM", "LAYERED_SPA", "FLOOD_MINSUM", "FLOOD_SPA", "MSG_F32", "MSG_F16", "MSG_FIX6",
+    "DEMAP_EXACT", "DEMAP_MAXLOG",
+]
+
+LAYERED_MINSUM, LAYERED_SPA, FLOOD_MINSUM, FLOOD_SPA = 0, 1, 2, 3
+MSG_F32, MSG_F16, MSG_FIX6 = 0, 1, 2
+DEMAP_EXACT, DEMAP_MAXLOG = 0, 1
+FLAG_NONFINITE, FLAG_TIMEOUT = 1, 2
+TUNE_L2_PREFETCH = 1
+
+
+class LdpcxError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__(f"{what}: {ldpcx_status_str(status)} ({status})")
+
+
+class CodeParams(C.Structure):
+    _fields_ = [("bg_shape", C.c_int), ("Z", C.c_int), ("seed", C.c_uint64), ("rows_kept", C.c_int),
+                ("punct_cols", C.c_int), ("n_tx", C.c_int)]
+
+
+class CodeInfo(C.Structure):
+    _fields_ = [("Z", C.c_int), ("rows", C.c_int), ("cols", C.c_int), ("kb", C.c_int), ("nnz", C.c_int),
+                ("max_row_deg", C.c_int), ("n", C.c_int), ("k", C.c_int), ("n_tx", C.c_int), ("p0", C.c_int),
+                ("edges", C.c_int64)]
+
+
+class DecodeOpts(C.Structure):
+    _fields_ = [("algo", C.c_int), ("iters", C.c_int), ("msg_prec", C.c_int), ("early_stop", C.c_int),
+                ("offset", C.c_float), ("clamp", C.c_float), ("weights", C.c_void_p)]
+
+
+class SimConfig(C.Structure):
+    _fields_ = [("code", C.c_void_p), ("m", C.c_int), ("demap_method", C.c_int), ("demap_clamp", C.c_float),
+                ("dec", DecodeOpts), ("seed", C.c_uint64), ("cw0", C.c_uint64), ("batch", C.c_int64),
+                ("max_batches", C.c_int64), ("min_bit_errors", C.c_int64), ("ebn0_db", C.POINTER(C.c_double)),
+                ("n_snr", C.c_int), ("stop_ber", C.c_double), ("use_graph", C.c_int)]
+
+
+class SimCounts(C.Structure):
+    _fields_ = [("bits", C.c_int64), ("bit_errors", C.c_int64), ("blocks", C.c_int64),
+                ("block_errors", C.c_int64), ("iter_sum", C.c_int64)]
+
+
+_lib = None
+_lock = threading.Lock()
+_vp, _i, _i64, _u64, _f, _sz = C.c_void_p, C.c_int, C.c_int64, C.c_uint64, C.c_float, C.c_size_t
+
+_SIGS = {
+    "ldpcx_status_str": ([_i], C.c_char_p),
+    "ldpcx_sync_status": ([_vp, C.POINTER(C.c_uint)], _i),
+    "qc_ldpc_build": ([C.POINTER(CodeParams), C.POINTER(_vp)], _i),
+    "qc_ldpc_free": ([_vp], _i),
+    "qc_ldpc_info": ([_vp, C.POINTER(CodeInfo)], _i),
+    "qc_ldpc_base": ([_vp, _vp, _i], _i),
+    "sim_tx": ([_vp, _u64, _u64, _i64, _i, _vp, _i64, _vp, _vp, _vp], _i),
+    "demap_app": ([_vp, _vp, _i64, _i64, _i64, _i, _i, _f, _vp, _vp], _i),
+    "ldpc_bp_workspace": ([_vp, _i64, C.POINTER(DecodeOpts), C.POINTER(_sz)], _i),
+    "ldpc_bp_decode": ([_vp, _vp, _i64, C.POINTER(DecodeOpts), _vp, _vp, _vp, _vp, _sz, _vp], _i),
+    "sim_count": ([_vp, _vp, _vp, _i64, _i, _vp, _vp], _i),
+    "sim_workspace": ([C.POINTER(SimConfig), C.POINTER(_sz)], _i),
+    "sim_run": ([C.POINTER(SimConfig), C.POINTER(SimCounts), C.POINTER(_i), _vp, _sz, _vp], _i),
+    "ldpcx_tune_set": ([_i, _i], _i),
+    "ldpcx_tune_get": ([_i, C.POINTER(_i)], _i),
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load_library(build_if_missing: bool = False):
+    """Load libldpcx.so (raises when it is missing: there is no fallback)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(_build.LIB):
+                if not build_if_missing:
+                    raise ImportError(f"libldpcx.so is not built ({_build.LIB}); run __graft_entry__.build()")
+                _build.build()
+            L = C.CDLL(_build.LIB)
+            for name, (args, res) in _SIGS.items():
+                fn = getattr(L, name)
+                fn.argtypes = args
+                fn.restype = res
+            _lib = L
+    return _lib
+
+
+def _check(st: int, what: str) -> None:
+    if st != 0:
+        raise LdpcxError(st, what)
+
+
+def _ptr(t) -> int | None:
+    if t is None:
+        return None
+    return t.data_ptr()
+
+
+def _stream(stream) -> int | None:
+    if stream is not None:
+        return stream if isinstance(stream, int) else stream.cuda_stream
+    import torch
+    return torch.cuda.current_stream().cuda_stream
+
+
+def _cuda_f32(t, name):
+    import torch
+    if t.device.type != "cuda" or t.dtype != torch.float32 or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous float32 CUDA tensor")
+    return t
+
+
+def ldpcx_status_str(status: int) -> str:
+    return load_library().ldpcx_status_str(status).decode()
+
+
+def ldpcx_sync_status(stream=None) -> tuple[int, int]:
+    """Synchronise and return (status, flags) latched by the kernels since the last call."""
+    flags = C.c_uint(0)
+    st = load_library().ldpcx_sync_status(_stream(stream), C.byref(flags))
+    return st, flags.value
+
+
+# --------------------------------------------------------------------------- codes
+class Code:
+    """Owner of an ldpcx_code_t (freed with the object)."""
+
+    def __init__(self, handle: int):
+        self.handle = handle
+        info = CodeInfo()
+        _check(load_library().qc_ldpc_info(handle, C.byref(info)), "qc_ldpc_info")
+        self.info = info
+        for f, _ in CodeInfo._fields_:
+            setattr(self, f, getattr(info, f))
+
+    def base(self):
+        import numpy as np
+        S = np.zeros(self.rows * self.cols, dtype=np.int16)
+        _check(load_library().qc_ldpc_base(self.handle, S.ctypes.data, S.size), "qc_ldpc_base")
+        return S.reshape(self.rows, self.cols)
+
+    def close(self):
+        if self.handle:
+            load_library().qc_ldpc_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def qc_ldpc_build(bg_shape: int, Z: int, seed: int | None = None, rows_kept: int = 0, punct_cols: int = 0,
+                  n_tx: int = 0) -> Code:
+    seed = (1 if bg_shape == 1 else 2) if seed is None else seed
+    p = CodeParams(bg_shape, Z, seed, rows_kept, punct_cols, n_tx)
+    h = C.c_void_p()
+    _check(load_library().qc_ldpc_build(C.byref(p), C.byref(h)), "qc_ldpc_build")
+    return Code(h.value)
+
+
+def qc_ldpc_free(code: Code) -> None:
+    code.close()
+
+
+def qc_ldpc_info(code: Code) -> CodeInfo:
+    return code.info
+
+
+def qc_ldpc_base(code: Code):
+    return code.base()
+
+
+# --------------------------------------------------------------------------- transmitter
+def sim_tx(code: Code, seed: int, cw0: int, B: int, m: int, no, y_out=None, info_out=None, stream=None):
+    """Source + encoder + Gray mapper + AWGN for codewords cw0..cw0+B-1.
+
+    no: CUDA float32 tensor with 1 (shared) or B (per codeword) entries.
+    Returns (y [B, S] or [B, S, 2], info [B, ceil(k/32)] int32 view of the packed bits)."""
+    import torch
+    S = code.n_tx // m
+    dev = no.device
+    if y_out is None:
+        y_out = torch.empty((B, S) if m == 1 else (B, S, 2), dtype=torch.float32, device=dev)
+    if info_out is None:
+        info_out = torch.empty((B, (code.k + 31) // 32), dtype=torch.int32, device=dev)
+    _cuda_f32(no, "no")
+    stride = 0 if no.numel() == 1 else 1
+    _check(load_library().sim_tx(code.handle, seed, cw0, B, m, _ptr(no), stride, _ptr(y_out), _ptr(info_out),
+                                 _stream(stream)), "sim_tx")
+    return y_out, info_out
+
+
+# --------------------------------------------------------------------------- demapper
+def demap_app(y, no, m: int, method: int = DEMAP_EXACT, clamp: float = 20.0, llr_out=None, stream=None):
+    """APP demapper: y [B, S] (m = 1) or [B, S, 2] -> LLRs [B, S*m]."""
+    import torch
+    _cuda_f32(y, "y")
+    _cuda_f32(no, "no")
+    B, S = y.shape[0], y.shape[1]
+    if llr_out is None:
+        llr_out = torch.empty((B, S * m), dtype=torch.float32, device=y.device)
+    stride = 0 if no.numel() == 1 else 1
+    _check(load_library().demap_app(_ptr(y), _ptr(no), stride, B, S, m, method, clamp, _ptr(llr_out),
+                                    _stream(stream)), "demap_app")
+    return llr_out
+
+
+# --------------------------------------------------------------------------- decoder
+def _opts(algo, iters, msg_prec, early_stop, offset, clamp, weights) -> DecodeOpts:
+    return DecodeOpts(algo, iters, msg_prec, int(bool(early_stop)), offset, clamp,
+                      None if weights is None else weights.data_ptr())
+
+
+def ldpc_bp_workspace(code: Code, B: int, *, algo: int = LAYERED_MINSUM, iters: int = 20, msg_prec: int = MSG_F32,
+                      early_stop: bool = False, offset: float = 0.5, clamp: float = 20.0, weights=None) -> int:
+    o = _opts(algo, iters, msg_prec, early_stop, offset, clamp, weights)
+    ws = C.c_size_t(0)
+    _check(load_library().ldpc_bp_workspace(code.handle, B, C.byref(o), C.byref(ws)), "ldpc_bp_workspace")
+    return ws.value
+
+
+def ldpc_bp_decode(code: Code, llr_ch, *, algo: int = LAYERED_MINSUM, iters: int = 20, msg_prec: int = MSG_F32,
+                   early_stop: bool = False, offset: float = 0.5, clamp: float = 20.0, weights=None,
+                   llr_out=False, bits_out=True, iters_out=True, ws=None, stream=None):
+    """Decode llr_ch [B, n_tx] (CUDA float32).
+
+    llr_out / bits_out / iters_out: a tensor to fill, True to allocate, or
+    False/None to skip. ws: a uint8 CUDA tensor of >= ldpc_bp_workspace bytes
+    (allocated here when None). Returns (llr_out, bits_out, iters_out)."""
+    import torch
+    _cuda_f32(llr_ch, "llr_ch")
+    B = llr_ch.shape[0]
+    dev = llr_ch.device
+    if weights is not None:
+        _cuda_f32(weights, "weights")
+    o = _opts(algo, iters, msg_prec, early_stop, offset, clamp, weights)
+    if llr_out is True:
+        llr_out = torch.empty((B, code.n), dtype=torch.float32, device=dev)
+    if bits_out is True:
+        bits_out = torch.empty((B, (code.k + 31) // 32), dtype=torch.int32, device=dev)
+    if iters_out is True:
+        iters_out = torch.empty((B,), dtype=torch.int32, device=dev)
+    llr_out = llr_out if llr_out is not False else None
+    bits_out = bits_out if bits_out is not False else None
+    iters_out = iters_out if iters_out is not False else None
+    need = ldpc_bp_workspace(code, B, algo=algo, iters=iters, msg_prec=msg_prec, early_stop=early_stop,
+                             offset=offset, clamp=clamp, weights=weights)
+    if ws is None:
+        ws = torch.empty(max(need, 1), dtype=torch.uint8, device=dev)
+    _check(load_library().ldpc_bp_decode(code.handle, _ptr(llr_ch), B, C.byref(o), _ptr(llr_out), _ptr(bits_out),
+                                         _ptr(iters_out), _ptr(ws), ws.numel() * ws.element_size(),
+                                         _stream(stream)), "ldpc_bp_decode")
+    return llr_out, bits_out, iters_out
+
+
+# --------------------------------------------------------------------------- counting and sweeps
+def sim_count(ref, hat, iters, k: int, counts, stream=None):
+    """Accumulate {bits, bit errors, blocks, block errors, iterations} into counts (CUDA int64[5])."""
+    B = ref.shape[0]
+    _check(load_library().sim_count(_ptr(ref), _ptr(hat), _ptr(iters), B, k, _ptr(counts), _stream(stream)),
+           "sim_count")
+    return counts
+
+
+def _sim_config(code: Code, ebn0_db, *, m, demap_method, demap_clamp, algo, iters, msg_prec, early_stop, offset,
+                clamp, seed, cw0, batch, max_batches, min_bit_errors, stop_ber, use_graph):
+    eb = (C.c_double * len(ebn0_db))(*ebn0_db)
+    cfg = SimConfig(code.handle, m, demap_method, demap_clamp,
+                    _opts(algo, iters, msg_prec, early_stop, offset, clamp, None), seed, cw0, batch, max_batches,
+                    min_bit_errors, C.cast(eb, C.POINTER(C.c_double)), len(ebn0_db), stop_ber, int(bool(use_graph)))
+    return cfg, eb
+
+
+_SIM_DEFAULTS = dict(m=4, demap_method=DEMAP_MAXLOG, demap_clamp=20.0, algo=LAYERED_MINSUM, iters=20,
+                     msg_prec=MSG_F16, early_stop=False, offset=0.5, clamp=20.0, seed=0x1DBC, cw0=0, batch=1024,
+                     max_batches=1, min_bit_errors=0, stop_ber=0.0, use_graph=True)
+
+
+def sim_workspace(code: Code, ebn0_db, **kw) -> int:
+    cfg, _keep = _sim_config(code, ebn0_db, **{**_SIM_DEFAULTS, **kw})
+    ws = C.c_size_t(0)
+    _check(load_library().sim_workspace(C.byref(cfg), C.byref(ws)), "sim_workspace")
+    return ws.value
+
+
+def sim_run(code: Code, ebn0_db, ws=None, stream=None, device=None, **kw):
+    """Monte-Carlo sweep; returns a list of dicts (one per point run)."""
+    import torch
+    args = {**_SIM_DEFAULTS, **kw}
+    cfg, _keep = _sim_config(code, list(ebn0_db), **args)
+    need = C.c_size_t(0)
+    _check(load_library().sim_workspace(C.byref(cfg), C.byref(need)), "sim_workspace")
+    if ws is None:
+        ws = torch.empty(need.value, dtype=torch.uint8, device=device or "cuda")
+    out = (SimCounts * max(1, len(ebn0_db)))()
+    pts = C.c_int(0)
+    _check(load_library().sim_run(C.byref(cfg), out, C.byref(pts), _ptr(ws), ws.numel(), _stream(stream)),
+           "sim_run")
+    return [dict(ebn0_db=float(ebn0_db[i]), bits=out[i].bits, bit_errors=out[i].bit_errors, blocks=out[i].blocks,
+                 block_errors=out[i].block_errors, iter_sum=out[i].iter_sum) for i in range(pts.value)]
+
+
+def ldpcx_tune_set(key: int, value: int) -> None:
+    _check(load_library().ldpcx_tune_set(key, value), "ldpcx_tune_set")
+
+
+def ldpcx_tune_get(key: int) -> int:
+    v = C.c_int(0)
+    _check(load_library().ldpcx_tune_get(key, C.byref(v)), "ldpcx_tune_get")
+    return v.value

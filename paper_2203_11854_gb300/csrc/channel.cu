@@ -1,0 +1,409 @@
+// Monte-Carlo transmitter (BinarySource -> LDPC5GEncoder -> Mapper -> AWGN of
+// the paper's Listing 1), APP demapper (Demapper("app")) and error counting
+// (compute_ber), all on the device.
+#include <math.h>
+
+#include "common.cuh"
+
+namespace ldpcx {
+namespace {
+
+__device__ unsigned int g_status;
+
+struct TxParams {
+    const uint32_t *blk;
+    const int32_t *row_ptr;
+    int Z, rows, kb, n, k, n_tx, p0;
+    int m;
+    float scale;         // 1/sqrt(2(4^h-1)/3): unit average symbol energy
+    uint64_t seed, cw0;
+    const uint64_t *cw0_dev;  // when set, *cw0_dev is added to cw0 (graph replays)
+    const float *no;
+    int64_t no_stride;
+    float *y;            // [B][S][2] or [B][S]
+    uint32_t *info;      // [B][kw] or null
+    int64_t B;
+    int G;               // codewords per CTA
+};
+
+// Gray PAM level of h bits taken from c at stride 2 (I: offset 0, Q: offset 1):
+// A = (1-2a0)(2^(h-1) - (1-2a1)(2^(h-2) - ... (1-2a_{h-1}))).
+__device__ __forceinline__ int pam_level(const uint8_t *c, int h) {
+    int inner = 1 - 2 * (int)c[2 * (h - 1)];
+    for (int i = h - 2; i >= 0; --i) inner = (1 - 2 * (int)c[2 * i]) * ((1 << (h - 1 - i)) - inner);
+    return inner;
+}
+
+// Box-Muller on one Philox word pair: u1 = ((a>>9)+0.5) 2^-23, u2 = (b>>8) 2^-24.
+__device__ __forceinline__ float2 box_muller(uint32_t a, uint32_t b) {
+    const float u1 = ((float)(a >> 9) + 0.5f) * (1.0f / 8388608.0f);
+    const float u2 = (float)(b >> 8) * (1.0f / 16777216.0f);
+    const float r = sqrtf(-2.0f * logf(u1));
+    float s, c;
+    sincospif(2.0f * u2, &s, &c);
+    return make_float2(r * c, r * s);
+}
+
+__global__ void __launch_bounds__(kMaxThreads) k_tx(const TxParams p) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint8_t *s_c = smem;  // [G][n] codeword bits, one byte each
+    const int kw = (p.k + 31) >> 5;
+    const int nq = (kw + 3) >> 2;  // Philox blocks of source bits per codeword
+    const int64_t cw_base = (int64_t)blockIdx.x * p.G;
+    const uint64_t cw0 = p.cw0 + (p.cw0_dev ? *p.cw0_dev : 0ull);
+
+    // a2: source bits (Philox stream 0), written packed and unpacked to smem
+    for (int i = threadIdx.x; i < p.G * nq; i += blockDim.x) {
+        const int gg = i / nq, q = i - gg * nq;
+        const int64_t cw = cw_base + gg;
+        if (cw >= p.B) continue;
+        const uint4 x = draw(p.seed, cw0 + (uint64_t)cw, 0u, (uint32_t)q);
+        const uint32_t w4[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int w = 4 * q + e;
+            if (w >= kw) break;
+            uint32_t word = w4[e];
+            const int valid = min(32, p.k - 32 * w);
+            if (valid < 32) word &= (1u << valid) - 1u;
+            if (p.info) p.info[cw * kw + w] = word;
+            uint8_t *dst = s_c + (size_t)gg * p.n + 32 * w;
+            for (int b = 0; b < valid; ++b) dst[b] = (uint8_t)((word >> b) & 1u);
+        }
+    }
+    __syncthreads();
+
+    // a3: systematic encoding, one thread per (codeword, z)
+    const int g = threadIdx.x / p.Z, z = threadIdx.x - g * p.Z;
+    const bool active = g < p.G && cw_base + g < p.B;
+    uint8_t *c = s_c + (size_t)(active ? g : 0) * p.n;
+    const int Z = p.Z;
+    auto at = [&](uint32_t b) -> uint8_t {
+        const int col = (int)(b >> 16);
+        int zz = z + (int)(b & 0xFFFFu);
+        zz -= (zz >= Z) ? Z : 0;
+        return c[col * Z + zz];
+    };
+    uint8_t lam[4] = {0, 0, 0, 0};
+    if (active) {
+        // lambda_r = sum over the systematic blocks of core row r
+        for (int r = 0; r < 4; ++r) {
+            uint8_t acc = 0;
+            for (int b = p.row_ptr[r]; b < p.row_ptr[r + 1]; ++b) {
+                const uint32_t bb = p.blk[b];
+                if ((int)(bb >> 16) < p.kb) acc ^= at(bb);
+            }
+            lam[r] = acc;
+        }
+        c[p.kb * Z + z] = lam[0] ^ lam[1] ^ lam[2] ^ lam[3];  // p_a: the core rows sum to [I 0 0 0]
+    }
+    __syncthreads();
+    if (active) {
+        const uint8_t pa = c[p.kb * Z + z];
+        const uint8_t pb = lam[0] ^ c[p.kb * Z + (z + 1 == Z ? 0 : z + 1)];  // row 0: P^1 p_a + p_b
+        const uint8_t pc = lam[1] ^ pa ^ pb;                                  // row 1: p_a + p_b + p_c
+        const uint8_t pd = lam[2] ^ pc;                                       // row 2: p_c + p_d
+        c[(p.kb + 1) * Z + z] = pb;
+        c[(p.kb + 2) * Z + z] = pc;
+        c[(p.kb + 3) * Z + z] = pd;
+    }
+    __syncthreads();
+    if (active) {
+        // extension rows only read columns < kb + 4, so they are independent
+        for (int r = 4; r < p.rows; ++r) {
+            uint8_t acc = 0;
+            const int own = p.kb + r;
+            for (int b = p.row_ptr[r]; b < p.row_ptr[r + 1]; ++b) {
+                const uint32_t bb = p.blk[b];
+                if ((int)(bb >> 16) != own) acc ^= at(bb);
+            }
+            c[own * Z + z] = acc;
+        }
+    }
+    __syncthreads();
+
+    // a4 + a5: Gray mapping and AWGN (Philox stream 1)
+    const int m = p.m, S = p.n_tx / m;
+    if (m == 1) {
+        const int nqs = (S + 3) >> 2;
+        for (int i = threadIdx.x; i < p.G * nqs; i += blockDim.x) {
+            const int gg = i / nqs, q = i - gg * nqs;
+            const int64_t cw = cw_base + gg;
+            if (cw >= p.B) continue;
+            const float sd = sqrtf(p.no[cw * p.no_stride] * 0.5f);
+            const uint4 x = draw(p.seed, cw0 + (uint64_t)cw, 1u, (uint32_t)q);
+            const float2 g01 = box_muller(x.x, x.y), g23 = box_muller(x.z, x.w);
+            const float gs[4] = {g01.x, g01.y, g23.x, g23.y};
+            const uint8_t *cb = s_c + (size_t)gg * p.n + p.p0;
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int s = 4 * q + e;
+                if (s < S) p.y[cw * S + s] = (1.0f - 2.0f * (float)cb[s]) + sd * gs[e];
+            }
+        }
+    } else {
+        const int h = m >> 1, nqs = (S + 1) >> 1;
+        for (int i = threadIdx.x; i < p.G * nqs; i += blockDim.x) {
+            const int gg = i / nqs, q = i - gg * nqs;
+            const int64_t cw = cw_base + gg;
+            if (cw >= p.B) continue;
+            const float sd = sqrtf(p.no[cw * p.no_stride] * 0.5f);
+            const uint4 x = draw(p.seed, cw0 + (uint64_t)cw, 1u, (uint32_t)q);
+            const float2 gn[2] = {box_muller(x.x, x.y), box_muller(x.z, x.w)};
+            const uint8_t *cb = s_c + (size_t)gg * p.n + p.p0;
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const int s = 2 * q + e;
+                if (s >= S) break;
+                const uint8_t *bits = cb + (size_t)s * m;
+                const float xi = (float)pam_level(bits, h) * p.scale;
+                const float xq = (float)pam_level(bits + 1, h) * p.scale;
+                reinterpret_cast<float2 *>(p.y)[cw * S + s] = make_float2(xi + sd * gn[e].x, xq + sd * gn[e].y);
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------- demapper
+// Per I/Q dimension: metrics d_l = -(y - A_l s)^2 / N0 over the 2^h PAM levels;
+// bit i of the dimension gets LSE/max over levels whose label has bit i = 0,
+// minus the same over bit i = 1.
+template <int H>
+__device__ __forceinline__ void demap_dim(float y, float inv_n0, float scale, int method, float clamp, float *out) {
+    constexpr int P = 1 << H;
+    float d[P];
+#pragma unroll
+    for (int l = 0; l < P; ++l) {
+        // label bits a_i = bit (H-1-i) of l; level by the Gray recursion
+        int inner = 1 - 2 * ((l >> 0) & 1);
+#pragma unroll
+        for (int i = H - 2; i >= 0; --i) inner = (1 - 2 * ((l >> (H - 1 - i)) & 1)) * ((1 << (H - 1 - i)) - inner);
+        const float e = y - (float)inner * scale;
+        d[l] = -(e * e) * inv_n0;
+    }
+#pragma unroll
+    for (int i = 0; i < H; ++i) {
+        const int bit = H - 1 - i;
+        float mx0 = -INFINITY, mx1 = -INFINITY;
+#pragma unroll
+        for (int l = 0; l < P; ++l) {
+            if ((l >> bit) & 1) mx1 = fmaxf(mx1, d[l]);
+            else mx0 = fmaxf(mx0, d[l]);
+        }
+        float L;
+        if (method == LDPCX_DEMAP_MAXLOG) {
+            L = mx0 - mx1;
+        } else {
+            float s0 = 0.0f, s1 = 0.0f;
+#pragma unroll
+            for (int l = 0; l < P; ++l) {
+                if ((l >> bit) & 1) s1 += expf(d[l] - mx1);
+                else s0 += expf(d[l] - mx0);
+            }
+            L = (mx0 - mx1) + (logf(s0) - logf(s1));
+        }
+        out[i] = fminf(fmaxf(L, -clamp), clamp);
+    }
+}
+
+template <int M>
+__global__ void __launch_bounds__(256) k_demap(const float *__restrict__ y, const float *__restrict__ no,
+                                               int64_t no_stride, int64_t B, int64_t S, int method, float clamp,
+                                               float scale, float *__restrict__ llr) {
+    const int64_t total = B * S;
+    bool bad = false;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = i / S;
+        const float inv_n0 = 1.0f / no[b * no_stride];
+        if constexpr (M == 1) {
+            float v = y[i];
+            float L = 4.0f * v * inv_n0;
+            if (!isfinite(v)) {
+                bad = true;
+                L = 0.0f;
+            }
+            llr[i] = fminf(fmaxf(L, -clamp), clamp);
+        } else {
+            constexpr int H = M / 2;
+            const float2 v = reinterpret_cast<const float2 *>(y)[i];
+            float oi[H], oq[H];
+            if (isfinite(v.x) && isfinite(v.y)) {
+                demap_dim<H>(v.x, inv_n0, scale, method, clamp, oi);
+                demap_dim<H>(v.y, inv_n0, scale, method, clamp, oq);
+            } else {
+                bad = true;
+#pragma unroll
+                for (int j = 0; j < H; ++j) oi[j] = oq[j] = 0.0f;
+            }
+            float *o = llr + i * M;
+            if constexpr (M == 2) {
+                reinterpret_cast<float2 *>(o)[0] = make_float2(oi[0], oq[0]);
+            } else if constexpr (M == 4) {
+                reinterpret_cast<float4 *>(o)[0] = make_float4(oi[0], oq[0], oi[1], oq[1]);
+            } else {
+#pragma unroll
+                for (int j = 0; j < H; ++j) {
+                    o[2 * j] = oi[j];
+                    o[2 * j + 1] = oq[j];
+                }
+            }
+        }
+    }
+    if (bad) latch(&g_status, LDPCX_FLAG_NONFINITE);
+}
+
+// ------------------------------------------------------------ error count
+__global__ void __launch_bounds__(256) k_count(const uint32_t *__restrict__ ref, const uint32_t *__restrict__ hat,
+                                               const int32_t *__restrict__ iters, int64_t B, int k,
+                                               unsigned long long *counts) {
+    const int kw = (k + 31) >> 5;
+    const int lane = threadIdx.x & 31;
+    __shared__ unsigned long long s_acc[3];
+    if (threadIdx.x < 3) s_acc[threadIdx.x] = 0ull;
+    __syncthreads();
+    unsigned long long be = 0, blk = 0, it = 0;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t cw = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); cw < B; cw += warps) {
+        unsigned e = 0;
+        for (int w = lane; w < kw; w += 32) e += __popc(ref[cw * kw + w] ^ hat[cw * kw + w]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xFFFFFFFFu, e, o);
+        if (lane == 0) {
+            be += e;
+            blk += e ? 1u : 0u;
+            it += iters ? (unsigned long long)iters[cw] : 0ull;
+        }
+    }
+    if (lane == 0) {
+        atomicAdd(&s_acc[0], be);
+        atomicAdd(&s_acc[1], blk);
+        atomicAdd(&s_acc[2], it);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        atomicAdd(&counts[1], s_acc[0]);
+        atomicAdd(&counts[3], s_acc[1]);
+        atomicAdd(&counts[4], s_acc[2]);
+        if (blockIdx.x == 0) {
+            atomicAdd(&counts[0], (unsigned long long)B * (unsigned long long)k);
+            atomicAdd(&counts[2], (unsigned long long)B);
+        }
+    }
+}
+
+__global__ void k_advance(uint64_t *cw0_dev, uint64_t inc) { *cw0_dev += inc; }
+
+bool valid_m(int m) { return m == 1 || m == 2 || m == 4 || m == 6 || m == 8; }
+
+float qam_scale(int m) {
+    if (m == 1) return 1.0f;
+    const int h = m / 2;
+    return (float)(1.0 / sqrt(2.0 * (double)((1 << (2 * h)) - 1) / 3.0));
+}
+
+}  // namespace
+
+unsigned int take_status_channel(cudaStream_t s) {
+    unsigned int v = 0, zero = 0;
+    if (cudaMemcpyFromSymbolAsync(&v, g_status, sizeof(v), 0, cudaMemcpyDeviceToHost, s) != cudaSuccess) return 0;
+    cudaMemcpyToSymbolAsync(g_status, &zero, sizeof(zero), 0, cudaMemcpyHostToDevice, s);
+    cudaStreamSynchronize(s);
+    return v;
+}
+
+}  // namespace ldpcx
+
+using namespace ldpcx;
+
+namespace ldpcx {
+
+int launch_tx(ldpcx_code_t c, uint64_t seed, uint64_t cw0, const uint64_t *cw0_dev, int64_t B, int m,
+              const float *no, int64_t no_stride, float *y_out, uint32_t *info_out, cudaStream_t stream) {
+    DevCode d;
+    int st = code_device(c, &d);
+    if (st) return st;
+    TxParams p{};
+    p.blk = d.blk;
+    p.row_ptr = d.row_ptr;
+    p.Z = c->Z;
+    p.rows = c->rows;
+    p.kb = c->kb;
+    p.n = c->n;
+    p.k = c->k;
+    p.n_tx = c->n_tx;
+    p.p0 = c->p0;
+    p.m = m;
+    p.scale = qam_scale(m);
+    p.seed = seed;
+    p.cw0 = cw0;
+    p.cw0_dev = cw0_dev;
+    p.no = no;
+    p.no_stride = no_stride;
+    p.y = y_out;
+    p.info = info_out;
+    p.B = B;
+    int G = kMaxThreads / c->Z;
+    if (G < 1) G = 1;
+    while (G > 1 && (size_t)G * c->n > 96 * 1024) --G;
+    p.G = G;
+    const size_t smem = (size_t)G * c->n;
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(k_tx, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return LDPCX_E_CUDA;
+    const int threads = (G * c->Z + 31) / 32 * 32;
+    const int64_t grid = (B + G - 1) / G;
+    k_tx<<<(unsigned)grid, threads, smem, stream>>>(p);
+    return cuda_status(cudaGetLastError());
+}
+
+int launch_advance(uint64_t *cw0_dev, uint64_t inc, cudaStream_t stream) {
+    k_advance<<<1, 1, 0, stream>>>(cw0_dev, inc);
+    return cuda_status(cudaGetLastError());
+}
+
+}  // namespace ldpcx
+
+extern "C" int sim_tx(ldpcx_code_t c, uint64_t seed, uint64_t cw0, int64_t B, int m, const float *no,
+                      int64_t no_stride, float *y_out, uint32_t *info_out, void *stream) {
+    if (!c || B < 0 || !valid_m(m) || (no_stride != 0 && no_stride != 1)) return LDPCX_E_INVAL;
+    if (c->n_tx % m != 0) return LDPCX_E_INVAL;
+    if (B == 0) return LDPCX_OK;
+    if (!no || !y_out) return LDPCX_E_INVAL;
+    return launch_tx(c, seed, cw0, nullptr, B, m, no, no_stride, y_out, info_out, (cudaStream_t)stream);
+}
+
+extern "C" int demap_app(const float *y, const float *no, int64_t no_stride, int64_t B, int64_t syms, int m,
+                         int method, float clamp, float *llr_out, void *stream) {
+    if (B < 0 || syms < 0 || !valid_m(m) || (no_stride != 0 && no_stride != 1)) return LDPCX_E_INVAL;
+    if (method != LDPCX_DEMAP_EXACT && method != LDPCX_DEMAP_MAXLOG) return LDPCX_E_INVAL;
+    if (!(clamp > 0.0f)) return LDPCX_E_INVAL;
+    if (B == 0 || syms == 0) return LDPCX_OK;
+    if (!y || !no || !llr_out) return LDPCX_E_INVAL;
+    const int64_t total = B * syms;
+    int64_t blocks = (total + 255) / 256;
+    const int64_t cap = (int64_t)sm_count() * 8;
+    if (blocks > cap) blocks = cap;
+    cudaStream_t s = (cudaStream_t)stream;
+    const float sc = qam_scale(m);
+    switch (m) {
+        case 1: k_demap<1><<<(unsigned)blocks, 256, 0, s>>>(y, no, no_stride, B, syms, method, clamp, sc, llr_out); break;
+        case 2: k_demap<2><<<(unsigned)blocks, 256, 0, s>>>(y, no, no_stride, B, syms, method, clamp, sc, llr_out); break;
+        case 4: k_demap<4><<<(unsigned)blocks, 256, 0, s>>>(y, no, no_stride, B, syms, method, clamp, sc, llr_out); break;
+        case 6: k_demap<6><<<(unsigned)blocks, 256, 0, s>>>(y, no, no_stride, B, syms, method, clamp, sc, llr_out); break;
+        default: k_demap<8><<<(unsigned)blocks, 256, 0, s>>>(y, no, no_stride, B, syms, method, clamp, sc, llr_out); break;
+    }
+    return cuda_status(cudaGetLastError());
+}
+
+extern "C" int sim_count(const uint32_t *ref, const uint32_t *hat, const int32_t *iters, int64_t B, int k,
+                         int64_t *counts, void *stream) {
+    if (B < 0 || k < 1 || !counts) return LDPCX_E_INVAL;
+    if (B == 0) return LDPCX_OK;
+    if (!ref || !hat) return LDPCX_E_INVAL;
+    int64_t blocks = (B + 7) / 8;
+    const int64_t cap = (int64_t)sm_count() * 4;
+    if (blocks > cap) blocks = cap;
+    k_count<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(ref, hat, iters, B, k,
+                                                                 reinterpret_cast<unsigned long long *>(counts));
+    return cuda_status(cudaGetLastError());
+}

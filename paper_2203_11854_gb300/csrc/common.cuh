@@ -1,0 +1,87 @@
+// Internal declarations shared by the translation units of libldpcx.so.
+// Nothing here is part of the C ABI (include/ldpcx.h is).
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <mutex>
+#include <vector>
+
+#include "ldpcx.h"
+
+namespace ldpcx {
+
+// Largest lifting size the kernels accept (one thread per check node of a
+// layer, at most 384 threads per CTA).
+constexpr int kMaxZ = 384;
+constexpr int kMaxThreads = 384;
+
+// Device-side view of a code's tables.
+struct DevCode {
+    const uint32_t *blk;    // [nnz] (col << 16) | shift, sorted by base row, then column
+    const int32_t *row_ptr; // [rows + 1] first block of each base row
+};
+
+}  // namespace ldpcx
+
+// The opaque code object behind ldpcx_code_t.
+struct ldpcx_code {
+    ldpcx_code_params params;
+    int Z, rows, cols, kb, nnz, max_deg, n, k, n_tx, p0;
+    std::vector<int16_t> S;        // rows x cols base matrix, -1 = zero block
+    std::vector<uint32_t> blk;     // nonzero blocks in row-major order
+    std::vector<int32_t> row_ptr;  // rows + 1
+    std::mutex mu;
+    int dev = -1;                  // device the tables live on
+    void *d_tables = nullptr;
+    ldpcx::DevCode d{};
+};
+
+namespace ldpcx {
+
+// Upload the code's tables to the current device on first use.
+int code_device(ldpcx_code_t code, DevCode *out);
+
+// Status words latched by the kernels of each translation unit.
+unsigned int take_status_decode(cudaStream_t s);
+unsigned int take_status_channel(cudaStream_t s);
+
+// Transmitter launch (source, encoder, mapper, AWGN); cw0_dev optional.
+int launch_tx(ldpcx_code_t c, uint64_t seed, uint64_t cw0, const uint64_t *cw0_dev, int64_t B, int m,
+              const float *no, int64_t no_stride, float *y_out, uint32_t *info_out, cudaStream_t stream);
+// *cw0_dev += inc on the device.
+int launch_advance(uint64_t *cw0_dev, uint64_t inc, cudaStream_t stream);
+
+// Per-device cached attribute: SM count.
+int sm_count();
+
+inline int cuda_status(cudaError_t e) { return e == cudaSuccess ? LDPCX_OK : LDPCX_E_CUDA; }
+
+// Set the device status word (atomic OR) -- used for conditions only the GPU sees.
+__device__ __forceinline__ void latch(unsigned int *word, unsigned int flag) { atomicOr(word, flag); }
+
+// Counter-based Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11): ten rounds of
+//   (hi0, lo0) = 0xD2511F53 * c0, (hi1, lo1) = 0xCD9E8D57 * c2,
+//   c <- (hi1 ^ c1 ^ k0, lo1, hi0 ^ c3 ^ k1, lo0),
+// with the key advanced by (0x9E3779B9, 0xBB67AE85) between rounds.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+    for (int i = 0; i < 10; ++i) {
+        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+        k.x += 0x9E3779B9u;
+        k.y += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// One 128-bit draw of the simulation: counter (q, cw lo, cw hi, stream), key = seed.
+__device__ __forceinline__ uint4 draw(uint64_t seed, uint64_t cw, uint32_t stream, uint32_t q) {
+    return philox4x32_10(make_uint4(q, (uint32_t)cw, (uint32_t)(cw >> 32), stream),
+                         make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+}
+
+}  // namespace ldpcx

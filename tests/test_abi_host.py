@@ -1,0 +1,119 @@
+"""CPU checks of the C ABI: the library builds, loads and exports every symbol
+that include/ldpcx.h declares; host-side code construction matches the oracle;
+argument validation answers before any device work."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "ldpcx.h")
+
+
+@pytest.fixture(scope="module")
+def lx():
+    import paper_2203_11854_gb300 as lx
+    lx._build.build()
+    lx.load_library()
+    return lx
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"^[A-Za-z_][\w\s\*]*?\b(\w+)\s*\(", text, flags=re.M)) - {"if", "while"})
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ["qc_ldpc_build", "demap_app", "ldpc_bp_decode", "sim_run", "sim_tx", "sim_count",
+                     "ldpc_bp_workspace", "qc_ldpc_free", "qc_ldpc_info", "ldpcx_sync_status"]:
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lx):
+    L = C.CDLL(lx.library_path())
+    missing = [n for n in declared_functions() if not hasattr(L, n)]
+    assert not missing
+
+
+def test_no_oracle_in_product():
+    pkg = os.path.join(ROOT, "paper_2203_11854_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                src = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in src and "from oracle" not in src and "ldpc_oracle" not in src, f
+
+
+@pytest.mark.parametrize("bg,Z,rows_kept", [(1, 384, 0), (2, 8, 0), (2, 64, 0), (1, 16, 13), (2, 128, 7)])
+def test_code_construction_matches_oracle(lx, orc, bg, Z, rows_kept):
+    code = lx.qc_ldpc_build(bg, Z, rows_kept=rows_kept, punct_cols=2 if bg == 1 else 0)
+    S_ref, kb = orc.base_matrix(bg, Z, 1 if bg == 1 else 2, rows_kept)
+    assert (code.base() == S_ref).all()
+    assert code.kb == kb and code.rows == S_ref.shape[0] and code.cols == S_ref.shape[1]
+    assert code.nnz == int((S_ref >= 0).sum())
+    assert code.edges == code.nnz * Z
+    assert code.n == S_ref.shape[1] * Z and code.k == kb * Z
+    assert code.max_row_deg == int((S_ref >= 0).sum(axis=1).max())
+    if bg == 1:
+        assert code.p0 == 2 * Z and code.n_tx == code.n - 2 * Z
+
+
+def test_golden_base_matrices(lx):
+    import json
+    gold = json.load(open(os.path.join(ROOT, "tests", "golden", "base_matrices.json")))
+    for entry in gold["codes"]:
+        code = lx.qc_ldpc_build(entry["bg"], entry["Z"], seed=entry["seed"])
+        assert code.base().tolist() == entry["S"], entry["name"]
+
+
+def test_argument_validation(lx):
+    L = lx.load_library()
+    h = C.c_void_p()
+    for bad in [lx.CodeParams(3, 8, 1, 0, 0, 0), lx.CodeParams(1, 1, 1, 0, 0, 0), lx.CodeParams(1, 385, 1, 0, 0, 0),
+                lx.CodeParams(1, 8, 1, 3, 0, 0), lx.CodeParams(1, 8, 1, 47, 0, 0), lx.CodeParams(2, 8, 1, 0, 11, 0),
+                lx.CodeParams(2, 8, 1, 0, 0, 10000)]:
+        assert L.qc_ldpc_build(C.byref(bad), C.byref(h)) == -1
+    assert L.qc_ldpc_build(None, C.byref(h)) == -1
+    code = lx.qc_ldpc_build(2, 8)
+    o = lx.DecodeOpts(0, 20, 0, 0, 0.5, 20.0, None)
+    ws = C.c_size_t(0)
+    assert L.ldpc_bp_workspace(code.handle, 10, C.byref(o), C.byref(ws)) == 0
+    assert ws.value == 10 * ((197 * 8 + 127) // 128 * 128) * 4
+    for fld, val in [("algo", 4), ("iters", 0), ("iters", 1001), ("msg_prec", 3), ("early_stop", 2),
+                     ("offset", -1.0), ("clamp", 0.0)]:
+        o2 = lx.DecodeOpts(0, 20, 0, 0, 0.5, 20.0, None)
+        setattr(o2, fld, val)
+        assert L.ldpc_bp_workspace(code.handle, 10, C.byref(o2), C.byref(ws)) == -1, fld
+    spa_fix6 = lx.DecodeOpts(1, 20, 2, 0, 0.5, 20.0, None)
+    assert L.ldpc_bp_workspace(code.handle, 10, C.byref(spa_fix6), C.byref(ws)) == -2
+    weighted_layered = lx.DecodeOpts(0, 20, 0, 0, 0.5, 20.0, 1234)
+    assert L.ldpc_bp_workspace(code.handle, 10, C.byref(weighted_layered), C.byref(ws)) == -1
+    # decode: null input, too-small workspace; B = 0 is a no-op
+    assert L.ldpc_bp_decode(code.handle, None, 4, C.byref(o), None, None, None, None, 0, None) == -1
+    assert L.ldpc_bp_decode(code.handle, 4096, 4, C.byref(o), None, None, None, 256, 16, None) == -4
+    assert L.ldpc_bp_decode(code.handle, None, 0, C.byref(o), None, None, None, None, 0, None) == 0
+    # demapper and transmitter enums
+    assert L.demap_app(16, 16, 0, 1, 1, 3, 0, 20.0, 16, None) == -1
+    assert L.demap_app(16, 16, 2, 1, 1, 2, 0, 20.0, 16, None) == -1
+    assert L.demap_app(16, 16, 0, 1, 1, 2, 5, 20.0, 16, None) == -1
+    assert L.sim_tx(code.handle, 1, 0, 4, 3, 16, 0, 16, 16, None) == -1
+    assert L.sim_count(16, 16, None, 4, 0, 16, None) == -1
+    assert lx.ldpcx_status_str(-4).startswith("LDPCX_E_WORKSPACE")
+
+
+@pytest.mark.skipif(os.environ.get("CUDA_VISIBLE_DEVICES") is None and __import__("torch").cuda.is_available(),
+                    reason="checks the no-device path")
+def test_no_device_is_reported(lx):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    L = lx.load_library()
+    code = lx.qc_ldpc_build(2, 8)
+    o = lx.DecodeOpts(0, 20, 0, 0, 0.5, 20.0, None)
+    st = L.ldpc_bp_decode(code.handle, 4096, 4, C.byref(o), None, None, None, 4096 * 256, 1 << 30, None)
+    assert st in (-8, -5)
+    assert L.ldpcx_sync_status(None, None) == -8
