@@ -101,21 +101,27 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def decoder_digest():
+    """sha256[:16] over the decoder sources (csrc/decode*), to tell whether an ncu summary is current."""
+    src = os.path.join(ROOT, "paper_2203_11854_gb300", "csrc")
+    blob = b"".join(open(os.path.join(src, f), "rb").read() for f in sorted(os.listdir(src)) if f.startswith("decode"))
+    return hashlib.sha256(blob).hexdigest()[:16]
+
+
 def profile_traffic():
-    """dram bytes per launch from the committed ncu summary, if the decoder source is unchanged since."""
+    """dram bytes per codeword from the committed ncu summary, if the decoder sources are unchanged since."""
     try:
         text = open(PROFILE).read()
     except OSError:
         return None, None
-    src = os.path.join(ROOT, "paper_2203_11854_gb300", "csrc", "decode.cu")
-    digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
     vals = {}
     for line in text.splitlines():
         if ":" in line and line.strip().startswith("- "):
             k, v = line.strip()[2:].split(":", 1)
             vals[k.strip()] = v.strip().strip("`")
-    if vals.get("decode.cu sha256[:16]") != digest:
-        return None, vals.get("decode.cu sha256[:16]")
+    digest = decoder_digest()
+    if vals.get("decode sources sha256[:16]") != digest:
+        return None, vals.get("decode sources sha256[:16]")
     try:
         return float(vals["dram bytes per codeword (full-launch scale)"]), digest
     except (KeyError, ValueError):

@@ -215,9 +215,12 @@ int ldpc_bp_decode(ldpcx_code_t code, const float *llr_ch, int64_t B, const ldpc
 
 /* Decoder tuning knobs (process-wide; read at each launch; the autotuner's
  * search space). LDPCX_TUNE_L2_PREFETCH: layered decoders prefetch into L2 the
- * message span of the layer this many layers ahead (0 = off, 0..16, default 3).
+ * message span of the layer this many layers ahead (0 = off, 0..16, default 0).
+ * LDPCX_TUNE_ZPT: check nodes per thread of the layered kernels (0 = auto = 1;
+ * 2 is honoured only when Z is even and the library was built with it).
  * Knobs change speed only, never results. */
 #define LDPCX_TUNE_L2_PREFETCH 1
+#define LDPCX_TUNE_ZPT 2
 int ldpcx_tune_set(int key, int value);
 int ldpcx_tune_get(int key, int *value);
 

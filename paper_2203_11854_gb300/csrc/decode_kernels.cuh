@@ -1,0 +1,724 @@
+// Device code of the belief-propagation decoders (LDPC5GDecoder of the paper's
+// Listing 1; min-sum BP as the custom CUDA op of Sec. IV-A), shared by the
+// kernel translation units decode_*.cu.
+//
+// Mapping: one thread per (codeword, z): for every base row (layer) r, thread
+// z owns check node r*Z + z. A base row touches each column at most once and
+// every circulant is a bijection, so the check nodes of a layer touch disjoint
+// variable nodes: a thread updates its check node with no communication, and
+// one __syncthreads() separates layers. The APP array of each codeword lives
+// in shared memory; the check-to-variable messages live in HBM in the
+// circulant-contiguous layout msg[cw][blk*Z + z] (blk = nonzero base block in
+// row-major order), so each block of a layer is one coalesced Z-wide stream,
+// and the whole layer is one contiguous span. Each thread reads and writes only
+// its own message slots, so messages need no synchronisation at all; the next
+// layer's messages are loaded into registers while the current layer computes,
+// and each layer runs a body specialised for its exact degree.
+//
+// Arithmetic is binary32 with explicit round-to-nearest intrinsics (no fused
+// multiply-add), in the operation order of the decoder definition in ldpcx.h.
+#pragma once
+
+#include <math.h>
+
+#include <type_traits>
+
+#include "common.cuh"
+
+namespace ldpcx {
+namespace dec {
+
+enum { kMinSum = 0, kSpa = 1 };
+enum { kF32 = LDPCX_MSG_F32, kF16 = LDPCX_MSG_F16, kFix6 = LDPCX_MSG_FIX6 };
+
+template <int P> struct MsgT;
+template <> struct MsgT<kF32> { using T = float; };
+template <> struct MsgT<kF16> { using T = __half; };
+template <> struct MsgT<kFix6> { using T = int8_t; };
+
+template <int P> __device__ __forceinline__ float msg_load(const typename MsgT<P>::T *p);
+template <> __device__ __forceinline__ float msg_load<kF32>(const float *p) { return __ldcg(p); }
+template <> __device__ __forceinline__ float msg_load<kF16>(const __half *p) {
+    return __half2float(__ushort_as_half(__ldcg(reinterpret_cast<const unsigned short *>(p))));
+}
+template <> __device__ __forceinline__ float msg_load<kFix6>(const int8_t *p) {
+    return (float)(int)__ldcg(reinterpret_cast<const signed char *>(p)) * 0.5f;
+}
+
+// Round a message to its storage format; returns the value used by the decoder
+// and writes the stored representation to *q.
+template <int P> __device__ __forceinline__ float msg_round(float r, typename MsgT<P>::T *q);
+template <> __device__ __forceinline__ float msg_round<kF32>(float r, float *q) {
+    *q = r;
+    return r;
+}
+template <> __device__ __forceinline__ float msg_round<kF16>(float r, __half *q) {
+    *q = __float2half_rn(r);
+    return __half2float(*q);
+}
+template <> __device__ __forceinline__ float msg_round<kFix6>(float r, int8_t *q) {
+    int v = (int)rintf(r * 2.0f);  // step 0.5; rintf rounds half to even
+    v = max(-31, min(31, v));
+    *q = (int8_t)v;
+    return (float)v * 0.5f;
+}
+
+template <int P> __device__ __forceinline__ void msg_store(typename MsgT<P>::T *p, typename MsgT<P>::T v);
+template <> __device__ __forceinline__ void msg_store<kF32>(float *p, float v) { __stcg(p, v); }
+template <> __device__ __forceinline__ void msg_store<kF16>(__half *p, __half v) {
+    __stcg(reinterpret_cast<unsigned short *>(p), __half_as_ushort(v));
+}
+template <> __device__ __forceinline__ void msg_store<kFix6>(int8_t *p, int8_t v) {
+    __stcg(reinterpret_cast<signed char *>(p), (signed char)v);
+}
+
+// phi(x) = -ln tanh(x/2) = ln(1 + 2/(e^x - 1)), for x > 0.
+__device__ __forceinline__ float phi(float x) { return log1pf(__fdiv_rn(2.0f, expm1f(x))); }
+
+struct Params {
+    const uint32_t *blk;
+    const int32_t *row_ptr;
+    int Z, rows, nnz, n, k, n_tx, p0;
+    int iters, early_stop;
+    float offset, clamp, phi_lo;  // phi_lo = phi(clamp)
+    const float *llr;             // [B][n_tx]
+    void *msg;                    // [B][msg_stride]
+    int64_t msg_stride;
+    const float *weights;         // flooding: [iters][nnz] or null
+    float *llr_out;               // [B][n] or null
+    uint32_t *bits_out;           // [B][kw] or null
+    int32_t *iters_out;           // [B] or null
+    int64_t B;
+    int G;                        // codewords per CTA
+    int pf_dist;                  // L2 prefetch distance in layers (0 = off)
+    int msg_size;                 // bytes per message
+    unsigned int *status;         // device status word (LDPCX_FLAG_*)
+};
+
+// Shared memory: app[G][n] (and a second APP array for flooding), blk[nnz],
+// row_ptr[rows+1], flag[G], done[G].
+__host__ __device__ inline size_t smem_bytes(const Params &p, int napp) {
+    return sizeof(float) * (size_t)napp * p.G * p.n + sizeof(uint32_t) * p.nnz + sizeof(int32_t) * (p.rows + 1) +
+           2 * sizeof(int) * p.G;
+}
+
+__device__ __forceinline__ float clamp_llr(float x, float c, bool &bad) {
+    if (!(x == x)) {  // NaN
+        bad = true;
+        return 0.0f;
+    }
+    if (isinf(x)) bad = true;
+    return fminf(fmaxf(x, -c), c);
+}
+
+// Load the channel LLRs of the CTA's codewords into app (placed: punctured and
+// untransmitted positions are 0).
+__device__ inline void load_channel(const Params &p, float *app, int64_t cw_base) {
+    bool bad = false;
+    for (int g = 0; g < p.G; ++g) {
+        const int64_t cw = cw_base + g;
+        for (int v = threadIdx.x; v < p.n; v += blockDim.x) {
+            float x = 0.0f;
+            const int t = v - p.p0;
+            if (cw < p.B && t >= 0 && t < p.n_tx) x = clamp_llr(p.llr[cw * p.n_tx + t], p.clamp, bad);
+            app[(size_t)g * p.n + v] = x + 0.0f;  // -0.0 -> +0.0 (same value)
+        }
+    }
+    if (bad) latch(p.status, LDPCX_FLAG_NONFINITE);
+}
+
+// Shared-memory block table entry: (col * Z) << 16 | shift. Variable node of
+// check node z of the block: col*Z + (z + shift) mod Z.
+__device__ __forceinline__ int vn_at(uint32_t vb, int z, int Z) {
+    int zz = z + (int)(vb & 0xFFFFu);
+    zz -= (zz >= Z) ? Z : 0;
+    return (int)(vb >> 16) + zz;
+}
+
+// Check-node rule on the variable-to-check inputs T[0..deg): prepare() reduces
+// the inputs to the check's state, value(j) then gives the (clamped, not yet
+// rounded) check-to-variable message of edge j.
+template <int DMAX, int ALGO> struct CheckNode;
+
+template <int DMAX> struct CheckNode<DMAX, kMinSum> {
+    float v1, v2;   // offset, floored and clamped smallest / second smallest |T|
+    int idx;        // first index of the smallest |T|
+    unsigned neg;   // bit j: T_j < 0
+    unsigned par;   // parity of the negative inputs
+    __device__ __forceinline__ void prepare(const float (&T)[DMAX], int deg, float offset, float clamp, float) {
+        float m1 = INFINITY, m2 = INFINITY;
+        idx = 0;
+        neg = 0;
+#pragma unroll
+        for (int j = 0; j < DMAX; ++j) {
+            if (j < deg) {
+                const float a = fabsf(T[j]);
+                const bool lt = a < m1;
+                m2 = lt ? m1 : fminf(m2, a);
+                m1 = lt ? a : m1;
+                idx = lt ? j : idx;
+                neg |= (T[j] < 0.0f ? 1u : 0u) << j;
+            }
+        }
+        par = __popc(neg) & 1u;
+        v1 = fminf(fmaxf(__fsub_rn(m1, offset), 0.0f), clamp);
+        v2 = fminf(fmaxf(__fsub_rn(m2, offset), 0.0f), clamp);
+    }
+    __device__ __forceinline__ float value(int j, float, float) const {
+        const float mag = (j == idx) ? v2 : v1;
+        return ((par ^ (neg >> j)) & 1u) ? -mag : mag;
+    }
+};
+
+// Layered min-sum check node. The layered APP never holds -0.0 (the channel
+// load maps -0.0 to +0.0, and T = APP - R, APP = T + R cannot create it), so the
+// IEEE sign bit of T equals (T < 0) and the sign product is an XOR of sign bits.
+// The message magnitude of edge j is m2 when |T_j| == m1, else m1: identical to
+// "m2 at the first index of the minimum", because m2 == m1 when the minimum is tied.
+template <int N> struct FastMinSum {
+    float v1, v2;  // offset, floored and clamped smallest / second smallest |T|
+    float m1;      // smallest |T|
+    unsigned sx;   // XOR of the sign bits of T
+    __device__ __forceinline__ void prepare(const float (&T)[N], int deg, float offset, float clamp) {
+        float a1 = INFINITY, a2 = INFINITY;
+        sx = 0;
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            if (j < deg) {
+                const float a = fabsf(T[j]);
+                a2 = fminf(a2, fmaxf(a1, a));
+                a1 = fminf(a1, a);
+                sx ^= __float_as_uint(T[j]);
+            }
+        }
+        m1 = a1;
+        v1 = fminf(fmaxf(__fsub_rn(a1, offset), 0.0f), clamp);
+        v2 = fminf(fmaxf(__fsub_rn(a2, offset), 0.0f), clamp);
+    }
+    __device__ __forceinline__ float value(float Tj) const {
+        const float mag = (fabsf(Tj) == m1) ? v2 : v1;
+        return __uint_as_float(__float_as_uint(mag) | ((sx ^ __float_as_uint(Tj)) & 0x80000000u));
+    }
+};
+
+template <int DMAX> struct CheckNode<DMAX, kSpa> {
+    float f[DMAX];       // phi(|T_j|) with the argument clamped to [phi(clamp), clamp]
+    float s_rest, s_all; // sum without the largest term / with it
+    int jm;              // index of the largest term
+    unsigned neg, par;
+    __device__ __forceinline__ void prepare(const float (&T)[DMAX], int deg, float, float clamp, float phi_lo) {
+        float fmax = -1.0f;
+        jm = 0;
+        neg = 0;
+#pragma unroll
+        for (int j = 0; j < DMAX; ++j) {
+            if (j < deg) {
+                const float a = fminf(fmaxf(fabsf(T[j]), phi_lo), clamp);
+                f[j] = phi(a);
+                const bool gt = f[j] > fmax;
+                fmax = gt ? f[j] : fmax;
+                jm = gt ? j : jm;
+                neg |= (T[j] < 0.0f ? 1u : 0u) << j;
+            }
+        }
+        par = __popc(neg) & 1u;
+        // Exclusive sums without cancellation: the largest term is left out of
+        // the running sum, so s_all - f_j (f_j <= largest) loses at most a bit.
+        s_rest = 0.0f;
+#pragma unroll
+        for (int j = 0; j < DMAX; ++j)
+            if (j < deg && j != jm) s_rest = __fadd_rn(s_rest, f[j]);
+        s_all = __fadd_rn(s_rest, fmax);
+    }
+    __device__ __forceinline__ float value(int j, float clamp, float phi_lo) const {
+        float x = (j == jm) ? s_rest : __fsub_rn(s_all, f[j]);
+        x = fminf(fmaxf(x, phi_lo), clamp);
+        const float mag = fminf(phi(x), clamp);
+        return ((par ^ (neg >> j)) & 1u) ? -mag : mag;
+    }
+};
+
+// Write final outputs of the CTA's codewords from app.
+__device__ inline void write_outputs(const Params &p, const float *app, int64_t cw_base, int iters_run, int g,
+                                     bool active, int z0) {
+    if (p.llr_out) {
+        for (int gg = 0; gg < p.G; ++gg) {
+            const int64_t cw = cw_base + gg;
+            if (cw >= p.B) break;
+            for (int v = threadIdx.x; v < p.n; v += blockDim.x) p.llr_out[cw * p.n + v] = app[(size_t)gg * p.n + v];
+        }
+    }
+    if (p.bits_out) {
+        const int kw = (p.k + 31) >> 5;
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+        for (int w = warp; w < p.G * kw; w += nwarps) {
+            const int gg = w / kw, ww = w - gg * kw;
+            const int pos = ww * 32 + lane;
+            const bool bit = pos < p.k && app[(size_t)gg * p.n + pos] < 0.0f;
+            const unsigned m = __ballot_sync(0xFFFFFFFFu, bit);
+            const int64_t cw = cw_base + gg;
+            if (lane == 0 && cw < p.B) p.bits_out[cw * kw + ww] = m;
+        }
+    }
+    if (p.iters_out && active && z0 == 0) p.iters_out[cw_base + g] = iters_run;
+}
+
+// Parity of every check node of the thread's z over the current hard decisions.
+__device__ __forceinline__ bool syndrome_bad(const Params &p, const uint32_t *s_vb, const int32_t *s_rp,
+                                             const float *app, int z) {
+    bool bad = false;
+    for (int r = 0; r < p.rows; ++r) {
+        unsigned par = 0;
+        for (int b = s_rp[r]; b < s_rp[r + 1]; ++b) par ^= app[vn_at(s_vb[b], z, p.Z)] < 0.0f ? 1u : 0u;
+        bad |= par != 0;
+    }
+    return bad;
+}
+
+// Copy the block table to shared memory as (col * Z) << 16 | shift.
+__device__ __forceinline__ void load_tables(const Params &p, uint32_t *s_vb, int32_t *s_rp) {
+    for (int i = threadIdx.x; i < p.nnz; i += blockDim.x) {
+        const uint32_t b = p.blk[i];
+        s_vb[i] = ((b >> 16) * (uint32_t)p.Z) << 16 | (b & 0xFFFFu);
+    }
+    for (int i = threadIdx.x; i <= p.rows; i += blockDim.x) s_rp[i] = p.row_ptr[i];
+}
+
+// Prefetch into L2 the message span of layer (r + dist) -- one contiguous span
+// per codeword -- so that the register prefetch one layer ahead hits L2.
+// Rounded out to 16-byte boundaries; the per-codeword stride is a multiple of
+// 128 messages, so the rounded span stays inside the workspace.
+__device__ __forceinline__ void l2_prefetch_layer(const Params &p, const int32_t *s_rp, int64_t cw_base, int r, int t) {
+    int rr = r + p.pf_dist, tt = t;
+    while (rr >= p.rows) {
+        rr -= p.rows;
+        ++tt;
+    }
+    if (tt < 1 || tt >= p.iters) return;  // iteration 0 reads no messages
+    const char *base = reinterpret_cast<const char *>(p.msg);
+    for (int gg = 0; gg < p.G; ++gg) {
+        const int64_t cw = cw_base + gg;
+        if (cw >= p.B) break;
+        const int64_t e0 = cw * p.msg_stride + (int64_t)s_rp[rr] * p.Z;
+        const int64_t e1 = cw * p.msg_stride + (int64_t)s_rp[rr + 1] * p.Z;
+        const int64_t b0 = (e0 * p.msg_size) & ~(int64_t)15;
+        const int64_t b1 = (e1 * p.msg_size + 15) & ~(int64_t)15;
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(base + b0), "r"((unsigned)(b1 - b0))
+                     : "memory");
+    }
+}
+
+// Message access for ZPT adjacent check nodes (z0 .. z0+ZPT-1, z0 a multiple
+// of ZPT): one vector load / store per block. The per-codeword message stride
+// is a multiple of 128 and Z is a multiple of ZPT, so the vectors are aligned.
+template <int PREC, int ZPT> struct MsgVec;
+
+template <int PREC> struct MsgVec<PREC, 1> {
+    using MT = typename MsgT<PREC>::T;
+    static __device__ __forceinline__ void load(const MT *p, float (&v)[1]) { v[0] = msg_load<PREC>(p); }
+    // round r to the storage format, return the rounded values in rq, store when asked
+    static __device__ __forceinline__ void round_store(MT *p, const float (&r)[1], float (&rq)[1], bool store) {
+        MT q;
+        rq[0] = msg_round<PREC>(r[0], &q);
+        if (store) msg_store<PREC>(p, q);
+    }
+};
+
+template <> struct MsgVec<kF32, 2> {
+    static __device__ __forceinline__ void load(const float *p, float (&v)[2]) {
+        const float2 x = __ldcg(reinterpret_cast<const float2 *>(p));
+        v[0] = x.x;
+        v[1] = x.y;
+    }
+    static __device__ __forceinline__ void round_store(float *p, const float (&r)[2], float (&rq)[2], bool store) {
+        rq[0] = r[0];
+        rq[1] = r[1];
+        if (store) __stcg(reinterpret_cast<float2 *>(p), make_float2(r[0], r[1]));
+    }
+};
+
+template <> struct MsgVec<kF16, 2> {
+    static __device__ __forceinline__ void load(const __half *p, float (&v)[2]) {
+        const unsigned int w = __ldcg(reinterpret_cast<const unsigned int *>(p));
+        const float2 f = __half22float2(*reinterpret_cast<const __half2 *>(&w));
+        v[0] = f.x;
+        v[1] = f.y;
+    }
+    static __device__ __forceinline__ void round_store(__half *p, const float (&r)[2], float (&rq)[2], bool store) {
+        const __half2 h = __floats2half2_rn(r[0], r[1]);  // round to nearest even, each half
+        const float2 f = __half22float2(h);
+        rq[0] = f.x;
+        rq[1] = f.y;
+        if (store) __stcg(reinterpret_cast<unsigned int *>(p), *reinterpret_cast<const unsigned int *>(&h));
+    }
+};
+
+template <> struct MsgVec<kFix6, 2> {
+    static __device__ __forceinline__ void load(const int8_t *p, float (&v)[2]) {
+        const unsigned short w = __ldcg(reinterpret_cast<const unsigned short *>(p));
+        v[0] = (float)(int)(signed char)(w & 0xFFu) * 0.5f;
+        v[1] = (float)(int)(signed char)(w >> 8) * 0.5f;
+    }
+    static __device__ __forceinline__ void round_store(int8_t *p, const float (&r)[2], float (&rq)[2], bool store) {
+        int8_t q0, q1;
+        rq[0] = msg_round<kFix6>(r[0], &q0);
+        rq[1] = msg_round<kFix6>(r[1], &q1);
+        if (store)
+            __stcg(reinterpret_cast<unsigned short *>(p),
+                   (unsigned short)((unsigned)(uint8_t)q0 | ((unsigned)(uint8_t)q1 << 8)));
+    }
+};
+
+// Variable node of check node z0 + k of a block: col*Z + (z0 + k + shift) mod Z.
+template <int ZPT>
+__device__ __forceinline__ void vn_vec(uint32_t vb, int z0, int Z, int (&v)[ZPT]) {
+    int zz = z0 + (int)(vb & 0xFFFFu);
+    zz -= (zz >= Z) ? Z : 0;
+    const int colZ = (int)(vb >> 16);
+    v[0] = colZ + zz;
+#pragma unroll
+    for (int k = 1; k < ZPT; ++k) {
+        ++zz;
+        zz = (zz == Z) ? 0 : zz;
+        v[k] = colZ + zz;
+    }
+}
+
+// Layers of degree up to kPf get an exact-degree body and have their messages
+// prefetched into registers one layer ahead; denser layers (the four core rows
+// of the 5G shapes) run one predicated body that loads its own messages.
+constexpr int kPf = 8;
+
+// Messages of one layer (D blocks, Z apart) into registers.
+template <int D, int PREC, int ZPT>
+__device__ __forceinline__ void load_layer(float (&R)[ZPT][kPf], const typename MsgT<PREC>::T *ml, int Z) {
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+        float v[ZPT];
+        MsgVec<PREC, ZPT>::load(ml + (size_t)j * Z, v);
+#pragma unroll
+        for (int k = 0; k < ZPT; ++k) R[k][j] = v[k];
+    }
+}
+
+// Layered update of check nodes z0 .. z0+ZPT-1 of one layer of degree deg <= DM
+// (D == 0: deg is a runtime value and the DM edge slots are predicated; else
+// deg == D exactly). Rc holds the old messages (prefetched) when D > 0; the
+// predicated body loads them itself (first iteration: zero).
+// T = APP - R_old, check-node rule, APP = T + R_new (rounded), store R_new.
+template <int D, int DM, int ALGO, int PREC, int ZPT>
+__device__ __forceinline__ void layer_update(const Params &p, int deg, float *app, const uint32_t *vb, int z0,
+                                             typename MsgT<PREC>::T *ml, const float (&Rc)[ZPT][kPf], bool load,
+                                             bool store) {
+    constexpr int N = D ? D : DM;
+    constexpr bool kKeepIdx = D != 0;  // exact (sparse) bodies keep their indices in registers
+    float T[ZPT][N];
+    int vi[ZPT][kKeepIdx ? N : 1];
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+        if (D || j < deg) {
+            float old[ZPT];
+            if (D) {
+#pragma unroll
+                for (int k = 0; k < ZPT; ++k) old[k] = Rc[k][j < kPf ? j : 0];
+            } else if (load) {
+                MsgVec<PREC, ZPT>::load(ml + (size_t)j * p.Z, old);
+            } else {
+#pragma unroll
+                for (int k = 0; k < ZPT; ++k) old[k] = 0.0f;
+            }
+            int v[ZPT];
+            vn_vec<ZPT>(vb[j], z0, p.Z, v);
+#pragma unroll
+            for (int k = 0; k < ZPT; ++k) {
+                if constexpr (kKeepIdx) vi[k][j] = v[k];
+                T[k][j] = __fsub_rn(app[v[k]], old[k]);
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < ZPT; ++k) T[k][j] = 0.0f;
+        }
+    }
+    using CN = typename std::conditional<ALGO == kMinSum, FastMinSum<N>, CheckNode<N, kSpa>>::type;
+    CN cn[ZPT];
+#pragma unroll
+    for (int k = 0; k < ZPT; ++k) {
+        if constexpr (ALGO == kMinSum) cn[k].prepare(T[k], D ? D : deg, p.offset, p.clamp);
+        else cn[k].prepare(T[k], D ? D : deg, p.offset, p.clamp, p.phi_lo);
+    }
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+        if (D || j < deg) {
+            float r[ZPT], rq[ZPT];
+#pragma unroll
+            for (int k = 0; k < ZPT; ++k) {
+                if constexpr (ALGO == kMinSum) r[k] = cn[k].value(T[k][j]);
+                else r[k] = cn[k].value(j, p.clamp, p.phi_lo);
+            }
+            MsgVec<PREC, ZPT>::round_store(ml + (size_t)j * p.Z, r, rq, store);
+            int v[ZPT];
+            if constexpr (kKeepIdx) {
+#pragma unroll
+                for (int k = 0; k < ZPT; ++k) v[k] = vi[k][j];
+            } else {
+                vn_vec<ZPT>(vb[j], z0, p.Z, v);  // dense body: recomputed, fewer live registers
+            }
+#pragma unroll
+            for (int k = 0; k < ZPT; ++k) app[v[k]] = __fadd_rn(T[k][j], rq[k]);
+        }
+    }
+}
+
+// One layer step of the layered schedule: prefetch the next layer's messages
+// into Rn (sparse layers), update layer r, then a block barrier.
+template <int DMAX, int ALGO, int PREC, int ZPT>
+__device__ __forceinline__ void layered_step(const Params &p, const uint32_t *s_vb, const int32_t *s_rp, float *app,
+                                             typename MsgT<PREC>::T *mp, int z0, int t, int r, bool done,
+                                             int64_t cw_base, const float (&Rc)[ZPT][kPf], float (&Rn)[ZPT][kPf]) {
+    const int b0 = s_rp[r], deg = s_rp[r + 1] - b0;
+    if (p.pf_dist > 0 && threadIdx.x == 0) l2_prefetch_layer(p, s_rp, cw_base, r, t);
+    int rn = r + 1, tn = t;
+    if (rn == p.rows) {
+        rn = 0;
+        tn = t + 1;
+    }
+    if (tn == 0) {
+#pragma unroll
+        for (int k = 0; k < ZPT; ++k)
+#pragma unroll
+            for (int j = 0; j < kPf; ++j) Rn[k][j] = 0.0f;  // iteration 0 starts from zero messages
+    } else if (!done && tn < p.iters) {
+        const int bn0 = s_rp[rn], degn = s_rp[rn + 1] - bn0;
+        const auto *ml = mp + (size_t)bn0 * p.Z;
+        switch (degn) {
+#define LDPCX_LOAD(d) \
+    case d:           \
+        load_layer<d, PREC, ZPT>(Rn, ml, p.Z); \
+        break;
+            LDPCX_LOAD(1) LDPCX_LOAD(2) LDPCX_LOAD(3) LDPCX_LOAD(4)
+            LDPCX_LOAD(5) LDPCX_LOAD(6) LDPCX_LOAD(7) LDPCX_LOAD(8)
+#undef LDPCX_LOAD
+            default: break;  // dense layer: loads its own messages
+        }
+    }
+    if (!done) {
+        const bool store = t + 1 < p.iters;  // the last iteration's messages are never read
+        auto *ml = mp + (size_t)b0 * p.Z;
+        const uint32_t *vb = s_vb + b0;
+        switch (deg) {
+#define LDPCX_UPDATE(d) \
+    case d:             \
+        layer_update<d, d, ALGO, PREC, ZPT>(p, d, app, vb, z0, ml, Rc, t > 0, store); \
+        break;
+            LDPCX_UPDATE(1) LDPCX_UPDATE(2) LDPCX_UPDATE(3) LDPCX_UPDATE(4)
+            LDPCX_UPDATE(5) LDPCX_UPDATE(6) LDPCX_UPDATE(7) LDPCX_UPDATE(8)
+#undef LDPCX_UPDATE
+            default:
+                layer_update<0, DMAX, ALGO, PREC, ZPT>(p, deg, app, vb, z0, ml, Rc, t > 0, store);
+                break;
+        }
+    }
+    __syncthreads();
+}
+
+// Parity of the check nodes of z0 .. z0+ZPT-1 over the current hard decisions.
+template <int ZPT>
+__device__ __forceinline__ bool syndrome_bad_vec(const Params &p, const uint32_t *s_vb, const int32_t *s_rp,
+                                                 const float *app, int z0) {
+    bool bad = false;
+    for (int r = 0; r < p.rows; ++r) {
+        unsigned par[ZPT];
+#pragma unroll
+        for (int k = 0; k < ZPT; ++k) par[k] = 0;
+        for (int b = s_rp[r]; b < s_rp[r + 1]; ++b) {
+            int v[ZPT];
+            vn_vec<ZPT>(s_vb[b], z0, p.Z, v);
+#pragma unroll
+            for (int k = 0; k < ZPT; ++k) par[k] ^= app[v[k]] < 0.0f ? 1u : 0u;
+        }
+#pragma unroll
+        for (int k = 0; k < ZPT; ++k) bad |= par[k] != 0;
+    }
+    return bad;
+}
+
+// Threads per CTA of the layered kernel: ZPT check nodes per thread.
+template <int ZPT> constexpr int layered_threads() { return kMaxThreads / ZPT; }
+
+template <int DMAX, int ALGO, int PREC, int ZPT>
+__global__ void __launch_bounds__(layered_threads<ZPT>(), 2) k_layered(const Params p) {
+    using MT = typename MsgT<PREC>::T;
+    extern __shared__ __align__(16) unsigned char smem[];
+    float *s_app_all = reinterpret_cast<float *>(smem);
+    uint32_t *s_vb = reinterpret_cast<uint32_t *>(s_app_all + (size_t)p.G * p.n);
+    int32_t *s_rp = reinterpret_cast<int32_t *>(s_vb + p.nnz);
+    int *s_flag = reinterpret_cast<int *>(s_rp + p.rows + 1);
+
+    load_tables(p, s_vb, s_rp);
+    const int64_t cw_base = (int64_t)blockIdx.x * p.G;
+    load_channel(p, s_app_all, cw_base);
+
+    const int zq = p.Z / ZPT;  // threads per codeword
+    const int g = threadIdx.x / zq, z0 = (threadIdx.x - g * zq) * ZPT;
+    const int64_t cw = cw_base + g;
+    const bool active = g < p.G && cw < p.B;
+    float *app = s_app_all + (size_t)(active ? g : 0) * p.n;
+    MT *mp = reinterpret_cast<MT *>(p.msg) + (active ? cw : 0) * p.msg_stride + z0;
+    bool done = !active;
+    int iters_run = 0;
+    __syncthreads();
+
+    // Ra / Rb alternate as current / prefetched messages (loop unrolled by two
+    // layer steps so that no register copies are needed).
+    float Ra[ZPT][kPf], Rb[ZPT][kPf];
+#pragma unroll
+    for (int k = 0; k < ZPT; ++k)
+#pragma unroll
+        for (int j = 0; j < kPf; ++j) Ra[k][j] = 0.0f;
+
+    int t = 0, r = 0;
+    // Advance to the next layer; at the end of an iteration run the early-stop
+    // check. Returns true when every codeword of the CTA has stopped.
+    auto advance = [&]() -> bool {
+        if (++r < p.rows) return false;
+        r = 0;
+        if (!done) iters_run = t + 1;
+        ++t;
+        if (!p.early_stop) return false;
+        if (threadIdx.x < p.G) s_flag[threadIdx.x] = 0;
+        __syncthreads();
+        if (!done && syndrome_bad_vec<ZPT>(p, s_vb, s_rp, app, z0)) s_flag[g] = 1;
+        __syncthreads();
+        if (!done && s_flag[g] == 0) done = true;
+        return __syncthreads_and(done);
+    };
+    while (t < p.iters) {
+        layered_step<DMAX, ALGO, PREC, ZPT>(p, s_vb, s_rp, app, mp, z0, t, r, done, cw_base, Ra, Rb);
+        if (advance() || t >= p.iters) break;
+        layered_step<DMAX, ALGO, PREC, ZPT>(p, s_vb, s_rp, app, mp, z0, t, r, done, cw_base, Rb, Ra);
+        if (advance()) break;
+    }
+    __syncthreads();
+    write_outputs(p, s_app_all, cw_base, iters_run, g, active, z0);
+}
+
+// Flooding update of check node z of one layer of degree deg <= DMAX:
+// T = w (APP_old - R_old), check-node rule, acc += R_new (rounded), store R_new.
+template <int DMAX, int ALGO, int PREC>
+__device__ __forceinline__ void flood_update(const Params &p, int deg, const float *app, float *acc,
+                                             const uint32_t *vb, int z, typename MsgT<PREC>::T *ml, const float *w,
+                                             bool load, bool store) {
+    using MT = typename MsgT<PREC>::T;
+    float T[DMAX];
+#pragma unroll
+    for (int j = 0; j < DMAX; ++j) {
+        T[j] = 0.0f;
+        if (j < deg) {
+            const float old = load ? msg_load<PREC>(ml + (size_t)j * p.Z) : 0.0f;
+            float v2c = __fsub_rn(app[vn_at(vb[j], z, p.Z)], old);
+            if (w) v2c = __fmul_rn(w[j], v2c);
+            T[j] = v2c;
+        }
+    }
+    CheckNode<DMAX, ALGO> cn;
+    cn.prepare(T, deg, p.offset, p.clamp, p.phi_lo);
+#pragma unroll
+    for (int j = 0; j < DMAX; ++j) {
+        if (j < deg) {
+            MT q;
+            const float rq = msg_round<PREC>(cn.value(j, p.clamp, p.phi_lo), &q);
+            if (store) msg_store<PREC>(ml + (size_t)j * p.Z, q);
+            const int v = vn_at(vb[j], z, p.Z);
+            acc[v] = __fadd_rn(acc[v], rq);
+        }
+    }
+}
+
+template <int DMAX, int ALGO, int PREC>
+__global__ void __launch_bounds__(kMaxThreads, 1) k_flooding(const Params p) {
+    using MT = typename MsgT<PREC>::T;
+    extern __shared__ __align__(16) unsigned char smem[];
+    float *s_a = reinterpret_cast<float *>(smem);
+    float *s_b = s_a + (size_t)p.G * p.n;
+    uint32_t *s_vb = reinterpret_cast<uint32_t *>(s_b + (size_t)p.G * p.n);
+    int32_t *s_rp = reinterpret_cast<int32_t *>(s_vb + p.nnz);
+    int *s_flag = reinterpret_cast<int *>(s_rp + p.rows + 1);
+    int *s_done = s_flag + p.G;
+
+    load_tables(p, s_vb, s_rp);
+    const int64_t cw_base = (int64_t)blockIdx.x * p.G;
+    for (int i = threadIdx.x; i < p.G; i += blockDim.x) s_done[i] = (cw_base + i >= p.B) ? 1 : 0;
+    load_channel(p, s_a, cw_base);
+
+    const int g = threadIdx.x / p.Z, z = threadIdx.x - g * p.Z;
+    const int64_t cw = cw_base + g;
+    const bool active = g < p.G && cw < p.B;
+    MT *mp = reinterpret_cast<MT *>(p.msg) + (active ? cw : 0) * p.msg_stride + z;
+    bool done = !active;
+    int iters_run = 0;
+    float *cur = s_a, *nxt = s_b;  // APP of the previous iteration / accumulator
+
+    for (int t = 0; t < p.iters; ++t) {
+        const bool store = t + 1 < p.iters;
+        __syncthreads();
+        // the accumulator starts from the channel LLRs; a stopped codeword
+        // carries its APP forward unchanged
+        {
+            bool bad = false;
+            for (int gg = 0; gg < p.G; ++gg) {
+                const int64_t c2 = cw_base + gg;
+                const bool keep = s_done[gg] != 0;
+                for (int v = threadIdx.x; v < p.n; v += blockDim.x) {
+                    float x = 0.0f;
+                    const int tt = v - p.p0;
+                    if (keep) x = cur[(size_t)gg * p.n + v];
+                    else if (c2 < p.B && tt >= 0 && tt < p.n_tx) x = clamp_llr(p.llr[c2 * p.n_tx + tt], p.clamp, bad);
+                    nxt[(size_t)gg * p.n + v] = x;
+                }
+            }
+        }
+        __syncthreads();
+        const float *app = cur + (size_t)(active ? g : 0) * p.n;
+        float *acc = nxt + (size_t)(active ? g : 0) * p.n;
+        const float *w_t = p.weights ? p.weights + (size_t)t * p.nnz : nullptr;
+        for (int r = 0; r < p.rows; ++r) {
+            const int b0 = s_rp[r], deg = s_rp[r + 1] - b0;
+            if (!done) {
+                auto *ml = mp + (size_t)b0 * p.Z;
+                const float *w = w_t ? w_t + b0 : nullptr;
+                flood_update<DMAX, ALGO, PREC>(p, deg, app, acc, s_vb + b0, z, ml, w, t > 0, store);
+            }
+            __syncthreads();  // rows add into the accumulator in ascending order
+        }
+        float *tmp = cur;
+        cur = nxt;
+        nxt = tmp;
+        if (!done) iters_run = t + 1;
+        if (p.early_stop) {
+            if (threadIdx.x < p.G) s_flag[threadIdx.x] = 0;
+            __syncthreads();
+            if (!done && syndrome_bad(p, s_vb, s_rp, cur + (size_t)g * p.n, z)) s_flag[g] = 1;
+            __syncthreads();
+            if (!done && s_flag[g] == 0) {
+                done = true;
+                if (z == 0) s_done[g] = 1;
+            }
+            if (__syncthreads_and(done)) break;
+        }
+    }
+    __syncthreads();
+    write_outputs(p, cur, cw_base, iters_run, g, active, z);
+}
+
+
+using KernelFn = void (*)(Params);
+
+// Kernel lookup per translation unit (nullptr when the combination is not built).
+// zpt: check nodes per thread (2 needs an even Z).
+KernelFn layered_kernel_f32(int dmax, int algo, int zpt);
+KernelFn layered_kernel_f16(int dmax, int algo, int zpt);
+KernelFn layered_kernel_fix6(int dmax, int algo, int zpt);
+KernelFn flooding_kernel(int dmax, int algo, int prec);
+
+}  // namespace dec
+}  // namespace ldpcx

@@ -1,0 +1,15 @@
+// Layered decoder kernels with FIX6 message storage.
+#include "decode_kernels.cuh"
+
+namespace ldpcx {
+namespace dec {
+
+KernelFn layered_kernel_fix6(int dmax, int algo, int zpt) {
+    constexpr int PREC = kFix6;
+    if (dmax > 20 || algo != kMinSum) return nullptr;
+    (void)zpt;  // one check node per thread (two per thread measured slower)
+    return dmax <= 12 ? k_layered<12, kMinSum, PREC, 1> : k_layered<20, kMinSum, PREC, 1>;
+}
+
+}  // namespace dec
+}  // namespace ldpcx
