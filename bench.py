@@ -116,8 +116,8 @@ def profile_traffic():
         return None, None
     vals = {}
     for line in text.splitlines():
-        if ":" in line and line.strip().startswith("- "):
-            k, v = line.strip()[2:].split(":", 1)
+        if ": " in line and line.strip().startswith("- "):
+            k, v = line.strip()[2:].split(": ", 1)
             vals[k.strip()] = v.strip().strip("`")
     digest = decoder_digest()
     if vals.get("decode sources sha256[:16]") != digest:
