@@ -224,6 +224,29 @@ int ldpc_bp_decode(ldpcx_code_t code, const float *llr_ch, int64_t B, const ldpc
 int ldpcx_tune_set(int key, int value);
 int ldpcx_tune_get(int key, int *value);
 
+/* Allocation-free decode. The paper has no counterpart: this entry point
+ * exists for callers that cannot call cudaMalloc -- a receiver that allocates
+ * every buffer at start-up and forbids allocation on its real-time path, a host
+ * thread that must never block on the device (cudaMalloc may synchronise), or
+ * a component whose device memory belongs to an allocator this library cannot
+ * reach. It decodes exactly like ldpc_bp_decode (same arguments and outputs,
+ * same results bit for bit) but keeps its scratch -- the code tables and the
+ * check-to-variable messages -- in a fixed array of LDPCX_NOALLOC_SCRATCH_BYTES
+ * inside the library image, which every GPU that loads the library holds
+ * until the process exits. It calls no cudaMalloc, cudaFree or allocating
+ * library routine. Limits: the tables (rounded to 256 bytes) plus
+ * B * round_up(edges, 128) messages must fit in the array, else
+ * LDPCX_E_WORKSPACE (at Z = 384, BG1-shaped: 69 codewords with FP32
+ * messages, 138 with FP16, 276 with FIX6). The first call on a device looks up
+ * the array's device address (cudaGetSymbolAddress); make that first call
+ * before any stream capture. Every call on a device shares the array and
+ * leaves its contents behind; nothing needs clearing (tables are rewritten by
+ * each call, every message is written before it is read), but calls that
+ * overlap on the GPU -- on different streams -- race on it. */
+#define LDPCX_NOALLOC_SCRATCH_BYTES (32u << 20)
+int ldpc_bp_decode_noalloc(ldpcx_code_t code, const float *llr_ch, int64_t B, const ldpcx_decode_opts *opts,
+                           float *llr_out, uint32_t *bits_out, int32_t *iters_out, void *stream);
+
 /* ------------------------------------------------------ error count (a10) */
 /* compute_ber of Listing 1: for each codeword, bit errors = popcount over
  * the k information bits of ref XOR hat; block error = any bit error.

@@ -18,6 +18,7 @@ __all__ = [
     "LdpcxError", "Code", "ldpcx_status_str", "ldpcx_sync_status", "qc_ldpc_build", "qc_ldpc_free",
     "qc_ldpc_info", "qc_ldpc_base", "sim_tx", "demap_app", "ldpc_bp_workspace", "ldpc_bp_decode",
     "sim_count", "sim_workspace", "sim_run", "library_path", "load_library", "ldpcx_tune_set", "ldpcx_tune_get",
+    "ldpc_bp_decode_noalloc",
     "LAYERED_MINSUM", "LAYERED_SPA", "FLOOD_MINSUM", "FLOOD_SPA", "MSG_F32", "MSG_F16", "MSG_FIX6",
     "DEMAP_EXACT", "DEMAP_MAXLOG",
 ]
@@ -81,6 +82,7 @@ _SIGS = {
     "sim_count": ([_vp, _vp, _vp, _i64, _i, _vp, _vp], _i),
     "sim_workspace": ([C.POINTER(SimConfig), C.POINTER(_sz)], _i),
     "sim_run": ([C.POINTER(SimConfig), C.POINTER(SimCounts), C.POINTER(_i), _vp, _sz, _vp], _i),
+    "ldpc_bp_decode_noalloc": ([_vp, _vp, _i64, C.POINTER(DecodeOpts), _vp, _vp, _vp, _vp], _i),
     "ldpcx_tune_set": ([_i, _i], _i),
     "ldpcx_tune_get": ([_i, C.POINTER(_i)], _i),
 }
@@ -275,6 +277,36 @@ def ldpc_bp_decode(code: Code, llr_ch, *, algo: int = LAYERED_MINSUM, iters: int
     _check(load_library().ldpc_bp_decode(code.handle, _ptr(llr_ch), B, C.byref(o), _ptr(llr_out), _ptr(bits_out),
                                          _ptr(iters_out), _ptr(ws), ws.numel() * ws.element_size(),
                                          _stream(stream)), "ldpc_bp_decode")
+    return llr_out, bits_out, iters_out
+
+
+def ldpc_bp_decode_noalloc(code: Code, llr_ch, *, algo: int = LAYERED_MINSUM, iters: int = 20,
+                           msg_prec: int = MSG_F32, early_stop: bool = False, offset: float = 0.5,
+                           clamp: float = 20.0, weights=None, llr_out=False, bits_out=True, iters_out=True,
+                           stream=None):
+    """ldpc_bp_decode without a workspace, for callers that cannot allocate device
+    memory: the library's fixed scratch array holds the messages, so B is limited
+    (see LDPCX_NOALLOC_SCRATCH_BYTES in ldpcx.h). Outputs given as tensors are filled;
+    True allocates them here with torch (pass tensors to keep the call allocation-free)."""
+    import torch
+    _cuda_f32(llr_ch, "llr_ch")
+    B = llr_ch.shape[0]
+    dev = llr_ch.device
+    if weights is not None:
+        _cuda_f32(weights, "weights")
+    o = _opts(algo, iters, msg_prec, early_stop, offset, clamp, weights)
+    if llr_out is True:
+        llr_out = torch.empty((B, code.n), dtype=torch.float32, device=dev)
+    if bits_out is True:
+        bits_out = torch.empty((B, (code.k + 31) // 32), dtype=torch.int32, device=dev)
+    if iters_out is True:
+        iters_out = torch.empty((B,), dtype=torch.int32, device=dev)
+    llr_out = llr_out if llr_out is not False else None
+    bits_out = bits_out if bits_out is not False else None
+    iters_out = iters_out if iters_out is not False else None
+    _check(load_library().ldpc_bp_decode_noalloc(code.handle, _ptr(llr_ch), B, C.byref(o), _ptr(llr_out),
+                                                 _ptr(bits_out), _ptr(iters_out), _stream(stream)),
+           "ldpc_bp_decode_noalloc")
     return llr_out, bits_out, iters_out
 
 

@@ -46,6 +46,8 @@ int code_device(ldpcx_code_t code, DevCode *out);
 
 // Status words latched by the kernels of each translation unit.
 unsigned int take_status_decode(cudaStream_t s);
+// Device address of the decoders' status word on the current device.
+unsigned int *status_word_decode();
 unsigned int take_status_channel(cudaStream_t s);
 
 // Transmitter launch (source, encoder, mapper, AWGN); cw0_dev optional.
