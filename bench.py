@@ -101,10 +101,13 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows)}
 
 
+KERNEL_SOURCES = ("decode_kernels.cuh", "decode_layered_f16.cu")  # the profiled kernel's own code
+
+
 def decoder_digest():
-    """sha256[:16] over the decoder sources (csrc/decode*), to tell whether an ncu summary is current."""
+    """sha256[:16] over the profiled kernel's sources, to tell whether an ncu summary is current."""
     src = os.path.join(ROOT, "paper_2203_11854_gb300", "csrc")
-    blob = b"".join(open(os.path.join(src, f), "rb").read() for f in sorted(os.listdir(src)) if f.startswith("decode"))
+    blob = b"".join(open(os.path.join(src, f), "rb").read() for f in KERNEL_SOURCES)
     return hashlib.sha256(blob).hexdigest()[:16]
 
 
@@ -120,8 +123,8 @@ def profile_traffic():
             k, v = line.strip()[2:].split(": ", 1)
             vals[k.strip()] = v.strip().strip("`")
     digest = decoder_digest()
-    if vals.get("decode sources sha256[:16]") != digest:
-        return None, vals.get("decode sources sha256[:16]")
+    if vals.get("kernel sources sha256[:16]") != digest:
+        return None, vals.get("kernel sources sha256[:16]")
     try:
         return float(vals["dram bytes per codeword (full-launch scale)"]), digest
     except (KeyError, ValueError):
