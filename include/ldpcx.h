@@ -247,6 +247,39 @@ int ldpcx_tune_get(int key, int *value);
 int ldpc_bp_decode_noalloc(ldpcx_code_t code, const float *llr_ch, int64_t B, const ldpcx_decode_opts *opts,
                            float *llr_out, uint32_t *bits_out, int32_t *iters_out, void *stream);
 
+/* ------------------------------------------- differentiable BP (a11) */
+/* Gradients through the unrolled decoder ("gradients can be specified" for a
+ * custom op, Sec. IV-A; end-to-end learning with a binary cross-entropy loss,
+ * Sec. III-C, Listing 2). Supported for weighted flooding sum-product
+ * (LDPCX_FLOOD_SPA, FP32 messages, no early stop): the forward pass
+ * ldpc_bp_decode_ckpt stores each iteration's check-to-variable messages C^t
+ * (t = 0 .. iters-2) as FP32 checkpoints; ldpc_bp_backward walks the
+ * iterations in reverse, recomputes APP^t = L + sum C^(t-1) and the check-node
+ * quantities of iteration t from the checkpoint, and propagates the adjoints
+ *   dC_e/dV_e' = s_e phi'(x_e) [lo < S_e < hi] phi'(a_e') sgn(V_e') [lo <= |V_e'| <= hi]
+ * (e' != e in the same check; x_e = clamp(S_e), a = clamp(|V|), phi'(x) =
+ * -1/sinh(x)), V_e = w (APP_v - C_e(old)), APP = L + sum C, L = clamp(llr_ch).
+ *
+ * ckpt bytes = 4 * max(iters-1, 1) * B * round_up(edges, 128). */
+int ldpc_bp_ckpt_bytes(ldpcx_code_t code, int64_t B, const ldpcx_decode_opts *opts, size_t *ckpt_bytes);
+/* ldpc_bp_decode plus checkpoints (device, >= ldpc_bp_ckpt_bytes, 16-byte aligned). */
+int ldpc_bp_decode_ckpt(ldpcx_code_t code, const float *llr_ch, int64_t B, const ldpcx_decode_opts *opts,
+                        float *llr_out, uint32_t *bits_out, int32_t *iters_out, void *ws, size_t ws_bytes,
+                        void *ckpt, size_t ckpt_bytes, void *stream);
+/* Workspace of ldpc_bp_backward: 4 * B * round_up(edges, 128) bytes (adjoint carry). */
+int ldpc_bp_backward_workspace(ldpcx_code_t code, int64_t B, const ldpcx_decode_opts *opts, size_t *ws_bytes);
+/* Adjoint of ldpc_bp_decode_ckpt with the same code, llr_ch, B and opts.
+ * grad_llr_out (device) [B][n]: dLoss/d(output APP).
+ * grad_llr_ch  (device) [B][n_tx]: dLoss/d(llr_ch), overwritten.
+ * grad_weights (device, or NULL) [iters][nnz]: dLoss/d(weights), ACCUMULATED
+ *              (+=, float atomics: the summation order is not fixed).
+ * opts->weights may be NULL (all ones). Errors: LDPCX_E_UNSUPPORTED for other
+ * algorithms, message formats or early stop, or a code too long for the
+ * kernel's shared memory (n > 13800). */
+int ldpc_bp_backward(ldpcx_code_t code, const float *llr_ch, int64_t B, const ldpcx_decode_opts *opts,
+                     const void *ckpt, size_t ckpt_bytes, const float *grad_llr_out, float *grad_llr_ch,
+                     float *grad_weights, void *ws, size_t ws_bytes, void *stream);
+
 /* ------------------------------------------------------ error count (a10) */
 /* compute_ber of Listing 1: for each codeword, bit errors = popcount over
  * the k information bits of ref XOR hat; block error = any bit error.

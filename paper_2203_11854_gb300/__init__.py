@@ -18,7 +18,8 @@ __all__ = [
     "LdpcxError", "Code", "ldpcx_status_str", "ldpcx_sync_status", "qc_ldpc_build", "qc_ldpc_free",
     "qc_ldpc_info", "qc_ldpc_base", "sim_tx", "demap_app", "ldpc_bp_workspace", "ldpc_bp_decode",
     "sim_count", "sim_workspace", "sim_run", "library_path", "load_library", "ldpcx_tune_set", "ldpcx_tune_get",
-    "ldpc_bp_decode_noalloc",
+    "ldpc_bp_decode_noalloc", "ldpc_bp_ckpt_bytes", "ldpc_bp_decode_ckpt", "ldpc_bp_backward_workspace",
+    "ldpc_bp_backward",
     "LAYERED_MINSUM", "LAYERED_SPA", "FLOOD_MINSUM", "FLOOD_SPA", "MSG_F32", "MSG_F16", "MSG_FIX6",
     "DEMAP_EXACT", "DEMAP_MAXLOG",
 ]
@@ -83,6 +84,10 @@ _SIGS = {
     "sim_workspace": ([C.POINTER(SimConfig), C.POINTER(_sz)], _i),
     "sim_run": ([C.POINTER(SimConfig), C.POINTER(SimCounts), C.POINTER(_i), _vp, _sz, _vp], _i),
     "ldpc_bp_decode_noalloc": ([_vp, _vp, _i64, C.POINTER(DecodeOpts), _vp, _vp, _vp, _vp], _i),
+    "ldpc_bp_ckpt_bytes": ([_vp, _i64, C.POINTER(DecodeOpts), C.POINTER(_sz)], _i),
+    "ldpc_bp_decode_ckpt": ([_vp, _vp, _i64, C.POINTER(DecodeOpts), _vp, _vp, _vp, _vp, _sz, _vp, _sz, _vp], _i),
+    "ldpc_bp_backward_workspace": ([_vp, _i64, C.POINTER(DecodeOpts), C.POINTER(_sz)], _i),
+    "ldpc_bp_backward": ([_vp, _vp, _i64, C.POINTER(DecodeOpts), _vp, _sz, _vp, _vp, _vp, _vp, _sz, _vp], _i),
     "ldpcx_tune_set": ([_i, _i], _i),
     "ldpcx_tune_get": ([_i, C.POINTER(_i)], _i),
 }
@@ -308,6 +313,66 @@ def ldpc_bp_decode_noalloc(code: Code, llr_ch, *, algo: int = LAYERED_MINSUM, it
                                                  _ptr(bits_out), _ptr(iters_out), _stream(stream)),
            "ldpc_bp_decode_noalloc")
     return llr_out, bits_out, iters_out
+
+
+# --------------------------------------------------------------------------- differentiable decoding
+def ldpc_bp_ckpt_bytes(code: Code, B: int, *, iters: int = 10, clamp: float = 20.0, weights=None) -> int:
+    o = _opts(FLOOD_SPA, iters, MSG_F32, False, 0.0, clamp, weights)
+    n = C.c_size_t(0)
+    _check(load_library().ldpc_bp_ckpt_bytes(code.handle, B, C.byref(o), C.byref(n)), "ldpc_bp_ckpt_bytes")
+    return n.value
+
+
+def ldpc_bp_decode_ckpt(code: Code, llr_ch, *, iters: int = 10, clamp: float = 20.0, weights=None, ckpt=None,
+                        stream=None):
+    """Weighted flooding sum-product forward that keeps per-iteration checkpoints.
+    Returns (llr_out [B, n], ckpt uint8 tensor)."""
+    import torch
+    _cuda_f32(llr_ch, "llr_ch")
+    B, dev = llr_ch.shape[0], llr_ch.device
+    if weights is not None:
+        _cuda_f32(weights, "weights")
+    o = _opts(FLOOD_SPA, iters, MSG_F32, False, 0.0, clamp, weights)
+    need = ldpc_bp_ckpt_bytes(code, B, iters=iters, clamp=clamp, weights=weights)
+    if ckpt is None:
+        ckpt = torch.empty(need, dtype=torch.uint8, device=dev)
+    ws = torch.empty(max(1, ldpc_bp_workspace(code, B, algo=FLOOD_SPA, iters=iters, clamp=clamp, weights=weights)),
+                     dtype=torch.uint8, device=dev)
+    llr_out = torch.empty((B, code.n), dtype=torch.float32, device=dev)
+    _check(load_library().ldpc_bp_decode_ckpt(code.handle, _ptr(llr_ch), B, C.byref(o), _ptr(llr_out), None, None,
+                                              _ptr(ws), ws.numel(), _ptr(ckpt), ckpt.numel(), _stream(stream)),
+           "ldpc_bp_decode_ckpt")
+    return llr_out, ckpt
+
+
+def ldpc_bp_backward_workspace(code: Code, B: int, *, iters: int = 10, clamp: float = 20.0, weights=None) -> int:
+    o = _opts(FLOOD_SPA, iters, MSG_F32, False, 0.0, clamp, weights)
+    n = C.c_size_t(0)
+    _check(load_library().ldpc_bp_backward_workspace(code.handle, B, C.byref(o), C.byref(n)),
+           "ldpc_bp_backward_workspace")
+    return n.value
+
+
+def ldpc_bp_backward(code: Code, llr_ch, ckpt, grad_llr_out, *, iters: int = 10, clamp: float = 20.0, weights=None,
+                     grad_weights=None, stream=None):
+    """Adjoint of ldpc_bp_decode_ckpt. Returns (grad_llr_ch [B, n_tx], grad_weights [iters, nnz] or None);
+    grad_weights, when given, is accumulated into."""
+    import torch
+    _cuda_f32(llr_ch, "llr_ch")
+    _cuda_f32(grad_llr_out, "grad_llr_out")
+    B, dev = llr_ch.shape[0], llr_ch.device
+    if weights is not None:
+        _cuda_f32(weights, "weights")
+        if grad_weights is None:
+            grad_weights = torch.zeros_like(weights)
+    o = _opts(FLOOD_SPA, iters, MSG_F32, False, 0.0, clamp, weights)
+    ws = torch.empty(max(1, ldpc_bp_backward_workspace(code, B, iters=iters, clamp=clamp, weights=weights)),
+                     dtype=torch.uint8, device=dev)
+    grad_llr = torch.empty_like(llr_ch)
+    _check(load_library().ldpc_bp_backward(code.handle, _ptr(llr_ch), B, C.byref(o), _ptr(ckpt), ckpt.numel(),
+                                           _ptr(grad_llr_out), _ptr(grad_llr), _ptr(grad_weights), _ptr(ws),
+                                           ws.numel(), _stream(stream)), "ldpc_bp_backward")
+    return grad_llr, grad_weights
 
 
 # --------------------------------------------------------------------------- counting and sweeps

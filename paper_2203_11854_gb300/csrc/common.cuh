@@ -48,6 +48,8 @@ int code_device(ldpcx_code_t code, DevCode *out);
 unsigned int take_status_decode(cudaStream_t s);
 // Device address of the decoders' status word on the current device.
 unsigned int *status_word_decode();
+// Bytes of the adjoint checkpoints for B codewords and `iters` iterations.
+size_t ckpt_bytes(const ldpcx_code *c, int64_t B, int iters);
 unsigned int take_status_channel(cudaStream_t s);
 
 // Transmitter launch (source, encoder, mapper, AWGN); cw0_dev optional.

@@ -92,9 +92,12 @@ extern "C" int ldpc_bp_workspace(ldpcx_code_t c, int64_t B, const ldpcx_decode_o
     return LDPCX_OK;
 }
 
-extern "C" int ldpc_bp_decode(ldpcx_code_t c, const float *llr_ch, int64_t B, const ldpcx_decode_opts *o,
-                              float *llr_out, uint32_t *bits_out, int32_t *iters_out, void *ws, size_t ws_bytes,
-                              void *stream) {
+namespace ldpcx {
+namespace {
+
+// Decode, optionally storing FP32 checkpoints of C^t (flooding only).
+int decode_impl(ldpcx_code_t c, const float *llr_ch, int64_t B, const ldpcx_decode_opts *o, float *llr_out,
+                uint32_t *bits_out, int32_t *iters_out, void *ws, size_t ws_bytes, float *ckpt, void *stream) {
     if (!c || B < 0 || (B > 0 && !llr_ch)) return LDPCX_E_INVAL;
     int st = check_opts(c, o);
     if (st) return st;
@@ -139,6 +142,8 @@ extern "C" int ldpc_bp_decode(ldpcx_code_t c, const float *llr_ch, int64_t B, co
     p.msg = ws;
     p.msg_stride = msg_stride(c);
     p.weights = o->weights;
+    p.ckpt = ckpt;
+    p.ckpt_tstride = B * msg_stride(c);
     p.llr_out = llr_out;
     p.bits_out = bits_out;
     p.iters_out = iters_out;
@@ -159,6 +164,49 @@ extern "C" int ldpc_bp_decode(ldpcx_code_t c, const float *llr_ch, int64_t B, co
     if (grid > 0x7FFFFFFF) return LDPCX_E_INVAL;
     fn<<<(unsigned)grid, threads, smem, (cudaStream_t)stream>>>(p);
     return cuda_status(cudaGetLastError());
+}
+
+// The adjoint supports weighted flooding sum-product with FP32 messages and a
+// fixed iteration count.
+int check_differentiable(const ldpcx_code *c, const ldpcx_decode_opts *o) {
+    int st = check_opts(c, o);
+    if (st) return st;
+    if (o->algo != LDPCX_FLOOD_SPA || o->msg_prec != LDPCX_MSG_F32 || o->early_stop) return LDPCX_E_UNSUPPORTED;
+    return LDPCX_OK;
+}
+
+}  // namespace
+
+size_t ckpt_bytes(const ldpcx_code *c, int64_t B, int iters) {
+    return sizeof(float) * (size_t)(iters > 1 ? iters - 1 : 1) * (size_t)B * (size_t)msg_stride(c);
+}
+
+}  // namespace ldpcx
+
+extern "C" int ldpc_bp_decode(ldpcx_code_t c, const float *llr_ch, int64_t B, const ldpcx_decode_opts *o,
+                              float *llr_out, uint32_t *bits_out, int32_t *iters_out, void *ws, size_t ws_bytes,
+                              void *stream) {
+    return ldpcx::decode_impl(c, llr_ch, B, o, llr_out, bits_out, iters_out, ws, ws_bytes, nullptr, stream);
+}
+
+extern "C" int ldpc_bp_ckpt_bytes(ldpcx_code_t c, int64_t B, const ldpcx_decode_opts *o, size_t *bytes) {
+    if (!c || !bytes || B < 0) return LDPCX_E_INVAL;
+    int st = ldpcx::check_differentiable(c, o);
+    if (st) return st;
+    *bytes = ldpcx::ckpt_bytes(c, B, o->iters);
+    return LDPCX_OK;
+}
+
+extern "C" int ldpc_bp_decode_ckpt(ldpcx_code_t c, const float *llr_ch, int64_t B, const ldpcx_decode_opts *o,
+                                   float *llr_out, uint32_t *bits_out, int32_t *iters_out, void *ws,
+                                   size_t ws_bytes, void *ckpt, size_t ckpt_bytes, void *stream) {
+    if (!c || B < 0) return LDPCX_E_INVAL;
+    int st = ldpcx::check_differentiable(c, o);
+    if (st) return st;
+    if (B == 0) return LDPCX_OK;
+    if (!ckpt || ckpt_bytes < ldpcx::ckpt_bytes(c, B, o->iters) || ((uintptr_t)ckpt & 15u))
+        return LDPCX_E_WORKSPACE;
+    return ldpcx::decode_impl(c, llr_ch, B, o, llr_out, bits_out, iters_out, ws, ws_bytes, (float *)ckpt, stream);
 }
 
 extern "C" int ldpcx_tune_set(int key, int value) {

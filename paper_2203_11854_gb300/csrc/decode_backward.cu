@@ -1,0 +1,292 @@
+// Adjoint of unrolled weighted flooding sum-product BP: gradients of a loss on
+// the output LLRs with respect to the channel LLRs and the per-iteration
+// per-base-block weights ("gradients can be specified" for a custom op,
+// Sec. IV-A; end-to-end learning, Sec. III-C).
+//
+// Forward (iteration t, edges e of check c, variable v(e)):
+//   APP^0 = L (clamped channel LLRs),  APP^(t+1) = L + sum_e C^t_e over v's edges
+//   V_e = w[t][blk(e)] (APP^t_v - C^(t-1)_e),  a_e = clamp(|V_e|, lo, hi),  f_e = phi(a_e)
+//   S_e = sum_{e' != e in c} f_e',  x_e = clamp(S_e, lo, hi),  C^t_e = s_e phi(x_e)
+// Reverse sweep, t = iters-1 .. 0, with gA^(t+1) = dLoss/dAPP^(t+1) known:
+//   gC_e  = gA^(t+1)_v + carry_e          (carry = -w gV from iteration t+1)
+//   u_e   = gC_e s_e phi'(x_e) [lo < S_e < hi]
+//   gV_e  = phi'(a_e) sgn(V_e) [lo <= |V_e| <= hi] sum_{e' != e} u_e'
+//   gw   += gV_e (APP^t_v - C^(t-1)_e),  gA^t_v += w gV_e,  carry_e = -w gV_e
+//   dLoss/dL = sum_t gA^t (through the channel clamp).
+// APP^t is recomputed from the checkpointed C^(t-1) in the forward's row order,
+// so it equals the forward's value bit for bit.
+#include <math.h>
+
+#include "decode_kernels.cuh"
+
+namespace ldpcx {
+namespace {
+
+struct BwdParams {
+    const uint32_t *blk;
+    const int32_t *row_ptr;
+    int Z, rows, nnz, n, n_tx, p0, iters;
+    float clamp, phi_lo;
+    const float *llr;       // [B][n_tx]
+    const float *weights;   // [iters][nnz] or null (all ones)
+    const float *ckpt;      // [iters-1][B][stride]
+    int64_t stride, tstride;
+    const float *grad_out;  // [B][n]
+    float *grad_llr;        // [B][n_tx]
+    float *grad_w;          // [iters][nnz] (accumulated) or null
+    float *carry;           // [B][stride]
+    int64_t B;
+    int G;
+};
+
+__device__ __forceinline__ float phi_f(float x) { return log1pf(__fdiv_rn(2.0f, expm1f(x))); }
+__device__ __forceinline__ float dphi_f(float x) { return -1.0f / sinhf(x); }
+
+__device__ __forceinline__ int vn_of(uint32_t vb, int z, int Z) {
+    int zz = z + (int)(vb & 0xFFFFu);
+    zz -= (zz >= Z) ? Z : 0;
+    return (int)(vb >> 16) + zz;
+}
+
+// Channel LLRs of codeword cw placed on the n positions and clamped (NaN -> 0).
+__device__ __forceinline__ float placed_llr(const BwdParams &p, int64_t cw, int v) {
+    const int t = v - p.p0;
+    if (cw >= p.B || t < 0 || t >= p.n_tx) return 0.0f;
+    const float x = p.llr[cw * p.n_tx + t];
+    if (!(x == x)) return 0.0f;
+    return fminf(fmaxf(x, -p.clamp), p.clamp);
+}
+
+template <int DMAX>
+__global__ void __launch_bounds__(kMaxThreads, 1) k_backward(const BwdParams p) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const size_t gn = (size_t)p.G * p.n;
+    float *s_app = reinterpret_cast<float *>(smem);
+    float *s_gin = s_app + gn;   // gA^(t+1)
+    float *s_gout = s_gin + gn;  // gA^t (accumulated)
+    float *s_gl = s_gout + gn;   // dLoss/dL
+    float *s_gw = s_gl + gn;     // [nnz] weight gradient of this iteration
+    uint32_t *s_vb = reinterpret_cast<uint32_t *>(s_gw + p.nnz);
+    int32_t *s_rp = reinterpret_cast<int32_t *>(s_vb + p.nnz);
+
+    for (int i = threadIdx.x; i < p.nnz; i += blockDim.x) {
+        const uint32_t b = p.blk[i];
+        s_vb[i] = ((b >> 16) * (uint32_t)p.Z) << 16 | (b & 0xFFFFu);
+        s_gw[i] = 0.0f;
+    }
+    for (int i = threadIdx.x; i <= p.rows; i += blockDim.x) s_rp[i] = p.row_ptr[i];
+    const int64_t cw_base = (int64_t)blockIdx.x * p.G;
+    for (int gg = 0; gg < p.G; ++gg) {
+        const int64_t c2 = cw_base + gg;
+        for (int v = threadIdx.x; v < p.n; v += blockDim.x) {
+            s_gin[(size_t)gg * p.n + v] = c2 < p.B ? p.grad_out[c2 * p.n + v] : 0.0f;
+            s_gl[(size_t)gg * p.n + v] = 0.0f;
+        }
+    }
+    const int g = threadIdx.x / p.Z, z = threadIdx.x - g * p.Z;
+    const int64_t cw = cw_base + g;
+    const bool active = g < p.G && cw < p.B;
+    const size_t off = (size_t)(active ? g : 0) * p.n;
+    float *carry = p.carry + (active ? cw : 0) * p.stride + z;
+    const float lo = p.phi_lo, hi = p.clamp;
+    float *gin = s_gin, *gout = s_gout;
+    __syncthreads();
+
+    for (int t = p.iters - 1; t >= 0; --t) {
+        // APP^t = L + sum of C^(t-1), added row by row as in the forward pass
+        for (int gg = 0; gg < p.G; ++gg)
+            for (int v = threadIdx.x; v < p.n; v += blockDim.x) s_app[(size_t)gg * p.n + v] = placed_llr(p, cw_base + gg, v);
+        __syncthreads();
+        const float *ck = t >= 1 ? p.ckpt + (size_t)(t - 1) * p.tstride + (active ? cw : 0) * p.stride + z : nullptr;
+        if (ck) {
+            for (int r = 0; r < p.rows; ++r) {
+                if (active)
+                    for (int b = s_rp[r]; b < s_rp[r + 1]; ++b) {
+                        const int v = vn_of(s_vb[b], z, p.Z);
+                        s_app[off + v] = __fadd_rn(s_app[off + v], ck[(size_t)b * p.Z]);
+                    }
+                __syncthreads();
+            }
+        }
+        // dLoss/dL collects every gA^(t+1); gA^t starts from zero
+        for (size_t i = threadIdx.x; i < gn; i += blockDim.x) {
+            s_gl[i] += gin[i];
+            gout[i] = 0.0f;
+        }
+        __syncthreads();
+        const float *w_t = p.weights ? p.weights + (size_t)t * p.nnz : nullptr;
+        const bool has_carry = t + 1 < p.iters;
+        for (int r = 0; r < p.rows; ++r) {
+            const int b0 = s_rp[r], deg = s_rp[r + 1] - b0;
+            float gw[DMAX];
+#pragma unroll
+            for (int j = 0; j < DMAX; ++j) gw[j] = 0.0f;
+            if (active) {
+                float V[DMAX], d[DMAX], f[DMAX], u[DMAX];
+                int vi[DMAX];
+                unsigned neg = 0;
+#pragma unroll
+                for (int j = 0; j < DMAX; ++j) {
+                    V[j] = d[j] = f[j] = u[j] = 0.0f;
+                    vi[j] = 0;
+                    if (j < deg) {
+                        vi[j] = vn_of(s_vb[b0 + j], z, p.Z);
+                        const float cold = ck ? ck[(size_t)(b0 + j) * p.Z] : 0.0f;
+                        d[j] = __fsub_rn(s_app[off + vi[j]], cold);
+                        V[j] = w_t ? __fmul_rn(w_t[b0 + j], d[j]) : d[j];
+                        f[j] = phi_f(fminf(fmaxf(fabsf(V[j]), lo), hi));
+                        neg |= (V[j] < 0.0f ? 1u : 0u) << j;
+                    }
+                }
+                const unsigned par = __popc(neg) & 1u;
+                // u_e = gC_e s_e phi'(x_e) [lo < S_e < hi]
+#pragma unroll
+                for (int j = 0; j < DMAX; ++j) {
+                    if (j < deg) {
+                        float S = 0.0f;
+#pragma unroll
+                        for (int i = 0; i < DMAX; ++i)
+                            if (i < deg && i != j) S += f[i];
+                        const float gC = gin[off + vi[j]] + (has_carry ? carry[(size_t)(b0 + j) * p.Z] : 0.0f);
+                        const float s = ((par ^ (neg >> j)) & 1u) ? -1.0f : 1.0f;
+                        u[j] = (S > lo && S < hi) ? gC * s * dphi_f(S) : 0.0f;
+                    }
+                }
+                // gV_e = phi'(a_e) sgn(V_e) [lo <= |V_e| <= hi] sum_{e' != e} u_e'
+#pragma unroll
+                for (int j = 0; j < DMAX; ++j) {
+                    if (j < deg) {
+                        float U = 0.0f;
+#pragma unroll
+                        for (int i = 0; i < DMAX; ++i)
+                            if (i < deg && i != j) U += u[i];
+                        const float a = fabsf(V[j]);
+                        const bool inside = a >= lo && a <= hi;
+                        const float gV = inside ? dphi_f(a) * (V[j] < 0.0f ? -1.0f : 1.0f) * U : 0.0f;
+                        const float w = w_t ? w_t[b0 + j] : 1.0f;
+                        gw[j] = gV * d[j];
+                        gout[off + vi[j]] += w * gV;
+                        carry[(size_t)(b0 + j) * p.Z] = -w * gV;
+                    }
+                }
+            }
+            // weight gradient: every lane of a warp is at the same block b0 + j
+            if (p.grad_w) {
+#pragma unroll
+                for (int j = 0; j < DMAX; ++j) {
+                    if (j < deg) {
+                        float x = gw[j];
+#pragma unroll
+                        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xFFFFFFFFu, x, o);
+                        if ((threadIdx.x & 31) == 0 && x != 0.0f) atomicAdd(&s_gw[b0 + j], x);
+                    }
+                }
+            }
+            __syncthreads();  // rows add into gA^t in ascending order
+        }
+        if (p.grad_w) {
+            for (int i = threadIdx.x; i < p.nnz; i += blockDim.x) {
+                atomicAdd(&p.grad_w[(size_t)t * p.nnz + i], s_gw[i]);
+                s_gw[i] = 0.0f;
+            }
+        }
+        float *tmp = gin;
+        gin = gout;
+        gout = tmp;
+        __syncthreads();
+    }
+    // dLoss/dL += gA^0, then through the channel clamp to the transmitted positions
+    for (size_t i = threadIdx.x; i < gn; i += blockDim.x) s_gl[i] += gin[i];
+    __syncthreads();
+    for (int gg = 0; gg < p.G; ++gg) {
+        const int64_t c2 = cw_base + gg;
+        if (c2 >= p.B) break;
+        for (int t = threadIdx.x; t < p.n_tx; t += blockDim.x) {
+            const float x = p.llr[c2 * p.n_tx + t];
+            const bool pass = (x == x) && fabsf(x) <= p.clamp;
+            p.grad_llr[c2 * p.n_tx + t] = pass ? s_gl[(size_t)gg * p.n + p.p0 + t] : 0.0f;
+        }
+    }
+}
+
+size_t bwd_smem(int G, int n, int nnz, int rows) {
+    return sizeof(float) * (4 * (size_t)G * n + nnz) + sizeof(uint32_t) * nnz + sizeof(int32_t) * (rows + 1);
+}
+
+int64_t stride_of(const ldpcx_code *c) {
+    const int64_t E = (int64_t)c->nnz * c->Z;
+    return (E + 127) / 128 * 128;
+}
+
+int check_bwd(const ldpcx_code *c, const ldpcx_decode_opts *o) {
+    size_t tmp = 0;
+    int st = ldpc_bp_workspace(const_cast<ldpcx_code *>(c), 1, o, &tmp);  // validates the options
+    if (st) return st;
+    if (o->algo != LDPCX_FLOOD_SPA || o->msg_prec != LDPCX_MSG_F32 || o->early_stop) return LDPCX_E_UNSUPPORTED;
+    if (bwd_smem(1, c->n, c->nnz, c->rows) > 216 * 1024) return LDPCX_E_UNSUPPORTED;
+    return LDPCX_OK;
+}
+
+}  // namespace
+}  // namespace ldpcx
+
+using namespace ldpcx;
+
+extern "C" int ldpc_bp_backward_workspace(ldpcx_code_t c, int64_t B, const ldpcx_decode_opts *o, size_t *ws) {
+    if (!c || !ws || B < 0 || !o) return LDPCX_E_INVAL;
+    int st = check_bwd(c, o);
+    if (st) return st;
+    *ws = sizeof(float) * (size_t)B * (size_t)stride_of(c);
+    return LDPCX_OK;
+}
+
+extern "C" int ldpc_bp_backward(ldpcx_code_t c, const float *llr_ch, int64_t B, const ldpcx_decode_opts *o,
+                                const void *ckpt, size_t ckpt_bytes_in, const float *grad_llr_out,
+                                float *grad_llr_ch, float *grad_weights, void *ws, size_t ws_bytes, void *stream) {
+    if (!c || B < 0 || !o) return LDPCX_E_INVAL;
+    int st = check_bwd(c, o);
+    if (st) return st;
+    if (B == 0) return LDPCX_OK;
+    if (!llr_ch || !grad_llr_out || !grad_llr_ch) return LDPCX_E_INVAL;
+    if (!ckpt || ckpt_bytes_in < ckpt_bytes(c, B, o->iters) || ((uintptr_t)ckpt & 15u)) return LDPCX_E_WORKSPACE;
+    const size_t need = sizeof(float) * (size_t)B * (size_t)stride_of(c);
+    if (!ws || ws_bytes < need || ((uintptr_t)ws & 15u)) return LDPCX_E_WORKSPACE;
+    DevCode d;
+    st = code_device(c, &d);
+    if (st) return st;
+
+    BwdParams p{};
+    p.blk = d.blk;
+    p.row_ptr = d.row_ptr;
+    p.Z = c->Z;
+    p.rows = c->rows;
+    p.nnz = c->nnz;
+    p.n = c->n;
+    p.n_tx = c->n_tx;
+    p.p0 = c->p0;
+    p.iters = o->iters;
+    p.clamp = o->clamp;
+    p.phi_lo = (float)log1p(2.0 / expm1((double)o->clamp));
+    p.llr = llr_ch;
+    p.weights = o->weights;
+    p.ckpt = (const float *)ckpt;
+    p.stride = stride_of(c);
+    p.tstride = B * p.stride;
+    p.grad_out = grad_llr_out;
+    p.grad_llr = grad_llr_ch;
+    p.grad_w = grad_weights;
+    p.carry = (float *)ws;
+    p.B = B;
+    int G = kMaxThreads / c->Z;
+    if (G < 1) G = 1;
+    while (G > 1 && bwd_smem(G, c->n, c->nnz, c->rows) > 216 * 1024) --G;
+    p.G = G;
+    const size_t smem = bwd_smem(G, c->n, c->nnz, c->rows);
+    auto fn = c->max_deg <= 12 ? k_backward<12> : k_backward<20>;
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return LDPCX_E_CUDA;
+    const int threads = (G * c->Z + 31) / 32 * 32;
+    const int64_t grid = (B + G - 1) / G;
+    fn<<<(unsigned)grid, threads, smem, (cudaStream_t)stream>>>(p);
+    return cudaGetLastError() == cudaSuccess ? LDPCX_OK : LDPCX_E_CUDA;
+}

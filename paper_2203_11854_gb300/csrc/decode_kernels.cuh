@@ -85,6 +85,8 @@ struct Params {
     void *msg;                    // [B][msg_stride]
     int64_t msg_stride;
     const float *weights;         // flooding: [iters][nnz] or null
+    float *ckpt;                  // flooding: C^t checkpoints [iters-1][B][msg_stride] (FP32) or null
+    int64_t ckpt_tstride;         // B * msg_stride
     float *llr_out;               // [B][n] or null
     uint32_t *bits_out;           // [B][kw] or null
     int32_t *iters_out;           // [B] or null
@@ -607,7 +609,7 @@ __global__ void __launch_bounds__(layered_threads<ZPT>(), 2) k_layered(const Par
 template <int DMAX, int ALGO, int PREC>
 __device__ __forceinline__ void flood_update(const Params &p, int deg, const float *app, float *acc,
                                              const uint32_t *vb, int z, typename MsgT<PREC>::T *ml, const float *w,
-                                             bool load, bool store) {
+                                             bool load, bool store, float *ck) {
     using MT = typename MsgT<PREC>::T;
     float T[DMAX];
 #pragma unroll
@@ -628,6 +630,7 @@ __device__ __forceinline__ void flood_update(const Params &p, int deg, const flo
             MT q;
             const float rq = msg_round<PREC>(cn.value(j, p.clamp, p.phi_lo), &q);
             if (store) msg_store<PREC>(ml + (size_t)j * p.Z, q);
+            if (ck) ck[(size_t)j * p.Z] = rq;  // checkpoint of C^t for the adjoint
             const int v = vn_at(vb[j], z, p.Z);
             acc[v] = __fadd_rn(acc[v], rq);
         }
@@ -686,7 +689,10 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_flooding(const Params p) {
             if (!done) {
                 auto *ml = mp + (size_t)b0 * p.Z;
                 const float *w = w_t ? w_t + b0 : nullptr;
-                flood_update<DMAX, ALGO, PREC>(p, deg, app, acc, s_vb + b0, z, ml, w, t > 0, store);
+                float *ck = (p.ckpt && store) ? p.ckpt + (size_t)t * p.ckpt_tstride + (size_t)cw * p.msg_stride +
+                                                    (size_t)b0 * p.Z + z
+                                              : nullptr;
+                flood_update<DMAX, ALGO, PREC>(p, deg, app, acc, s_vb + b0, z, ml, w, t > 0, store, ck);
             }
             __syncthreads();  // rows add into the accumulator in ascending order
         }
