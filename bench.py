@@ -281,6 +281,7 @@ def run_gpu(args):
         variants = {}
         if not args.quick:
             variants = measure_variants(lx, code, llr, bits, its, stream, args, pk)
+            variants["mixed_batch"] = measure_mixed(lx, stream, args)
         e2e = measure_e2e(lx, code, y, info, n0, dec, stream, args, dev)
         cpu = None if (world > 1 or args.no_cpu) else cpu_baseline(args.cpu_seconds)
         result = {
@@ -338,6 +339,53 @@ def measure_variants(lx, code, llr, bits, its, stream, args, pk):
         del ws
     if "minsum_f32" in out and "minsum_f16" in out:
         out["f16_over_f32"] = out["minsum_f32"]["decode_ms"] / out["minsum_f16"]["decode_ms"]
+    return out
+
+
+def measure_mixed(lx, stream, args):
+    """Uneven batch (8192 codewords over 48 codes: Z 16..384, both shapes, rates 1/3..8/9, QPSK/16/64-QAM,
+    Eb/N0 within 1 dB of each waterfall), layered min-sum FP16 with early stop: one persistent launch against
+    one launch per code group."""
+    import torch
+    from paper_2203_11854_gb300 import workloads
+    groups, infos, desc = workloads.mixed_batch(8192, seed=11)
+    dec = dict(algo=lx.LAYERED_MINSUM, iters=20, msg_prec=lx.MSG_F16, early_stop=True)
+    ws = torch.empty(lx.ldpc_bp_mixed_workspace(groups, **dec), dtype=torch.uint8, device="cuda")
+    wss = [torch.empty(max(1, lx.ldpc_bp_workspace(c, l.shape[0], **dec)), dtype=torch.uint8, device="cuda")
+           for c, l in groups]
+    bits_info = sum(c.k * l.shape[0] for c, l in groups)
+
+    def persistent():
+        return lx.ldpc_bp_decode_mixed(groups, **dec, ws=ws, stream=stream)
+
+    def per_group():
+        return [lx.ldpc_bp_decode(c, l, **dec, ws=w, stream=stream) for (c, l), w in zip(groups, wss)]
+
+    out = {}
+    for name, fn in (("persistent", persistent), ("per_group", per_group)):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 5
+        a.record(stream)
+        for _ in range(reps):
+            res = fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / reps
+        out[name] = {"ms": ms, "gbps": bits_info / (ms * 1e-3) / 1e9}
+    # decoded bits agree between the two launches, and the error counts of the batch
+    counts = torch.zeros(5, dtype=torch.int64, device="cuda")
+    res = persistent()
+    for (c, l), info, (_, b_, it) in zip(groups, infos, res):
+        lx.sim_count(info, b_, it, c.k, counts)
+    cnt = counts.cpu().tolist()
+    out.update(desc)
+    out["speedup"] = out["per_group"]["ms"] / out["persistent"]["ms"]
+    out["ber"] = cnt[1] / cnt[0]
+    out["bler"] = cnt[3] / cnt[2]
+    out["mean_iters"] = cnt[4] / cnt[2]
     return out
 
 

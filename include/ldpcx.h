@@ -247,6 +247,34 @@ int ldpcx_tune_get(int key, int *value);
 int ldpc_bp_decode_noalloc(ldpcx_code_t code, const float *llr_ch, int64_t B, const ldpcx_decode_opts *opts,
                            float *llr_out, uint32_t *bits_out, int32_t *iters_out, void *stream);
 
+/* -------------------------------------------- mixed-size batch (a12) */
+/* One persistent launch decodes a batch mixing codes of different lifting
+ * sizes, base-graph shapes and rates -- the per-example differing execution
+ * the paper names as the reason for custom CUDA ops (Sec. III-D, Sec. IV-A).
+ * The batch is a list of groups, one per code. Work items (up to G codewords
+ * of one code, G = the codewords one CTA decodes together) are ordered by
+ * nominal cost (edges x codewords, largest first) and pulled by resident CTAs
+ * from a device queue with atomicAdd; a CTA decodes an item to the end
+ * (including early stop) before it pulls the next. Layered schedules only.
+ * Results equal ldpc_bp_decode on each group separately, bit for bit. */
+typedef struct {
+    ldpcx_code_t code;
+    int64_t B;             /* codewords of this group (>= 0) */
+    const float *llr_ch;   /* device [B][n_tx of the code] */
+    float *llr_out;        /* device [B][n] or NULL */
+    uint32_t *bits_out;    /* device [B][ceil(k/32)] or NULL */
+    int32_t *iters_out;    /* device [B] or NULL */
+} ldpcx_batch_group;
+
+/* Workspace bytes for the groups: queue, item list, and message scratch for
+ * each resident CTA (not per codeword). Needs the current device (SM count). */
+int ldpc_bp_mixed_workspace(const ldpcx_batch_group *groups, int n_groups, const ldpcx_decode_opts *opts,
+                            size_t *ws_bytes);
+/* Decode all groups in one persistent launch. ws: device, >= the workspace
+ * bytes, 256-byte aligned; it is written (queue, items) before the launch. */
+int ldpc_bp_decode_mixed(const ldpcx_batch_group *groups, int n_groups, const ldpcx_decode_opts *opts, void *ws,
+                         size_t ws_bytes, void *stream);
+
 /* ------------------------------------------- differentiable BP (a11) */
 /* Gradients through the unrolled decoder ("gradients can be specified" for a
  * custom op, Sec. IV-A; end-to-end learning with a binary cross-entropy loss,

@@ -18,7 +18,7 @@ __all__ = [
     "LdpcxError", "Code", "ldpcx_status_str", "ldpcx_sync_status", "qc_ldpc_build", "qc_ldpc_free",
     "qc_ldpc_info", "qc_ldpc_base", "sim_tx", "demap_app", "ldpc_bp_workspace", "ldpc_bp_decode",
     "sim_count", "sim_workspace", "sim_run", "library_path", "load_library", "ldpcx_tune_set", "ldpcx_tune_get",
-    "ldpc_bp_decode_noalloc", "ldpc_bp_ckpt_bytes", "ldpc_bp_decode_ckpt", "ldpc_bp_backward_workspace",
+    "ldpc_bp_decode_noalloc", "ldpc_bp_mixed_workspace", "ldpc_bp_decode_mixed", "ldpc_bp_ckpt_bytes", "ldpc_bp_decode_ckpt", "ldpc_bp_backward_workspace",
     "ldpc_bp_backward",
     "LAYERED_MINSUM", "LAYERED_SPA", "FLOOD_MINSUM", "FLOOD_SPA", "MSG_F32", "MSG_F16", "MSG_FIX6",
     "DEMAP_EXACT", "DEMAP_MAXLOG",
@@ -60,6 +60,11 @@ class SimConfig(C.Structure):
                 ("n_snr", C.c_int), ("stop_ber", C.c_double), ("use_graph", C.c_int)]
 
 
+class BatchGroup(C.Structure):
+    _fields_ = [("code", C.c_void_p), ("B", C.c_int64), ("llr_ch", C.c_void_p), ("llr_out", C.c_void_p),
+                ("bits_out", C.c_void_p), ("iters_out", C.c_void_p)]
+
+
 class SimCounts(C.Structure):
     _fields_ = [("bits", C.c_int64), ("bit_errors", C.c_int64), ("blocks", C.c_int64),
                 ("block_errors", C.c_int64), ("iter_sum", C.c_int64)]
@@ -84,6 +89,8 @@ _SIGS = {
     "sim_workspace": ([C.POINTER(SimConfig), C.POINTER(_sz)], _i),
     "sim_run": ([C.POINTER(SimConfig), C.POINTER(SimCounts), C.POINTER(_i), _vp, _sz, _vp], _i),
     "ldpc_bp_decode_noalloc": ([_vp, _vp, _i64, C.POINTER(DecodeOpts), _vp, _vp, _vp, _vp], _i),
+    "ldpc_bp_mixed_workspace": ([C.POINTER(BatchGroup), _i, C.POINTER(DecodeOpts), C.POINTER(_sz)], _i),
+    "ldpc_bp_decode_mixed": ([C.POINTER(BatchGroup), _i, C.POINTER(DecodeOpts), _vp, _sz, _vp], _i),
     "ldpc_bp_ckpt_bytes": ([_vp, _i64, C.POINTER(DecodeOpts), C.POINTER(_sz)], _i),
     "ldpc_bp_decode_ckpt": ([_vp, _vp, _i64, C.POINTER(DecodeOpts), _vp, _vp, _vp, _vp, _sz, _vp, _sz, _vp], _i),
     "ldpc_bp_backward_workspace": ([_vp, _i64, C.POINTER(DecodeOpts), C.POINTER(_sz)], _i),
@@ -313,6 +320,52 @@ def ldpc_bp_decode_noalloc(code: Code, llr_ch, *, algo: int = LAYERED_MINSUM, it
                                                  _ptr(bits_out), _ptr(iters_out), _stream(stream)),
            "ldpc_bp_decode_noalloc")
     return llr_out, bits_out, iters_out
+
+
+# --------------------------------------------------------------------------- mixed-size batches
+def _groups(groups, llr_out):
+    import torch
+    arr = (BatchGroup * len(groups))()
+    outs = []
+    for i, (code, llr) in enumerate(groups):
+        _cuda_f32(llr, "llr_ch")
+        B, dev = llr.shape[0], llr.device
+        lo = torch.empty((B, code.n), dtype=torch.float32, device=dev) if llr_out else None
+        bits = torch.empty((B, (code.k + 31) // 32), dtype=torch.int32, device=dev)
+        its = torch.empty((B,), dtype=torch.int32, device=dev)
+        arr[i] = BatchGroup(code.handle, B, llr.data_ptr(), _ptr(lo), bits.data_ptr(), its.data_ptr())
+        outs.append((lo, bits, its))
+    return arr, outs
+
+
+def ldpc_bp_mixed_workspace(groups, *, algo: int = LAYERED_MINSUM, iters: int = 20, msg_prec: int = MSG_F16,
+                            early_stop: bool = True, offset: float = 0.5, clamp: float = 20.0) -> int:
+    arr, _ = _groups(groups, False)
+    o = _opts(algo, iters, msg_prec, early_stop, offset, clamp, None)
+    n = C.c_size_t(0)
+    _check(load_library().ldpc_bp_mixed_workspace(arr, len(groups), C.byref(o), C.byref(n)),
+           "ldpc_bp_mixed_workspace")
+    return n.value
+
+
+def ldpc_bp_decode_mixed(groups, *, algo: int = LAYERED_MINSUM, iters: int = 20, msg_prec: int = MSG_F16,
+                         early_stop: bool = True, offset: float = 0.5, clamp: float = 20.0, llr_out: bool = False,
+                         ws=None, stream=None):
+    """Decode a batch mixing codes in one persistent launch.
+
+    groups: list of (Code, llr_ch [B_i, n_tx_i] CUDA float32). Returns a list of
+    (llr_out or None, bits [B_i, ceil(k_i/32)], iters [B_i]) per group."""
+    import torch
+    arr, outs = _groups(groups, llr_out)
+    o = _opts(algo, iters, msg_prec, early_stop, offset, clamp, None)
+    n = C.c_size_t(0)
+    L = load_library()
+    _check(L.ldpc_bp_mixed_workspace(arr, len(groups), C.byref(o), C.byref(n)), "ldpc_bp_mixed_workspace")
+    if ws is None:
+        ws = torch.empty(n.value, dtype=torch.uint8, device=groups[0][1].device)
+    _check(L.ldpc_bp_decode_mixed(arr, len(groups), C.byref(o), _ptr(ws), ws.numel(), _stream(stream)),
+           "ldpc_bp_decode_mixed")
+    return outs
 
 
 # --------------------------------------------------------------------------- differentiable decoding

@@ -547,17 +547,20 @@ __device__ __forceinline__ bool syndrome_bad_vec(const Params &p, const uint32_t
 // Threads per CTA of the layered kernel: ZPT check nodes per thread.
 template <int ZPT> constexpr int layered_threads() { return kMaxThreads / ZPT; }
 
+// One tile of the layered schedule: the G codewords cw_base .. cw_base+G-1 of
+// p, decoded by the whole CTA. Messages of codeword cw live at
+// msg + (cw - msg_cw0) * msg_stride (msg_cw0 = 0: one slot per codeword of the
+// batch; msg_cw0 = cw_base: one slot per codeword of the tile).
 template <int DMAX, int ALGO, int PREC, int ZPT>
-__global__ void __launch_bounds__(layered_threads<ZPT>(), 2) k_layered(const Params p) {
+__device__ __forceinline__ void layered_tile(const Params &p, int64_t cw_base, int64_t msg_cw0,
+                                             unsigned char *smem) {
     using MT = typename MsgT<PREC>::T;
-    extern __shared__ __align__(16) unsigned char smem[];
     float *s_app_all = reinterpret_cast<float *>(smem);
     uint32_t *s_vb = reinterpret_cast<uint32_t *>(s_app_all + (size_t)p.G * p.n);
     int32_t *s_rp = reinterpret_cast<int32_t *>(s_vb + p.nnz);
     int *s_flag = reinterpret_cast<int *>(s_rp + p.rows + 1);
 
     load_tables(p, s_vb, s_rp);
-    const int64_t cw_base = (int64_t)blockIdx.x * p.G;
     load_channel(p, s_app_all, cw_base);
 
     const int zq = p.Z / ZPT;  // threads per codeword
@@ -565,7 +568,7 @@ __global__ void __launch_bounds__(layered_threads<ZPT>(), 2) k_layered(const Par
     const int64_t cw = cw_base + g;
     const bool active = g < p.G && cw < p.B;
     float *app = s_app_all + (size_t)(active ? g : 0) * p.n;
-    MT *mp = reinterpret_cast<MT *>(p.msg) + (active ? cw : 0) * p.msg_stride + z0;
+    MT *mp = reinterpret_cast<MT *>(p.msg) + (active ? cw - msg_cw0 : 0) * p.msg_stride + z0;
     bool done = !active;
     int iters_run = 0;
     __syncthreads();
@@ -602,6 +605,12 @@ __global__ void __launch_bounds__(layered_threads<ZPT>(), 2) k_layered(const Par
     }
     __syncthreads();
     write_outputs(p, s_app_all, cw_base, iters_run, g, active, z0);
+}
+
+template <int DMAX, int ALGO, int PREC, int ZPT>
+__global__ void __launch_bounds__(layered_threads<ZPT>(), 2) k_layered(const Params p) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    layered_tile<DMAX, ALGO, PREC, ZPT>(p, (int64_t)blockIdx.x * p.G, 0, smem);
 }
 
 // Flooding update of check node z of one layer of degree deg <= DMAX:

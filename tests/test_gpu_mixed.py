@@ -1,0 +1,78 @@
+"""One persistent launch over a batch that mixes codes (ldpc_bp_decode_mixed).
+
+Each group's outputs (APP LLRs, hard decisions, iteration counts) must equal
+ldpc_bp_decode on that group alone, bit for bit, and the FP32-replay oracle on
+a sampled group; groups span both base-graph shapes, lifting sizes 8..384,
+truncated rates, ragged sizes and an empty group.
+"""
+import numpy as np
+import pytest
+
+from tests import inputs
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+GROUPS = [
+    # (bg, Z, rows_kept, punct, B)
+    (1, 384, 0, 2, 7),
+    (2, 64, 0, 2, 37),
+    (1, 16, 13, 2, 100),
+    (2, 128, 7, 2, 9),
+    (1, 256, 24, 2, 5),
+    (2, 8, 0, 0, 130),
+    (2, 32, 4, 2, 0),
+]
+
+
+@pytest.fixture(scope="module")
+def lx():
+    import paper_2203_11854_gb300 as lx
+    assert torch.cuda.is_available()
+    lx.load_library()
+    return lx
+
+
+def build_groups(lx, orc, seed=3):
+    out = []
+    for i, (bg, Z, rk, punct, B) in enumerate(GROUPS):
+        code = lx.qc_ldpc_build(bg, Z, rows_kept=rk, punct_cols=punct)
+        cw = np.zeros((B, code.n), dtype=np.uint8)
+        if 0 < B and Z <= 64:  # real codewords where the oracle encoder is quick
+            ocode = orc.Code(bg, Z, rows_kept=rk, punct_cols=punct)
+            cw = ocode.encoder.encode(inputs.info_bits(seed + i, B, ocode.k))
+        L = inputs.gaussian_llrs(cw, 2.6, seed + 10 * i)
+        L_tx = np.ascontiguousarray(L[:, code.p0:code.p0 + code.n_tx])
+        out.append((code, torch.from_numpy(L_tx).cuda()))
+    return out
+
+
+@pytest.mark.parametrize("algo,prec", [(0, 1), (0, 0), (0, 2), (1, 0)])
+def test_mixed_equals_per_group(lx, orc, algo, prec):
+    groups = build_groups(lx, orc)
+    res = lx.ldpc_bp_decode_mixed(groups, algo=algo, iters=12, msg_prec=prec, early_stop=True, llr_out=True)
+    stopped = 0
+    for (code, llr), (lo, bits, its) in zip(groups, res):
+        ref = lx.ldpc_bp_decode(code, llr, algo=algo, iters=12, msg_prec=prec, early_stop=True, llr_out=True)
+        assert torch.equal(lo, ref[0]) and torch.equal(bits, ref[1]) and torch.equal(its, ref[2])
+        stopped += int((its < 12).sum()) if its.numel() else 0
+    assert stopped > 0
+    assert lx.ldpcx_sync_status()[0] == 0
+
+
+def test_mixed_group_against_oracle(lx, orc):
+    groups = build_groups(lx, orc)
+    res = lx.ldpc_bp_decode_mixed(groups, algo=0, iters=12, msg_prec=1, early_stop=True, llr_out=True)
+    code, llr = groups[2]
+    bg, Z, rk, punct, B = GROUPS[2]
+    ocode = orc.Code(bg, Z, rows_kept=rk, punct_cols=punct)
+    app, hard, its = orc.decode(ocode.graph, orc.place_llr(llr.cpu().numpy().astype(np.float64), ocode.p0, ocode.n),
+                                algo=0, iters=12, prec=1, store=1, early_stop=True)
+    assert np.array_equal(res[2][0].cpu().numpy(), app.astype(np.float32))
+    assert np.array_equal(res[2][2].cpu().numpy(), its)
+
+
+def test_mixed_rejects_flooding(lx, orc):
+    groups = build_groups(lx, orc)
+    with pytest.raises(lx.LdpcxError):
+        lx.ldpc_bp_decode_mixed(groups, algo=lx.FLOOD_SPA, iters=5, msg_prec=0)
