@@ -311,16 +311,21 @@ def run_gpu(args):
 
 
 def measure_variants(lx, code, llr, bits, its, stream, args, pk):
-    """Decode-kernel time of the other message formats and check-node rules on the same LLRs."""
+    """Decode-kernel time of the other message formats and check-node rules on the same LLRs, each with
+    its own autotuned launch knobs (tuned on 1024 codewords; the knobs never change results)."""
     import torch
+    from paper_2203_11854_gb300 import autotune
     out = {}
     reps = max(3, min(args.steps, 10))
+    cache = f"/tmp/ldpcx_autotune_{os.getpid()}.json"
     for name, algo, prec, s_msg in [("minsum_f32", lx.LAYERED_MINSUM, lx.MSG_F32, 4),
                                     ("minsum_f16", lx.LAYERED_MINSUM, lx.MSG_F16, 2),
                                     ("minsum_fix6", lx.LAYERED_MINSUM, lx.MSG_FIX6, 1),
                                     ("spa_f32", lx.LAYERED_SPA, lx.MSG_F32, 4),
                                     ("spa_f16", lx.LAYERED_SPA, lx.MSG_F16, 2)]:
         dec = dict(algo=algo, iters=ITERS, msg_prec=prec, offset=OFFSET, clamp=CLAMP)
+        tuned = autotune.tune(code, B=1024, algo=algo, msg_prec=prec, iters=ITERS, cache_path=cache)["best"]
+        autotune.apply(code, algo=algo, msg_prec=prec, iters=ITERS, cache_path=cache)
         ws = torch.empty(lx.ldpc_bp_workspace(code, B, **dec), dtype=torch.uint8, device=llr.device)
         for _ in range(2):
             lx.ldpc_bp_decode(code, llr, **dec, bits_out=bits, iters_out=its, ws=ws, stream=stream)
@@ -335,10 +340,17 @@ def measure_variants(lx, code, llr, bits, its, stream, args, pk):
         alg = B * (code.edges * s_msg * 2 * (ITERS - 1) + 4 * code.n_tx + code.k / 8)
         out[name] = {"decode_ms": ms, "gbps": B * code.k / (ms * 1e-3) / 1e9,
                      "edge_updates_per_s": B * code.edges * ITERS / (ms * 1e-3),
-                     "hbm_frac": alg / (ms * 1e-3) / 1e9 / pk["hbm_gbs"]}
+                     "hbm_frac": alg / (ms * 1e-3) / 1e9 / pk["hbm_gbs"],
+                     "knobs": {"l2_prefetch": tuned["l2_prefetch"], "cw_per_cta": tuned["cw_per_cta"]}}
+        lx.ldpcx_tune_set(lx.TUNE_L2_PREFETCH, 0)
+        lx.ldpcx_tune_set(lx.TUNE_CW_PER_CTA, 0)
         del ws
     if "minsum_f32" in out and "minsum_f16" in out:
         out["f16_over_f32"] = out["minsum_f32"]["decode_ms"] / out["minsum_f16"]["decode_ms"]
+    try:
+        os.remove(cache)
+    except OSError:
+        pass
     return out
 
 

@@ -218,9 +218,13 @@ int ldpc_bp_decode(ldpcx_code_t code, const float *llr_ch, int64_t B, const ldpc
  * message span of the layer this many layers ahead (0 = off, 0..16, default 0).
  * LDPCX_TUNE_ZPT: check nodes per thread of the layered kernels (0 = auto = 1;
  * 2 is honoured only when Z is even and the library was built with it).
+ * LDPCX_TUNE_CW_PER_CTA: codewords decoded together by one CTA of
+ * ldpc_bp_decode (0 = automatic: about 384 check nodes per CTA within the
+ * shared-memory budget; a smaller value gives smaller CTAs, more per SM).
  * Knobs change speed only, never results. */
 #define LDPCX_TUNE_L2_PREFETCH 1
 #define LDPCX_TUNE_ZPT 2
+#define LDPCX_TUNE_CW_PER_CTA 3
 int ldpcx_tune_set(int key, int value);
 int ldpcx_tune_get(int key, int *value);
 

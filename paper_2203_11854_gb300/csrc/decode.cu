@@ -43,6 +43,10 @@ int check_opts(const ldpcx_code *c, const ldpcx_decode_opts *o) {
     return LDPCX_OK;
 }
 
+std::atomic<int> g_pf_dist{0};
+std::atomic<int> g_zpt{0};
+std::atomic<int> g_cw_per_cta{0};  // 0 = automatic
+
 // Codewords per CTA: enough check-node threads to fill ~384 threads, bounded
 // by the shared memory that keeps two CTAs per SM (layered) or one (flooding).
 int pick_G(const ldpcx_code *c, bool layered) {
@@ -51,11 +55,12 @@ int pick_G(const ldpcx_code *c, bool layered) {
     int G = kMaxThreads / c->Z;
     if (G < 1) G = 1;
     while (G > 1 && per_cw * G > budget) --G;
+    const int want = g_cw_per_cta.load();
+    if (want > 0 && want < G) G = want;  // autotuner: smaller tiles, more CTAs per SM
     return G;
 }
 
-std::atomic<int> g_pf_dist{0};
-std::atomic<int> g_zpt{0};  // check nodes per thread of the layered kernels: 0 = auto (1), 1, 2
+  // check nodes per thread of the layered kernels: 0 = auto (1), 1, 2
 
 }  // namespace
 
@@ -220,6 +225,11 @@ extern "C" int ldpcx_tune_set(int key, int value) {
         g_zpt.store(value);
         return LDPCX_OK;
     }
+    if (key == LDPCX_TUNE_CW_PER_CTA) {
+        if (value < 0 || value > kMaxThreads) return LDPCX_E_INVAL;
+        g_cw_per_cta.store(value);
+        return LDPCX_OK;
+    }
     return LDPCX_E_INVAL;
 }
 
@@ -231,6 +241,10 @@ extern "C" int ldpcx_tune_get(int key, int *value) {
     }
     if (key == LDPCX_TUNE_ZPT) {
         *value = g_zpt.load();
+        return LDPCX_OK;
+    }
+    if (key == LDPCX_TUNE_CW_PER_CTA) {
+        *value = g_cw_per_cta.load();
         return LDPCX_OK;
     }
     return LDPCX_E_INVAL;
