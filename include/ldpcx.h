@@ -221,10 +221,14 @@ int ldpc_bp_decode(ldpcx_code_t code, const float *llr_ch, int64_t B, const ldpc
  * LDPCX_TUNE_CW_PER_CTA: codewords decoded together by one CTA of
  * ldpc_bp_decode (0 = automatic: about 384 check nodes per CTA within the
  * shared-memory budget; a smaller value gives smaller CTAs, more per SM).
+ * LDPCX_TUNE_SPECIALISED: 1 (default) = use the layered min-sum kernels built
+ * for a compile-time lifting size when one exists for the code's Z (384);
+ * 0 = always the generic kernel.
  * Knobs change speed only, never results. */
 #define LDPCX_TUNE_L2_PREFETCH 1
 #define LDPCX_TUNE_ZPT 2
 #define LDPCX_TUNE_CW_PER_CTA 3
+#define LDPCX_TUNE_SPECIALISED 4
 int ldpcx_tune_set(int key, int value);
 int ldpcx_tune_get(int key, int *value);
 

@@ -14,8 +14,16 @@ using namespace dec;
 
 __device__ unsigned int g_status;
 
-KernelFn pick_kernel(int max_deg, bool layered, int algo, int prec, int zpt) {
+std::atomic<int> g_specialised{1};  // use compile-time-Z kernels when built
+
+KernelFn pick_kernel(int max_deg, bool layered, int algo, int prec, int zpt, int Z) {
     if (!layered) return flooding_kernel(max_deg, algo, prec);
+    if (zpt == 1 && g_specialised.load()) {
+        KernelFn f = prec == kF32 ? layered_kernel_zc_f32(max_deg, algo, Z)
+                   : prec == kF16 ? layered_kernel_zc_f16(max_deg, algo, Z)
+                                  : layered_kernel_zc_fix6(max_deg, algo, Z);
+        if (f) return f;
+    }
     if (prec == kF32) return layered_kernel_f32(max_deg, algo, zpt);
     if (prec == kF16) return layered_kernel_f16(max_deg, algo, zpt);
     return layered_kernel_fix6(max_deg, algo, zpt);
@@ -121,10 +129,10 @@ int decode_impl(ldpcx_code_t c, const float *llr_ch, int64_t B, const ldpcx_deco
         const int want = g_zpt.load();
         zpt = (want == 2 && c->Z % 2 == 0) ? 2 : 1;
     }
-    KernelFn fn = pick_kernel(c->max_deg, layered, algo, o->msg_prec, zpt);
+    KernelFn fn = pick_kernel(c->max_deg, layered, algo, o->msg_prec, zpt, c->Z);
     if (!fn && zpt == 2) {  // two check nodes per thread not built: fall back to one
         zpt = 1;
-        fn = pick_kernel(c->max_deg, layered, algo, o->msg_prec, zpt);
+        fn = pick_kernel(c->max_deg, layered, algo, o->msg_prec, zpt, c->Z);
     }
     if (!fn) return LDPCX_E_UNSUPPORTED;
 
@@ -230,6 +238,11 @@ extern "C" int ldpcx_tune_set(int key, int value) {
         g_cw_per_cta.store(value);
         return LDPCX_OK;
     }
+    if (key == LDPCX_TUNE_SPECIALISED) {
+        if (value < 0 || value > 1) return LDPCX_E_INVAL;
+        g_specialised.store(value);
+        return LDPCX_OK;
+    }
     return LDPCX_E_INVAL;
 }
 
@@ -245,6 +258,10 @@ extern "C" int ldpcx_tune_get(int key, int *value) {
     }
     if (key == LDPCX_TUNE_CW_PER_CTA) {
         *value = g_cw_per_cta.load();
+        return LDPCX_OK;
+    }
+    if (key == LDPCX_TUNE_SPECIALISED) {
+        *value = g_specialised.load();
         return LDPCX_OK;
     }
     return LDPCX_E_INVAL;

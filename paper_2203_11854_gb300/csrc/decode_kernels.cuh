@@ -408,10 +408,11 @@ __device__ __forceinline__ void load_layer(float (&R)[ZPT][kPf], const typename 
 // deg == D exactly). Rc holds the old messages (prefetched) when D > 0; the
 // predicated body loads them itself (first iteration: zero).
 // T = APP - R_old, check-node rule, APP = T + R_new (rounded), store R_new.
-template <int D, int DM, int ALGO, int PREC, int ZPT>
+template <int D, int DM, int ALGO, int PREC, int ZPT, int ZC>
 __device__ __forceinline__ void layer_update(const Params &p, int deg, float *app, const uint32_t *vb, int z0,
                                              typename MsgT<PREC>::T *ml, const float (&Rc)[ZPT][kPf], bool load,
                                              bool store) {
+    const int ZV = ZC ? ZC : p.Z;  // lifting size (compile-time when ZC != 0)
     constexpr int N = D ? D : DM;
     constexpr bool kKeepIdx = D != 0;  // exact (sparse) bodies keep their indices in registers
     float T[ZPT][N];
@@ -424,13 +425,13 @@ __device__ __forceinline__ void layer_update(const Params &p, int deg, float *ap
 #pragma unroll
                 for (int k = 0; k < ZPT; ++k) old[k] = Rc[k][j < kPf ? j : 0];
             } else if (load) {
-                MsgVec<PREC, ZPT>::load(ml + (size_t)j * p.Z, old);
+                MsgVec<PREC, ZPT>::load(ml + (size_t)j * ZV, old);
             } else {
 #pragma unroll
                 for (int k = 0; k < ZPT; ++k) old[k] = 0.0f;
             }
             int v[ZPT];
-            vn_vec<ZPT>(vb[j], z0, p.Z, v);
+            vn_vec<ZPT>(vb[j], z0, ZV, v);
 #pragma unroll
             for (int k = 0; k < ZPT; ++k) {
                 if constexpr (kKeepIdx) vi[k][j] = v[k];
@@ -457,13 +458,13 @@ __device__ __forceinline__ void layer_update(const Params &p, int deg, float *ap
                 if constexpr (ALGO == kMinSum) r[k] = cn[k].value(T[k][j]);
                 else r[k] = cn[k].value(j, p.clamp, p.phi_lo);
             }
-            MsgVec<PREC, ZPT>::round_store(ml + (size_t)j * p.Z, r, rq, store);
+            MsgVec<PREC, ZPT>::round_store(ml + (size_t)j * ZV, r, rq, store);
             int v[ZPT];
             if constexpr (kKeepIdx) {
 #pragma unroll
                 for (int k = 0; k < ZPT; ++k) v[k] = vi[k][j];
             } else {
-                vn_vec<ZPT>(vb[j], z0, p.Z, v);  // dense body: recomputed, fewer live registers
+                vn_vec<ZPT>(vb[j], z0, ZV, v);  // dense body: recomputed, fewer live registers
             }
 #pragma unroll
             for (int k = 0; k < ZPT; ++k) app[v[k]] = __fadd_rn(T[k][j], rq[k]);
@@ -473,10 +474,11 @@ __device__ __forceinline__ void layer_update(const Params &p, int deg, float *ap
 
 // One layer step of the layered schedule: prefetch the next layer's messages
 // into Rn (sparse layers), update layer r, then a block barrier.
-template <int DMAX, int ALGO, int PREC, int ZPT>
+template <int DMAX, int ALGO, int PREC, int ZPT, int ZC>
 __device__ __forceinline__ void layered_step(const Params &p, const uint32_t *s_vb, const int32_t *s_rp, float *app,
                                              typename MsgT<PREC>::T *mp, int z0, int t, int r, bool done,
                                              int64_t cw_base, const float (&Rc)[ZPT][kPf], float (&Rn)[ZPT][kPf]) {
+    const int ZV = ZC ? ZC : p.Z;  // lifting size (compile-time when ZC != 0)
     const int b0 = s_rp[r], deg = s_rp[r + 1] - b0;
     if (p.pf_dist > 0 && threadIdx.x == 0) l2_prefetch_layer(p, s_rp, cw_base, r, t);
     int rn = r + 1, tn = t;
@@ -491,11 +493,11 @@ __device__ __forceinline__ void layered_step(const Params &p, const uint32_t *s_
             for (int j = 0; j < kPf; ++j) Rn[k][j] = 0.0f;  // iteration 0 starts from zero messages
     } else if (!done && tn < p.iters) {
         const int bn0 = s_rp[rn], degn = s_rp[rn + 1] - bn0;
-        const auto *ml = mp + (size_t)bn0 * p.Z;
+        const auto *ml = mp + (size_t)bn0 * ZV;
         switch (degn) {
 #define LDPCX_LOAD(d) \
     case d:           \
-        load_layer<d, PREC, ZPT>(Rn, ml, p.Z); \
+        load_layer<d, PREC, ZPT>(Rn, ml, ZV); \
         break;
             LDPCX_LOAD(1) LDPCX_LOAD(2) LDPCX_LOAD(3) LDPCX_LOAD(4)
             LDPCX_LOAD(5) LDPCX_LOAD(6) LDPCX_LOAD(7) LDPCX_LOAD(8)
@@ -505,18 +507,18 @@ __device__ __forceinline__ void layered_step(const Params &p, const uint32_t *s_
     }
     if (!done) {
         const bool store = t + 1 < p.iters;  // the last iteration's messages are never read
-        auto *ml = mp + (size_t)b0 * p.Z;
+        auto *ml = mp + (size_t)b0 * ZV;
         const uint32_t *vb = s_vb + b0;
         switch (deg) {
 #define LDPCX_UPDATE(d) \
     case d:             \
-        layer_update<d, d, ALGO, PREC, ZPT>(p, d, app, vb, z0, ml, Rc, t > 0, store); \
+        layer_update<d, d, ALGO, PREC, ZPT, ZC>(p, d, app, vb, z0, ml, Rc, t > 0, store); \
         break;
             LDPCX_UPDATE(1) LDPCX_UPDATE(2) LDPCX_UPDATE(3) LDPCX_UPDATE(4)
             LDPCX_UPDATE(5) LDPCX_UPDATE(6) LDPCX_UPDATE(7) LDPCX_UPDATE(8)
 #undef LDPCX_UPDATE
             default:
-                layer_update<0, DMAX, ALGO, PREC, ZPT>(p, deg, app, vb, z0, ml, Rc, t > 0, store);
+                layer_update<0, DMAX, ALGO, PREC, ZPT, ZC>(p, deg, app, vb, z0, ml, Rc, t > 0, store);
                 break;
         }
     }
@@ -524,9 +526,10 @@ __device__ __forceinline__ void layered_step(const Params &p, const uint32_t *s_
 }
 
 // Parity of the check nodes of z0 .. z0+ZPT-1 over the current hard decisions.
-template <int ZPT>
+template <int ZPT, int ZC>
 __device__ __forceinline__ bool syndrome_bad_vec(const Params &p, const uint32_t *s_vb, const int32_t *s_rp,
                                                  const float *app, int z0) {
+    const int ZV = ZC ? ZC : p.Z;  // lifting size (compile-time when ZC != 0)
     bool bad = false;
     for (int r = 0; r < p.rows; ++r) {
         unsigned par[ZPT];
@@ -534,7 +537,7 @@ __device__ __forceinline__ bool syndrome_bad_vec(const Params &p, const uint32_t
         for (int k = 0; k < ZPT; ++k) par[k] = 0;
         for (int b = s_rp[r]; b < s_rp[r + 1]; ++b) {
             int v[ZPT];
-            vn_vec<ZPT>(s_vb[b], z0, p.Z, v);
+            vn_vec<ZPT>(s_vb[b], z0, ZV, v);
 #pragma unroll
             for (int k = 0; k < ZPT; ++k) par[k] ^= app[v[k]] < 0.0f ? 1u : 0u;
         }
@@ -551,9 +554,10 @@ template <int ZPT> constexpr int layered_threads() { return kMaxThreads / ZPT; }
 // p, decoded by the whole CTA. Messages of codeword cw live at
 // msg + (cw - msg_cw0) * msg_stride (msg_cw0 = 0: one slot per codeword of the
 // batch; msg_cw0 = cw_base: one slot per codeword of the tile).
-template <int DMAX, int ALGO, int PREC, int ZPT>
+template <int DMAX, int ALGO, int PREC, int ZPT, int ZC = 0>
 __device__ __forceinline__ void layered_tile(const Params &p, int64_t cw_base, int64_t msg_cw0,
                                              unsigned char *smem) {
+    const int ZV = ZC ? ZC : p.Z;  // lifting size (compile-time when ZC != 0)
     using MT = typename MsgT<PREC>::T;
     float *s_app_all = reinterpret_cast<float *>(smem);
     uint32_t *s_vb = reinterpret_cast<uint32_t *>(s_app_all + (size_t)p.G * p.n);
@@ -563,7 +567,7 @@ __device__ __forceinline__ void layered_tile(const Params &p, int64_t cw_base, i
     load_tables(p, s_vb, s_rp);
     load_channel(p, s_app_all, cw_base);
 
-    const int zq = p.Z / ZPT;  // threads per codeword
+    const int zq = ZV / ZPT;  // threads per codeword
     const int g = threadIdx.x / zq, z0 = (threadIdx.x - g * zq) * ZPT;
     const int64_t cw = cw_base + g;
     const bool active = g < p.G && cw < p.B;
@@ -592,25 +596,26 @@ __device__ __forceinline__ void layered_tile(const Params &p, int64_t cw_base, i
         if (!p.early_stop) return false;
         if (threadIdx.x < p.G) s_flag[threadIdx.x] = 0;
         __syncthreads();
-        if (!done && syndrome_bad_vec<ZPT>(p, s_vb, s_rp, app, z0)) s_flag[g] = 1;
+        if (!done && syndrome_bad_vec<ZPT, ZC>(p, s_vb, s_rp, app, z0)) s_flag[g] = 1;
         __syncthreads();
         if (!done && s_flag[g] == 0) done = true;
         return __syncthreads_and(done);
     };
     while (t < p.iters) {
-        layered_step<DMAX, ALGO, PREC, ZPT>(p, s_vb, s_rp, app, mp, z0, t, r, done, cw_base, Ra, Rb);
+        layered_step<DMAX, ALGO, PREC, ZPT, ZC>(p, s_vb, s_rp, app, mp, z0, t, r, done, cw_base, Ra, Rb);
         if (advance() || t >= p.iters) break;
-        layered_step<DMAX, ALGO, PREC, ZPT>(p, s_vb, s_rp, app, mp, z0, t, r, done, cw_base, Rb, Ra);
+        layered_step<DMAX, ALGO, PREC, ZPT, ZC>(p, s_vb, s_rp, app, mp, z0, t, r, done, cw_base, Rb, Ra);
         if (advance()) break;
     }
     __syncthreads();
     write_outputs(p, s_app_all, cw_base, iters_run, g, active, z0);
 }
 
-template <int DMAX, int ALGO, int PREC, int ZPT>
+// ZC: compile-time lifting size (0 = the runtime p.Z).
+template <int DMAX, int ALGO, int PREC, int ZPT, int ZC = 0>
 __global__ void __launch_bounds__(layered_threads<ZPT>(), 2) k_layered(const Params p) {
     extern __shared__ __align__(16) unsigned char smem[];
-    layered_tile<DMAX, ALGO, PREC, ZPT>(p, (int64_t)blockIdx.x * p.G, 0, smem);
+    layered_tile<DMAX, ALGO, PREC, ZPT, ZC>(p, (int64_t)blockIdx.x * p.G, 0, smem);
 }
 
 // Flooding update of check node z of one layer of degree deg <= DMAX:
@@ -734,6 +739,11 @@ KernelFn layered_kernel_f32(int dmax, int algo, int zpt);
 KernelFn layered_kernel_f16(int dmax, int algo, int zpt);
 KernelFn layered_kernel_fix6(int dmax, int algo, int zpt);
 KernelFn flooding_kernel(int dmax, int algo, int prec);
+// Layered min-sum kernels specialised for a compile-time lifting size (nullptr
+// when none is built for Z): the hot loop's addresses become immediates.
+KernelFn layered_kernel_zc_f32(int dmax, int algo, int Z);
+KernelFn layered_kernel_zc_f16(int dmax, int algo, int Z);
+KernelFn layered_kernel_zc_fix6(int dmax, int algo, int Z);
 
 }  // namespace dec
 }  // namespace ldpcx

@@ -12,5 +12,12 @@ KernelFn layered_kernel_f32(int dmax, int algo, int zpt) {
     return dmax <= 12 ? k_layered<12, kSpa, PREC, 1> : k_layered<20, kSpa, PREC, 1>;
 }
 
+KernelFn layered_kernel_zc_f32(int dmax, int algo, int Z) {
+    constexpr int PREC = kF32;
+    if (algo != kMinSum || dmax > 20) return nullptr;
+    if (Z == 384) return dmax <= 12 ? k_layered<12, kMinSum, PREC, 1, 384> : k_layered<20, kMinSum, PREC, 1, 384>;
+    return nullptr;
+}
+
 }  // namespace dec
 }  // namespace ldpcx
