@@ -224,11 +224,17 @@ int ldpc_bp_decode(ldpcx_code_t code, const float *llr_ch, int64_t B, const ldpc
  * LDPCX_TUNE_SPECIALISED: 1 (default) = use the layered min-sum kernels built
  * for a compile-time lifting size when one exists for the code's Z (384);
  * 0 = always the generic kernel.
+ * LDPCX_TUNE_CN_STATE: 1 (default) = layered min-sum keeps, per check node,
+ * the two rounded message magnitudes and per-edge "took the second minimum" and
+ * sign bits instead of one stored message per edge (4, 8 or 16 bytes per check
+ * node); every message is rebuilt exactly, so results are identical. Used when
+ * the state fits the per-edge workspace. 0 = per-edge messages.
  * Knobs change speed only, never results. */
 #define LDPCX_TUNE_L2_PREFETCH 1
 #define LDPCX_TUNE_ZPT 2
 #define LDPCX_TUNE_CW_PER_CTA 3
 #define LDPCX_TUNE_SPECIALISED 4
+#define LDPCX_TUNE_CN_STATE 5
 int ldpcx_tune_set(int key, int value);
 int ldpcx_tune_get(int key, int *value);
 

@@ -5,7 +5,7 @@
 
 #include <atomic>
 
-#include "decode_kernels.cuh"
+#include "decode_cns.cuh"
 
 namespace ldpcx {
 namespace {
@@ -15,6 +15,15 @@ using namespace dec;
 __device__ unsigned int g_status;
 
 std::atomic<int> g_specialised{1};  // use compile-time-Z kernels when built
+std::atomic<int> g_cns{1};          // layered min-sum keeps check-node state instead of per-edge messages
+
+// Bytes of the check-node state of one codeword in format prec.
+int64_t cns_bytes(const ldpcx_code *c, int prec) {
+    const int32_t *rp = c->row_ptr.data();
+    if (prec == kF32) return cns_bytes_per_cw<kF32>(rp, c->rows, c->Z);
+    if (prec == kF16) return cns_bytes_per_cw<kF16>(rp, c->rows, c->Z);
+    return cns_bytes_per_cw<kFix6>(rp, c->rows, c->Z);
+}
 
 KernelFn pick_kernel(int max_deg, bool layered, int algo, int prec, int zpt, int Z) {
     if (!layered) return flooding_kernel(max_deg, algo, prec);
@@ -167,7 +176,15 @@ int decode_impl(ldpcx_code_t c, const float *llr_ch, int64_t B, const ldpcx_deco
     p.status = status_word_decode();
     if (!p.status) return LDPCX_E_CUDA;
 
-    const size_t smem = smem_bytes(p, layered ? 1 : 2);
+    size_t smem = smem_bytes(p, layered ? 1 : 2);
+    if (layered && algo == kMinSum && zpt == 1 && g_cns.load() &&
+        cns_bytes(c, o->msg_prec) <= p.msg_stride * p.msg_size) {
+        KernelFn f = layered_cns_kernel(c->max_deg, o->msg_prec, g_specialised.load() ? c->Z : 0);
+        if (f) {
+            fn = f;
+            smem = cns_smem_bytes(p);
+        }
+    }
     if (smem > 227 * 1024) return LDPCX_E_UNSUPPORTED;
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return LDPCX_E_CUDA;
@@ -243,6 +260,11 @@ extern "C" int ldpcx_tune_set(int key, int value) {
         g_specialised.store(value);
         return LDPCX_OK;
     }
+    if (key == LDPCX_TUNE_CN_STATE) {
+        if (value < 0 || value > 1) return LDPCX_E_INVAL;
+        g_cns.store(value);
+        return LDPCX_OK;
+    }
     return LDPCX_E_INVAL;
 }
 
@@ -262,6 +284,10 @@ extern "C" int ldpcx_tune_get(int key, int *value) {
     }
     if (key == LDPCX_TUNE_SPECIALISED) {
         *value = g_specialised.load();
+        return LDPCX_OK;
+    }
+    if (key == LDPCX_TUNE_CN_STATE) {
+        *value = g_cns.load();
         return LDPCX_OK;
     }
     return LDPCX_E_INVAL;

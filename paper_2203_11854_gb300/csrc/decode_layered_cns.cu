@@ -1,0 +1,22 @@
+// Layered min-sum kernels with check-node state (decode_cns.cuh), generic and
+// specialised for Z = 384, for FP32, FP16 and 6-bit message formats.
+#include "decode_cns.cuh"
+
+namespace ldpcx {
+namespace dec {
+
+template <int PREC>
+KernelFn cns_for(int dmax, int Z) {
+    if (Z == 384) return dmax <= 12 ? k_layered_cns<12, PREC, 384> : k_layered_cns<20, PREC, 384>;
+    return dmax <= 12 ? k_layered_cns<12, PREC, 0> : k_layered_cns<20, PREC, 0>;
+}
+
+KernelFn layered_cns_kernel(int dmax, int prec, int Z) {
+    if (dmax > 20) return nullptr;
+    if (prec == kF32) return cns_for<kF32>(dmax, Z);
+    if (prec == kF16) return cns_for<kF16>(dmax, Z);
+    return cns_for<kFix6>(dmax, Z);
+}
+
+}  // namespace dec
+}  // namespace ldpcx
