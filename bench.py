@@ -101,7 +101,7 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows)}
 
 
-KERNEL_SOURCES = ("decode_kernels.cuh", "decode_layered_f16.cu")  # the profiled kernel's own code
+KERNEL_SOURCES = ("decode_kernels.cuh", "decode_cns.cuh", "decode_layered_cns.cu")  # the profiled kernel's code
 
 
 def decoder_digest():
@@ -268,9 +268,11 @@ def run_gpu(args):
     value = world * B * code.k / (ms_per_step * 1e-3) / 1e9
     edge_updates = world * B * code.edges * ITERS / (ms_per_step * 1e-3)
 
-    # decode-kernel roofline: algorithmic bytes per launch / mean decode launch time
-    s_msg = 2
-    alg_bytes = B * (code.edges * s_msg * 2 * (ITERS - 1) + 4 * code.n_tx + code.k / 8)
+    # decode-kernel roofline: algorithmic bytes per launch / mean decode launch time. The message
+    # bytes are those of the storage format the decoder uses (check-node state for layered min-sum):
+    # one read and one write per iteration except the first read and the last write.
+    cn_state, msg_cw = lx.ldpc_bp_msg_format(code, **{k: dec[k] for k in ("algo", "iters", "msg_prec")})
+    alg_bytes = B * (msg_cw * 2 * (ITERS - 1) + 4 * code.n_tx + code.k / 8)
     dec_mean = sum(dec_ms) / len(dec_ms)
     pk, pk_kind = peaks()
     achieved = alg_bytes / (dec_mean * 1e-3) / 1e9
@@ -296,7 +298,9 @@ def run_gpu(args):
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
                          "frac": achieved / pk["hbm_gbs"],
                          "traffic": None if traffic_cw is None else traffic_cw * B,
-                         "kernel": "k_layered<20, min-sum, fp16>",
+                         "kernel": "k_layered_cns<20, fp16, Z=384>" if cn_state else "k_layered<20, min-sum, fp16>",
+                         "message_format": "check-node state" if cn_state else "per-edge messages",
+                         "message_bytes_per_codeword_iteration": msg_cw,
                          "peak_kind": f"{pk_kind} HBM copy bandwidth",
                          "algorithmic_bytes_per_launch": alg_bytes},
             "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
@@ -337,10 +341,12 @@ def measure_variants(lx, code, llr, bits, its, stream, args, pk):
         b.record(stream)
         torch.cuda.synchronize()
         ms = a.elapsed_time(b) / reps
-        alg = B * (code.edges * s_msg * 2 * (ITERS - 1) + 4 * code.n_tx + code.k / 8)
+        cns, msg_cw = lx.ldpc_bp_msg_format(code, algo=algo, iters=ITERS, msg_prec=prec)
+        alg = B * (msg_cw * 2 * (ITERS - 1) + 4 * code.n_tx + code.k / 8)
         out[name] = {"decode_ms": ms, "gbps": B * code.k / (ms * 1e-3) / 1e9,
                      "edge_updates_per_s": B * code.edges * ITERS / (ms * 1e-3),
                      "hbm_frac": alg / (ms * 1e-3) / 1e9 / pk["hbm_gbs"],
+                     "message_format": "check-node state" if cns else "per-edge messages",
                      "knobs": {"l2_prefetch": tuned["l2_prefetch"], "cw_per_cta": tuned["cw_per_cta"]}}
         lx.ldpcx_tune_set(lx.TUNE_L2_PREFETCH, 0)
         lx.ldpcx_tune_set(lx.TUNE_CW_PER_CTA, 0)

@@ -200,6 +200,12 @@ typedef struct {
  * storage: B * round_up(edges, 64) messages of the chosen format). */
 int ldpc_bp_workspace(ldpcx_code_t code, int64_t B, const ldpcx_decode_opts *opts, size_t *ws_bytes);
 
+/* The message storage ldpc_bp_decode will use for this code and options:
+ * *cn_state = 1 when layered min-sum keeps check-node state (see
+ * LDPCX_TUNE_CN_STATE), 0 for per-edge messages; *bytes_per_cw = bytes of
+ * message storage one codeword reads or writes in one full iteration. */
+int ldpc_bp_msg_format(ldpcx_code_t code, const ldpcx_decode_opts *opts, int *cn_state, int64_t *bytes_per_cw);
+
 /* Decode B codewords.
  * llr_ch   (device) [B][n_tx] float channel LLRs of the transmitted positions.
  * llr_out  (device, or NULL) [B][n] float final APP LLRs.

@@ -18,7 +18,7 @@ __all__ = [
     "LdpcxError", "Code", "ldpcx_status_str", "ldpcx_sync_status", "qc_ldpc_build", "qc_ldpc_free",
     "qc_ldpc_info", "qc_ldpc_base", "sim_tx", "demap_app", "ldpc_bp_workspace", "ldpc_bp_decode",
     "sim_count", "sim_workspace", "sim_run", "library_path", "load_library", "ldpcx_tune_set", "ldpcx_tune_get",
-    "ldpc_bp_decode_noalloc", "ldpc_bp_mixed_workspace", "ldpc_bp_decode_mixed", "ldpc_bp_ckpt_bytes", "ldpc_bp_decode_ckpt", "ldpc_bp_backward_workspace",
+    "ldpc_bp_decode_noalloc", "ldpc_bp_msg_format", "ldpc_bp_mixed_workspace", "ldpc_bp_decode_mixed", "ldpc_bp_ckpt_bytes", "ldpc_bp_decode_ckpt", "ldpc_bp_backward_workspace",
     "ldpc_bp_backward",
     "LAYERED_MINSUM", "LAYERED_SPA", "FLOOD_MINSUM", "FLOOD_SPA", "MSG_F32", "MSG_F16", "MSG_FIX6",
     "DEMAP_EXACT", "DEMAP_MAXLOG",
@@ -89,6 +89,7 @@ _SIGS = {
     "sim_workspace": ([C.POINTER(SimConfig), C.POINTER(_sz)], _i),
     "sim_run": ([C.POINTER(SimConfig), C.POINTER(SimCounts), C.POINTER(_i), _vp, _sz, _vp], _i),
     "ldpc_bp_decode_noalloc": ([_vp, _vp, _i64, C.POINTER(DecodeOpts), _vp, _vp, _vp, _vp], _i),
+    "ldpc_bp_msg_format": ([_vp, C.POINTER(DecodeOpts), C.POINTER(_i), C.POINTER(_i64)], _i),
     "ldpc_bp_mixed_workspace": ([C.POINTER(BatchGroup), _i, C.POINTER(DecodeOpts), C.POINTER(_sz)], _i),
     "ldpc_bp_decode_mixed": ([C.POINTER(BatchGroup), _i, C.POINTER(DecodeOpts), _vp, _sz, _vp], _i),
     "ldpc_bp_ckpt_bytes": ([_vp, _i64, C.POINTER(DecodeOpts), C.POINTER(_sz)], _i),
@@ -256,6 +257,16 @@ def ldpc_bp_workspace(code: Code, B: int, *, algo: int = LAYERED_MINSUM, iters: 
     ws = C.c_size_t(0)
     _check(load_library().ldpc_bp_workspace(code.handle, B, C.byref(o), C.byref(ws)), "ldpc_bp_workspace")
     return ws.value
+
+
+def ldpc_bp_msg_format(code: Code, *, algo: int = LAYERED_MINSUM, iters: int = 20, msg_prec: int = MSG_F32,
+                       early_stop: bool = False, offset: float = 0.5, clamp: float = 20.0) -> tuple[bool, int]:
+    """(check-node state used?, message-storage bytes per codeword per iteration)."""
+    o = _opts(algo, iters, msg_prec, early_stop, offset, clamp, None)
+    cs, nb = C.c_int(0), C.c_int64(0)
+    _check(load_library().ldpc_bp_msg_format(code.handle, C.byref(o), C.byref(cs), C.byref(nb)),
+           "ldpc_bp_msg_format")
+    return bool(cs.value), nb.value
 
 
 def ldpc_bp_decode(code: Code, llr_ch, *, algo: int = LAYERED_MINSUM, iters: int = 20, msg_prec: int = MSG_F32,

@@ -219,6 +219,21 @@ extern "C" int ldpc_bp_decode(ldpcx_code_t c, const float *llr_ch, int64_t B, co
     return ldpcx::decode_impl(c, llr_ch, B, o, llr_out, bits_out, iters_out, ws, ws_bytes, nullptr, stream);
 }
 
+extern "C" int ldpc_bp_msg_format(ldpcx_code_t c, const ldpcx_decode_opts *o, int *cn_state,
+                                  int64_t *bytes_per_cw) {
+    if (!c || !cn_state || !bytes_per_cw) return LDPCX_E_INVAL;
+    int st = ldpcx::check_opts(c, o);
+    if (st) return st;
+    const bool minsum_layered = o->algo == LDPCX_LAYERED_MINSUM;
+    const int64_t edge_bytes = (int64_t)c->nnz * c->Z * (int64_t)ldpcx::msg_bytes(o->msg_prec);
+    const int64_t cns = ldpcx::cns_bytes(c, o->msg_prec);
+    const bool use = minsum_layered && ldpcx::g_cns.load() && ldpcx::g_zpt.load() != 2 &&
+                     cns <= ldpcx::msg_stride(c) * (int64_t)ldpcx::msg_bytes(o->msg_prec);
+    *cn_state = use ? 1 : 0;
+    *bytes_per_cw = use ? cns : edge_bytes;
+    return LDPCX_OK;
+}
+
 extern "C" int ldpc_bp_ckpt_bytes(ldpcx_code_t c, int64_t B, const ldpcx_decode_opts *o, size_t *bytes) {
     if (!c || !bytes || B < 0) return LDPCX_E_INVAL;
     int st = ldpcx::check_differentiable(c, o);
