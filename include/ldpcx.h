@@ -235,12 +235,17 @@ int ldpc_bp_decode(ldpcx_code_t code, const float *llr_ch, int64_t B, const ldpc
  * sign bits instead of one stored message per edge (4, 8 or 16 bytes per check
  * node); every message is rebuilt exactly, so results are identical. Used when
  * the state fits the per-edge workspace. 0 = per-edge messages.
+ * LDPCX_TUNE_SCHEDULE: 1 (default) = with check-node state, a code whose row
+ * degrees are those of a full base graph of its shape (every code of
+ * qc_ldpc_build with rows_kept = 0) runs a kernel with that layer schedule
+ * compiled in; 0 = the kernel that reads the schedule from the row table.
  * Knobs change speed only, never results. */
 #define LDPCX_TUNE_L2_PREFETCH 1
 #define LDPCX_TUNE_ZPT 2
 #define LDPCX_TUNE_CW_PER_CTA 3
 #define LDPCX_TUNE_SPECIALISED 4
 #define LDPCX_TUNE_CN_STATE 5
+#define LDPCX_TUNE_SCHEDULE 6
 int ldpcx_tune_set(int key, int value);
 int ldpcx_tune_get(int key, int *value);
 

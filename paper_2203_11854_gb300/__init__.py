@@ -28,7 +28,7 @@ LAYERED_MINSUM, LAYERED_SPA, FLOOD_MINSUM, FLOOD_SPA = 0, 1, 2, 3
 MSG_F32, MSG_F16, MSG_FIX6 = 0, 1, 2
 DEMAP_EXACT, DEMAP_MAXLOG = 0, 1
 FLAG_NONFINITE, FLAG_TIMEOUT = 1, 2
-TUNE_L2_PREFETCH, TUNE_ZPT, TUNE_CW_PER_CTA, TUNE_SPECIALISED, TUNE_CN_STATE = 1, 2, 3, 4, 5
+TUNE_L2_PREFETCH, TUNE_ZPT, TUNE_CW_PER_CTA, TUNE_SPECIALISED, TUNE_CN_STATE, TUNE_SCHEDULE = 1, 2, 3, 4, 5, 6
 
 
 class LdpcxError(RuntimeError):

@@ -5,7 +5,7 @@
 
 #include <atomic>
 
-#include "decode_cns.cuh"
+#include "decode_cns_sched.cuh"
 
 namespace ldpcx {
 namespace {
@@ -16,6 +16,26 @@ __device__ unsigned int g_status;
 
 std::atomic<int> g_specialised{1};  // use compile-time-Z kernels when built
 std::atomic<int> g_cns{1};          // layered min-sum keeps check-node state instead of per-edge messages
+std::atomic<int> g_sched{1};        // ... with the full base graph's layer schedule compiled in
+
+// Row degrees of c equal those of the full base graph of shape bg.
+template <int BG> bool sched_matches(const ldpcx_code *c) {
+    using S = Sched<BG>;
+    if (c->rows != S::rows) return false;
+    for (int r = 0; r < c->rows; ++r) {
+        const int d = c->row_ptr[r + 1] - c->row_ptr[r];
+        const int want = r == 0 ? S::dc0 : r == 1 ? S::dc1 : r == 2 ? S::dc2 : r == 3 ? S::dc3
+                       : r < 4 + S::n_hi ? S::d_hi : S::d_lo;
+        if (d != want) return false;
+    }
+    return true;
+}
+
+int sched_shape(const ldpcx_code *c) {
+    if (c->params.bg_shape == 1 && sched_matches<1>(c)) return 1;
+    if (c->params.bg_shape == 2 && sched_matches<2>(c)) return 2;
+    return 0;
+}
 
 // Bytes of the check-node state of one codeword in format prec.
 int64_t cns_bytes(const ldpcx_code *c, int prec) {
@@ -179,7 +199,9 @@ int decode_impl(ldpcx_code_t c, const float *llr_ch, int64_t B, const ldpcx_deco
     size_t smem = smem_bytes(p, layered ? 1 : 2);
     if (layered && algo == kMinSum && zpt == 1 && g_cns.load() &&
         cns_bytes(c, o->msg_prec) <= p.msg_stride * p.msg_size) {
-        KernelFn f = layered_cns_kernel(c->max_deg, o->msg_prec, g_specialised.load() ? c->Z : 0);
+        const int zs = g_specialised.load() ? c->Z : 0;
+        const int bg = g_sched.load() ? sched_shape(c) : 0;
+        KernelFn f = bg ? layered_cns_sched_kernel(bg, o->msg_prec, zs) : layered_cns_kernel(c->max_deg, o->msg_prec, zs);
         if (f) {
             fn = f;
             smem = cns_smem_bytes(p);
@@ -280,6 +302,11 @@ extern "C" int ldpcx_tune_set(int key, int value) {
         g_cns.store(value);
         return LDPCX_OK;
     }
+    if (key == LDPCX_TUNE_SCHEDULE) {
+        if (value < 0 || value > 1) return LDPCX_E_INVAL;
+        g_sched.store(value);
+        return LDPCX_OK;
+    }
     return LDPCX_E_INVAL;
 }
 
@@ -303,6 +330,10 @@ extern "C" int ldpcx_tune_get(int key, int *value) {
     }
     if (key == LDPCX_TUNE_CN_STATE) {
         *value = g_cns.load();
+        return LDPCX_OK;
+    }
+    if (key == LDPCX_TUNE_SCHEDULE) {
+        *value = g_sched.load();
         return LDPCX_OK;
     }
     return LDPCX_E_INVAL;

@@ -26,7 +26,7 @@ namespace ldpcx {
 namespace dec {
 
 template <int PREC>
-__host__ __device__ inline int cns_slot_bytes(int d) {
+__host__ __device__ constexpr int cns_slot_bytes(int d) {
     if (PREC == kF32) return 16;
     if (PREC == kF16) return d <= 16 ? 8 : 16;
     return d <= 11 ? 4 : d <= 22 ? 8 : 16;
@@ -68,15 +68,24 @@ template <> struct CnsMag<kF16> {
     }
 };
 template <> struct CnsMag<kFix6> {
-    int q1, q2;  // magnitude codes 0..31 (steps of 0.5)
+    int q1, q2;      // magnitude codes 0..31 (steps of 0.5)
+    float r1, r2;    // their values
     __device__ __forceinline__ void set(float v1, float v2) {
         q1 = min(31, (int)rintf(v1 * 2.0f));
         q2 = min(31, (int)rintf(v2 * 2.0f));
+        values();
     }
-    // the 6-bit store holds a signed integer: no negative zero
+    __device__ __forceinline__ void values() {
+        r1 = (float)q1 * 0.5f;
+        r2 = (float)q2 * 0.5f;
+    }
+    // The 6-bit store holds a signed integer, so it has no negative zero; a
+    // zero message here may carry the sign bit. Both give the same sums: the
+    // APP and T values are never -0 (the channel load maps -0 to +0, and
+    // x - x = +0 under round-to-nearest), and for such x, x + (-0) = x - (-0) = x.
     __device__ __forceinline__ float msg(unsigned eq, unsigned neg) const {
-        const int q = eq ? q2 : q1;
-        return (float)(neg ? -q : q) * 0.5f;
+        const float m = eq ? r2 : r1;
+        return __uint_as_float(__float_as_uint(m) | (neg << 31));
     }
 };
 
@@ -129,6 +138,7 @@ __device__ __forceinline__ void cns_unpack(const uint4 &s, int d, CnsMag<PREC> &
             eq = s.y;
             neg = s.z;
         }
+        m.values();
     }
 }
 
@@ -147,12 +157,24 @@ __device__ __forceinline__ void cns_store(unsigned char *p, int bytes, const uin
     else __stcg(reinterpret_cast<unsigned *>(p), v.x);
 }
 
+// Byte offset in the APP array of the variable node of check node z in a
+// block with table entry at = {4 (col Z + shift), Z - shift}:
+// 4 (col Z + (z + shift) mod Z) = at.x + 4z - (z >= at.y ? 4Z : 0).
+__device__ __forceinline__ int vn_off(const int2 at, int z, int ZV) {
+    int off = at.x + 4 * z;
+    if (z >= at.y) off -= 4 * ZV;
+    return off;
+}
+__device__ __forceinline__ float &app_at(float *app, int off) {
+    return *reinterpret_cast<float *>(reinterpret_cast<char *>(app) + off);
+}
+
 // Layered min-sum update of check node z of one layer of degree d (D = d
 // exactly, or D = 0 with d <= DM at run time): rebuild the old messages from
 // the old state, T = APP - R_old, check-node rule, APP = T + R_new, store the
 // new state.
 template <int D, int DM, int PREC, int ZC>
-__device__ __forceinline__ void cns_update(const Params &p, int deg, float *app, const uint32_t *vb, int z,
+__device__ __forceinline__ void cns_update(const Params &p, int deg, float *app, const int2 *at, int z,
                                            const uint4 &s_old, unsigned char *slot, int sbytes, bool store) {
     const int ZV = ZC ? ZC : p.Z;
     constexpr int N = D ? D : DM;
@@ -166,9 +188,9 @@ __device__ __forceinline__ void cns_update(const Params &p, int deg, float *app,
     for (int j = 0; j < N; ++j) {
         T[j] = 0.0f;
         if (D || j < d) {
-            const int v = vn_at(vb[j], z, ZV);
+            const int v = vn_off(at[j], z, ZV);
             if constexpr (D != 0) vi[j] = v;
-            T[j] = __fsub_rn(app[v], mo.msg((eqo >> j) & 1u, (nego >> j) & 1u));
+            T[j] = __fsub_rn(app_at(app, v), mo.msg((eqo >> j) & 1u, (nego >> j) & 1u));
         }
     }
     FastMinSum<N> cn;
@@ -185,8 +207,8 @@ __device__ __forceinline__ void cns_update(const Params &p, int deg, float *app,
             neg |= n << j;
             int v;
             if constexpr (D != 0) v = vi[j];
-            else v = vn_at(vb[j], z, ZV);
-            app[v] = __fadd_rn(T[j], mn.msg(e, n));
+            else v = vn_off(at[j], z, ZV);
+            app_at(app, v) = __fadd_rn(T[j], mn.msg(e, n));
         }
     }
     if (store) cns_store(slot, sbytes, cns_pack<PREC>(mn, eq, neg, d));
@@ -195,7 +217,7 @@ __device__ __forceinline__ void cns_update(const Params &p, int deg, float *app,
 // One layer step: prefetch the state of layer r + 2 into s_far, update layer r
 // from s_cur, then a block barrier.
 template <int DMAX, int PREC, int ZC>
-__device__ __forceinline__ void cns_step(const Params &p, const uint32_t *s_vb, const int32_t *s_rp,
+__device__ __forceinline__ void cns_step(const Params &p, const int2 *s_at, const int32_t *s_rp,
                                          const int32_t *s_soff, float *app, unsigned char *st, int z, int t, int r,
                                          bool done, const uint4 &s_cur, uint4 &s_far) {
     const int ZV = ZC ? ZC : p.Z;
@@ -215,17 +237,17 @@ __device__ __forceinline__ void cns_step(const Params &p, const uint32_t *s_vb, 
         const bool store = t + 1 < p.iters;  // the last iteration's state is never read
         const int sb = cns_slot_bytes<PREC>(deg);
         unsigned char *slot = st + s_soff[r] + (size_t)z * sb;
-        const uint32_t *vb = s_vb + b0;
+        const int2 *at = s_at + b0;
         switch (deg) {
 #define LDPCX_CNS(dd) \
     case dd:          \
-        cns_update<dd, dd, PREC, ZC>(p, dd, app, vb, z, s_cur, slot, sb, store); \
+        cns_update<dd, dd, PREC, ZC>(p, dd, app, at, z, s_cur, slot, sb, store); \
         break;
             LDPCX_CNS(1) LDPCX_CNS(2) LDPCX_CNS(3) LDPCX_CNS(4)
             LDPCX_CNS(5) LDPCX_CNS(6) LDPCX_CNS(7) LDPCX_CNS(8)
 #undef LDPCX_CNS
             default:
-                cns_update<0, DMAX, PREC, ZC>(p, deg, app, vb, z, s_cur, slot, sb, store);
+                cns_update<0, DMAX, PREC, ZC>(p, deg, app, at, z, s_cur, slot, sb, store);
                 break;
         }
     }
@@ -242,7 +264,9 @@ __host__ __device__ inline int64_t cns_bytes_per_cw(const int32_t *row_ptr, int 
     return off;
 }
 
-__host__ __device__ inline size_t cns_smem_bytes(const Params &p) { return smem_bytes(p, 1) + sizeof(int32_t) * p.rows; }
+__host__ __device__ inline size_t cns_smem_bytes(const Params &p) {
+    return smem_bytes(p, 1) + sizeof(int32_t) * p.rows + sizeof(int2) * p.nnz + 8;
+}
 
 template <int DMAX, int PREC, int ZC = 0>
 __global__ void __launch_bounds__(kMaxThreads, 2) k_layered_cns(const Params p) {
@@ -253,6 +277,7 @@ __global__ void __launch_bounds__(kMaxThreads, 2) k_layered_cns(const Params p) 
     int32_t *s_rp = reinterpret_cast<int32_t *>(s_vb + p.nnz);
     int *s_flag = reinterpret_cast<int *>(s_rp + p.rows + 1);
     int32_t *s_soff = reinterpret_cast<int32_t *>(s_flag + 2 * p.G);
+    int2 *s_at = reinterpret_cast<int2 *>((reinterpret_cast<uintptr_t>(s_soff + p.rows) + 7) & ~(uintptr_t)7);
 
     load_tables(p, s_vb, s_rp);
     const int64_t cw_base = (int64_t)blockIdx.x * p.G;
@@ -264,6 +289,11 @@ __global__ void __launch_bounds__(kMaxThreads, 2) k_layered_cns(const Params p) 
             s_soff[r] = off;
             off += (cns_slot_bytes<PREC>(s_rp[r + 1] - s_rp[r]) * ZV + 15) / 16 * 16;
         }
+    }
+    for (int i = threadIdx.x; i < p.nnz; i += blockDim.x) {
+        const uint32_t vb = s_vb[i];
+        const int sh = (int)(vb & 0xFFFFu);
+        s_at[i] = make_int2(4 * ((int)(vb >> 16) + sh), ZV - sh);
     }
     const int g = threadIdx.x / ZV, z = threadIdx.x - g * ZV;
     const int64_t cw = cw_base + g;
@@ -292,11 +322,11 @@ __global__ void __launch_bounds__(kMaxThreads, 2) k_layered_cns(const Params p) 
         return __syncthreads_and(done);
     };
     while (t < p.iters) {
-        cns_step<DMAX, PREC, ZC>(p, s_vb, s_rp, s_soff, app, st, z, t, r, done, sa, sc);
+        cns_step<DMAX, PREC, ZC>(p, s_at, s_rp, s_soff, app, st, z, t, r, done, sa, sc);
         if (advance() || t >= p.iters) break;
-        cns_step<DMAX, PREC, ZC>(p, s_vb, s_rp, s_soff, app, st, z, t, r, done, sb, sa);
+        cns_step<DMAX, PREC, ZC>(p, s_at, s_rp, s_soff, app, st, z, t, r, done, sb, sa);
         if (advance() || t >= p.iters) break;
-        cns_step<DMAX, PREC, ZC>(p, s_vb, s_rp, s_soff, app, st, z, t, r, done, sc, sb);
+        cns_step<DMAX, PREC, ZC>(p, s_at, s_rp, s_soff, app, st, z, t, r, done, sc, sb);
         if (advance()) break;
     }
     __syncthreads();

@@ -1,0 +1,181 @@
+// Layered min-sum with check-node state on the full 5G-shaped base graphs,
+// with the layer schedule compiled in.
+//
+// The row degrees of a full base graph depend on its shape alone (the seed
+// moves blocks within a row, never changes how many there are): four core
+// rows of the systematic degree plus 2, 3, 2, 2 dual-diagonal blocks, then
+// extension rows in two runs of equal degree. So one iteration is four steps
+// of exact degree followed by two loops of fixed degree, and no step looks up
+// a row table or dispatches on a degree. Slot offsets and table offsets
+// advance by constants. Everything else -- the update, the state format, the
+// prefetch of the state two layers ahead and the early stop -- is that of
+// k_layered_cns, so results are the same bit for bit.
+#pragma once
+
+#include "decode_cns.cuh"
+
+namespace ldpcx {
+namespace dec {
+
+template <int BG> struct Sched;
+template <> struct Sched<1> {
+    static constexpr int rows = 46, dc0 = 18, dc1 = 19, dc2 = 18, dc3 = 18, n_hi = 33, d_hi = 6, d_lo = 5;
+};
+template <> struct Sched<2> {
+    static constexpr int rows = 42, dc0 = 10, dc1 = 11, dc2 = 10, dc3 = 10, n_hi = 4, d_hi = 5, d_lo = 4;
+};
+
+template <int BG, int PREC> struct SchedLayout {
+    using S = Sched<BG>;
+    static constexpr int sb_core = cns_slot_bytes<PREC>(S::dc1);  // slot bytes of the core rows
+    static constexpr int sb_ext = cns_slot_bytes<PREC>(S::d_hi);  // and of the extension rows
+    static constexpr int b_hi = S::dc0 + S::dc1 + S::dc2 + S::dc3;  // first block of the extension rows
+    static constexpr int b_lo = b_hi + S::n_hi * S::d_hi;
+    static_assert(cns_slot_bytes<PREC>(S::dc0) == sb_core && cns_slot_bytes<PREC>(S::dc2) == sb_core &&
+                      cns_slot_bytes<PREC>(S::dc3) == sb_core && cns_slot_bytes<PREC>(S::d_lo) == sb_ext,
+                  "one slot size per run of rows");
+};
+
+// The three registers of the state ring by step phase.
+template <int K> __device__ __forceinline__ uint4 &ring(uint4 &a, uint4 &b, uint4 &c) {
+    if constexpr (K % 3 == 0) return a;
+    else if constexpr (K % 3 == 1) return b;
+    else return c;
+}
+
+// Geometry of one codeword's state: region bytes of a core and of an extension row.
+struct SchedGeo {
+    int Lc, Le;
+    __device__ __forceinline__ int off(int r) const { return r < 4 ? r * Lc : 4 * Lc + (r - 4) * Le; }
+};
+
+// One layer step of degree D on row r (blocks from b0, slots from off):
+// prefetch the state of layer r + 2 into s_far, update from s_cur, barrier.
+template <int D, int BG, int PREC, int ZC>
+__device__ __forceinline__ void sched_step(const Params &p, const int2 *s_at, float *app, unsigned char *st, int z,
+                                           int t, int r, int b0, int off, const SchedGeo &geo, bool done,
+                                           const uint4 &s_cur, uint4 &s_far) {
+    using S = Sched<BG>;
+    using L = SchedLayout<BG, PREC>;
+    int r2 = r + 2, t2 = t;
+    if (r2 >= S::rows) {
+        r2 -= S::rows;
+        ++t2;
+    }
+    if (t2 == 0) {
+        s_far = make_uint4(0u, 0u, 0u, 0u);  // iteration 0 starts from zero messages
+    } else if (!done && t2 < p.iters) {
+        if (r2 < 4) s_far = cns_load(st + geo.off(r2) + z * L::sb_core, L::sb_core);
+        else s_far = cns_load(st + geo.off(r2) + z * L::sb_ext, L::sb_ext);
+    }
+    if (!done) {
+        constexpr int SB = cns_slot_bytes<PREC>(D);
+        cns_update<D, D, PREC, ZC>(p, D, app, s_at + b0, z, s_cur, st + off + z * SB, SB, t + 1 < p.iters);
+    }
+    __syncthreads();
+}
+
+// COUNT consecutive rows of degree D from row r0, the first at ring phase PH.
+template <int D, int COUNT, int PH, int BG, int PREC, int ZC>
+__device__ __forceinline__ void sched_run(const Params &p, const int2 *s_at, float *app, unsigned char *st, int z,
+                                          int t, int r0, int b0, int off0, int Lrow, const SchedGeo &geo, bool done,
+                                          uint4 &a, uint4 &b, uint4 &c) {
+    int r = r0, bb = b0, off = off0;
+#pragma unroll 1
+    for (int i = 0; i < COUNT / 3; ++i) {
+        sched_step<D, BG, PREC, ZC>(p, s_at, app, st, z, t, r, bb, off, geo, done, ring<PH>(a, b, c),
+                                    ring<PH + 2>(a, b, c));
+        sched_step<D, BG, PREC, ZC>(p, s_at, app, st, z, t, r + 1, bb + D, off + Lrow, geo, done,
+                                    ring<PH + 1>(a, b, c), ring<PH + 3>(a, b, c));
+        sched_step<D, BG, PREC, ZC>(p, s_at, app, st, z, t, r + 2, bb + 2 * D, off + 2 * Lrow, geo, done,
+                                    ring<PH + 2>(a, b, c), ring<PH + 4>(a, b, c));
+        r += 3;
+        bb += 3 * D;
+        off += 3 * Lrow;
+    }
+    if constexpr (COUNT % 3 >= 1)
+        sched_step<D, BG, PREC, ZC>(p, s_at, app, st, z, t, r, bb, off, geo, done, ring<PH>(a, b, c),
+                                    ring<PH + 2>(a, b, c));
+    if constexpr (COUNT % 3 == 2)
+        sched_step<D, BG, PREC, ZC>(p, s_at, app, st, z, t, r + 1, bb + D, off + Lrow, geo, done,
+                                    ring<PH + 1>(a, b, c), ring<PH + 3>(a, b, c));
+}
+
+template <int BG, int PREC, int ZC = 0>
+__global__ void __launch_bounds__(kMaxThreads, 2) k_layered_cns_sched(const Params p) {
+    using S = Sched<BG>;
+    using L = SchedLayout<BG, PREC>;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int ZV = ZC ? ZC : p.Z;
+    float *s_app_all = reinterpret_cast<float *>(smem);
+    uint32_t *s_vb = reinterpret_cast<uint32_t *>(s_app_all + (size_t)p.G * p.n);
+    int32_t *s_rp = reinterpret_cast<int32_t *>(s_vb + p.nnz);
+    int *s_flag = reinterpret_cast<int *>(s_rp + p.rows + 1);
+    int2 *s_at = reinterpret_cast<int2 *>((reinterpret_cast<uintptr_t>(s_flag + 2 * p.G) + 7) & ~(uintptr_t)7);
+
+    load_tables(p, s_vb, s_rp);
+    const int64_t cw_base = (int64_t)blockIdx.x * p.G;
+    load_channel(p, s_app_all, cw_base);
+    __syncthreads();
+    for (int i = threadIdx.x; i < p.nnz; i += blockDim.x) {
+        const uint32_t vb = s_vb[i];
+        const int sh = (int)(vb & 0xFFFFu);
+        s_at[i] = make_int2(4 * ((int)(vb >> 16) + sh), ZV - sh);
+    }
+    const int g = threadIdx.x / ZV, z = threadIdx.x - g * ZV;
+    const int64_t cw = cw_base + g;
+    const bool active = g < p.G && cw < p.B;
+    float *app = s_app_all + (size_t)(active ? g : 0) * p.n;
+    unsigned char *st = reinterpret_cast<unsigned char *>(p.msg) + (active ? cw : 0) * p.msg_stride * p.msg_size;
+    bool done = !active;
+    int iters_run = 0;
+    SchedGeo geo;
+    geo.Lc = (L::sb_core * ZV + 15) / 16 * 16;
+    geo.Le = (L::sb_ext * ZV + 15) / 16 * 16;
+    __syncthreads();
+
+    uint4 a = make_uint4(0u, 0u, 0u, 0u), b = a, c = a;
+    for (int t = 0; t < p.iters; ++t) {
+        sched_run<S::dc0, 1, 0, BG, PREC, ZC>(p, s_at, app, st, z, t, 0, 0, 0, geo.Lc, geo, done, a, b, c);
+        sched_run<S::dc1, 1, 1, BG, PREC, ZC>(p, s_at, app, st, z, t, 1, S::dc0, geo.Lc, geo.Lc, geo, done, a, b,
+                                              c);
+        sched_run<S::dc2, 1, 2, BG, PREC, ZC>(p, s_at, app, st, z, t, 2, S::dc0 + S::dc1, 2 * geo.Lc, geo.Lc, geo,
+                                              done, a, b, c);
+        sched_run<S::dc3, 1, 3, BG, PREC, ZC>(p, s_at, app, st, z, t, 3, S::dc0 + S::dc1 + S::dc2, 3 * geo.Lc,
+                                              geo.Lc, geo, done, a, b, c);
+        sched_run<S::d_hi, S::n_hi, 4, BG, PREC, ZC>(p, s_at, app, st, z, t, 4, L::b_hi, 4 * geo.Lc, geo.Le, geo,
+                                                     done, a, b, c);
+        sched_run<S::d_lo, S::rows - 4 - S::n_hi, 4 + S::n_hi, BG, PREC, ZC>(
+            p, s_at, app, st, z, t, 4 + S::n_hi, L::b_lo, 4 * geo.Lc + S::n_hi * geo.Le, geo.Le, geo, done, a, b, c);
+        // the next iteration's first step finds its state at phase rows mod 3
+        if constexpr (S::rows % 3 == 1) {
+            const uint4 x = a;
+            a = b;
+            b = c;
+            c = x;
+        } else if constexpr (S::rows % 3 == 2) {
+            const uint4 x = c;
+            c = b;
+            b = a;
+            a = x;
+        }
+        if (!done) iters_run = t + 1;
+        if (p.early_stop) {
+            if (threadIdx.x < p.G) s_flag[threadIdx.x] = 0;
+            __syncthreads();
+            if (!done && syndrome_bad_vec<1, ZC>(p, s_vb, s_rp, app, z)) s_flag[g] = 1;
+            __syncthreads();
+            if (!done && s_flag[g] == 0) done = true;
+            if (__syncthreads_and(done)) break;
+        }
+    }
+    __syncthreads();
+    write_outputs(p, s_app_all, cw_base, iters_run, g, active, z);
+}
+
+// Kernel for a code whose row degrees follow the full base graph of shape bg
+// (1 or 2), or nullptr.
+KernelFn layered_cns_sched_kernel(int bg, int prec, int Z);
+
+}  // namespace dec
+}  // namespace ldpcx

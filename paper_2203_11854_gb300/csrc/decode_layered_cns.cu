@@ -1,6 +1,7 @@
 // Layered min-sum kernels with check-node state (decode_cns.cuh), generic and
-// specialised for Z = 384, for FP32, FP16 and 6-bit message formats.
-#include "decode_cns.cuh"
+// specialised for Z = 384, for FP32, FP16 and 6-bit message formats, and the
+// lookup of the compiled-schedule variants (decode_cns_sched_*.cu).
+#include "decode_cns_sched.cuh"
 
 namespace ldpcx {
 namespace dec {
@@ -9,6 +10,16 @@ template <int PREC>
 KernelFn cns_for(int dmax, int Z) {
     if (Z == 384) return dmax <= 12 ? k_layered_cns<12, PREC, 384> : k_layered_cns<20, PREC, 384>;
     return dmax <= 12 ? k_layered_cns<12, PREC, 0> : k_layered_cns<20, PREC, 0>;
+}
+
+KernelFn cns_sched_f32(int bg, int Z);
+KernelFn cns_sched_f16(int bg, int Z);
+KernelFn cns_sched_fix6(int bg, int Z);
+
+KernelFn layered_cns_sched_kernel(int bg, int prec, int Z) {
+    if (prec == kF32) return cns_sched_f32(bg, Z);
+    if (prec == kF16) return cns_sched_f16(bg, Z);
+    return cns_sched_fix6(bg, Z);
 }
 
 KernelFn layered_cns_kernel(int dmax, int prec, int Z) {
