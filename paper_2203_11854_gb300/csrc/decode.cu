@@ -201,7 +201,23 @@ int decode_impl(ldpcx_code_t c, const float *llr_ch, int64_t B, const ldpcx_deco
         cns_bytes(c, o->msg_prec) <= p.msg_stride * p.msg_size) {
         const int zs = g_specialised.load() ? c->Z : 0;
         const int bg = g_sched.load() ? sched_shape(c) : 0;
-        KernelFn f = bg ? layered_cns_sched_kernel(bg, o->msg_prec, zs) : layered_cns_kernel(c->max_deg, o->msg_prec, zs);
+        SchedFn sf = bg && c->nnz <= kSchedMaxBlocks ? layered_cns_sched_kernel(bg, o->msg_prec, zs) : nullptr;
+        if (sf) {
+            SchedTab tab;
+            for (int i = 0; i < c->nnz; ++i) {
+                const int col = (int)(c->blk[(size_t)i] >> 16), sh = (int)(c->blk[(size_t)i] & 0xFFFFu);
+                tab.at[i] = make_int2(4 * (col * c->Z + sh), c->Z - sh);
+            }
+            smem = smem_bytes(p, 1);
+            if (smem > 227 * 1024) return LDPCX_E_UNSUPPORTED;
+            if (cudaFuncSetAttribute(sf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+                return LDPCX_E_CUDA;
+            const int64_t grid = (B + p.G - 1) / p.G;
+            if (grid > 0x7FFFFFFF) return LDPCX_E_INVAL;
+            sf<<<(unsigned)grid, (p.G * p.Z + 31) / 32 * 32, smem, (cudaStream_t)stream>>>(p, tab);
+            return cuda_status(cudaGetLastError());
+        }
+        KernelFn f = layered_cns_kernel(c->max_deg, o->msg_prec, zs);
         if (f) {
             fn = f;
             smem = cns_smem_bytes(p);

@@ -36,6 +36,14 @@ template <int BG, int PREC> struct SchedLayout {
                   "one slot size per run of rows");
 };
 
+// Block table of the schedule, passed by value as a kernel parameter so that
+// every lookup is a warp-uniform constant-bank read: entry b = {4 (col Z +
+// shift), Z - shift} of block b in row-major order.
+constexpr int kSchedMaxBlocks = 316;
+struct SchedTab {
+    int2 at[kSchedMaxBlocks];
+};
+
 // The three registers of the state ring by step phase.
 template <int K> __device__ __forceinline__ uint4 &ring(uint4 &a, uint4 &b, uint4 &c) {
     if constexpr (K % 3 == 0) return a;
@@ -102,7 +110,7 @@ __device__ __forceinline__ void sched_run(const Params &p, const int2 *s_at, flo
 }
 
 template <int BG, int PREC, int ZC = 0>
-__global__ void __launch_bounds__(kMaxThreads, 2) k_layered_cns_sched(const Params p) {
+__global__ void __launch_bounds__(kMaxThreads, 2) k_layered_cns_sched(const Params p, const __grid_constant__ SchedTab tab) {
     using S = Sched<BG>;
     using L = SchedLayout<BG, PREC>;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -111,17 +119,11 @@ __global__ void __launch_bounds__(kMaxThreads, 2) k_layered_cns_sched(const Para
     uint32_t *s_vb = reinterpret_cast<uint32_t *>(s_app_all + (size_t)p.G * p.n);
     int32_t *s_rp = reinterpret_cast<int32_t *>(s_vb + p.nnz);
     int *s_flag = reinterpret_cast<int *>(s_rp + p.rows + 1);
-    int2 *s_at = reinterpret_cast<int2 *>((reinterpret_cast<uintptr_t>(s_flag + 2 * p.G) + 7) & ~(uintptr_t)7);
+    const int2 *s_at = tab.at;
 
-    load_tables(p, s_vb, s_rp);
+    load_tables(p, s_vb, s_rp);  // for the syndrome check
     const int64_t cw_base = (int64_t)blockIdx.x * p.G;
     load_channel(p, s_app_all, cw_base);
-    __syncthreads();
-    for (int i = threadIdx.x; i < p.nnz; i += blockDim.x) {
-        const uint32_t vb = s_vb[i];
-        const int sh = (int)(vb & 0xFFFFu);
-        s_at[i] = make_int2(4 * ((int)(vb >> 16) + sh), ZV - sh);
-    }
     const int g = threadIdx.x / ZV, z = threadIdx.x - g * ZV;
     const int64_t cw = cw_base + g;
     const bool active = g < p.G && cw < p.B;
@@ -173,9 +175,11 @@ __global__ void __launch_bounds__(kMaxThreads, 2) k_layered_cns_sched(const Para
     write_outputs(p, s_app_all, cw_base, iters_run, g, active, z);
 }
 
+using SchedFn = void (*)(Params, SchedTab);
+
 // Kernel for a code whose row degrees follow the full base graph of shape bg
 // (1 or 2), or nullptr.
-KernelFn layered_cns_sched_kernel(int bg, int prec, int Z);
+SchedFn layered_cns_sched_kernel(int bg, int prec, int Z);
 
 }  // namespace dec
 }  // namespace ldpcx

@@ -6,7 +6,7 @@
 namespace ldpcx {
 namespace dec {
 
-KernelFn cns_sched_f16(int bg, int Z) {
+SchedFn cns_sched_f16(int bg, int Z) {
     if (bg == 1) return Z == 384 ? k_layered_cns_sched<1, kF16, 384> : k_layered_cns_sched<1, kF16, 0>;
     if (bg == 2) return Z == 384 ? k_layered_cns_sched<2, kF16, 384> : k_layered_cns_sched<2, kF16, 0>;
     return nullptr;

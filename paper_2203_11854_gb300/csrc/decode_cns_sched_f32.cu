@@ -6,7 +6,7 @@
 namespace ldpcx {
 namespace dec {
 
-KernelFn cns_sched_f32(int bg, int Z) {
+SchedFn cns_sched_f32(int bg, int Z) {
     if (bg == 1) return Z == 384 ? k_layered_cns_sched<1, kF32, 384> : k_layered_cns_sched<1, kF32, 0>;
     if (bg == 2) return Z == 384 ? k_layered_cns_sched<2, kF32, 384> : k_layered_cns_sched<2, kF32, 0>;
     return nullptr;

@@ -172,6 +172,13 @@ template <int DMAX> struct CheckNode<DMAX, kMinSum> {
     }
 };
 
+// min(|a|, |b|) with the sign bit sign(a) XOR sign(b) (inputs are never NaN).
+__device__ __forceinline__ float min_xorsign_abs(float a, float b) {
+    float d;
+    asm("min.xorsign.abs.f32 %0, %1, %2;" : "=f"(d) : "f"(a), "f"(b));
+    return d;
+}
+
 // Layered min-sum check node. The layered APP never holds -0.0 (the channel
 // load maps -0.0 to +0.0, and T = APP - R, APP = T + R cannot create it), so the
 // IEEE sign bit of T equals (T < 0) and the sign product is an XOR of sign bits.
@@ -182,17 +189,18 @@ template <int N> struct FastMinSum {
     float m1;      // smallest |T|
     unsigned sx;   // XOR of the sign bits of T
     __device__ __forceinline__ void prepare(const float (&T)[N], int deg, float offset, float clamp) {
-        float a1 = INFINITY, a2 = INFINITY;
-        sx = 0;
+        // acc: magnitude = smallest |T| so far, sign bit = XOR of the sign bits
+        // so far (min.xorsign.abs does both in one instruction)
+        float acc = INFINITY, a2 = INFINITY;
 #pragma unroll
         for (int j = 0; j < N; ++j) {
             if (j < deg) {
-                const float a = fabsf(T[j]);
-                a2 = fminf(a2, fmaxf(a1, a));
-                a1 = fminf(a1, a);
-                sx ^= __float_as_uint(T[j]);
+                a2 = fminf(a2, fmaxf(fabsf(acc), fabsf(T[j])));
+                acc = min_xorsign_abs(acc, T[j]);
             }
         }
+        const float a1 = fabsf(acc);
+        sx = __float_as_uint(acc);
         m1 = a1;
         v1 = fminf(fmaxf(__fsub_rn(a1, offset), 0.0f), clamp);
         v2 = fminf(fmaxf(__fsub_rn(a2, offset), 0.0f), clamp);

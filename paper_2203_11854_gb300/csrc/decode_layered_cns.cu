@@ -12,11 +12,11 @@ KernelFn cns_for(int dmax, int Z) {
     return dmax <= 12 ? k_layered_cns<12, PREC, 0> : k_layered_cns<20, PREC, 0>;
 }
 
-KernelFn cns_sched_f32(int bg, int Z);
-KernelFn cns_sched_f16(int bg, int Z);
-KernelFn cns_sched_fix6(int bg, int Z);
+SchedFn cns_sched_f32(int bg, int Z);
+SchedFn cns_sched_f16(int bg, int Z);
+SchedFn cns_sched_fix6(int bg, int Z);
 
-KernelFn layered_cns_sched_kernel(int bg, int prec, int Z) {
+SchedFn layered_cns_sched_kernel(int bg, int prec, int Z) {
     if (prec == kF32) return cns_sched_f32(bg, Z);
     if (prec == kF16) return cns_sched_f16(bg, Z);
     return cns_sched_fix6(bg, Z);
