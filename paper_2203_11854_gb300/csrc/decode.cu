@@ -195,6 +195,7 @@ int decode_impl(ldpcx_code_t c, const float *llr_ch, int64_t B, const ldpcx_deco
     p.msg_size = (int)msg_bytes(o->msg_prec);
     p.status = status_word_decode();
     if (!p.status) return LDPCX_E_CUDA;
+    set_int_constants(p);
 
     size_t smem = smem_bytes(p, layered ? 1 : 2);
     if (layered && algo == kMinSum && zpt == 1 && g_cns.load() &&

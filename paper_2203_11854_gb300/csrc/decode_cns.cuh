@@ -159,11 +159,14 @@ __device__ __forceinline__ void cns_store(unsigned char *p, int bytes, const uin
 
 // Byte offset in the APP array of the variable node of check node z in a
 // block with table entry at = {4 (col Z + shift), Z - shift}:
-// 4 (col Z + (z + shift) mod Z) = at.x + 4z - (z >= at.y ? 4Z : 0).
-__device__ __forceinline__ int vn_off(const int2 at, int z, int ZV) {
-    int off = at.x + 4 * z;
-    if (z >= at.y) off -= 4 * ZV;
-    return off;
+// 4 (col Z + (z + shift) mod Z) = at.x + 4z - (z >= at.y ? 4Z : 0), computed
+// on the FMA pipe: f = (z + 1024 - at.y) >> 10 is 1 exactly when z >= at.y
+// (both lie in [0, Z], Z <= 384), taken as the high word of a product with
+// 2^22; then off = 4z + at.x - 4Z f.
+__device__ __forceinline__ int vn_off_fma(const Params &p, const int2 at, int z) {
+    const unsigned x = (unsigned)z * p.k_one + (unsigned)(1024 - at.y);
+    const unsigned f = __umulhi(x, p.k_two22);
+    return (int)((unsigned)z * p.k_four + (unsigned)at.x + f * p.k_neg4z);
 }
 __device__ __forceinline__ float &app_at(float *app, int off) {
     return *reinterpret_cast<float *>(reinterpret_cast<char *>(app) + off);
@@ -173,10 +176,17 @@ __device__ __forceinline__ float &app_at(float *app, int off) {
 // exactly, or D = 0 with d <= DM at run time): rebuild the old messages from
 // the old state, T = APP - R_old, check-node rule, APP = T + R_new, store the
 // new state.
+//
+// Integer work is balanced between the ALU and FMA pipes: the APP offset by
+// vn_off_fma; in the second pass the sign of the new message is bit 31 of U =
+// bits(T) + (sign bit of the product), an addition modulo 2^32 that flips
+// exactly bit 31; n = U >> 31 as a high-word product with 2; the message bits
+// are n 2^31 + bits(magnitude); the neg mask is built by Horner's rule over the
+// edges in descending order (the updates of one row touch distinct APP
+// entries, so their order changes no result).
 template <int D, int DM, int PREC, int ZC>
 __device__ __forceinline__ void cns_update(const Params &p, int deg, float *app, const int2 *at, int z,
                                            const uint4 &s_old, unsigned char *slot, int sbytes, bool store) {
-    const int ZV = ZC ? ZC : p.Z;
     constexpr int N = D ? D : DM;
     const int d = D ? D : deg;
     CnsMag<PREC> mo;
@@ -188,7 +198,7 @@ __device__ __forceinline__ void cns_update(const Params &p, int deg, float *app,
     for (int j = 0; j < N; ++j) {
         T[j] = 0.0f;
         if (D || j < d) {
-            const int v = vn_off(at[j], z, ZV);
+            const int v = vn_off_fma(p, at[j], z);
             if constexpr (D != 0) vi[j] = v;
             T[j] = __fsub_rn(app_at(app, v), mo.msg((eqo >> j) & 1u, (nego >> j) & 1u));
         }
@@ -198,17 +208,20 @@ __device__ __forceinline__ void cns_update(const Params &p, int deg, float *app,
     CnsMag<PREC> mn;
     mn.set(cn.v1, cn.v2);
     unsigned eq = 0, neg = 0;
+    const unsigned sxs = cn.sx & 0x80000000u;
+    const unsigned b1 = __float_as_uint(mn.r1), b2 = __float_as_uint(mn.r2);
 #pragma unroll
-    for (int j = 0; j < N; ++j) {
+    for (int j = N - 1; j >= 0; --j) {
         if (D || j < d) {
-            const unsigned e = fabsf(T[j]) == cn.m1 ? 1u : 0u;
-            const unsigned n = (cn.sx ^ __float_as_uint(T[j])) >> 31;
-            eq |= e << j;
-            neg |= n << j;
+            const bool e = fabsf(T[j]) == cn.m1;
+            const unsigned U = __float_as_uint(T[j]) * p.k_one + sxs;
+            const unsigned n = __umulhi(U, p.k_two);
+            neg = neg * p.k_two + n;
+            if (e) eq |= 1u << j;
             int v;
             if constexpr (D != 0) v = vi[j];
-            else v = vn_off(at[j], z, ZV);
-            app_at(app, v) = __fadd_rn(T[j], mn.msg(e, n));
+            else v = vn_off_fma(p, at[j], z);
+            app_at(app, v) = __fadd_rn(T[j], __uint_as_float(n * p.k_two31 + (e ? b2 : b1)));
         }
     }
     if (store) cns_store(slot, sbytes, cns_pack<PREC>(mn, eq, neg, d));

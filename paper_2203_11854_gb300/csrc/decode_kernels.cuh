@@ -95,7 +95,21 @@ struct Params {
     int pf_dist;                  // L2 prefetch distance in layers (0 = off)
     int msg_size;                 // bytes per message
     unsigned int *status;         // device status word (LDPCX_FLAG_*)
+    // Integer constants read from the parameter space, so that products with
+    // them stay integer multiply-adds (FMA pipe) instead of being turned into
+    // shifts and logic ops on the ALU pipe, which bounds the layered min-sum
+    // kernels. one = 1, two = 2, four = 4, two22 = 2^22, two31 = 2^31, neg4z = -4Z.
+    unsigned k_one, k_two, k_four, k_two22, k_two31, k_neg4z;
 };
+
+inline void set_int_constants(Params &p) {
+    p.k_one = 1u;
+    p.k_two = 2u;
+    p.k_four = 4u;
+    p.k_two22 = 1u << 22;
+    p.k_two31 = 1u << 31;
+    p.k_neg4z = (unsigned)(-4 * p.Z);
+}
 
 // Shared memory: app[G][n] (and a second APP array for flooding), blk[nnz],
 // row_ptr[rows+1], flag[G], done[G].
