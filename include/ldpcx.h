@@ -222,8 +222,9 @@ int ldpc_bp_decode(ldpcx_code_t code, const float *llr_ch, int64_t B, const ldpc
 /* Decoder tuning knobs (process-wide; read at each launch; the autotuner's
  * search space). LDPCX_TUNE_L2_PREFETCH: layered decoders prefetch into L2 the
  * message span of the layer this many layers ahead (0 = off, 0..16, default 0).
- * LDPCX_TUNE_ZPT: check nodes per thread of the layered kernels (0 = auto = 1;
- * 2 is honoured only when Z is even and the library was built with it).
+ * LDPCX_TUNE_ZPT: check nodes per thread of the layered min-sum kernels with
+ * a compiled-in schedule (LDPCX_TUNE_SCHEDULE): 0 = auto = 1; 2 = check nodes
+ * z and z + Z/2, honoured when Z is even. Other kernels use one.
  * LDPCX_TUNE_CW_PER_CTA: codewords decoded together by one CTA of
  * ldpc_bp_decode (0 = automatic: about 384 check nodes per CTA within the
  * shared-memory budget; a smaller value gives smaller CTAs, more per SM).

@@ -202,7 +202,8 @@ int decode_impl(ldpcx_code_t c, const float *llr_ch, int64_t B, const ldpcx_deco
         cns_bytes(c, o->msg_prec) <= p.msg_stride * p.msg_size) {
         const int zs = g_specialised.load() ? c->Z : 0;
         const int bg = g_sched.load() ? sched_shape(c) : 0;
-        SchedFn sf = bg && c->nnz <= kSchedMaxBlocks ? layered_cns_sched_kernel(bg, o->msg_prec, zs) : nullptr;
+        const int kpt = g_zpt.load() == 2 && c->Z % 2 == 0 ? 2 : 1;  // check nodes per thread
+        SchedFn sf = bg && c->nnz <= kSchedMaxBlocks ? layered_cns_sched_kernel(bg, o->msg_prec, zs, kpt) : nullptr;
         if (sf) {
             SchedTab tab;
             for (int i = 0; i < c->nnz; ++i) {
@@ -215,7 +216,7 @@ int decode_impl(ldpcx_code_t c, const float *llr_ch, int64_t B, const ldpcx_deco
                 return LDPCX_E_CUDA;
             const int64_t grid = (B + p.G - 1) / p.G;
             if (grid > 0x7FFFFFFF) return LDPCX_E_INVAL;
-            sf<<<(unsigned)grid, (p.G * p.Z + 31) / 32 * 32, smem, (cudaStream_t)stream>>>(p, tab);
+            sf<<<(unsigned)grid, (p.G * (p.Z / kpt) + 31) / 32 * 32, smem, (cudaStream_t)stream>>>(p, tab);
             return cuda_status(cudaGetLastError());
         }
         KernelFn f = layered_cns_kernel(c->max_deg, o->msg_prec, zs);
@@ -266,7 +267,7 @@ extern "C" int ldpc_bp_msg_format(ldpcx_code_t c, const ldpcx_decode_opts *o, in
     const bool minsum_layered = o->algo == LDPCX_LAYERED_MINSUM;
     const int64_t edge_bytes = (int64_t)c->nnz * c->Z * (int64_t)ldpcx::msg_bytes(o->msg_prec);
     const int64_t cns = ldpcx::cns_bytes(c, o->msg_prec);
-    const bool use = minsum_layered && ldpcx::g_cns.load() && ldpcx::g_zpt.load() != 2 &&
+    const bool use = minsum_layered && ldpcx::g_cns.load() &&
                      cns <= ldpcx::msg_stride(c) * (int64_t)ldpcx::msg_bytes(o->msg_prec);
     *cn_state = use ? 1 : 0;
     *bytes_per_cw = use ? cns : edge_bytes;

@@ -10,6 +10,12 @@
 // advance by constants. Everything else -- the update, the state format, the
 // prefetch of the state two layers ahead and the early stop -- is that of
 // k_layered_cns, so results are the same bit for bit.
+//
+// A thread may own K = 2 check nodes of each row, z and z + Z/2 (Z even): the
+// K updates are interleaved pass by pass (all APP loads, all check-node rules,
+// all APP stores), so one warp carries two independent dependency chains and
+// the per-row work (schedule, barrier, table reads) is shared. Each access of
+// a warp still covers 32 consecutive APP entries, free of bank conflicts.
 #pragma once
 
 #include "decode_cns.cuh"
@@ -44,10 +50,11 @@ struct SchedTab {
     int2 at[kSchedMaxBlocks];
 };
 
-// The three registers of the state ring by step phase.
-template <int K> __device__ __forceinline__ uint4 &ring(uint4 &a, uint4 &b, uint4 &c) {
-    if constexpr (K % 3 == 0) return a;
-    else if constexpr (K % 3 == 1) return b;
+// The three state registers of the ring by step phase (K slots each).
+template <int Ph, int K>
+__device__ __forceinline__ uint4 (&ring(uint4 (&a)[K], uint4 (&b)[K], uint4 (&c)[K]))[K] {
+    if constexpr (Ph % 3 == 0) return a;
+    else if constexpr (Ph % 3 == 1) return b;
     else return c;
 }
 
@@ -57,12 +64,64 @@ struct SchedGeo {
     __device__ __forceinline__ int off(int r) const { return r < 4 ? r * Lc : 4 * Lc + (r - 4) * Le; }
 };
 
+// Layered min-sum update of the K check nodes zk[0..K) of a row of exact
+// degree D (the rule of cns_update, pass by pass over the K nodes).
+template <int D, int PREC, int K>
+__device__ __forceinline__ void cns_update_k(const Params &p, float *app, const int2 *at, const int (&zk)[K],
+                                             const uint4 (&s_old)[K], unsigned char *row, bool store) {
+    constexpr int SB = cns_slot_bytes<PREC>(D);
+    CnsMag<PREC> mo[K];
+    unsigned eqo[K], nego[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) cns_unpack<PREC>(s_old[k], D, mo[k], eqo[k], nego[k]);
+    float T[K][D];
+    int vi[K][D];
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+        const int2 a = at[j];
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            vi[k][j] = vn_off_fma(p, a, zk[k]);
+            T[k][j] = __fsub_rn(app_at(app, vi[k][j]), mo[k].msg((eqo[k] >> j) & 1u, (nego[k] >> j) & 1u));
+        }
+    }
+    FastMinSum<D> cn[K];
+    CnsMag<PREC> mn[K];
+    unsigned eq[K], neg[K], sxs[K], b1[K], b2[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        cn[k].prepare(T[k], D, p.offset, p.clamp);
+        mn[k].set(cn[k].v1, cn[k].v2);
+        eq[k] = 0;
+        neg[k] = 0;
+        sxs[k] = cn[k].sx & 0x80000000u;
+        b1[k] = __float_as_uint(mn[k].r1);
+        b2[k] = __float_as_uint(mn[k].r2);
+    }
+#pragma unroll
+    for (int j = D - 1; j >= 0; --j) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const bool e = fabsf(T[k][j]) == cn[k].m1;
+            const unsigned U = __float_as_uint(T[k][j]) * p.k_one + sxs[k];
+            const unsigned n = __umulhi(U, p.k_two);
+            neg[k] = neg[k] * p.k_two + n;
+            if (e) eq[k] |= 1u << j;
+            app_at(app, vi[k][j]) = __fadd_rn(T[k][j], __uint_as_float(n * p.k_two31 + (e ? b2[k] : b1[k])));
+        }
+    }
+    if (store) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) cns_store(row + zk[k] * SB, SB, cns_pack<PREC>(mn[k], eq[k], neg[k], D));
+    }
+}
+
 // One layer step of degree D on row r (blocks from b0, slots from off):
 // prefetch the state of layer r + 2 into s_far, update from s_cur, barrier.
-template <int D, int BG, int PREC, int ZC>
-__device__ __forceinline__ void sched_step(const Params &p, const int2 *s_at, float *app, unsigned char *st, int z,
-                                           int t, int r, int b0, int off, const SchedGeo &geo, bool done,
-                                           const uint4 &s_cur, uint4 &s_far) {
+template <int D, int BG, int PREC, int K>
+__device__ __forceinline__ void sched_step(const Params &p, const int2 *s_at, float *app, unsigned char *st,
+                                           const int (&zk)[K], int t, int r, int b0, int off, const SchedGeo &geo,
+                                           bool done, const uint4 (&s_cur)[K], uint4 (&s_far)[K]) {
     using S = Sched<BG>;
     using L = SchedLayout<BG, PREC>;
     int r2 = r + 2, t2 = t;
@@ -71,50 +130,56 @@ __device__ __forceinline__ void sched_step(const Params &p, const int2 *s_at, fl
         ++t2;
     }
     if (t2 == 0) {
-        s_far = make_uint4(0u, 0u, 0u, 0u);  // iteration 0 starts from zero messages
+#pragma unroll
+        for (int k = 0; k < K; ++k) s_far[k] = make_uint4(0u, 0u, 0u, 0u);  // iteration 0: zero messages
     } else if (!done && t2 < p.iters) {
-        if (r2 < 4) s_far = cns_load(st + geo.off(r2) + z * L::sb_core, L::sb_core);
-        else s_far = cns_load(st + geo.off(r2) + z * L::sb_ext, L::sb_ext);
+        const unsigned char *row2 = st + geo.off(r2);
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            if (r2 < 4) s_far[k] = cns_load(row2 + zk[k] * L::sb_core, L::sb_core);
+            else s_far[k] = cns_load(row2 + zk[k] * L::sb_ext, L::sb_ext);
+        }
     }
-    if (!done) {
-        constexpr int SB = cns_slot_bytes<PREC>(D);
-        cns_update<D, D, PREC, ZC>(p, D, app, s_at + b0, z, s_cur, st + off + z * SB, SB, t + 1 < p.iters);
-    }
+    if (!done) cns_update_k<D, PREC, K>(p, app, s_at + b0, zk, s_cur, st + off, t + 1 < p.iters);
     __syncthreads();
 }
 
 // COUNT consecutive rows of degree D from row r0, the first at ring phase PH.
-template <int D, int COUNT, int PH, int BG, int PREC, int ZC>
-__device__ __forceinline__ void sched_run(const Params &p, const int2 *s_at, float *app, unsigned char *st, int z,
-                                          int t, int r0, int b0, int off0, int Lrow, const SchedGeo &geo, bool done,
-                                          uint4 &a, uint4 &b, uint4 &c) {
+template <int D, int COUNT, int PH, int BG, int PREC, int K>
+__device__ __forceinline__ void sched_run(const Params &p, const int2 *s_at, float *app, unsigned char *st,
+                                          const int (&zk)[K], int t, int r0, int b0, int off0, int Lrow,
+                                          const SchedGeo &geo, bool done, uint4 (&a)[K], uint4 (&b)[K],
+                                          uint4 (&c)[K]) {
     int r = r0, bb = b0, off = off0;
 #pragma unroll 1
     for (int i = 0; i < COUNT / 3; ++i) {
-        sched_step<D, BG, PREC, ZC>(p, s_at, app, st, z, t, r, bb, off, geo, done, ring<PH>(a, b, c),
-                                    ring<PH + 2>(a, b, c));
-        sched_step<D, BG, PREC, ZC>(p, s_at, app, st, z, t, r + 1, bb + D, off + Lrow, geo, done,
-                                    ring<PH + 1>(a, b, c), ring<PH + 3>(a, b, c));
-        sched_step<D, BG, PREC, ZC>(p, s_at, app, st, z, t, r + 2, bb + 2 * D, off + 2 * Lrow, geo, done,
-                                    ring<PH + 2>(a, b, c), ring<PH + 4>(a, b, c));
+        sched_step<D, BG, PREC, K>(p, s_at, app, st, zk, t, r, bb, off, geo, done, ring<PH, K>(a, b, c),
+                                   ring<PH + 2, K>(a, b, c));
+        sched_step<D, BG, PREC, K>(p, s_at, app, st, zk, t, r + 1, bb + D, off + Lrow, geo, done,
+                                   ring<PH + 1, K>(a, b, c), ring<PH + 3, K>(a, b, c));
+        sched_step<D, BG, PREC, K>(p, s_at, app, st, zk, t, r + 2, bb + 2 * D, off + 2 * Lrow, geo, done,
+                                   ring<PH + 2, K>(a, b, c), ring<PH + 4, K>(a, b, c));
         r += 3;
         bb += 3 * D;
         off += 3 * Lrow;
     }
     if constexpr (COUNT % 3 >= 1)
-        sched_step<D, BG, PREC, ZC>(p, s_at, app, st, z, t, r, bb, off, geo, done, ring<PH>(a, b, c),
-                                    ring<PH + 2>(a, b, c));
+        sched_step<D, BG, PREC, K>(p, s_at, app, st, zk, t, r, bb, off, geo, done, ring<PH, K>(a, b, c),
+                                   ring<PH + 2, K>(a, b, c));
     if constexpr (COUNT % 3 == 2)
-        sched_step<D, BG, PREC, ZC>(p, s_at, app, st, z, t, r + 1, bb + D, off + Lrow, geo, done,
-                                    ring<PH + 1>(a, b, c), ring<PH + 3>(a, b, c));
+        sched_step<D, BG, PREC, K>(p, s_at, app, st, zk, t, r + 1, bb + D, off + Lrow, geo, done,
+                                   ring<PH + 1, K>(a, b, c), ring<PH + 3, K>(a, b, c));
 }
 
-template <int BG, int PREC, int ZC = 0>
-__global__ void __launch_bounds__(kMaxThreads, 2) k_layered_cns_sched(const Params p, const __grid_constant__ SchedTab tab) {
+// K check nodes per thread: G codewords per CTA of G Z / K threads.
+template <int BG, int PREC, int ZC = 0, int K = 1>
+__global__ void __launch_bounds__(kMaxThreads / K, 2)
+    k_layered_cns_sched(const Params p, const __grid_constant__ SchedTab tab) {
     using S = Sched<BG>;
     using L = SchedLayout<BG, PREC>;
     extern __shared__ __align__(16) unsigned char smem[];
     const int ZV = ZC ? ZC : p.Z;
+    const int H = ZV / K;  // threads per codeword
     float *s_app_all = reinterpret_cast<float *>(smem);
     uint32_t *s_vb = reinterpret_cast<uint32_t *>(s_app_all + (size_t)p.G * p.n);
     int32_t *s_rp = reinterpret_cast<int32_t *>(s_vb + p.nnz);
@@ -124,7 +189,10 @@ __global__ void __launch_bounds__(kMaxThreads, 2) k_layered_cns_sched(const Para
     load_tables(p, s_vb, s_rp);  // for the syndrome check
     const int64_t cw_base = (int64_t)blockIdx.x * p.G;
     load_channel(p, s_app_all, cw_base);
-    const int g = threadIdx.x / ZV, z = threadIdx.x - g * ZV;
+    const int g = threadIdx.x / H, z = threadIdx.x - g * H;
+    int zk[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) zk[k] = z + k * H;
     const int64_t cw = cw_base + g;
     const bool active = g < p.G && cw < p.B;
     float *app = s_app_all + (size_t)(active ? g : 0) * p.n;
@@ -136,36 +204,44 @@ __global__ void __launch_bounds__(kMaxThreads, 2) k_layered_cns_sched(const Para
     geo.Le = (L::sb_ext * ZV + 15) / 16 * 16;
     __syncthreads();
 
-    uint4 a = make_uint4(0u, 0u, 0u, 0u), b = a, c = a;
+    uint4 a[K], b[K], c[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) a[k] = b[k] = c[k] = make_uint4(0u, 0u, 0u, 0u);
     for (int t = 0; t < p.iters; ++t) {
-        sched_run<S::dc0, 1, 0, BG, PREC, ZC>(p, s_at, app, st, z, t, 0, 0, 0, geo.Lc, geo, done, a, b, c);
-        sched_run<S::dc1, 1, 1, BG, PREC, ZC>(p, s_at, app, st, z, t, 1, S::dc0, geo.Lc, geo.Lc, geo, done, a, b,
-                                              c);
-        sched_run<S::dc2, 1, 2, BG, PREC, ZC>(p, s_at, app, st, z, t, 2, S::dc0 + S::dc1, 2 * geo.Lc, geo.Lc, geo,
-                                              done, a, b, c);
-        sched_run<S::dc3, 1, 3, BG, PREC, ZC>(p, s_at, app, st, z, t, 3, S::dc0 + S::dc1 + S::dc2, 3 * geo.Lc,
-                                              geo.Lc, geo, done, a, b, c);
-        sched_run<S::d_hi, S::n_hi, 4, BG, PREC, ZC>(p, s_at, app, st, z, t, 4, L::b_hi, 4 * geo.Lc, geo.Le, geo,
-                                                     done, a, b, c);
-        sched_run<S::d_lo, S::rows - 4 - S::n_hi, 4 + S::n_hi, BG, PREC, ZC>(
-            p, s_at, app, st, z, t, 4 + S::n_hi, L::b_lo, 4 * geo.Lc + S::n_hi * geo.Le, geo.Le, geo, done, a, b, c);
+        sched_run<S::dc0, 1, 0, BG, PREC, K>(p, s_at, app, st, zk, t, 0, 0, 0, geo.Lc, geo, done, a, b, c);
+        sched_run<S::dc1, 1, 1, BG, PREC, K>(p, s_at, app, st, zk, t, 1, S::dc0, geo.Lc, geo.Lc, geo, done, a, b,
+                                             c);
+        sched_run<S::dc2, 1, 2, BG, PREC, K>(p, s_at, app, st, zk, t, 2, S::dc0 + S::dc1, 2 * geo.Lc, geo.Lc, geo,
+                                             done, a, b, c);
+        sched_run<S::dc3, 1, 3, BG, PREC, K>(p, s_at, app, st, zk, t, 3, S::dc0 + S::dc1 + S::dc2, 3 * geo.Lc,
+                                             geo.Lc, geo, done, a, b, c);
+        sched_run<S::d_hi, S::n_hi, 4, BG, PREC, K>(p, s_at, app, st, zk, t, 4, L::b_hi, 4 * geo.Lc, geo.Le, geo,
+                                                    done, a, b, c);
+        sched_run<S::d_lo, S::rows - 4 - S::n_hi, 4 + S::n_hi, BG, PREC, K>(
+            p, s_at, app, st, zk, t, 4 + S::n_hi, L::b_lo, 4 * geo.Lc + S::n_hi * geo.Le, geo.Le, geo, done, a, b, c);
         // the next iteration's first step finds its state at phase rows mod 3
-        if constexpr (S::rows % 3 == 1) {
-            const uint4 x = a;
-            a = b;
-            b = c;
-            c = x;
-        } else if constexpr (S::rows % 3 == 2) {
-            const uint4 x = c;
-            c = b;
-            b = a;
-            a = x;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            if constexpr (S::rows % 3 == 1) {
+                const uint4 x = a[k];
+                a[k] = b[k];
+                b[k] = c[k];
+                c[k] = x;
+            } else if constexpr (S::rows % 3 == 2) {
+                const uint4 x = c[k];
+                c[k] = b[k];
+                b[k] = a[k];
+                a[k] = x;
+            }
         }
         if (!done) iters_run = t + 1;
         if (p.early_stop) {
             if (threadIdx.x < p.G) s_flag[threadIdx.x] = 0;
             __syncthreads();
-            if (!done && syndrome_bad_vec<1, ZC>(p, s_vb, s_rp, app, z)) s_flag[g] = 1;
+            bool bad = false;
+#pragma unroll
+            for (int k = 0; k < K; ++k) bad |= !done && syndrome_bad_vec<1, ZC>(p, s_vb, s_rp, app, zk[k]);
+            if (bad) s_flag[g] = 1;
             __syncthreads();
             if (!done && s_flag[g] == 0) done = true;
             if (__syncthreads_and(done)) break;
@@ -178,8 +254,8 @@ __global__ void __launch_bounds__(kMaxThreads, 2) k_layered_cns_sched(const Para
 using SchedFn = void (*)(Params, SchedTab);
 
 // Kernel for a code whose row degrees follow the full base graph of shape bg
-// (1 or 2), or nullptr.
-SchedFn layered_cns_sched_kernel(int bg, int prec, int Z);
+// (1 or 2) with k check nodes per thread (1, or 2 when Z is even), or nullptr.
+SchedFn layered_cns_sched_kernel(int bg, int prec, int Z, int k);
 
 }  // namespace dec
 }  // namespace ldpcx

@@ -7,7 +7,7 @@ namespace dec {
 KernelFn layered_kernel_f16(int dmax, int algo, int zpt) {
     constexpr int PREC = kF16;
     if (dmax > 20) return nullptr;
-    (void)zpt;  // one check node per thread (two per thread measured slower: bank conflicts, fewer warps)
+    if (zpt != 1) return nullptr;  // one check node per thread (two measured slower here: bank conflicts)
     if (algo == kMinSum) return dmax <= 12 ? k_layered<12, kMinSum, PREC, 1> : k_layered<20, kMinSum, PREC, 1>;
     return dmax <= 12 ? k_layered<12, kSpa, PREC, 1> : k_layered<20, kSpa, PREC, 1>;
 }

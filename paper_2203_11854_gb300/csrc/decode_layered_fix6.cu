@@ -7,7 +7,7 @@ namespace dec {
 KernelFn layered_kernel_fix6(int dmax, int algo, int zpt) {
     constexpr int PREC = kFix6;
     if (dmax > 20 || algo != kMinSum) return nullptr;
-    (void)zpt;  // one check node per thread (two per thread measured slower)
+    if (zpt != 1) return nullptr;  // one check node per thread (two measured slower here: bank conflicts)
     return dmax <= 12 ? k_layered<12, kMinSum, PREC, 1> : k_layered<20, kMinSum, PREC, 1>;
 }
 

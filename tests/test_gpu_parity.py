@@ -299,19 +299,23 @@ def test_repeat_calls_are_deterministic(lx, orc):
 @pytest.mark.parametrize("prec", [0, 1, 2])
 def test_kernel_variants_agree(lx, orc, name, prec):
     """Per-edge messages, check-node state with the row table, check-node state
-    with the compiled-in schedule, generic and compile-time Z: identical outputs."""
+    with the compiled-in schedule (one or two check nodes per thread), generic
+    and compile-time Z: identical outputs."""
     ocode, u, cw, L_tx = make_case(orc, name, 1.9, 23)
     code = gpu_code(lx, name)
     outs = []
     try:
-        for cns, sched, spec in [(0, 0, 1), (1, 0, 1), (1, 1, 1), (1, 1, 0), (0, 0, 0)]:
+        for cns, sched, spec, zpt in [(0, 0, 1, 0), (1, 0, 1, 0), (1, 1, 1, 0), (1, 1, 0, 0), (0, 0, 0, 0),
+                                      (1, 1, 1, 2), (1, 1, 0, 2), (0, 0, 1, 2), (1, 0, 1, 2)]:
             lx.ldpcx_tune_set(lx.TUNE_CN_STATE, cns)
             lx.ldpcx_tune_set(lx.TUNE_SCHEDULE, sched)
             lx.ldpcx_tune_set(lx.TUNE_SPECIALISED, spec)
+            lx.ldpcx_tune_set(lx.TUNE_ZPT, zpt)
             outs.append(lx.ldpc_bp_decode(code, cuda(L_tx), algo=lx.LAYERED_MINSUM, iters=9, msg_prec=prec,
                                           early_stop=True, llr_out=True))
     finally:
         for key in (lx.TUNE_CN_STATE, lx.TUNE_SCHEDULE, lx.TUNE_SPECIALISED):
             lx.ldpcx_tune_set(key, 1)
+        lx.ldpcx_tune_set(lx.TUNE_ZPT, 0)
     for o in outs[1:]:
         assert all(torch.equal(a, b) for a, b in zip(o, outs[0]))
