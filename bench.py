@@ -24,6 +24,7 @@ the paper ships no code) on a bounded sample of the same workload.
 from __future__ import annotations
 
 import argparse
+import datetime
 import hashlib
 import json
 import os
@@ -59,23 +60,34 @@ def peaks():
 
 
 class Clocks:
-    """Samples nvidia-smi SM clocks and throttle reasons during the timed region."""
+    """Samples nvidia-smi SM clocks and throttle reasons every 20 ms; keeps the samples whose
+    timestamps fall inside the timed region (begin() / end() mark it on the host clock)."""
 
-    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+    Q = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
          "clocks_event_reasons.sw_power_cap")
 
     def __init__(self, index):
         self.index, self.proc, self.path = index, None, None
+        self.t0 = self.t1 = None
 
     def start(self):
         try:
             self.path = f"/tmp/ldpcx_clocks_{os.getpid()}.csv"
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "20"],
                                          stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            t = time.time()
+            while time.time() - t < 5.0 and os.path.getsize(self.path) == 0:
+                time.sleep(0.01)  # sampling has started before the timed region does
         except Exception:
             self.proc = None
+
+    def begin(self):
+        self.t0 = time.time()
+
+    def end(self):
+        self.t1 = time.time()
 
     def stop(self):
         if not self.proc:
@@ -88,20 +100,29 @@ class Clocks:
         rows = []
         for line in open(self.path):
             parts = [p.strip() for p in line.split(",")]
-            if len(parts) == 7:
-                rows.append(parts)
+            if len(parts) != 8:
+                continue
+            try:
+                ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+            except ValueError:
+                continue
+            rows.append((ts, parts[1:]))
         os.remove(self.path)
-        if not rows:
+        inside = [r for ts, r in rows if self.t0 is not None and self.t0 <= ts <= self.t1]
+        if not inside:  # a region shorter than the sampling period: the samples nearest to it
+            mid = 0.5 * (self.t0 + self.t1) if self.t0 is not None else 0.0
+            inside = [r for ts, r in sorted(rows, key=lambda x: abs(x[0] - mid))[:2]]
+        if not inside:
             return None
-        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
-        mx = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        sm = [float(r[0]) for r in inside if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in inside if r[1].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in rows for i in range(4) if r[3 + i].lower() == "active"})
+        reasons = sorted({names[i] for r in inside for i in range(4) if r[3 + i].lower() == "active"})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(rows)}
+                "reasons": reasons, "samples": len(inside), "interval_ms": 20}
 
 
-KERNEL_SOURCES = ("decode_kernels.cuh", "decode_cns.cuh", "decode_layered_cns.cu")  # the profiled kernel's code
+KERNEL_SOURCES = ("decode_kernels.cuh", "decode_cns.cuh", "decode_cns_sched.cuh", "decode_cns_sched_f16.cu")  # profiled kernel
 
 
 def decoder_digest():
@@ -244,10 +265,11 @@ def run_gpu(args):
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     dec_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks.start()
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    clocks.start()
+    clocks.begin()
     t_start = torch.cuda.Event(enable_timing=True)
     t_end = torch.cuda.Event(enable_timing=True)
     t_start.record(stream)
@@ -257,6 +279,7 @@ def run_gpu(args):
         ends[i].record(stream)
     t_end.record(stream)
     torch.cuda.synchronize()
+    clocks.end()
     if dist:
         dist.barrier()
     clk = clocks.stop()
@@ -298,7 +321,7 @@ def run_gpu(args):
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
                          "frac": achieved / pk["hbm_gbs"],
                          "traffic": None if traffic_cw is None else traffic_cw * B,
-                         "kernel": "k_layered_cns<20, fp16, Z=384>" if cn_state else "k_layered<20, min-sum, fp16>",
+                         "kernel": "k_layered_cns_sched<BG1, fp16, Z=384>" if cn_state else "k_layered<20, min-sum, fp16>",
                          "message_format": "check-node state" if cn_state else "per-edge messages",
                          "message_bytes_per_codeword_iteration": msg_cw,
                          "peak_kind": f"{pk_kind} HBM copy bandwidth",
@@ -443,7 +466,7 @@ def measure_e2e(lx, code, y_dev, info_dev, n0, dec, stream, args, dev):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--quick", action="store_true", help="skip the per-variant decode timings")

@@ -67,17 +67,27 @@ template <> struct CnsMag<kF16> {
         return __uint_as_float(__float_as_uint(m) | (neg << 31));
     }
 };
+// Integer <-> float for 0 <= x < 2^22 with FP32 adds instead of conversion
+// instructions: adding 1.5 * 2^23 puts the integer nearest to x (ties to even,
+// the FADD's rounding) in the low mantissa bits; subtracting it back is exact.
+constexpr float kMagic = 12582912.0f;  // 1.5 * 2^23, bits 0x4B400000
+__device__ __forceinline__ float fix6_round(float x) { return __fsub_rn(__fadd_rn(x, kMagic), kMagic); }
+__device__ __forceinline__ float fix6_value(unsigned q) { return __fsub_rn(__uint_as_float(0x4B400000u | q), kMagic); }
+
 template <> struct CnsMag<kFix6> {
     int q1, q2;      // magnitude codes 0..31 (steps of 0.5)
     float r1, r2;    // their values
+    // q = min(31, rint(2 v)) for 0 <= v <= clamp (2 v < 2^22)
     __device__ __forceinline__ void set(float v1, float v2) {
-        q1 = min(31, (int)rintf(v1 * 2.0f));
-        q2 = min(31, (int)rintf(v2 * 2.0f));
-        values();
+        const float a = fminf(fix6_round(v1 * 2.0f), 31.0f), b = fminf(fix6_round(v2 * 2.0f), 31.0f);
+        q1 = (int)(__float_as_uint(__fadd_rn(a, kMagic)) & 63u);
+        q2 = (int)(__float_as_uint(__fadd_rn(b, kMagic)) & 63u);
+        r1 = a * 0.5f;
+        r2 = b * 0.5f;
     }
     __device__ __forceinline__ void values() {
-        r1 = (float)q1 * 0.5f;
-        r2 = (float)q2 * 0.5f;
+        r1 = fix6_value((unsigned)q1) * 0.5f;
+        r2 = fix6_value((unsigned)q2) * 0.5f;
     }
     // The 6-bit store holds a signed integer, so it has no negative zero; a
     // zero message here may carry the sign bit. Both give the same sums: the

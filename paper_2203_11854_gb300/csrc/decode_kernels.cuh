@@ -127,10 +127,43 @@ __device__ __forceinline__ float clamp_llr(float x, float c, bool &bad) {
     return fminf(fmaxf(x, -c), c);
 }
 
+__device__ __forceinline__ float4 clamp_llr4(float4 x, float c, bool &bad) {
+    return make_float4(clamp_llr(x.x, c, bad) + 0.0f, clamp_llr(x.y, c, bad) + 0.0f, clamp_llr(x.z, c, bad) + 0.0f,
+                       clamp_llr(x.w, c, bad) + 0.0f);
+}
+
 // Load the channel LLRs of the CTA's codewords into app (placed: punctured and
-// untransmitted positions are 0).
+// untransmitted positions are 0). When the row layout allows, 16-byte loads,
+// four per thread in flight (streaming: the LLRs are read once).
 __device__ inline void load_channel(const Params &p, float *app, int64_t cw_base) {
     bool bad = false;
+    if (((p.p0 | p.n_tx | p.n) & 3) == 0 && (reinterpret_cast<uintptr_t>(p.llr) & 15u) == 0) {
+        const int bd = blockDim.x, n4 = p.n_tx >> 2;
+        for (int g = 0; g < p.G; ++g) {
+            const int64_t cw = cw_base + g;
+            float *a = app + (size_t)g * p.n;
+            for (int v = threadIdx.x; v < p.p0; v += bd) a[v] = 0.0f;
+            for (int v = p.p0 + p.n_tx + threadIdx.x; v < p.n; v += bd) a[v] = 0.0f;
+            float4 *dst = reinterpret_cast<float4 *>(a + p.p0);
+            if (cw >= p.B) {
+                for (int i = threadIdx.x; i < n4; i += bd) dst[i] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                continue;
+            }
+            const float4 *src = reinterpret_cast<const float4 *>(p.llr + cw * p.n_tx);
+            int i = threadIdx.x;
+            for (; i + 3 * bd < n4; i += 4 * bd) {
+                const float4 x0 = __ldcs(src + i), x1 = __ldcs(src + i + bd), x2 = __ldcs(src + i + 2 * bd),
+                             x3 = __ldcs(src + i + 3 * bd);
+                dst[i] = clamp_llr4(x0, p.clamp, bad);
+                dst[i + bd] = clamp_llr4(x1, p.clamp, bad);
+                dst[i + 2 * bd] = clamp_llr4(x2, p.clamp, bad);
+                dst[i + 3 * bd] = clamp_llr4(x3, p.clamp, bad);
+            }
+            for (; i < n4; i += bd) dst[i] = clamp_llr4(__ldcs(src + i), p.clamp, bad);
+        }
+        if (bad) latch(p.status, LDPCX_FLAG_NONFINITE);
+        return;
+    }
     for (int g = 0; g < p.G; ++g) {
         const int64_t cw = cw_base + g;
         for (int v = threadIdx.x; v < p.n; v += blockDim.x) {
