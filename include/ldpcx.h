@@ -206,6 +206,16 @@ int ldpc_bp_workspace(ldpcx_code_t code, int64_t B, const ldpcx_decode_opts *opt
  * message storage one codeword reads or writes in one full iteration. */
 int ldpc_bp_msg_format(ldpcx_code_t code, const ldpcx_decode_opts *opts, int *cn_state, int64_t *bytes_per_cw);
 
+/* The sum-product check-node function phi(x) = -ln tanh(x/2) = ln(1 + 2/(e^x
+ * - 1)) as the decoders evaluate it, on n device floats x (each in
+ * [phi(clamp), clamp] as the decoders use it; x > 0 required). fast = 0: from
+ * the CUDA library functions expm1f, IEEE division and log1pf (flooding
+ * decoders and the adjoint); fast = 1: from the hardware 2^x, 1/x and log2
+ * approximations with Taylor series where a difference would cancel (layered
+ * sum-product). Exposed so that tests can bound both against FP64.
+ * Asynchronous on stream; LDPCX_E_INVAL for n < 0 or null pointers with n > 0. */
+int ldpcx_phi(const float *x, float *out, int64_t n, int fast, void *stream);
+
 /* Decode B codewords.
  * llr_ch   (device) [B][n_tx] float channel LLRs of the transmitted positions.
  * llr_out  (device, or NULL) [B][n] float final APP LLRs.

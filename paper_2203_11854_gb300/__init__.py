@@ -19,7 +19,7 @@ __all__ = [
     "qc_ldpc_info", "qc_ldpc_base", "sim_tx", "demap_app", "ldpc_bp_workspace", "ldpc_bp_decode",
     "sim_count", "sim_workspace", "sim_run", "library_path", "load_library", "ldpcx_tune_set", "ldpcx_tune_get",
     "ldpc_bp_decode_noalloc", "ldpc_bp_msg_format", "ldpc_bp_mixed_workspace", "ldpc_bp_decode_mixed", "ldpc_bp_ckpt_bytes", "ldpc_bp_decode_ckpt", "ldpc_bp_backward_workspace",
-    "ldpc_bp_backward",
+    "ldpc_bp_backward", "ldpcx_phi",
     "LAYERED_MINSUM", "LAYERED_SPA", "FLOOD_MINSUM", "FLOOD_SPA", "MSG_F32", "MSG_F16", "MSG_FIX6",
     "DEMAP_EXACT", "DEMAP_MAXLOG",
 ]
@@ -90,6 +90,7 @@ _SIGS = {
     "sim_run": ([C.POINTER(SimConfig), C.POINTER(SimCounts), C.POINTER(_i), _vp, _sz, _vp], _i),
     "ldpc_bp_decode_noalloc": ([_vp, _vp, _i64, C.POINTER(DecodeOpts), _vp, _vp, _vp, _vp], _i),
     "ldpc_bp_msg_format": ([_vp, C.POINTER(DecodeOpts), C.POINTER(_i), C.POINTER(_i64)], _i),
+    "ldpcx_phi": ([_vp, _vp, _i64, _i, _vp], _i),
     "ldpc_bp_mixed_workspace": ([C.POINTER(BatchGroup), _i, C.POINTER(DecodeOpts), C.POINTER(_sz)], _i),
     "ldpc_bp_decode_mixed": ([C.POINTER(BatchGroup), _i, C.POINTER(DecodeOpts), _vp, _sz, _vp], _i),
     "ldpc_bp_ckpt_bytes": ([_vp, _i64, C.POINTER(DecodeOpts), C.POINTER(_sz)], _i),
@@ -267,6 +268,15 @@ def ldpc_bp_msg_format(code: Code, *, algo: int = LAYERED_MINSUM, iters: int = 2
     _check(load_library().ldpc_bp_msg_format(code.handle, C.byref(o), C.byref(cs), C.byref(nb)),
            "ldpc_bp_msg_format")
     return bool(cs.value), nb.value
+
+
+def ldpcx_phi(x, *, fast: bool = False, out=None, stream=None):
+    """phi(x) = ln(1 + 2/(e^x - 1)) as the decoders evaluate it (x: CUDA float32)."""
+    import torch
+    assert x.is_cuda and x.dtype == torch.float32 and x.is_contiguous()
+    out = torch.empty_like(x) if out is None else out
+    _check(load_library().ldpcx_phi(_ptr(x), _ptr(out), x.numel(), int(bool(fast)), _stream(stream)), "ldpcx_phi")
+    return out
 
 
 def ldpc_bp_decode(code: Code, llr_ch, *, algo: int = LAYERED_MINSUM, iters: int = 20, msg_prec: int = MSG_F32,

@@ -3,6 +3,7 @@
 // decode_flood.cu.
 #include <math.h>
 
+#include <algorithm>
 #include <atomic>
 
 #include "decode_cns_sched.cuh"
@@ -257,6 +258,23 @@ extern "C" int ldpc_bp_decode(ldpcx_code_t c, const float *llr_ch, int64_t B, co
                               float *llr_out, uint32_t *bits_out, int32_t *iters_out, void *ws, size_t ws_bytes,
                               void *stream) {
     return ldpcx::decode_impl(c, llr_ch, B, o, llr_out, bits_out, iters_out, ws, ws_bytes, nullptr, stream);
+}
+
+namespace ldpcx {
+namespace {
+__global__ void k_phi(const float *x, float *out, int64_t n, int fast) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = fast ? dec::phi_fast(x[i]) : dec::phi(x[i]);
+}
+}  // namespace
+}  // namespace ldpcx
+
+extern "C" int ldpcx_phi(const float *x, float *out, int64_t n, int fast, void *stream) {
+    if (n < 0 || (n > 0 && (!x || !out))) return LDPCX_E_INVAL;
+    if (n == 0) return LDPCX_OK;
+    const int64_t blocks = std::min<int64_t>((n + 255) / 256, 4096);
+    ldpcx::k_phi<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(x, out, n, fast);
+    return ldpcx::cuda_status(cudaGetLastError());
 }
 
 extern "C" int ldpc_bp_msg_format(ldpcx_code_t c, const ldpcx_decode_opts *o, int *cn_state,

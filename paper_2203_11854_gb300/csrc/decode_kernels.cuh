@@ -75,6 +75,25 @@ template <> __device__ __forceinline__ void msg_store<kFix6>(int8_t *p, int8_t v
 // phi(x) = -ln tanh(x/2) = ln(1 + 2/(e^x - 1)), for x > 0.
 __device__ __forceinline__ float phi(float x) { return log1pf(__fdiv_rn(2.0f, expm1f(x))); }
 
+// The same function from the hardware approximations of 2^x, 1/x and log2 x,
+// for phi(clamp) <= x <= clamp. Where a difference of nearly equal numbers
+// would cancel, the Taylor series is used instead:
+//   e^x - 1 = x + x^2/2 + x^3/6 + x^4/24 + O(x^5)  for x < 1/16
+//             (truncation below x^4/120 < 5e-7 relative),
+//   ln(1+y) = y - y^2/2 + y^3/3 - y^4/4 + O(y^5)     for y < 1/16
+//             (truncation below y^4/5 < 4e-6 relative).
+// Otherwise e^x - 1 >= 0.064 loses at most a factor e^x/(e^x - 1) < 17 of the
+// exponential's relative error, and ln(1+y) >= 0.06 is taken where log2 is
+// accurate in absolute terms; the result stays within about 2e-5 relative.
+__device__ __forceinline__ float phi_fast(float x) {
+    const float em1 = x < 0.0625f ? x * (1.0f + x * (0.5f + x * (1.0f / 6.0f + x * (1.0f / 24.0f))))
+                                  : __expf(x) - 1.0f;
+    const float y = __fdividef(2.0f, em1);
+    return y < 0.0625f ? y * (1.0f - y * (0.5f - y * (1.0f / 3.0f - y * 0.25f))) : __logf(1.0f + y);
+}
+
+template <bool FAST> __device__ __forceinline__ float phi_t(float x) { return FAST ? phi_fast(x) : phi(x); }
+
 struct Params {
     const uint32_t *blk;
     const int32_t *row_ptr;
@@ -187,9 +206,9 @@ __device__ __forceinline__ int vn_at(uint32_t vb, int z, int Z) {
 // Check-node rule on the variable-to-check inputs T[0..deg): prepare() reduces
 // the inputs to the check's state, value(j) then gives the (clamped, not yet
 // rounded) check-to-variable message of edge j.
-template <int DMAX, int ALGO> struct CheckNode;
+template <int DMAX, int ALGO, bool FAST = false> struct CheckNode;
 
-template <int DMAX> struct CheckNode<DMAX, kMinSum> {
+template <int DMAX, bool FAST> struct CheckNode<DMAX, kMinSum, FAST> {
     float v1, v2;   // offset, floored and clamped smallest / second smallest |T|
     int idx;        // first index of the smallest |T|
     unsigned neg;   // bit j: T_j < 0
@@ -258,7 +277,9 @@ template <int N> struct FastMinSum {
     }
 };
 
-template <int DMAX> struct CheckNode<DMAX, kSpa> {
+// Sum-product check node; FAST evaluates phi with phi_fast (layered kernels),
+// otherwise with the library functions (flooding, whose adjoint recomputes it).
+template <int DMAX, bool FAST> struct CheckNode<DMAX, kSpa, FAST> {
     float f[DMAX];       // phi(|T_j|) with the argument clamped to [phi(clamp), clamp]
     float s_rest, s_all; // sum without the largest term / with it
     int jm;              // index of the largest term
@@ -271,7 +292,7 @@ template <int DMAX> struct CheckNode<DMAX, kSpa> {
         for (int j = 0; j < DMAX; ++j) {
             if (j < deg) {
                 const float a = fminf(fmaxf(fabsf(T[j]), phi_lo), clamp);
-                f[j] = phi(a);
+                f[j] = phi_t<FAST>(a);
                 const bool gt = f[j] > fmax;
                 fmax = gt ? f[j] : fmax;
                 jm = gt ? j : jm;
@@ -290,7 +311,7 @@ template <int DMAX> struct CheckNode<DMAX, kSpa> {
     __device__ __forceinline__ float value(int j, float clamp, float phi_lo) const {
         float x = (j == jm) ? s_rest : __fsub_rn(s_all, f[j]);
         x = fminf(fmaxf(x, phi_lo), clamp);
-        const float mag = fminf(phi(x), clamp);
+        const float mag = fminf(phi_t<FAST>(x), clamp);
         return ((par ^ (neg >> j)) & 1u) ? -mag : mag;
     }
 };
@@ -497,7 +518,7 @@ __device__ __forceinline__ void layer_update(const Params &p, int deg, float *ap
             for (int k = 0; k < ZPT; ++k) T[k][j] = 0.0f;
         }
     }
-    using CN = typename std::conditional<ALGO == kMinSum, FastMinSum<N>, CheckNode<N, kSpa>>::type;
+    using CN = typename std::conditional<ALGO == kMinSum, FastMinSum<N>, CheckNode<N, kSpa, true>>::type;
     CN cn[ZPT];
 #pragma unroll
     for (int k = 0; k < ZPT; ++k) {
