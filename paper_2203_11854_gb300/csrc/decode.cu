@@ -6,7 +6,7 @@
 #include <algorithm>
 #include <atomic>
 
-#include "decode_cns_sched.cuh"
+#include "decode_edge_sched.cuh"
 
 namespace ldpcx {
 namespace {
@@ -139,6 +139,24 @@ namespace ldpcx {
 namespace {
 
 // Decode, optionally storing FP32 checkpoints of C^t (flooding only).
+// Launch a compiled-schedule kernel: block table as a kernel parameter, one
+// CTA per p.G codewords with kpt check nodes per thread.
+int launch_sched(SchedFn sf, const ldpcx_code *c, const Params &p, int64_t B, int kpt, void *stream) {
+    SchedTab tab;
+    for (int i = 0; i < c->nnz; ++i) {
+        const int col = (int)(c->blk[(size_t)i] >> 16), sh = (int)(c->blk[(size_t)i] & 0xFFFFu);
+        tab.at[i] = make_int2(4 * (col * c->Z + sh), c->Z - sh);
+    }
+    const size_t smem = smem_bytes(p, 1);
+    if (smem > 227 * 1024) return LDPCX_E_UNSUPPORTED;
+    if (cudaFuncSetAttribute(sf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return LDPCX_E_CUDA;
+    const int64_t grid = (B + p.G - 1) / p.G;
+    if (grid > 0x7FFFFFFF) return LDPCX_E_INVAL;
+    sf<<<(unsigned)grid, (p.G * (p.Z / kpt) + 31) / 32 * 32, smem, (cudaStream_t)stream>>>(p, tab);
+    return cuda_status(cudaGetLastError());
+}
+
 int decode_impl(ldpcx_code_t c, const float *llr_ch, int64_t B, const ldpcx_decode_opts *o, float *llr_out,
                 uint32_t *bits_out, int32_t *iters_out, void *ws, size_t ws_bytes, float *ckpt, void *stream) {
     if (!c || B < 0 || (B > 0 && !llr_ch)) return LDPCX_E_INVAL;
@@ -199,27 +217,21 @@ int decode_impl(ldpcx_code_t c, const float *llr_ch, int64_t B, const ldpcx_deco
     set_int_constants(p);
 
     size_t smem = smem_bytes(p, layered ? 1 : 2);
+    // layered sum-product on a full base graph: per-edge messages, compiled-in schedule
+    if (layered && algo == kSpa && zpt == 1 && g_sched.load()) {
+        const int bg = sched_shape(c);
+        SchedFn sf = bg && c->nnz <= kSchedMaxBlocks
+                         ? layered_edge_sched_kernel(bg, algo, o->msg_prec, g_specialised.load() ? c->Z : 0)
+                         : nullptr;
+        if (sf) return launch_sched(sf, c, p, B, 1, stream);
+    }
     if (layered && algo == kMinSum && zpt == 1 && g_cns.load() &&
         cns_bytes(c, o->msg_prec) <= p.msg_stride * p.msg_size) {
         const int zs = g_specialised.load() ? c->Z : 0;
         const int bg = g_sched.load() ? sched_shape(c) : 0;
         const int kpt = g_zpt.load() == 2 && c->Z % 2 == 0 ? 2 : 1;  // check nodes per thread
         SchedFn sf = bg && c->nnz <= kSchedMaxBlocks ? layered_cns_sched_kernel(bg, o->msg_prec, zs, kpt) : nullptr;
-        if (sf) {
-            SchedTab tab;
-            for (int i = 0; i < c->nnz; ++i) {
-                const int col = (int)(c->blk[(size_t)i] >> 16), sh = (int)(c->blk[(size_t)i] & 0xFFFFu);
-                tab.at[i] = make_int2(4 * (col * c->Z + sh), c->Z - sh);
-            }
-            smem = smem_bytes(p, 1);
-            if (smem > 227 * 1024) return LDPCX_E_UNSUPPORTED;
-            if (cudaFuncSetAttribute(sf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-                return LDPCX_E_CUDA;
-            const int64_t grid = (B + p.G - 1) / p.G;
-            if (grid > 0x7FFFFFFF) return LDPCX_E_INVAL;
-            sf<<<(unsigned)grid, (p.G * (p.Z / kpt) + 31) / 32 * 32, smem, (cudaStream_t)stream>>>(p, tab);
-            return cuda_status(cudaGetLastError());
-        }
+        if (sf) return launch_sched(sf, c, p, B, kpt, stream);
         KernelFn f = layered_cns_kernel(c->max_deg, o->msg_prec, zs);
         if (f) {
             fn = f;

@@ -319,3 +319,24 @@ def test_kernel_variants_agree(lx, orc, name, prec):
         lx.ldpcx_tune_set(lx.TUNE_ZPT, 0)
     for o in outs[1:]:
         assert all(torch.equal(a, b) for a, b in zip(o, outs[0]))
+
+
+@pytest.mark.parametrize("name", ["bg2_z64", "bg1_z384", "bg2_z200"])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_spa_schedule_variants_agree(lx, orc, name, prec):
+    """Layered sum-product: the compiled-in schedule equals the row-table kernel
+    bit for bit (same arithmetic, same order)."""
+    ocode, u, cw, L_tx = make_case(orc, name, 2.4, 31)
+    code = gpu_code(lx, name)
+    outs = []
+    try:
+        for sched, spec in [(0, 1), (1, 1), (1, 0)]:
+            lx.ldpcx_tune_set(lx.TUNE_SCHEDULE, sched)
+            lx.ldpcx_tune_set(lx.TUNE_SPECIALISED, spec)
+            outs.append(lx.ldpc_bp_decode(code, cuda(L_tx), algo=lx.LAYERED_SPA, iters=7, msg_prec=prec,
+                                          early_stop=True, llr_out=True))
+    finally:
+        lx.ldpcx_tune_set(lx.TUNE_SCHEDULE, 1)
+        lx.ldpcx_tune_set(lx.TUNE_SPECIALISED, 1)
+    for o in outs[1:]:
+        assert all(torch.equal(a, b) for a, b in zip(o, outs[0]))
