@@ -48,7 +48,7 @@ def workload_config(batch=None):
                         "layered offset min-sum (0.5), 20 iterations, FP16 messages" % (batch, EBN0),
             "code": "BG1-shaped 46x68, 316 blocks, Z=384, n=26112, k=8448, 2Z punctured",
             "batch": batch, "modulation": "16-QAM", "ebn0_db": EBN0, "iters": ITERS, "msg": "fp16",
-            "l2": "inputs larger than L2 (y %d MB, LLR %d MB, messages %d MB): no flush"
+            "l2": "inputs larger than L2 (y %d MB, LLR %d MB, message workspace %d MB): no flush"
                   % (batch * 6336 * 8 >> 20, batch * 25344 * 4 >> 20, batch * 121344 * 2 >> 20)}
 
 
@@ -307,6 +307,7 @@ def run_gpu(args):
         if not args.quick:
             variants = measure_variants(lx, code, llr, bits, its, stream, args, pk)
             variants["mixed_batch"] = measure_mixed(lx, stream, args)
+            variants["sweep_256qam"] = measure_sweep(lx, code, pk)
         e2e = measure_e2e(lx, code, y, info, n0, dec, stream, args, dev)
         cpu = None if (world > 1 or args.no_cpu) else cpu_baseline(args.cpu_seconds)
         result = {
@@ -380,6 +381,41 @@ def measure_variants(lx, code, llr, bits, its, stream, args, pk):
         os.remove(cache)
     except OSError:
         pass
+    return out
+
+
+def measure_sweep(lx, code, pk):
+    """Graph-captured Monte-Carlo sweep: 256-QAM, max-log demapper, layered min-sum (20 iterations, no early
+    stop), 16384 codewords per launch, Eb/N0 from 0 dB in 0.25 dB steps until a point's BER < 1e-6; FP16 and
+    6-bit messages on the same codewords and noise draws. Reports the whole-sweep throughput (chain of every
+    point), the decoder's HBM fraction over the sweep time and the Eb/N0 at BER 1e-4 of each format."""
+    import torch
+    from paper_2203_11854_gb300 import ber
+    grid = [0.25 * i for i in range(57)]  # 0 .. 14 dB
+    batch = 16384
+    out = {"modulation": "256-QAM", "codewords_per_launch": batch, "step_db": 0.25}
+    for name, prec in (("fp16", lx.MSG_F16), ("fix6", lx.MSG_FIX6)):
+        kw = dict(m=8, demap_method=lx.DEMAP_MAXLOG, algo=lx.LAYERED_MINSUM, iters=ITERS, msg_prec=prec,
+                  offset=OFFSET, clamp=CLAMP, seed=SEED, cw0=1 << 36, batch=batch, max_batches=1, stop_ber=1e-6,
+                  use_graph=True)
+        ws = torch.empty(lx.sim_workspace(code, grid, **kw), dtype=torch.uint8, device="cuda")
+        lx.sim_run(code, grid[:1], ws=ws, **kw)  # warm-up: graph capture, first-touch
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        pts = lx.sim_run(code, grid, ws=ws, **kw)
+        torch.cuda.synchronize()
+        sec = time.perf_counter() - t0
+        _, msg_cw = lx.ldpc_bp_msg_format(code, algo=lx.LAYERED_MINSUM, iters=ITERS, msg_prec=prec)
+        cws = sum(q["blocks"] for q in pts)
+        dec_bytes = cws * (msg_cw * 2 * (ITERS - 1) + 4 * code.n_tx + code.k / 8)
+        curve = [(q["ebn0_db"], q["bit_errors"] / q["bits"]) for q in pts]
+        out[name] = {"points": len(pts), "codewords": cws, "seconds": sec,
+                     "gbps": cws * code.k / sec / 1e9,
+                     "hbm_frac": dec_bytes / sec / 1e9 / pk["hbm_gbs"],
+                     "ebn0_at_1e-4_db": ber.crossing(curve), "last_point": [curve[-1][0], curve[-1][1]]}
+        del ws
+    c16, c6 = out["fp16"]["ebn0_at_1e-4_db"], out["fix6"]["ebn0_at_1e-4_db"]
+    out["fix6_minus_fp16_db_at_1e-4"] = None if c16 is None or c6 is None else c6 - c16
     return out
 
 
