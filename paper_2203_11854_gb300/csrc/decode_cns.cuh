@@ -291,9 +291,13 @@ __host__ __device__ inline size_t cns_smem_bytes(const Params &p) {
     return smem_bytes(p, 1) + sizeof(int32_t) * p.rows + sizeof(int2) * p.nnz + 8;
 }
 
+// Check-node-state layered min-sum of the G codewords cw_base .. cw_base+G-1
+// of p by the whole CTA, the schedule read from the row table. The state of
+// codeword cw lives at msg + (cw - msg_cw0) * msg_stride * msg_size
+// (msg_cw0 = 0: one slot per codeword of the batch; msg_cw0 = cw_base: one
+// slot per codeword of the tile, as in the persistent mixed-batch kernel).
 template <int DMAX, int PREC, int ZC = 0>
-__global__ void __launch_bounds__(kMaxThreads, 2) k_layered_cns(const Params p) {
-    extern __shared__ __align__(16) unsigned char smem[];
+__device__ __forceinline__ void cns_tile(const Params &p, int64_t cw_base, int64_t msg_cw0, unsigned char *smem) {
     const int ZV = ZC ? ZC : p.Z;
     float *s_app_all = reinterpret_cast<float *>(smem);
     uint32_t *s_vb = reinterpret_cast<uint32_t *>(s_app_all + (size_t)p.G * p.n);
@@ -303,7 +307,6 @@ __global__ void __launch_bounds__(kMaxThreads, 2) k_layered_cns(const Params p) 
     int2 *s_at = reinterpret_cast<int2 *>((reinterpret_cast<uintptr_t>(s_soff + p.rows) + 7) & ~(uintptr_t)7);
 
     load_tables(p, s_vb, s_rp);
-    const int64_t cw_base = (int64_t)blockIdx.x * p.G;
     load_channel(p, s_app_all, cw_base);
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -322,7 +325,8 @@ __global__ void __launch_bounds__(kMaxThreads, 2) k_layered_cns(const Params p) 
     const int64_t cw = cw_base + g;
     const bool active = g < p.G && cw < p.B;
     float *app = s_app_all + (size_t)(active ? g : 0) * p.n;
-    unsigned char *st = reinterpret_cast<unsigned char *>(p.msg) + (active ? cw : 0) * p.msg_stride * p.msg_size;
+    unsigned char *st =
+        reinterpret_cast<unsigned char *>(p.msg) + (active ? cw - msg_cw0 : 0) * p.msg_stride * p.msg_size;
     bool done = !active;
     int iters_run = 0;
     __syncthreads();
@@ -354,6 +358,12 @@ __global__ void __launch_bounds__(kMaxThreads, 2) k_layered_cns(const Params p) 
     }
     __syncthreads();
     write_outputs(p, s_app_all, cw_base, iters_run, g, active, z);
+}
+
+template <int DMAX, int PREC, int ZC = 0>
+__global__ void __launch_bounds__(kMaxThreads, 2) k_layered_cns(const Params p) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    cns_tile<DMAX, PREC, ZC>(p, (int64_t)blockIdx.x * p.G, 0, smem);
 }
 
 KernelFn layered_cns_kernel(int dmax, int prec, int Z);

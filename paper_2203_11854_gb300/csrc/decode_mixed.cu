@@ -1,13 +1,14 @@
 // Mixed-size batch in one persistent launch: resident CTAs pull work items
 // (up to G codewords of one code) from a device queue, longest first, and run
-// the layered tile of decode_kernels.cuh on each. Message scratch is one slot
-// per resident CTA, sized for the largest item.
+// a layered tile on each: the check-node-state tile (decode_cns.cuh) for
+// min-sum, the per-edge tile (decode_kernels.cuh) otherwise. Message scratch
+// is one slot per resident CTA, sized for the largest item.
 #include <math.h>
 
 #include <algorithm>
 #include <vector>
 
-#include "decode_kernels.cuh"
+#include "decode_cns.cuh"
 
 namespace ldpcx {
 namespace {
@@ -18,6 +19,7 @@ struct GroupDesc {
     const uint32_t *blk;
     const int32_t *row_ptr;
     int Z, rows, nnz, n, k, n_tx, p0, G;
+    int cns;  // min-sum with check-node state in the message slot
     int64_t B, stride;
     const float *llr;
     float *llr_out;
@@ -41,6 +43,7 @@ struct MixedParams {
     int iters, early_stop;
     float offset, clamp, phi_lo;
     unsigned int *status;
+    unsigned k_one, k_two, k_four, k_two22, k_two31;  // as Params (opaque integer constants)
 };
 
 template <int DMAX, int ALGO, int PREC>
@@ -80,7 +83,18 @@ __global__ void __launch_bounds__(kMaxThreads, 2) k_mixed(const MixedParams m) {
         p.pf_dist = 0;
         p.msg_size = PREC == kF32 ? 4 : PREC == kF16 ? 2 : 1;
         p.status = m.status;
-        layered_tile<DMAX, ALGO, PREC, 1>(p, item.cw_base, item.cw_base, smem);
+        p.k_one = m.k_one;
+        p.k_two = m.k_two;
+        p.k_four = m.k_four;
+        p.k_two22 = m.k_two22;
+        p.k_two31 = m.k_two31;
+        p.k_neg4z = (unsigned)(-4 * gd.Z) * m.k_one;
+        if constexpr (ALGO == kMinSum) {
+            if (gd.cns) cns_tile<DMAX, PREC, 0>(p, item.cw_base, item.cw_base, smem);
+            else layered_tile<DMAX, ALGO, PREC, 1>(p, item.cw_base, item.cw_base, smem);
+        } else {
+            layered_tile<DMAX, ALGO, PREC, 1>(p, item.cw_base, item.cw_base, smem);
+        }
         __syncthreads();  // every thread has read s_item before it is overwritten
     }
 }
@@ -122,6 +136,21 @@ size_t tile_smem(const ldpcx_code *c, int G) {
            2 * sizeof(int) * G;
 }
 
+// Shared memory of the check-node-state tile: the per-edge tile's plus the
+// row slot offsets and the {offset, wrap} block table (cns_smem_bytes).
+size_t cns_tile_smem(const ldpcx_code *c, int G) {
+    return tile_smem(c, G) + sizeof(int32_t) * c->rows + sizeof(int2) * c->nnz + 8;
+}
+
+// Check-node state of a codeword fits its per-edge message slot.
+bool cns_fits(const ldpcx_code *c, int prec, int64_t slot_bytes) {
+    const int32_t *rp = c->row_ptr.data();
+    const int64_t b = prec == kF32   ? cns_bytes_per_cw<kF32>(rp, c->rows, c->Z)
+                      : prec == kF16 ? cns_bytes_per_cw<kF16>(rp, c->rows, c->Z)
+                                     : cns_bytes_per_cw<kFix6>(rp, c->rows, c->Z);
+    return b <= slot_bytes;
+}
+
 struct Plan {
     size_t off_groups, off_items, off_scratch, total, slot_bytes, smem;
     int n_items, grid, dmax;
@@ -145,7 +174,9 @@ int plan(const ldpcx_batch_group *groups, int n_groups, const ldpcx_decode_opts 
         const int G = group_G(g.code);
         pl->n_items += (int)((g.B + G - 1) / G);
         pl->slot_bytes = std::max(pl->slot_bytes, (size_t)G * (size_t)stride_of(g.code) * msgb);
-        pl->smem = std::max(pl->smem, tile_smem(g.code, G));
+        const bool cns = o->algo == LDPCX_LAYERED_MINSUM &&
+                         cns_fits(g.code, o->msg_prec, stride_of(g.code) * (int64_t)msgb);
+        pl->smem = std::max(pl->smem, cns ? cns_tile_smem(g.code, G) : tile_smem(g.code, G));
         pl->dmax = std::max(pl->dmax, g.code->max_deg);
     }
     if (pl->smem + 64 > 227 * 1024) return LDPCX_E_UNSUPPORTED;  // + the kernel's static queue slot
@@ -209,6 +240,10 @@ extern "C" int ldpc_bp_decode_mixed(const ldpcx_batch_group *groups, int n_group
         gd.G = group_G(c);
         gd.B = g.B;
         gd.stride = stride_of(c);
+        gd.cns = o->algo == LDPCX_LAYERED_MINSUM &&
+                 cns_fits(c, o->msg_prec, gd.stride * (int64_t)(o->msg_prec == LDPCX_MSG_F32   ? 4
+                                                                : o->msg_prec == LDPCX_MSG_F16 ? 2
+                                                                                               : 1));
         gd.llr = g.llr_ch;
         gd.llr_out = g.llr_out;
         gd.bits = g.bits_out;
@@ -247,6 +282,11 @@ extern "C" int ldpc_bp_decode_mixed(const ldpcx_batch_group *groups, int n_group
     m.clamp = o->clamp;
     m.phi_lo = (float)log1p(2.0 / expm1((double)o->clamp));
     m.status = status;
+    m.k_one = 1u;
+    m.k_two = 2u;
+    m.k_four = 4u;
+    m.k_two22 = 1u << 22;
+    m.k_two31 = 1u << 31;
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem) != cudaSuccess)
         return LDPCX_E_CUDA;
     fn<<<(unsigned)pl.grid, kMaxThreads, pl.smem, s>>>(m);
