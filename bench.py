@@ -346,11 +346,14 @@ def measure_variants(lx, code, llr, bits, its, stream, args, pk):
     out = {}
     reps = max(3, min(args.steps, 10))
     cache = f"/tmp/ldpcx_autotune_{os.getpid()}.json"
-    for name, algo, prec, s_msg in [("minsum_f32", lx.LAYERED_MINSUM, lx.MSG_F32, 4),
-                                    ("minsum_f16", lx.LAYERED_MINSUM, lx.MSG_F16, 2),
-                                    ("minsum_fix6", lx.LAYERED_MINSUM, lx.MSG_FIX6, 1),
-                                    ("spa_f32", lx.LAYERED_SPA, lx.MSG_F32, 4),
-                                    ("spa_f16", lx.LAYERED_SPA, lx.MSG_F16, 2)]:
+    for name, algo, prec, cns in [("minsum_f32", lx.LAYERED_MINSUM, lx.MSG_F32, 1),
+                                  ("minsum_f16", lx.LAYERED_MINSUM, lx.MSG_F16, 1),
+                                  ("minsum_fix6", lx.LAYERED_MINSUM, lx.MSG_FIX6, 1),
+                                  ("minsum_f32_per_edge", lx.LAYERED_MINSUM, lx.MSG_F32, 0),
+                                  ("minsum_f16_per_edge", lx.LAYERED_MINSUM, lx.MSG_F16, 0),
+                                  ("spa_f32", lx.LAYERED_SPA, lx.MSG_F32, 1),
+                                  ("spa_f16", lx.LAYERED_SPA, lx.MSG_F16, 1)]:
+        lx.ldpcx_tune_set(lx.TUNE_CN_STATE, cns)
         dec = dict(algo=algo, iters=ITERS, msg_prec=prec, offset=OFFSET, clamp=CLAMP)
         tuned = autotune.tune(code, B=1024, algo=algo, msg_prec=prec, iters=ITERS, cache_path=cache)["best"]
         autotune.apply(code, algo=algo, msg_prec=prec, iters=ITERS, cache_path=cache)
@@ -365,18 +368,26 @@ def measure_variants(lx, code, llr, bits, its, stream, args, pk):
         b.record(stream)
         torch.cuda.synchronize()
         ms = a.elapsed_time(b) / reps
-        cns, msg_cw = lx.ldpc_bp_msg_format(code, algo=algo, iters=ITERS, msg_prec=prec)
+        cn_state, msg_cw = lx.ldpc_bp_msg_format(code, algo=algo, iters=ITERS, msg_prec=prec)
         alg = B * (msg_cw * 2 * (ITERS - 1) + 4 * code.n_tx + code.k / 8)
         out[name] = {"decode_ms": ms, "gbps": B * code.k / (ms * 1e-3) / 1e9,
                      "edge_updates_per_s": B * code.edges * ITERS / (ms * 1e-3),
                      "hbm_frac": alg / (ms * 1e-3) / 1e9 / pk["hbm_gbs"],
-                     "message_format": "check-node state" if cns else "per-edge messages",
-                     "knobs": {"l2_prefetch": tuned["l2_prefetch"], "cw_per_cta": tuned["cw_per_cta"]}}
-        lx.ldpcx_tune_set(lx.TUNE_L2_PREFETCH, 0)
-        lx.ldpcx_tune_set(lx.TUNE_CW_PER_CTA, 0)
+                     "message_format": "check-node state" if cn_state else "per-edge messages",
+                     "knobs": {k: tuned[k] for k in ("l2_prefetch", "cw_per_cta", "zpt")}}
+        if algo == lx.LAYERED_SPA:
+            # three MUFU operations (2^x, 1/x, log2) per phi, two phi per edge update; nominal 16 MUFU
+            # results per clock per SM (4 per sub-partition) at the 2070 MHz maximum SM clock
+            mufu_peak = 16 * torch.cuda.get_device_properties(0).multi_processor_count * 2.07e9
+            out[name]["mufu_frac"] = 6 * B * code.edges * ITERS / (ms * 1e-3) / mufu_peak
+        for key in (lx.TUNE_L2_PREFETCH, lx.TUNE_CW_PER_CTA, lx.TUNE_ZPT):
+            lx.ldpcx_tune_set(key, 0)
         del ws
+    lx.ldpcx_tune_set(lx.TUNE_CN_STATE, 1)
     if "minsum_f32" in out and "minsum_f16" in out:
         out["f16_over_f32"] = out["minsum_f32"]["decode_ms"] / out["minsum_f16"]["decode_ms"]
+        out["f16_over_f32_per_edge_plain_path"] = (out["minsum_f32_per_edge"]["decode_ms"]
+                                                   / out["minsum_f16"]["decode_ms"])
     try:
         os.remove(cache)
     except OSError:

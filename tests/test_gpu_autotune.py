@@ -16,12 +16,16 @@ def test_tune_cache_apply(tmp_path):
     for bg, Z, prec in [(2, 64, lx.MSG_F16), (1, 384, lx.MSG_F32)]:
         code = lx.qc_ldpc_build(bg, Z, punct_cols=2 if bg == 1 else 0)
         res = autotune.tune(code, B=256, algo=lx.LAYERED_MINSUM, msg_prec=prec, iters=8, cache_path=cache)
-        assert len(res["timings"]) >= 4 and res["best"]["ms"] > 0
+        assert len(res["timings"]) >= 2 and res["best"]["ms"] > 0
+        # check-node state: one and two check nodes per thread are both candidates
+        assert {t["zpt"] for t in res["timings"]} == {0, 2}
         assert lx.ldpcx_tune_get(lx.TUNE_L2_PREFETCH) == 0 and lx.ldpcx_tune_get(lx.TUNE_CW_PER_CTA) == 0
+        assert lx.ldpcx_tune_get(lx.TUNE_ZPT) == 0
         best = autotune.apply(code, algo=lx.LAYERED_MINSUM, msg_prec=prec, iters=8, cache_path=cache)
         assert best is not None
         assert lx.ldpcx_tune_get(lx.TUNE_L2_PREFETCH) == best["l2_prefetch"]
         assert lx.ldpcx_tune_get(lx.TUNE_CW_PER_CTA) == best["cw_per_cta"]
-        lx.ldpcx_tune_set(lx.TUNE_L2_PREFETCH, 0)
-        lx.ldpcx_tune_set(lx.TUNE_CW_PER_CTA, 0)
+        assert lx.ldpcx_tune_get(lx.TUNE_ZPT) == best["zpt"]
+        for key in (lx.TUNE_L2_PREFETCH, lx.TUNE_CW_PER_CTA, lx.TUNE_ZPT):
+            lx.ldpcx_tune_set(key, 0)
     assert len(json.load(open(cache))) == 2
