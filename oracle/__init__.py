@@ -83,6 +83,10 @@ def lib():
             L.orc_n0_from_ebn0.argtypes = [C.c_double, C.c_int, C.c_int, C.c_int]
             L.orc_n0_from_ebn0.restype = C.c_double
             L.orc_demap.argtypes = [_f64p, C.c_int64, C.c_int, C.c_int, _f64p, C.c_int, C.c_double, _f64p]
+            L.orc_demap_prior.argtypes = [_f64p, C.c_int64, C.c_int, C.c_int, _f64p, C.c_int, C.c_double,
+                                          C.c_void_p, C.c_int, _f64p]
+            L.orc_apriori.argtypes = [_u8p, C.c_int64, C.c_int64, C.c_double, C.c_uint64, C.c_uint64, _f64p]
+            L.orc_apriori.restype = None
             L.orc_place_llr.argtypes = [_f64p, C.c_int64, C.c_int, C.c_int, C.c_int, _f64p]
             L.orc_to_half.argtypes = [C.c_double]
             L.orc_to_half.restype = C.c_double
@@ -264,6 +268,28 @@ def demap(y: np.ndarray, m: int, N0, method: int = DEMAP_EXACT, clamp: float = 2
     llr = np.zeros((B, S * m), dtype=np.float64)
     _check(lib().orc_demap(y.reshape(-1), B, S, m, n0, method, clamp, llr.reshape(-1)), "demap")
     return llr
+
+
+def demap_prior(y: np.ndarray, m: int, N0, prior=None, method: int = DEMAP_EXACT, clamp: float = 20.0,
+                mode: int = 1) -> np.ndarray:
+    """Demapper with a-priori LLRs (mode 0: a-posteriori, 1: extrinsic), full 2-D FP64 sums."""
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    B, S = y.shape[0], y.shape[1]
+    n0 = np.broadcast_to(np.asarray(N0, dtype=np.float64), (B,)).copy()
+    llr = np.zeros((B, S * m), dtype=np.float64)
+    pr = None if prior is None else np.ascontiguousarray(prior, dtype=np.float64).reshape(-1)
+    _check(lib().orc_demap_prior(y.reshape(-1), B, S, m, n0, method, clamp,
+                                 None if pr is None else pr.ctypes.data, mode, llr.reshape(-1)), "demap_prior")
+    return llr
+
+
+def apriori(bits: np.ndarray, sigma: float, seed: int, cw0: int) -> np.ndarray:
+    """Consistent Gaussian a-priori LLRs of the unpacked bits [B, N] (Philox stream 2)."""
+    bits = np.ascontiguousarray(bits, dtype=np.uint8)
+    B, N = bits.shape
+    out = np.zeros((B, N), dtype=np.float64)
+    lib().orc_apriori(bits.reshape(-1), B, N, float(sigma), seed, cw0, out.reshape(-1))
+    return out
 
 
 def place_llr(llr_tx: np.ndarray, p0: int, n: int) -> np.ndarray:

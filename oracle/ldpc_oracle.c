@@ -502,6 +502,94 @@ int orc_demap(const double *y, int64_t B, int S, int m, const double *N0, int me
     return ORC_OK;
 }
 
+/* ------------------------------------------------------------------------- */
+/* Demapper with prior (feature list of Section III: "Demapper with prior").  */
+/* With a-priori LLRs La_j = ln P(b_j=0)/P(b_j=1), the prior of point x is     */
+/* prod_j P(b_j(x)), and ln P(b_j) = (1 - 2 b_j) La_j / 2 - ln(e^{La_j/2} +    */
+/* e^{-La_j/2}); the normaliser is the same for every x and cancels. So       */
+/*   APP_i = ln sum_{x: b_i=0} exp(m(x)) - ln sum_{x: b_i=1} exp(m(x)),        */
+/*   m(x) = -|y-x|^2/N0 + sum_j (1 - 2 b_j(x)) La_j / 2,                       */
+/* and the extrinsic value is the same ratio with the j = i term left out of  */
+/* m(x) (computed as such here, not as APP_i - La_i).  Full 2-D sums over the */
+/* 2^m points; max-log replaces each log-sum-exp by its largest term.         */
+/* prior: [B][S*m] (NULL = zero); mode 0 = APP, 1 = extrinsic.                */
+/* ------------------------------------------------------------------------- */
+int orc_demap_prior(const double *y, int64_t B, int S, int m, const double *N0, int method, double clamp,
+                    const double *prior, int mode, double *llr)
+{
+    int64_t b;
+    int P = 1 << m, h = m / 2, s, i, j, p;
+    double pts_re[256], pts_im[256];
+    uint8_t lab[256][8];
+    double sc = orc_qam_scale(m);
+    if (m != 1 && (m < 2 || m > 8 || (m & 1))) return ORC_E_INVAL;
+    if (mode != 0 && mode != 1) return ORC_E_INVAL;
+    for (p = 0; p < P; ++p) {
+        uint8_t bits[8], aI[4], aQ[4];
+        for (i = 0; i < m; ++i) bits[i] = (uint8_t)((p >> (m - 1 - i)) & 1);
+        for (i = 0; i < m; ++i) lab[p][i] = bits[i];
+        if (m == 1) { pts_re[p] = 1.0 - 2.0 * bits[0]; pts_im[p] = 0.0; continue; }
+        for (i = 0; i < h; ++i) { aI[i] = bits[2 * i]; aQ[i] = bits[2 * i + 1]; }
+        pts_re[p] = sc * pam_level(aI, h);
+        pts_im[p] = sc * pam_level(aQ, h);
+    }
+    for (b = 0; b < B; ++b) {
+        for (s = 0; s < S; ++s) {
+            double yr, yi, dist[256], v0[128], v1[128];
+            const double *la = prior ? prior + (b * S + s) * m : NULL;
+            if (m == 1) { yr = y[b * S + s]; yi = 0.0; }
+            else { yr = y[(b * S + s) * 2]; yi = y[(b * S + s) * 2 + 1]; }
+            for (p = 0; p < P; ++p) {
+                double dr = yr - pts_re[p], di = yi - pts_im[p];
+                dist[p] = -(dr * dr + di * di) / N0[b];
+            }
+            for (i = 0; i < m; ++i) {
+                int c0 = 0, c1 = 0;
+                double L;
+                for (p = 0; p < P; ++p) {
+                    double mt = dist[p];
+                    for (j = 0; j < m; ++j) {
+                        if (!la || (mode == 1 && j == i)) continue;
+                        mt += (lab[p][j] ? -0.5 : 0.5) * la[j];
+                    }
+                    if (lab[p][i]) v1[c1++] = mt;
+                    else v0[c0++] = mt;
+                }
+                L = lse_or_max(v0, c0, method) - lse_or_max(v1, c1, method);
+                if (L > clamp) L = clamp;
+                if (L < -clamp) L = -clamp;
+                llr[(b * S + s) * m + i] = L;
+            }
+        }
+    }
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------- */
+/* A-priori LLRs of the consistent Gaussian model used for EXIT charts (ten   */
+/* Brink, IEEE Trans. Commun. 2001): L = (sigma^2/2)(1 - 2c) + sigma g, g     */
+/* standard Gaussian by Box-Muller on Philox stream 2, block t/4, pairs       */
+/* (x0,x1) -> g[4q], g[4q+1] and (x2,x3) -> g[4q+2], g[4q+3] as orc_awgn.      */
+/* bits: [B][N] unpacked reference bits; out: [B][N].                          */
+/* ------------------------------------------------------------------------- */
+void orc_apriori(const uint8_t *bits, int64_t B, int64_t N, double sigma, uint64_t seed, uint64_t cw0, double *out)
+{
+    int64_t b, t;
+    double mu = 0.5 * sigma * sigma;
+    for (b = 0; b < B; ++b) {
+        uint32_t blk[4];
+        double g[4];
+        for (t = 0; t < N; ++t) {
+            if ((t & 3) == 0) {
+                philox_block(seed, cw0 + (uint64_t)b, 2u, (uint32_t)(t >> 2), blk);
+                orc_gauss_pair(blk[0], blk[1], &g[0], &g[1]);
+                orc_gauss_pair(blk[2], blk[3], &g[2], &g[3]);
+            }
+            out[b * N + t] = (bits[b * N + t] ? -mu : mu) + sigma * g[t & 3];
+        }
+    }
+}
+
 /* Puncturing / truncation: the decoder input has n positions; position v gets
  * the transmitted LLR v - p0 when p0 <= v < p0 + n_tx, else 0 (no information). */
 void orc_place_llr(const double *llr_tx, int64_t B, int n_tx, int p0, int n, double *llr)
