@@ -353,6 +353,58 @@ int ldpc_bp_backward(ldpcx_code_t code, const float *llr_ch, int64_t B, const ld
 int sim_count(const uint32_t *ref, const uint32_t *hat, const int32_t *iters, int64_t B, int k,
               int64_t *counts, void *stream);
 
+/* ------------------------- demapper with prior, EXIT charts (next row 1) */
+/* The feature list of the paper names a demapper with prior and EXIT chart
+ * simulations (Section III, list of FEC features). These entry points close
+ * the bit-interleaved coded modulation loop with iterative demapping and
+ * decoding (BICM-ID) and measure extrinsic information transfer.
+ *
+ * sim_codewords: the codewords sim_tx transmits for the same (code, seed, cw0,
+ * B) -- same source bits, same encoder -- packed into cw_out (device)
+ * [B][ceil(n/32)]: bit v of codeword b is bit (v mod 32) of word v/32 (all n
+ * positions, punctured and untransmitted ones included). */
+int sim_codewords(ldpcx_code_t code, uint64_t seed, uint64_t cw0, int64_t B, uint32_t *cw_out, void *stream);
+
+/* demap_app with a-priori LLRs La (same layout as llr_out; NULL = all zero).
+ * With label bits b_j(x) of point x, the metric of x is
+ *   -|y-x|^2/N0 + sum_j (1 - 2 b_j(x)) La_j / 2
+ * (log prior of x up to a constant, L = ln P(b=0)/P(b=1)), and
+ *   out = LDPCX_DEMAP_OUT_APP:       LSE_{b_i=0} - LSE_{b_i=1} of the metric
+ *         LDPCX_DEMAP_OUT_EXTRINSIC: the same with bit i's own prior term
+ *                                    left out (= APP - La_i)
+ * (max instead of LSE for LDPCX_DEMAP_MAXLOG), per I/Q dimension (exact for
+ * Gray square QAM: the prior and distance terms of the other dimension
+ * cancel), clamped to [-clamp, clamp]. Arguments as demap_app. */
+#define LDPCX_DEMAP_OUT_APP 0
+#define LDPCX_DEMAP_OUT_EXTRINSIC 1
+int demap_app_prior(const float *y, const float *no, int64_t no_stride, int64_t B, int64_t syms_per_cw, int m,
+                    int method, float clamp, const float *llr_prior, int out_mode, float *llr_out, void *stream);
+
+/* A-priori LLRs of the consistent Gaussian model of EXIT analysis:
+ *   L = (sigma^2 / 2)(1 - 2 c) + sigma g,
+ * c = bit (bit_off + t) of the packed row bits[b * bits_stride + ...] (words,
+ * bit order as sim_codewords), g standard Gaussian by Box-Muller from Philox
+ * stream 2 with key (seed) and counter (t/4, (cw0 + b) lo32, hi32, 2), words
+ * as in sim_tx (Gaussian t uses block t/4: (x0,x1) for t mod 4 in {0,1},
+ * (x2,x3) for {2,3}). out (device) [B][N] float. sigma >= 0. */
+int llr_apriori(const uint32_t *bits, int64_t bits_stride, int64_t bit_off, int64_t B, int64_t N, float sigma,
+                uint64_t seed, uint64_t cw0, float *out, void *stream);
+
+/* Mutual information estimate between bits and LLRs (time average, valid
+ * for consistent LLRs): acc[0] += sum over b, t of log2(1 + exp(-(1 - 2c) L)),
+ * acc[1] += B N, so that I = 1 - acc[0] / acc[1]. llr (device) [B][N]; bits
+ * as llr_apriori; acc (device) double[2], accumulated (float64 atomics: the
+ * summation order is not fixed). */
+int llr_mutual_info(const float *llr, int64_t B, int64_t N, const uint32_t *bits, int64_t bits_stride,
+                    int64_t bit_off, double *acc, void *stream);
+
+/* Extrinsic LLRs of a decode on the transmitted positions:
+ *   out[b][t] = app[b][p0 + t] - llr_in[b][t],  t < n_tx,
+ * app (device) [B][n] from ldpc_bp_decode's llr_out, llr_in (device) [B][n_tx]
+ * its channel input, out (device) [B][n_tx], clamped to [-clamp, clamp]. */
+int ldpc_extrinsic(ldpcx_code_t code, const float *app, const float *llr_in, int64_t B, float clamp, float *out,
+                   void *stream);
+
 /* -------------------------------------------------- Monte-Carlo run (a13) */
 /* A BER/BLER sweep over Eb/N0 points (the loop around Listing 1): for each
  * point, batches of `batch` codewords run sim_tx -> demap_app -> ldpc_bp_decode

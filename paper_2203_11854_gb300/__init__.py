@@ -19,7 +19,8 @@ __all__ = [
     "qc_ldpc_info", "qc_ldpc_base", "sim_tx", "demap_app", "ldpc_bp_workspace", "ldpc_bp_decode",
     "sim_count", "sim_workspace", "sim_run", "library_path", "load_library", "ldpcx_tune_set", "ldpcx_tune_get",
     "ldpc_bp_decode_noalloc", "ldpc_bp_msg_format", "ldpc_bp_mixed_workspace", "ldpc_bp_decode_mixed", "ldpc_bp_ckpt_bytes", "ldpc_bp_decode_ckpt", "ldpc_bp_backward_workspace",
-    "ldpc_bp_backward", "ldpcx_phi",
+    "ldpc_bp_backward", "ldpcx_phi", "sim_codewords", "demap_app_prior", "llr_apriori", "llr_mutual_info",
+    "ldpc_extrinsic", "DEMAP_OUT_APP", "DEMAP_OUT_EXTRINSIC",
     "LAYERED_MINSUM", "LAYERED_SPA", "FLOOD_MINSUM", "FLOOD_SPA", "MSG_F32", "MSG_F16", "MSG_FIX6",
     "DEMAP_EXACT", "DEMAP_MAXLOG",
 ]
@@ -27,6 +28,7 @@ __all__ = [
 LAYERED_MINSUM, LAYERED_SPA, FLOOD_MINSUM, FLOOD_SPA = 0, 1, 2, 3
 MSG_F32, MSG_F16, MSG_FIX6 = 0, 1, 2
 DEMAP_EXACT, DEMAP_MAXLOG = 0, 1
+DEMAP_OUT_APP, DEMAP_OUT_EXTRINSIC = 0, 1
 FLAG_NONFINITE, FLAG_TIMEOUT = 1, 2
 TUNE_L2_PREFETCH, TUNE_ZPT, TUNE_CW_PER_CTA, TUNE_SPECIALISED, TUNE_CN_STATE, TUNE_SCHEDULE = 1, 2, 3, 4, 5, 6
 
@@ -83,6 +85,11 @@ _SIGS = {
     "qc_ldpc_base": ([_vp, _vp, _i], _i),
     "sim_tx": ([_vp, _u64, _u64, _i64, _i, _vp, _i64, _vp, _vp, _vp], _i),
     "demap_app": ([_vp, _vp, _i64, _i64, _i64, _i, _i, _f, _vp, _vp], _i),
+    "sim_codewords": ([_vp, _u64, _u64, _i64, _vp, _vp], _i),
+    "demap_app_prior": ([_vp, _vp, _i64, _i64, _i64, _i, _i, _f, _vp, _i, _vp, _vp], _i),
+    "llr_apriori": ([_vp, _i64, _i64, _i64, _i64, _f, _u64, _u64, _vp, _vp], _i),
+    "llr_mutual_info": ([_vp, _i64, _i64, _vp, _i64, _i64, _vp, _vp], _i),
+    "ldpc_extrinsic": ([_vp, _vp, _vp, _i64, _f, _vp, _vp], _i),
     "ldpc_bp_workspace": ([_vp, _i64, C.POINTER(DecodeOpts), C.POINTER(_sz)], _i),
     "ldpc_bp_decode": ([_vp, _vp, _i64, C.POINTER(DecodeOpts), _vp, _vp, _vp, _vp, _sz, _vp], _i),
     "sim_count": ([_vp, _vp, _vp, _i64, _i, _vp, _vp], _i),
@@ -244,6 +251,75 @@ def demap_app(y, no, m: int, method: int = DEMAP_EXACT, clamp: float = 20.0, llr
     _check(load_library().demap_app(_ptr(y), _ptr(no), stride, B, S, m, method, clamp, _ptr(llr_out),
                                     _stream(stream)), "demap_app")
     return llr_out
+
+
+def demap_app_prior(y, no, m: int, prior=None, *, method: int = DEMAP_EXACT, clamp: float = 20.0,
+                    out_mode: int = DEMAP_OUT_EXTRINSIC, llr_out=None, stream=None):
+    """APP demapper with a-priori LLRs prior [B, S*m] (None = zero): a-posteriori (DEMAP_OUT_APP) or
+    extrinsic (DEMAP_OUT_EXTRINSIC) LLRs [B, S*m]."""
+    import torch
+    _cuda_f32(y, "y")
+    _cuda_f32(no, "no")
+    B, S = y.shape[0], y.shape[1]
+    if prior is not None:
+        _cuda_f32(prior, "prior")
+        assert prior.shape == (B, S * m)
+    if llr_out is None:
+        llr_out = torch.empty((B, S * m), dtype=torch.float32, device=y.device)
+    stride = 0 if no.numel() == 1 else 1
+    _check(load_library().demap_app_prior(_ptr(y), _ptr(no), stride, B, S, m, method, clamp,
+                                          None if prior is None else _ptr(prior), out_mode, _ptr(llr_out),
+                                          _stream(stream)), "demap_app_prior")
+    return llr_out
+
+
+def sim_codewords(code: "Code", seed: int, cw0: int, B: int, out=None, stream=None):
+    """The codewords sim_tx sends for (seed, cw0, B), packed: int32 [B, ceil(n/32)]."""
+    import torch
+    nw = (code.n + 31) // 32
+    if out is None:
+        out = torch.empty((B, nw), dtype=torch.int32, device="cuda")
+    _check(load_library().sim_codewords(code.handle, seed, cw0, B, _ptr(out), _stream(stream)), "sim_codewords")
+    return out
+
+
+def llr_apriori(bits, bit_off: int, N: int, sigma: float, *, seed: int = 0x1DBC, cw0: int = 0, out=None,
+                stream=None):
+    """Consistent Gaussian a-priori LLRs [B, N] of bits[:, bit_off : bit_off + N] (packed int32 rows)."""
+    import torch
+    B = bits.shape[0]
+    if out is None:
+        out = torch.empty((B, N), dtype=torch.float32, device=bits.device)
+    _check(load_library().llr_apriori(_ptr(bits), bits.shape[1], bit_off, B, N, sigma, seed, cw0, _ptr(out),
+                                      _stream(stream)), "llr_apriori")
+    return out
+
+
+def llr_mutual_info(llr, bits, bit_off: int = 0, acc=None, stream=None):
+    """Mutual information between the LLRs [B, N] and bits[:, bit_off : bit_off + N]; returns the float
+    (synchronises) unless an accumulator acc (CUDA float64 [2]) is given, which is then updated."""
+    import torch
+    B, N = llr.shape
+    own = acc is None
+    if own:
+        acc = torch.zeros(2, dtype=torch.float64, device=llr.device)
+    _check(load_library().llr_mutual_info(_ptr(llr), B, N, _ptr(bits), bits.shape[1], bit_off, _ptr(acc),
+                                          _stream(stream)), "llr_mutual_info")
+    if own:
+        a = acc.cpu().tolist()
+        return 1.0 - a[0] / a[1] if a[1] else float("nan")
+    return acc
+
+
+def ldpc_extrinsic(code: "Code", app, llr_in, *, clamp: float = 20.0, out=None, stream=None):
+    """Extrinsic LLRs [B, n_tx] = app[:, p0 : p0 + n_tx] - llr_in, clamped."""
+    import torch
+    B = llr_in.shape[0]
+    if out is None:
+        out = torch.empty((B, code.n_tx), dtype=torch.float32, device=llr_in.device)
+    _check(load_library().ldpc_extrinsic(code.handle, _ptr(app), _ptr(llr_in), B, clamp, _ptr(out),
+                                         _stream(stream)), "ldpc_extrinsic")
+    return out
 
 
 # --------------------------------------------------------------------------- decoder

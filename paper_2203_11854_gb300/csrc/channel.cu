@@ -22,6 +22,7 @@ struct TxParams {
     int64_t no_stride;
     float *y;            // [B][S][2] or [B][S]
     uint32_t *info;      // [B][kw] or null
+    uint32_t *cw_out;    // [B][ceil(n/32)] packed codeword bits or null
     int64_t B;
     int G;               // codewords per CTA
 };
@@ -121,6 +122,21 @@ __global__ void __launch_bounds__(kMaxThreads) k_tx(const TxParams p) {
         }
     }
     __syncthreads();
+
+    // the codewords themselves, packed 32 positions per word by warp ballots
+    if (p.cw_out) {
+        const int nw = (p.n + 31) >> 5;
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+        for (int w = warp; w < p.G * nw; w += nwarps) {
+            const int gg = w / nw, ww = w - gg * nw;
+            const int64_t cw = cw_base + gg;
+            const int pos = ww * 32 + lane;
+            const bool bit = cw < p.B && pos < p.n && s_c[(size_t)gg * p.n + pos] != 0;
+            const unsigned word = __ballot_sync(0xFFFFFFFFu, bit);
+            if (lane == 0 && cw < p.B) p.cw_out[cw * nw + ww] = word;
+        }
+    }
+    if (!p.y) return;  // codewords only: no barrier follows
 
     // a4 + a5: Gray mapping and AWGN (Philox stream 1)
     const int m = p.m, S = p.n_tx / m;
@@ -252,6 +268,158 @@ __global__ void __launch_bounds__(256) k_demap(const float *__restrict__ y, cons
     if (bad) latch(&g_status, LDPCX_FLAG_NONFINITE);
 }
 
+// ------------------------------------------------------ demapper with prior
+// demap_dim with a-priori LLRs la[0..H) of the dimension's bits: the metric of
+// level l gains sum_i (1 - 2 a_i(l)) la_i / 2. Extrinsic output leaves bit i's
+// own term out, which shifts the two sets of bit i by -la_i/2 and +la_i/2, so
+// it is the a-posteriori value minus la_i.
+template <int H>
+__device__ __forceinline__ void demap_dim_prior(float y, float inv_n0, float scale, int method, float clamp,
+                                                const float *la, int out_mode, float *out) {
+    constexpr int P = 1 << H;
+    float d[P];
+#pragma unroll
+    for (int l = 0; l < P; ++l) {
+        int inner = 1 - 2 * ((l >> 0) & 1);
+#pragma unroll
+        for (int i = H - 2; i >= 0; --i) inner = (1 - 2 * ((l >> (H - 1 - i)) & 1)) * ((1 << (H - 1 - i)) - inner);
+        const float e = y - (float)inner * scale;
+        float pr = 0.0f;
+#pragma unroll
+        for (int i = 0; i < H; ++i) pr += ((l >> (H - 1 - i)) & 1) ? -la[i] : la[i];
+        d[l] = fmaf(0.5f, pr, -(e * e) * inv_n0);
+    }
+#pragma unroll
+    for (int i = 0; i < H; ++i) {
+        const int bit = H - 1 - i;
+        float mx0 = -INFINITY, mx1 = -INFINITY;
+#pragma unroll
+        for (int l = 0; l < P; ++l) {
+            if ((l >> bit) & 1) mx1 = fmaxf(mx1, d[l]);
+            else mx0 = fmaxf(mx0, d[l]);
+        }
+        float L;
+        if (method == LDPCX_DEMAP_MAXLOG) {
+            L = mx0 - mx1;
+        } else {
+            float s0 = 0.0f, s1 = 0.0f;
+#pragma unroll
+            for (int l = 0; l < P; ++l) {
+                if ((l >> bit) & 1) s1 += expf(d[l] - mx1);
+                else s0 += expf(d[l] - mx0);
+            }
+            L = (mx0 - mx1) + (logf(s0) - logf(s1));
+        }
+        if (out_mode == LDPCX_DEMAP_OUT_EXTRINSIC) L -= la[i];
+        out[i] = fminf(fmaxf(L, -clamp), clamp);
+    }
+}
+
+template <int M>
+__global__ void __launch_bounds__(256) k_demap_prior(const float *__restrict__ y, const float *__restrict__ no,
+                                                     int64_t no_stride, int64_t B, int64_t S, int method, float clamp,
+                                                     float scale, const float *__restrict__ prior, int out_mode,
+                                                     float *__restrict__ llr) {
+    const int64_t total = B * S;
+    bool bad = false;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = i / S;
+        const float inv_n0 = 1.0f / no[b * no_stride];
+        if constexpr (M == 1) {
+            const float v = y[i], la = prior ? prior[i] : 0.0f;
+            float L = 4.0f * v * inv_n0;
+            if (!isfinite(v)) {
+                bad = true;
+                L = 0.0f;
+            }
+            if (out_mode == LDPCX_DEMAP_OUT_APP) L += la;
+            llr[i] = fminf(fmaxf(L, -clamp), clamp);
+        } else {
+            constexpr int H = M / 2;
+            const float2 v = reinterpret_cast<const float2 *>(y)[i];
+            float lai[H], laq[H], oi[H], oq[H];
+#pragma unroll
+            for (int j = 0; j < H; ++j) {
+                lai[j] = prior ? prior[i * M + 2 * j] : 0.0f;
+                laq[j] = prior ? prior[i * M + 2 * j + 1] : 0.0f;
+            }
+            if (isfinite(v.x) && isfinite(v.y)) {
+                demap_dim_prior<H>(v.x, inv_n0, scale, method, clamp, lai, out_mode, oi);
+                demap_dim_prior<H>(v.y, inv_n0, scale, method, clamp, laq, out_mode, oq);
+            } else {
+                bad = true;
+#pragma unroll
+                for (int j = 0; j < H; ++j) oi[j] = oq[j] = 0.0f;
+            }
+            float *o = llr + i * M;
+#pragma unroll
+            for (int j = 0; j < H; ++j) {
+                o[2 * j] = oi[j];
+                o[2 * j + 1] = oq[j];
+            }
+        }
+    }
+    if (bad) latch(&g_status, LDPCX_FLAG_NONFINITE);
+}
+
+// ------------------------------------------- EXIT: a-priori LLRs, information
+__device__ __forceinline__ unsigned bit_at(const uint32_t *row, int64_t v) {
+    return (row[v >> 5] >> (v & 31)) & 1u;
+}
+
+__global__ void __launch_bounds__(256) k_apriori(const uint32_t *__restrict__ bits, int64_t bits_stride,
+                                                 int64_t bit_off, int64_t B, int64_t N, float sigma, uint64_t seed,
+                                                 uint64_t cw0, float *__restrict__ out) {
+    const int64_t nq = (N + 3) >> 2;  // Philox blocks per row: four Gaussians each
+    const float mu = 0.5f * sigma * sigma;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < B * nq; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = i / nq, q = i - b * nq;
+        const uint4 x = draw(seed, cw0 + (uint64_t)b, 2u, (uint32_t)q);
+        const float2 g01 = box_muller(x.x, x.y), g23 = box_muller(x.z, x.w);
+        const float g[4] = {g01.x, g01.y, g23.x, g23.y};
+        const uint32_t *row = bits + b * bits_stride;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int64_t t = 4 * q + e;
+            if (t < N) out[b * N + t] = fmaf(sigma, g[e], bit_at(row, bit_off + t) ? -mu : mu);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_mutual_info(const float *__restrict__ llr, int64_t B, int64_t N,
+                                                     const uint32_t *__restrict__ bits, int64_t bits_stride,
+                                                     int64_t bit_off, double *acc) {
+    double sum = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < B * N; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = i / N, t = i - b * N;
+        const float L = llr[i];
+        const float x = bit_at(bits + b * bits_stride, bit_off + t) ? -L : L;  // (1 - 2c) L
+        // log2(1 + e^-x) = (max(-x, 0) + ln(1 + e^-|x|)) / ln 2, without overflow
+        sum += (double)(fmaxf(-x, 0.0f) + log1pf(expf(-fabsf(x)))) * 1.4426950408889634;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xFFFFFFFFu, sum, o);
+    __shared__ double s_part[8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) s_part[warp] = sum;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s_part[w];
+        atomicAdd(&acc[0], t);
+        if (blockIdx.x == 0) atomicAdd(&acc[1], (double)B * (double)N);
+    }
+}
+
+__global__ void __launch_bounds__(256) k_extrinsic(const float *__restrict__ app, const float *__restrict__ in,
+                                                   int64_t B, int n, int p0, int n_tx, float clamp,
+                                                   float *__restrict__ out) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < B * n_tx; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = i / n_tx, t = i - b * n_tx;
+        out[i] = fminf(fmaxf(app[b * n + p0 + t] - in[i], -clamp), clamp);
+    }
+}
+
 // ------------------------------------------------------------ error count
 __global__ void __launch_bounds__(256) k_count(const uint32_t *__restrict__ ref, const uint32_t *__restrict__ hat,
                                                const int32_t *__restrict__ iters, int64_t B, int k,
@@ -318,7 +486,8 @@ using namespace ldpcx;
 namespace ldpcx {
 
 int launch_tx(ldpcx_code_t c, uint64_t seed, uint64_t cw0, const uint64_t *cw0_dev, int64_t B, int m,
-              const float *no, int64_t no_stride, float *y_out, uint32_t *info_out, cudaStream_t stream) {
+              const float *no, int64_t no_stride, float *y_out, uint32_t *info_out, cudaStream_t stream,
+              uint32_t *cw_out) {
     DevCode d;
     int st = code_device(c, &d);
     if (st) return st;
@@ -341,6 +510,7 @@ int launch_tx(ldpcx_code_t c, uint64_t seed, uint64_t cw0, const uint64_t *cw0_d
     p.no_stride = no_stride;
     p.y = y_out;
     p.info = info_out;
+    p.cw_out = cw_out;
     p.B = B;
     int G = kMaxThreads / c->Z;
     if (G < 1) G = 1;
@@ -405,5 +575,78 @@ extern "C" int sim_count(const uint32_t *ref, const uint32_t *hat, const int32_t
     if (blocks > cap) blocks = cap;
     k_count<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(ref, hat, iters, B, k,
                                                                  reinterpret_cast<unsigned long long *>(counts));
+    return cuda_status(cudaGetLastError());
+}
+
+extern "C" int sim_codewords(ldpcx_code_t c, uint64_t seed, uint64_t cw0, int64_t B, uint32_t *cw_out,
+                             void *stream) {
+    if (!c || B < 0) return LDPCX_E_INVAL;
+    if (B == 0) return LDPCX_OK;
+    if (!cw_out) return LDPCX_E_INVAL;
+    return launch_tx(c, seed, cw0, nullptr, B, 2, nullptr, 0, nullptr, nullptr, (cudaStream_t)stream, cw_out);
+}
+
+extern "C" int demap_app_prior(const float *y, const float *no, int64_t no_stride, int64_t B, int64_t syms, int m,
+                               int method, float clamp, const float *prior, int out_mode, float *llr_out,
+                               void *stream) {
+    if (B < 0 || syms < 0 || !valid_m(m) || (no_stride != 0 && no_stride != 1)) return LDPCX_E_INVAL;
+    if (method != LDPCX_DEMAP_EXACT && method != LDPCX_DEMAP_MAXLOG) return LDPCX_E_INVAL;
+    if (out_mode != LDPCX_DEMAP_OUT_APP && out_mode != LDPCX_DEMAP_OUT_EXTRINSIC) return LDPCX_E_INVAL;
+    if (!(clamp > 0.0f)) return LDPCX_E_INVAL;
+    if (B == 0 || syms == 0) return LDPCX_OK;
+    if (!y || !no || !llr_out) return LDPCX_E_INVAL;
+    int64_t blocks = (B * syms + 255) / 256;
+    const int64_t cap = (int64_t)sm_count() * 8;
+    if (blocks > cap) blocks = cap;
+    cudaStream_t s = (cudaStream_t)stream;
+    const float sc = qam_scale(m);
+#define LDPCX_DP(MM) \
+    k_demap_prior<MM><<<(unsigned)blocks, 256, 0, s>>>(y, no, no_stride, B, syms, method, clamp, sc, prior, out_mode, llr_out)
+    switch (m) {
+        case 1: LDPCX_DP(1); break;
+        case 2: LDPCX_DP(2); break;
+        case 4: LDPCX_DP(4); break;
+        case 6: LDPCX_DP(6); break;
+        default: LDPCX_DP(8); break;
+    }
+#undef LDPCX_DP
+    return cuda_status(cudaGetLastError());
+}
+
+extern "C" int llr_apriori(const uint32_t *bits, int64_t bits_stride, int64_t bit_off, int64_t B, int64_t N,
+                           float sigma, uint64_t seed, uint64_t cw0, float *out, void *stream) {
+    if (B < 0 || N < 0 || bit_off < 0 || !(sigma >= 0.0f) || isinf(sigma)) return LDPCX_E_INVAL;
+    if (B == 0 || N == 0) return LDPCX_OK;
+    if (!bits || !out || bits_stride * 32 < bit_off + N) return LDPCX_E_INVAL;
+    int64_t blocks = (B * ((N + 3) >> 2) + 255) / 256;
+    const int64_t cap = (int64_t)sm_count() * 8;
+    if (blocks > cap) blocks = cap;
+    k_apriori<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(bits, bits_stride, bit_off, B, N, sigma, seed, cw0,
+                                                                  out);
+    return cuda_status(cudaGetLastError());
+}
+
+extern "C" int llr_mutual_info(const float *llr, int64_t B, int64_t N, const uint32_t *bits, int64_t bits_stride,
+                               int64_t bit_off, double *acc, void *stream) {
+    if (B < 0 || N < 0 || bit_off < 0 || !acc) return LDPCX_E_INVAL;
+    if (B == 0 || N == 0) return LDPCX_OK;
+    if (!llr || !bits || bits_stride * 32 < bit_off + N) return LDPCX_E_INVAL;
+    int64_t blocks = (B * N + 255) / 256;
+    const int64_t cap = (int64_t)sm_count() * 4;
+    if (blocks > cap) blocks = cap;
+    k_mutual_info<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(llr, B, N, bits, bits_stride, bit_off, acc);
+    return cuda_status(cudaGetLastError());
+}
+
+extern "C" int ldpc_extrinsic(ldpcx_code_t c, const float *app, const float *llr_in, int64_t B, float clamp,
+                              float *out, void *stream) {
+    if (!c || B < 0 || !(clamp > 0.0f)) return LDPCX_E_INVAL;
+    if (B == 0) return LDPCX_OK;
+    if (!app || !llr_in || !out) return LDPCX_E_INVAL;
+    int64_t blocks = (B * c->n_tx + 255) / 256;
+    const int64_t cap = (int64_t)sm_count() * 8;
+    if (blocks > cap) blocks = cap;
+    k_extrinsic<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(app, llr_in, B, c->n, c->p0, c->n_tx, clamp,
+                                                                    out);
     return cuda_status(cudaGetLastError());
 }
