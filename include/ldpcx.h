@@ -399,9 +399,11 @@ int llr_mutual_info(const float *llr, int64_t B, int64_t N, const uint32_t *bits
                     int64_t bit_off, double *acc, void *stream);
 
 /* Extrinsic LLRs of a decode on the transmitted positions:
- *   out[b][t] = app[b][p0 + t] - llr_in[b][t],  t < n_tx,
+ *   out[b][t] = app[b][p0 + t] - clip(llr_in[b][t]),  t < n_tx,
  * app (device) [B][n] from ldpc_bp_decode's llr_out, llr_in (device) [B][n_tx]
- * its channel input, out (device) [B][n_tx], clamped to [-clamp, clamp]. */
+ * its channel input, clip = clamping to [-clamp, clamp] as the decoder does
+ * with its input (pass the decode's clamp); out (device) [B][n_tx], clamped
+ * to [-clamp, clamp]. */
 int ldpc_extrinsic(ldpcx_code_t code, const float *app, const float *llr_in, int64_t B, float clamp, float *out,
                    void *stream);
 

@@ -312,7 +312,7 @@ def llr_mutual_info(llr, bits, bit_off: int = 0, acc=None, stream=None):
 
 
 def ldpc_extrinsic(code: "Code", app, llr_in, *, clamp: float = 20.0, out=None, stream=None):
-    """Extrinsic LLRs [B, n_tx] = app[:, p0 : p0 + n_tx] - llr_in, clamped."""
+    """Extrinsic LLRs [B, n_tx] = app[:, p0 : p0 + n_tx] - clip(llr_in), clipped to +-clamp (the decode's clamp)."""
     import torch
     B = llr_in.shape[0]
     if out is None:

@@ -416,7 +416,8 @@ __global__ void __launch_bounds__(256) k_extrinsic(const float *__restrict__ app
                                                    float *__restrict__ out) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < B * n_tx; i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t b = i / n_tx, t = i - b * n_tx;
-        out[i] = fminf(fmaxf(app[b * n + p0 + t] - in[i], -clamp), clamp);
+        const float x = fminf(fmaxf(in[i], -clamp), clamp);  // the input as the decoder clamped it
+        out[i] = fminf(fmaxf(app[b * n + p0 + t] - x, -clamp), clamp);
     }
 }
 

@@ -83,6 +83,12 @@ def test_extrinsic_is_output_minus_input(lx, orc):
     ext = lx.ldpc_extrinsic(code, app, L, clamp=1e4).cpu().numpy()
     ref = app.cpu().numpy()[:, code.p0:code.p0 + code.n_tx] - llr
     assert np.array_equal(ext, ref)
+    # inputs beyond the clamp: the decoder saw them clamped, and so does the subtraction
+    big = L * 30.0
+    app2, _, _ = lx.ldpc_bp_decode(code, big, iters=5, llr_out=True)
+    ext2 = lx.ldpc_extrinsic(code, app2, big, clamp=20.0).cpu().numpy()
+    ref2 = np.clip(app2.cpu().numpy()[:, code.p0:code.p0 + code.n_tx] - np.clip(llr * 30.0, -20, 20), -20, 20)
+    assert np.array_equal(ext2, ref2)
 
 
 def test_library_J_matches_oracle():
@@ -96,7 +102,7 @@ def test_library_J_matches_oracle():
 def test_exit_curves_and_bicm_id(lx):
     from paper_2203_11854_gb300 import exit as lexit
     code = lx.qc_ldpc_build(2, 64)
-    ia = [0.0, 0.2, 0.4, 0.6, 0.8, 0.95]
+    ia = [0.0, 0.2, 0.4, 0.6, 0.8, 0.95, 1.0]
     dec = lexit.decoder_curve(code, ia, B=128, iters=10)
     ie = [e for _, e in dec]
     # more a-priori information never gives less extrinsic information, and an informative input gives
