@@ -86,6 +86,8 @@ def lib():
             L.orc_demap_prior.argtypes = [_f64p, C.c_int64, C.c_int, C.c_int, _f64p, C.c_int, C.c_double,
                                           C.c_void_p, C.c_int, _f64p]
             L.orc_apriori.argtypes = [_u8p, C.c_int64, C.c_int64, C.c_double, C.c_uint64, C.c_uint64, _f64p]
+            L.orc_demap_points.argtypes = [_f64p, C.c_int64, C.c_int, C.c_int, _f64p, _f64p, C.c_int, C.c_double,
+                                           _f64p]
             L.orc_apriori.restype = None
             L.orc_place_llr.argtypes = [_f64p, C.c_int64, C.c_int, C.c_int, C.c_int, _f64p]
             L.orc_to_half.argtypes = [C.c_double]
@@ -281,6 +283,27 @@ def demap_prior(y: np.ndarray, m: int, N0, prior=None, method: int = DEMAP_EXACT
     _check(lib().orc_demap_prior(y.reshape(-1), B, S, m, n0, method, clamp,
                                  None if pr is None else pr.ctypes.data, mode, llr.reshape(-1)), "demap_prior")
     return llr
+
+
+def demap_points(y: np.ndarray, m: int, N0, points: np.ndarray, method: int = DEMAP_EXACT,
+                 clamp: float = 20.0) -> np.ndarray:
+    """APP demapper over the constellation points [2^m, 2] (label of point l = l, MSB first), y [B, S, 2]."""
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    B, S = y.shape[0], y.shape[1]
+    n0 = np.broadcast_to(np.asarray(N0, dtype=np.float64), (B,)).copy()
+    pts = np.ascontiguousarray(points, dtype=np.float64).reshape(-1)
+    llr = np.zeros((B, S * m), dtype=np.float64)
+    _check(lib().orc_demap_points(y.reshape(-1), B, S, m, n0, pts, method, clamp, llr.reshape(-1)),
+           "demap_points")
+    return llr
+
+
+def qam_points(m: int) -> np.ndarray:
+    """The Gray QAM of the mapper as points [2^m, 2], point l carrying label l (MSB first)."""
+    P = 1 << m
+    bits = ((np.arange(P)[:, None] >> (m - 1 - np.arange(m))[None, :]) & 1).astype(np.uint8)
+    x = map_bits(bits, m)
+    return np.ascontiguousarray(x[:, 0, :])
 
 
 def apriori(bits: np.ndarray, sigma: float, seed: int, cw0: int) -> np.ndarray:

@@ -566,6 +566,43 @@ int orc_demap_prior(const double *y, int64_t B, int S, int m, const double *N0, 
 }
 
 /* ------------------------------------------------------------------------- */
+/* APP demapper over an arbitrary constellation (Listing 2's trainable        */
+/* Constellation with the Demapper): point l = (pr[l], pi[l]) carries label  */
+/* bits b_j = (l >> (m-1-j)) & 1, and                                        */
+/*   L_i = ln sum_{l: b_i=0} exp(-|y-p_l|^2/N0) - ln sum_{l: b_i=1} exp(.)   */
+/* over all 2^m points (method 1: max-log).  y: [B][S][2]; out [B][S*m].     */
+/* ------------------------------------------------------------------------- */
+int orc_demap_points(const double *y, int64_t B, int S, int m, const double *N0, const double *pts, int method,
+                     double clamp, double *llr)
+{
+    int64_t b;
+    int P = 1 << m, s, i, p;
+    if (m < 1 || m > 8) return ORC_E_INVAL;
+    for (b = 0; b < B; ++b) {
+        for (s = 0; s < S; ++s) {
+            double yr = y[(b * S + s) * 2], yi = y[(b * S + s) * 2 + 1], metric[256], v0[128], v1[128];
+            for (p = 0; p < P; ++p) {
+                double dr = yr - pts[2 * p], di = yi - pts[2 * p + 1];
+                metric[p] = -(dr * dr + di * di) / N0[b];
+            }
+            for (i = 0; i < m; ++i) {
+                int c0 = 0, c1 = 0;
+                double L;
+                for (p = 0; p < P; ++p) {
+                    if ((p >> (m - 1 - i)) & 1) v1[c1++] = metric[p];
+                    else v0[c0++] = metric[p];
+                }
+                L = lse_or_max(v0, c0, method) - lse_or_max(v1, c1, method);
+                if (L > clamp) L = clamp;
+                if (L < -clamp) L = -clamp;
+                llr[(b * S + s) * m + i] = L;
+            }
+        }
+    }
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------- */
 /* A-priori LLRs of the consistent Gaussian model used for EXIT charts (ten   */
 /* Brink, IEEE Trans. Commun. 2001): L = (sigma^2/2)(1 - 2c) + sigma g, g     */
 /* standard Gaussian by Box-Muller on Philox stream 2, block t/4, pairs       */
