@@ -407,6 +407,52 @@ int llr_mutual_info(const float *llr, int64_t B, int64_t N, const uint32_t *bits
 int ldpc_extrinsic(ldpcx_code_t code, const float *app, const float *llr_in, int64_t B, float clamp, float *out,
                    void *stream);
 
+/* --------------- trainable constellation, end-to-end gradients (next row 3) */
+/* Listing 2 of the paper makes the constellation trainable and learns it
+ * end to end through mapper, AWGN and demapper with a binary cross-entropy
+ * loss. These entry points run that chain and its adjoint with a constellation
+ * given as 2^m complex points: point l has label bits b_j = (l >> (m-1-j)) & 1
+ * (b_0 the most significant; the Gray QAM of sim_tx puts its point with label
+ * l there). m in {2, 4, 6, 8}; points (device) [2^m][2] float (re, im), used as
+ * given (normalise them to the wanted energy first).
+ *
+ * sim_tx_points: sim_tx with the constellation `points` -- same source bits,
+ * encoder and AWGN draws; symbol s of codeword b carries the transmitted bits
+ * p0 + s m .. p0 + s m + m - 1 as its label. cw_out (device, or NULL) as
+ * sim_codewords. */
+int sim_tx_points(ldpcx_code_t code, uint64_t seed, uint64_t cw0, int64_t B, int m, const float *points,
+                  const float *no, int64_t no_stride, float *y_out, uint32_t *cw_out, void *stream);
+
+/* APP demapper over an arbitrary constellation (full 2-D sums, no
+ * separability): L_i = LSE_{l: b_i(l)=0}(-|y - p_l|^2/N0) - LSE_{b_i(l)=1}(.)
+ * (max for LDPCX_DEMAP_MAXLOG), clamped to [-clamp, clamp].
+ * y (device) [B][S][2]; llr_out (device) [B][S*m]. */
+int demap_points(const float *y, const float *no, int64_t no_stride, int64_t B, int64_t S, int m,
+                 const float *points, int method, float clamp, float *llr_out, void *stream);
+
+/* Adjoint of demap_points (exact method only) for the loss gradient
+ * grad_llr (device) [B][S*m]: writes grad_y (device) [B][S][2] and ADDS to
+ * grad_points (device) [2^m][2] (float atomics: the summation order is not
+ * fixed). Outputs at the clamp have zero derivative. */
+int demap_points_backward(const float *y, const float *no, int64_t no_stride, int64_t B, int64_t S, int m,
+                          const float *points, float clamp, const float *grad_llr, float *grad_y,
+                          float *grad_points, void *stream);
+
+/* Adjoint of the mapper of sim_tx_points: ADDS grad_x[b][s] (device
+ * [B][S][2], the gradient at the transmitted symbol; AWGN passes it
+ * unchanged) to grad_points[label of symbol (b, s)]. cw (device) packed
+ * codewords as sim_codewords; the labels are read from positions p0 + s m. */
+int map_points_backward(ldpcx_code_t code, const uint32_t *cw, int64_t B, int m, const float *grad_x,
+                        float *grad_points, void *stream);
+
+/* Binary cross-entropy of LLRs against bits (Listing 2's loss; with
+ * L = ln P0/P1 the logits are -L): loss_acc (device double[1]) +=
+ * sum_{b,t} ln(1 + exp(-(1 - 2c) L)); grad_llr (device [B][N], or NULL) =
+ * scale * d/dL of that sum = -scale (1 - 2c) / (1 + exp((1 - 2c) L)).
+ * bits, bits_stride, bit_off as llr_apriori. */
+int llr_bce(const float *llr, int64_t B, int64_t N, const uint32_t *bits, int64_t bits_stride, int64_t bit_off,
+            float scale, double *loss_acc, float *grad_llr, void *stream);
+
 /* -------------------------------------------------- Monte-Carlo run (a13) */
 /* A BER/BLER sweep over Eb/N0 points (the loop around Listing 1): for each
  * point, batches of `batch` codewords run sim_tx -> demap_app -> ldpc_bp_decode

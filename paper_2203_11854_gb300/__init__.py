@@ -20,7 +20,8 @@ __all__ = [
     "sim_count", "sim_workspace", "sim_run", "library_path", "load_library", "ldpcx_tune_set", "ldpcx_tune_get",
     "ldpc_bp_decode_noalloc", "ldpc_bp_msg_format", "ldpc_bp_mixed_workspace", "ldpc_bp_decode_mixed", "ldpc_bp_ckpt_bytes", "ldpc_bp_decode_ckpt", "ldpc_bp_backward_workspace",
     "ldpc_bp_backward", "ldpcx_phi", "sim_codewords", "demap_app_prior", "llr_apriori", "llr_mutual_info",
-    "ldpc_extrinsic", "DEMAP_OUT_APP", "DEMAP_OUT_EXTRINSIC",
+    "ldpc_extrinsic", "DEMAP_OUT_APP", "DEMAP_OUT_EXTRINSIC", "sim_tx_points", "demap_points",
+    "demap_points_backward", "map_points_backward", "llr_bce",
     "LAYERED_MINSUM", "LAYERED_SPA", "FLOOD_MINSUM", "FLOOD_SPA", "MSG_F32", "MSG_F16", "MSG_FIX6",
     "DEMAP_EXACT", "DEMAP_MAXLOG",
 ]
@@ -90,6 +91,11 @@ _SIGS = {
     "llr_apriori": ([_vp, _i64, _i64, _i64, _i64, _f, _u64, _u64, _vp, _vp], _i),
     "llr_mutual_info": ([_vp, _i64, _i64, _vp, _i64, _i64, _vp, _vp], _i),
     "ldpc_extrinsic": ([_vp, _vp, _vp, _i64, _f, _vp, _vp], _i),
+    "sim_tx_points": ([_vp, _u64, _u64, _i64, _i, _vp, _vp, _i64, _vp, _vp, _vp], _i),
+    "demap_points": ([_vp, _vp, _i64, _i64, _i64, _i, _vp, _i, _f, _vp, _vp], _i),
+    "demap_points_backward": ([_vp, _vp, _i64, _i64, _i64, _i, _vp, _f, _vp, _vp, _vp, _vp], _i),
+    "map_points_backward": ([_vp, _vp, _i64, _i, _vp, _vp, _vp], _i),
+    "llr_bce": ([_vp, _i64, _i64, _vp, _i64, _i64, _f, _vp, _vp, _vp], _i),
     "ldpc_bp_workspace": ([_vp, _i64, C.POINTER(DecodeOpts), C.POINTER(_sz)], _i),
     "ldpc_bp_decode": ([_vp, _vp, _i64, C.POINTER(DecodeOpts), _vp, _vp, _vp, _vp, _sz, _vp], _i),
     "sim_count": ([_vp, _vp, _vp, _i64, _i, _vp, _vp], _i),
@@ -320,6 +326,70 @@ def ldpc_extrinsic(code: "Code", app, llr_in, *, clamp: float = 20.0, out=None, 
     _check(load_library().ldpc_extrinsic(code.handle, _ptr(app), _ptr(llr_in), B, clamp, _ptr(out),
                                          _stream(stream)), "ldpc_extrinsic")
     return out
+
+
+def sim_tx_points(code: "Code", seed: int, cw0: int, B: int, m: int, points, no, y_out=None, cw_out=None,
+                  stream=None):
+    """sim_tx with the constellation points [2^m, 2] (CUDA float32, point l carries label l, MSB first).
+    Returns (y [B, S, 2], packed codewords [B, ceil(n/32)] or None)."""
+    import torch
+    _cuda_f32(points, "points")
+    _cuda_f32(no, "no")
+    S = code.n_tx // m
+    if y_out is None:
+        y_out = torch.empty((B, S, 2), dtype=torch.float32, device=points.device)
+    stride = 0 if no.numel() == 1 else 1
+    _check(load_library().sim_tx_points(code.handle, seed, cw0, B, m, _ptr(points), _ptr(no), stride, _ptr(y_out),
+                                        _ptr(cw_out), _stream(stream)), "sim_tx_points")
+    return y_out, cw_out
+
+
+def demap_points(y, no, m: int, points, *, method: int = DEMAP_EXACT, clamp: float = 20.0, llr_out=None,
+                 stream=None):
+    """APP demapper over the constellation points [2^m, 2]: y [B, S, 2] -> LLRs [B, S*m]."""
+    import torch
+    _cuda_f32(y, "y")
+    _cuda_f32(no, "no")
+    _cuda_f32(points, "points")
+    B, S = y.shape[0], y.shape[1]
+    if llr_out is None:
+        llr_out = torch.empty((B, S * m), dtype=torch.float32, device=y.device)
+    stride = 0 if no.numel() == 1 else 1
+    _check(load_library().demap_points(_ptr(y), _ptr(no), stride, B, S, m, _ptr(points), method, clamp,
+                                       _ptr(llr_out), _stream(stream)), "demap_points")
+    return llr_out
+
+
+def demap_points_backward(y, no, m: int, points, grad_llr, grad_points, *, clamp: float = 20.0, grad_y=None,
+                          stream=None):
+    """Adjoint of demap_points (exact): returns grad_y [B, S, 2]; adds into grad_points [2^m, 2]."""
+    import torch
+    B, S = y.shape[0], y.shape[1]
+    if grad_y is None:
+        grad_y = torch.empty_like(y)
+    stride = 0 if no.numel() == 1 else 1
+    _check(load_library().demap_points_backward(_ptr(y), _ptr(no), stride, B, S, m, _ptr(points), clamp,
+                                                _ptr(grad_llr), _ptr(grad_y), _ptr(grad_points), _stream(stream)),
+           "demap_points_backward")
+    return grad_y
+
+
+def map_points_backward(code: "Code", cw, m: int, grad_x, grad_points, stream=None):
+    """Adds the symbol gradients grad_x [B, S, 2] into grad_points [2^m, 2] by label."""
+    _check(load_library().map_points_backward(code.handle, _ptr(cw), cw.shape[0], m, _ptr(grad_x),
+                                              _ptr(grad_points), _stream(stream)), "map_points_backward")
+    return grad_points
+
+
+def llr_bce(llr, bits, bit_off: int = 0, *, scale: float = 1.0, grad=True, stream=None):
+    """(sum of ln(1 + exp(-(1-2c) L)) as a CUDA float64 [1] tensor, scale * its gradient [B, N] or None)."""
+    import torch
+    B, N = llr.shape
+    acc = torch.zeros(1, dtype=torch.float64, device=llr.device)
+    g = torch.empty_like(llr) if grad else None
+    _check(load_library().llr_bce(_ptr(llr), B, N, _ptr(bits), bits.shape[1], bit_off, scale, _ptr(acc), _ptr(g),
+                                  _stream(stream)), "llr_bce")
+    return acc, g
 
 
 # --------------------------------------------------------------------------- decoder

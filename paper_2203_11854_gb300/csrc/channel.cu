@@ -23,6 +23,7 @@ struct TxParams {
     float *y;            // [B][S][2] or [B][S]
     uint32_t *info;      // [B][kw] or null
     uint32_t *cw_out;    // [B][ceil(n/32)] packed codeword bits or null
+    const float2 *points;  // [2^m] constellation by label (MSB first), or null for the Gray QAM
     int64_t B;
     int G;               // codewords per CTA
 };
@@ -172,8 +173,17 @@ __global__ void __launch_bounds__(kMaxThreads) k_tx(const TxParams p) {
                 const int s = 2 * q + e;
                 if (s >= S) break;
                 const uint8_t *bits = cb + (size_t)s * m;
-                const float xi = (float)pam_level(bits, h) * p.scale;
-                const float xq = (float)pam_level(bits + 1, h) * p.scale;
+                float xi, xq;
+                if (p.points) {
+                    int l = 0;
+                    for (int j = 0; j < m; ++j) l = (l << 1) | bits[j];
+                    const float2 pt = p.points[l];
+                    xi = pt.x;
+                    xq = pt.y;
+                } else {
+                    xi = (float)pam_level(bits, h) * p.scale;
+                    xq = (float)pam_level(bits + 1, h) * p.scale;
+                }
                 reinterpret_cast<float2 *>(p.y)[cw * S + s] = make_float2(xi + sd * gn[e].x, xq + sd * gn[e].y);
             }
         }
@@ -421,6 +431,190 @@ __global__ void __launch_bounds__(256) k_extrinsic(const float *__restrict__ app
     }
 }
 
+// ------------------------------------------ arbitrary constellation (next 3)
+// Online log-sum-exp: (mx, s) represents mx + ln s; adding term d.
+__device__ __forceinline__ void lse_add(float &mx, float &s, float d) {
+    if (d > mx) {
+        s = s * expf(mx - d) + 1.0f;
+        mx = d;
+    } else {
+        s += expf(d - mx);
+    }
+}
+
+// Points into shared memory (2^m float2).
+__device__ __forceinline__ void load_points(const float *points, int P, float2 *s_pts) {
+    for (int l = threadIdx.x; l < P; l += blockDim.x) s_pts[l] = reinterpret_cast<const float2 *>(points)[l];
+    __syncthreads();
+}
+
+template <int M>
+__global__ void __launch_bounds__(256) k_demap_points(const float *__restrict__ y, const float *__restrict__ no,
+                                                      int64_t no_stride, int64_t B, int64_t S,
+                                                      const float *__restrict__ points, int method, float clamp,
+                                                      float *__restrict__ llr) {
+    constexpr int P = 1 << M;
+    __shared__ float2 s_pts[P];
+    load_points(points, P, s_pts);
+    bool bad = false;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < B * S; i += (int64_t)gridDim.x * blockDim.x) {
+        const float inv_n0 = 1.0f / no[(i / S) * no_stride];
+        const float2 v = reinterpret_cast<const float2 *>(y)[i];
+        float out[M];
+        if (isfinite(v.x) && isfinite(v.y)) {
+            float mx0[M], s0[M], mx1[M], s1[M];
+#pragma unroll
+            for (int j = 0; j < M; ++j) {
+                mx0[j] = mx1[j] = -INFINITY;
+                s0[j] = s1[j] = 0.0f;
+            }
+            for (int l = 0; l < P; ++l) {
+                const float dr = v.x - s_pts[l].x, di = v.y - s_pts[l].y;
+                const float d = -(dr * dr + di * di) * inv_n0;
+#pragma unroll
+                for (int j = 0; j < M; ++j) {
+                    const bool one = (l >> (M - 1 - j)) & 1;
+                    if (method == LDPCX_DEMAP_MAXLOG) {
+                        if (one) mx1[j] = fmaxf(mx1[j], d);
+                        else mx0[j] = fmaxf(mx0[j], d);
+                    } else if (one) {
+                        lse_add(mx1[j], s1[j], d);
+                    } else {
+                        lse_add(mx0[j], s0[j], d);
+                    }
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < M; ++j) {
+                float L = mx0[j] - mx1[j];
+                if (method != LDPCX_DEMAP_MAXLOG) L += logf(s0[j]) - logf(s1[j]);
+                out[j] = fminf(fmaxf(L, -clamp), clamp);
+            }
+        } else {
+            bad = true;
+#pragma unroll
+            for (int j = 0; j < M; ++j) out[j] = 0.0f;
+        }
+#pragma unroll
+        for (int j = 0; j < M; ++j) llr[i * M + j] = out[j];
+    }
+    if (bad) latch(&g_status, LDPCX_FLAG_NONFINITE);
+}
+
+// Adjoint of the exact demapper: with w^0_j(l) = exp(d_l - LSE_0j), w^1_j(l) =
+// exp(d_l - LSE_1j), dL_j/dd_l = w^0_j(l) or -w^1_j(l) by bit j of l, so
+// g_l = sum_j gL_j (+-w_j(l)); dd_l/dy = -2 (y - p_l)/N0 = -dd_l/dp_l. Outputs
+// held at the clamp pass no gradient. Point gradients are summed per block in
+// shared memory, then added to grad_points once per block.
+template <int M>
+__global__ void __launch_bounds__(256) k_demap_points_bwd(const float *__restrict__ y, const float *__restrict__ no,
+                                                          int64_t no_stride, int64_t B, int64_t S,
+                                                          const float *__restrict__ points, float clamp,
+                                                          const float *__restrict__ gllr, float *__restrict__ gy,
+                                                          float *__restrict__ gpts) {
+    constexpr int P = 1 << M;
+    __shared__ float2 s_pts[P];
+    __shared__ float s_g[2 * P];
+    for (int l = threadIdx.x; l < 2 * P; l += blockDim.x) s_g[l] = 0.0f;
+    load_points(points, P, s_pts);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < B * S; i += (int64_t)gridDim.x * blockDim.x) {
+        const float inv_n0 = 1.0f / no[(i / S) * no_stride];
+        const float2 v = reinterpret_cast<const float2 *>(y)[i];
+        float2 g_y = make_float2(0.0f, 0.0f);
+        if (isfinite(v.x) && isfinite(v.y)) {
+            float mx0[M], s0[M], mx1[M], s1[M], gl[M];
+#pragma unroll
+            for (int j = 0; j < M; ++j) {
+                mx0[j] = mx1[j] = -INFINITY;
+                s0[j] = s1[j] = 0.0f;
+            }
+            for (int l = 0; l < P; ++l) {
+                const float dr = v.x - s_pts[l].x, di = v.y - s_pts[l].y;
+                const float d = -(dr * dr + di * di) * inv_n0;
+#pragma unroll
+                for (int j = 0; j < M; ++j) {
+                    if ((l >> (M - 1 - j)) & 1) lse_add(mx1[j], s1[j], d);
+                    else lse_add(mx0[j], s0[j], d);
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < M; ++j) {
+                const float l0 = mx0[j] + logf(s0[j]), l1 = mx1[j] + logf(s1[j]);
+                mx0[j] = l0;  // now the log-sum-exp values
+                mx1[j] = l1;
+                const float L = l0 - l1;
+                gl[j] = (L > -clamp && L < clamp) ? gllr[i * M + j] : 0.0f;
+            }
+            for (int l = 0; l < P; ++l) {
+                const float dr = v.x - s_pts[l].x, di = v.y - s_pts[l].y;
+                const float d = -(dr * dr + di * di) * inv_n0;
+                float g = 0.0f;
+#pragma unroll
+                for (int j = 0; j < M; ++j) {
+                    if ((l >> (M - 1 - j)) & 1) g -= gl[j] * expf(d - mx1[j]);
+                    else g += gl[j] * expf(d - mx0[j]);
+                }
+                const float c = 2.0f * g * inv_n0;
+                g_y.x -= c * dr;
+                g_y.y -= c * di;
+                atomicAdd(&s_g[2 * l], c * dr);
+                atomicAdd(&s_g[2 * l + 1], c * di);
+            }
+        }
+        reinterpret_cast<float2 *>(gy)[i] = g_y;
+    }
+    __syncthreads();
+    for (int l = threadIdx.x; l < 2 * P; l += blockDim.x)
+        if (s_g[l] != 0.0f) atomicAdd(&gpts[l], s_g[l]);
+}
+
+// Adjoint of the mapper: grad_points[label(b, s)] += grad_x[b][s].
+__global__ void __launch_bounds__(256) k_map_points_bwd(const uint32_t *__restrict__ cw, int64_t nw, int p0, int m,
+                                                        int64_t B, int64_t S, const float *__restrict__ gx,
+                                                        float *__restrict__ gpts) {
+    __shared__ float s_g[512];
+    const int P = 1 << m;
+    for (int l = threadIdx.x; l < 2 * P; l += blockDim.x) s_g[l] = 0.0f;
+    __syncthreads();
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < B * S; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = i / S, s = i - b * S;
+        const uint32_t *row = cw + b * nw;
+        int l = 0;
+        for (int j = 0; j < m; ++j) l = (l << 1) | (int)bit_at(row, p0 + s * m + j);
+        const float2 g = reinterpret_cast<const float2 *>(gx)[i];
+        atomicAdd(&s_g[2 * l], g.x);
+        atomicAdd(&s_g[2 * l + 1], g.y);
+    }
+    __syncthreads();
+    for (int l = threadIdx.x; l < 2 * P; l += blockDim.x)
+        if (s_g[l] != 0.0f) atomicAdd(&gpts[l], s_g[l]);
+}
+
+// Binary cross-entropy of LLRs (logits -L) and its gradient.
+__global__ void __launch_bounds__(256) k_bce(const float *__restrict__ llr, int64_t B, int64_t N,
+                                             const uint32_t *__restrict__ bits, int64_t bits_stride, int64_t bit_off,
+                                             float scale, double *acc, float *__restrict__ grad) {
+    double sum = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < B * N; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = i / N, t = i - b * N;
+        const float sgn = bit_at(bits + b * bits_stride, bit_off + t) ? -1.0f : 1.0f;  // 1 - 2c
+        const float x = sgn * llr[i];
+        sum += (double)(fmaxf(-x, 0.0f) + log1pf(expf(-fabsf(x))));  // ln(1 + e^-x)
+        if (grad) grad[i] = -scale * sgn / (1.0f + expf(x));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xFFFFFFFFu, sum, o);
+    __shared__ double s_part[8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) s_part[warp] = sum;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s_part[w];
+        atomicAdd(&acc[0], t);
+    }
+}
+
 // ------------------------------------------------------------ error count
 __global__ void __launch_bounds__(256) k_count(const uint32_t *__restrict__ ref, const uint32_t *__restrict__ hat,
                                                const int32_t *__restrict__ iters, int64_t B, int k,
@@ -488,7 +682,7 @@ namespace ldpcx {
 
 int launch_tx(ldpcx_code_t c, uint64_t seed, uint64_t cw0, const uint64_t *cw0_dev, int64_t B, int m,
               const float *no, int64_t no_stride, float *y_out, uint32_t *info_out, cudaStream_t stream,
-              uint32_t *cw_out) {
+              uint32_t *cw_out, const float *points) {
     DevCode d;
     int st = code_device(c, &d);
     if (st) return st;
@@ -512,6 +706,7 @@ int launch_tx(ldpcx_code_t c, uint64_t seed, uint64_t cw0, const uint64_t *cw0_d
     p.y = y_out;
     p.info = info_out;
     p.cw_out = cw_out;
+    p.points = reinterpret_cast<const float2 *>(points);
     p.B = B;
     int G = kMaxThreads / c->Z;
     if (G < 1) G = 1;
@@ -649,5 +844,86 @@ extern "C" int ldpc_extrinsic(ldpcx_code_t c, const float *app, const float *llr
     if (blocks > cap) blocks = cap;
     k_extrinsic<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(app, llr_in, B, c->n, c->p0, c->n_tx, clamp,
                                                                     out);
+    return cuda_status(cudaGetLastError());
+}
+
+extern "C" int sim_tx_points(ldpcx_code_t c, uint64_t seed, uint64_t cw0, int64_t B, int m, const float *points,
+                             const float *no, int64_t no_stride, float *y_out, uint32_t *cw_out, void *stream) {
+    if (!c || B < 0 || (m != 2 && m != 4 && m != 6 && m != 8) || (no_stride != 0 && no_stride != 1))
+        return LDPCX_E_INVAL;
+    if (c->n_tx % m != 0) return LDPCX_E_INVAL;
+    if (B == 0) return LDPCX_OK;
+    if (!points || !no || !y_out) return LDPCX_E_INVAL;
+    return launch_tx(c, seed, cw0, nullptr, B, m, no, no_stride, y_out, nullptr, (cudaStream_t)stream, cw_out,
+                     points);
+}
+
+namespace {
+int grid_for(int64_t work, int per_sm) {
+    int64_t blocks = (work + 255) / 256;
+    const int64_t cap = (int64_t)sm_count() * per_sm;
+    if (blocks > cap) blocks = cap;
+    return (int)(blocks < 1 ? 1 : blocks);
+}
+bool valid_points_m(int m) { return m == 2 || m == 4 || m == 6 || m == 8; }
+}  // namespace
+
+extern "C" int demap_points(const float *y, const float *no, int64_t no_stride, int64_t B, int64_t S, int m,
+                            const float *points, int method, float clamp, float *llr_out, void *stream) {
+    if (B < 0 || S < 0 || !valid_points_m(m) || (no_stride != 0 && no_stride != 1) || !(clamp > 0.0f))
+        return LDPCX_E_INVAL;
+    if (method != LDPCX_DEMAP_EXACT && method != LDPCX_DEMAP_MAXLOG) return LDPCX_E_INVAL;
+    if (B == 0 || S == 0) return LDPCX_OK;
+    if (!y || !no || !points || !llr_out) return LDPCX_E_INVAL;
+    const int g = grid_for(B * S, 8);
+    cudaStream_t st = (cudaStream_t)stream;
+    switch (m) {
+        case 2: k_demap_points<2><<<g, 256, 0, st>>>(y, no, no_stride, B, S, points, method, clamp, llr_out); break;
+        case 4: k_demap_points<4><<<g, 256, 0, st>>>(y, no, no_stride, B, S, points, method, clamp, llr_out); break;
+        case 6: k_demap_points<6><<<g, 256, 0, st>>>(y, no, no_stride, B, S, points, method, clamp, llr_out); break;
+        default: k_demap_points<8><<<g, 256, 0, st>>>(y, no, no_stride, B, S, points, method, clamp, llr_out); break;
+    }
+    return cuda_status(cudaGetLastError());
+}
+
+extern "C" int demap_points_backward(const float *y, const float *no, int64_t no_stride, int64_t B, int64_t S,
+                                     int m, const float *points, float clamp, const float *grad_llr, float *grad_y,
+                                     float *grad_points, void *stream) {
+    if (B < 0 || S < 0 || !valid_points_m(m) || (no_stride != 0 && no_stride != 1) || !(clamp > 0.0f))
+        return LDPCX_E_INVAL;
+    if (B == 0 || S == 0) return LDPCX_OK;
+    if (!y || !no || !points || !grad_llr || !grad_y || !grad_points) return LDPCX_E_INVAL;
+    const int g = grid_for(B * S, 4);
+    cudaStream_t st = (cudaStream_t)stream;
+#define LDPCX_DPB(MM) \
+    k_demap_points_bwd<MM><<<g, 256, 0, st>>>(y, no, no_stride, B, S, points, clamp, grad_llr, grad_y, grad_points)
+    switch (m) {
+        case 2: LDPCX_DPB(2); break;
+        case 4: LDPCX_DPB(4); break;
+        case 6: LDPCX_DPB(6); break;
+        default: LDPCX_DPB(8); break;
+    }
+#undef LDPCX_DPB
+    return cuda_status(cudaGetLastError());
+}
+
+extern "C" int map_points_backward(ldpcx_code_t c, const uint32_t *cw, int64_t B, int m, const float *grad_x,
+                                   float *grad_points, void *stream) {
+    if (!c || B < 0 || !valid_points_m(m) || c->n_tx % m != 0) return LDPCX_E_INVAL;
+    if (B == 0) return LDPCX_OK;
+    if (!cw || !grad_x || !grad_points) return LDPCX_E_INVAL;
+    const int64_t S = c->n_tx / m, nw = (c->n + 31) / 32;
+    k_map_points_bwd<<<grid_for(B * S, 4), 256, 0, (cudaStream_t)stream>>>(cw, nw, c->p0, m, B, S, grad_x,
+                                                                         grad_points);
+    return cuda_status(cudaGetLastError());
+}
+
+extern "C" int llr_bce(const float *llr, int64_t B, int64_t N, const uint32_t *bits, int64_t bits_stride,
+                       int64_t bit_off, float scale, double *loss_acc, float *grad_llr, void *stream) {
+    if (B < 0 || N < 0 || bit_off < 0 || !loss_acc) return LDPCX_E_INVAL;
+    if (B == 0 || N == 0) return LDPCX_OK;
+    if (!llr || !bits || bits_stride * 32 < bit_off + N) return LDPCX_E_INVAL;
+    k_bce<<<grid_for(B * N, 4), 256, 0, (cudaStream_t)stream>>>(llr, B, N, bits, bits_stride, bit_off, scale,
+                                                                 loss_acc, grad_llr);
     return cuda_status(cudaGetLastError());
 }

@@ -53,10 +53,11 @@ size_t ckpt_bytes(const ldpcx_code *c, int64_t B, int iters);
 unsigned int take_status_channel(cudaStream_t s);
 
 // Transmitter launch (source, encoder, mapper, AWGN); cw0_dev optional;
-// y_out null: codewords only (packed into cw_out).
+// y_out null: codewords only (packed into cw_out); points: a constellation by
+// label instead of the Gray QAM.
 int launch_tx(ldpcx_code_t c, uint64_t seed, uint64_t cw0, const uint64_t *cw0_dev, int64_t B, int m,
               const float *no, int64_t no_stride, float *y_out, uint32_t *info_out, cudaStream_t stream,
-              uint32_t *cw_out = nullptr);
+              uint32_t *cw_out = nullptr, const float *points = nullptr);
 // *cw0_dev += inc on the device.
 int launch_advance(uint64_t *cw0_dev, uint64_t inc, cudaStream_t stream);
 

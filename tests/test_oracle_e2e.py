@@ -63,7 +63,7 @@ def test_autograd_matches_finite_differences(orc):
     P = torch.from_numpy(pts).requires_grad_(True)
     loss = e2e.chain_loss(P, torch.from_numpy(lab), torch.from_numpy(noise), torch.from_numpy(n0), m)
     loss.backward()
-    assert float(loss) == pytest.approx(loss_c(pts), rel=1e-12)
+    assert float(loss.detach()) == pytest.approx(loss_c(pts), rel=1e-12)
     g = P.grad.numpy()
     h = 1e-6
     for idx in [(0, 0), (3, 1), (7, 0), (12, 1), (15, 0)]:
