@@ -308,6 +308,7 @@ def run_gpu(args):
             variants = measure_variants(lx, code, llr, bits, its, stream, args, pk)
             variants["mixed_batch"] = measure_mixed(lx, stream, args)
             variants["sweep_256qam"] = measure_sweep(lx, code, pk)
+            variants["grad_step"] = measure_grad_step(lx)
         e2e = measure_e2e(lx, code, y, info, n0, dec, stream, args, dev)
         cpu = None if (world > 1 or args.no_cpu) else cpu_baseline(args.cpu_seconds)
         result = {
@@ -428,6 +429,38 @@ def measure_sweep(lx, code, pk):
     c16, c6 = out["fp16"]["ebn0_at_1e-4_db"], out["fix6"]["ebn0_at_1e-4_db"]
     out["fix6_minus_fp16_db_at_1e-4"] = None if c16 is None or c6 is None else c6 - c16
     return out
+
+
+def measure_grad_step(lx):
+    """Config 4's training step: weighted flooding sum-product, BG2-shaped Z=64, batch 2048, 10 iterations,
+    forward with checkpoints plus the hand-written adjoint (ldpc_bp_decode_ckpt + ldpc_bp_backward)."""
+    import torch
+    from paper_2203_11854_gb300.autograd import LdpcBP
+    code = lx.qc_ldpc_build(2, 64)
+    B, iters = 2048, 10
+    g = torch.Generator(device="cuda")
+    g.manual_seed(3)
+    llr = (2.0 + 2.0 * torch.randn((B, code.n_tx), device="cuda", generator=g)).float().requires_grad_(True)
+    w = torch.ones((iters, code.nnz), device="cuda", requires_grad=True)
+
+    def step():
+        out = LdpcBP.apply(llr, w, code, iters, 20.0)
+        out.sum().backward()
+
+    for _ in range(2):
+        step()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 5
+    a.record()
+    for _ in range(reps):
+        step()
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / reps
+    return {"ms_per_step": ms, "codewords_per_s": B / (ms * 1e-3),
+            "edge_updates_per_s": 2 * B * code.edges * iters / (ms * 1e-3),
+            "workload": "BG2-shaped Z=64, batch 2048, 10 flooding SPA iterations, forward + adjoint"}
 
 
 def measure_mixed(lx, stream, args):
