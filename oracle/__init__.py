@@ -33,6 +33,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "ldpc_oracle.c")
+_SRCS = [_SRC, os.path.join(_HERE, "polar_oracle.c")]
 _LIB_PATH = os.path.join(_HERE, "libldpc_oracle.so")
 _lib = None
 _lock = threading.Lock()
@@ -51,12 +52,13 @@ _i64p = np.ctypeslib.ndpointer(dtype=np.int64, flags="C_CONTIGUOUS")
 
 
 def build(force: bool = False) -> str:
-    """Compile ldpc_oracle.c with gcc (no fast-math, no FMA contraction)."""
-    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+    """Compile ldpc_oracle.c and polar_oracle.c with gcc (no fast-math, no FMA contraction)."""
+    if force or not os.path.exists(_LIB_PATH) or any(os.path.getmtime(_LIB_PATH) < os.path.getmtime(f)
+                                                       for f in _SRCS):
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
         subprocess.check_call([
             "gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
-            "-o", tmp, _SRC, "-lm", "-lpthread",
+            "-o", tmp, *_SRCS, "-lm", "-lpthread",
         ])
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -86,6 +88,14 @@ def lib():
             L.orc_demap_prior.argtypes = [_f64p, C.c_int64, C.c_int, C.c_int, _f64p, C.c_int, C.c_double,
                                           C.c_void_p, C.c_int, _f64p]
             L.orc_apriori.argtypes = [_u8p, C.c_int64, C.c_int64, C.c_double, C.c_uint64, C.c_uint64, _f64p]
+            L.orc_polar_bhatt.argtypes = [C.c_int, C.c_double, _f64p]
+            L.orc_polar_info_set.argtypes = [C.c_int, C.c_double, C.c_int, _i32p, _u8p]
+            L.orc_polar_encode.argtypes = [C.c_int, _u8p, _u8p]
+            L.orc_polar_encode.restype = None
+            L.orc_crc.argtypes = [_u8p, C.c_int, C.c_uint64, C.c_int, _u8p]
+            L.orc_crc.restype = None
+            L.orc_polar_scl.argtypes = [C.c_int, _f64p, C.c_int64, _u8p, _i32p, C.c_int, C.c_int, C.c_uint64,
+                                        C.c_int, C.c_int, _u8p, _f64p]
             L.orc_demap_points.argtypes = [_f64p, C.c_int64, C.c_int, C.c_int, _f64p, _f64p, C.c_int, C.c_double,
                                            _f64p]
             L.orc_apriori.restype = None
@@ -296,6 +306,51 @@ def demap_points(y: np.ndarray, m: int, N0, points: np.ndarray, method: int = DE
     _check(lib().orc_demap_points(y.reshape(-1), B, S, m, n0, pts, method, clamp, llr.reshape(-1)),
            "demap_points")
     return llr
+
+
+# ----------------------------------------------------------------- polar codes
+def polar_bhatt(n: int, design_esn0_db: float) -> np.ndarray:
+    z = np.zeros(1 << n, dtype=np.float64)
+    _check(lib().orc_polar_bhatt(n, design_esn0_db, z), "polar_bhatt")
+    return z
+
+
+def polar_info_set(n: int, K: int, design_esn0_db: float):
+    """(info indices ascending int32 [K], frozen mask uint8 [N])."""
+    info = np.zeros(max(K, 1), dtype=np.int32)
+    frozen = np.zeros(1 << n, dtype=np.uint8)
+    _check(lib().orc_polar_info_set(n, design_esn0_db, K, info, frozen), "polar_info_set")
+    return info[:K], frozen
+
+
+def polar_encode(u: np.ndarray) -> np.ndarray:
+    u = np.ascontiguousarray(u, dtype=np.uint8)
+    out = np.zeros_like(u)
+    n = int(np.log2(u.shape[-1]))
+    for r in range(u.reshape(-1, u.shape[-1]).shape[0]):
+        lib().orc_polar_encode(n, u.reshape(-1, u.shape[-1])[r], out.reshape(-1, u.shape[-1])[r])
+    return out
+
+
+def crc(bits: np.ndarray, g: int, r: int) -> np.ndarray:
+    bits = np.ascontiguousarray(bits, dtype=np.uint8)
+    out = np.zeros(r, dtype=np.uint8)
+    lib().orc_crc(bits, bits.size, g, r, out)
+    return out
+
+
+def polar_scl(llr: np.ndarray, frozen: np.ndarray, info: np.ndarray, L: int, g: int = 0, r: int = 0,
+              prec: int = 0):
+    """(u_hat uint8 [B, N], path metric [B]) of CRC-aided SCL (L = 1: SC)."""
+    llr = np.ascontiguousarray(llr, dtype=np.float64)
+    B, N = llr.shape
+    n = int(np.log2(N))
+    uh = np.zeros((B, N), dtype=np.uint8)
+    pm = np.zeros(B, dtype=np.float64)
+    _check(lib().orc_polar_scl(n, llr.reshape(-1), B, np.ascontiguousarray(frozen, dtype=np.uint8),
+                               np.ascontiguousarray(info, dtype=np.int32), len(info), L, g, r, prec,
+                               uh.reshape(-1), pm), "polar_scl")
+    return uh, pm
 
 
 def qam_points(m: int) -> np.ndarray:
