@@ -453,6 +453,43 @@ int map_points_backward(ldpcx_code_t code, const uint32_t *cw, int64_t B, int m,
 int llr_bce(const float *llr, int64_t B, int64_t N, const uint32_t *bits, int64_t bits_stride, int64_t bit_off,
             float scale, double *loss_acc, float *grad_llr, void *stream);
 
+/* ----------------------------------- polar codes, SC/SCL decoding (next row 4) */
+/* The paper lists polar codes with SC, SCL and SCL-CRC decoders among its FEC
+ * features (Section III) and names the polar SCL decoder as a custom CUDA
+ * kernel case (Section IV-A). Conventions:
+ *  - N = 2^n (n in 2..10), encoder x = u F^{(x)n}, F = [[1,0],[1,1]], natural
+ *    order; BPSK x -> 1 - 2x on a real AWGN channel, L = ln P0/P1;
+ *  - information set: the K bit channels of smallest Bhattacharyya parameter
+ *    z_i, where z_i applies to z0 = exp(-Es/N0 at the design point) the
+ *    transforms z -> 2z - z^2 (bit 0 of i) or z -> z^2 (bit 1) for the bits of
+ *    i from the most significant down (ties: the larger index); the 3GPP
+ *    reliability sequence is not used (not available to this build);
+ *  - the K information positions carry, in ascending order, K - r data bits
+ *    and their r-bit CRC (generator g with the x^r term, remainder of the data
+ *    most significant first, zero initial state); r = 0: no CRC;
+ *  - SCL (L = 1: SC) in the LLR domain with f(a,b) = sgn(a) sgn(b) min(|a|,|b|),
+ *    g(a,b,u) = b + (1-2u) a, path metric PM += |L_i| when the decision
+ *    disagrees with sign(L_i) (decision 1 iff L < 0; frozen bits are 0);
+ *    candidates (path l, bit b) ordered c = 2l + b, the L smallest (PM, c)
+ *    survive in ascending c; CRC-aided selection of the smallest (PM, list
+ *    index) among the paths that pass the CRC, else among all. */
+typedef struct ldpcx_polar *ldpcx_polar_t;
+int polar_build(int n, int K, float design_esn0_db, uint64_t crc_poly, int crc_r, ldpcx_polar_t *out);
+int polar_free(ldpcx_polar_t code);
+/* info_out (host, or NULL) [K] ascending information positions. */
+int polar_info(ldpcx_polar_t code, int *N, int *K, int *crc_r, int32_t *info_out);
+/* Transmitter: data bits (Philox stream 0, word w of codeword b from block
+ * w/4 with counter (w/4, (cw0+b) lo32, hi32, 0), as sim_tx), CRC, encoder,
+ * BPSK and AWGN (Philox stream 1 as sim_tx for m = 1).
+ * y_out (device) [B][N] float; data_out (device, or NULL) [B][ceil((K-r)/32)]. */
+int polar_sim_tx(ldpcx_polar_t code, uint64_t seed, uint64_t cw0, int64_t B, const float *no, int64_t no_stride,
+                 float *y_out, uint32_t *data_out, void *stream);
+/* CRC-aided SCL decoding of llr (device) [B][N] with list size L in 1..32.
+ * data_out (device) [B][ceil((K-r)/32)] packed data bits of the chosen path;
+ * pm_out (device, or NULL) [B] its path metric. */
+int polar_scl_decode(ldpcx_polar_t code, const float *llr, int64_t B, int L, uint32_t *data_out, float *pm_out,
+                     void *stream);
+
 /* -------------------------------------------------- Monte-Carlo run (a13) */
 /* A BER/BLER sweep over Eb/N0 points (the loop around Listing 1): for each
  * point, batches of `batch` codewords run sim_tx -> demap_app -> ldpc_bp_decode

@@ -21,7 +21,8 @@ __all__ = [
     "ldpc_bp_decode_noalloc", "ldpc_bp_msg_format", "ldpc_bp_mixed_workspace", "ldpc_bp_decode_mixed", "ldpc_bp_ckpt_bytes", "ldpc_bp_decode_ckpt", "ldpc_bp_backward_workspace",
     "ldpc_bp_backward", "ldpcx_phi", "sim_codewords", "demap_app_prior", "llr_apriori", "llr_mutual_info",
     "ldpc_extrinsic", "DEMAP_OUT_APP", "DEMAP_OUT_EXTRINSIC", "sim_tx_points", "demap_points",
-    "demap_points_backward", "map_points_backward", "llr_bce",
+    "demap_points_backward", "map_points_backward", "llr_bce", "PolarCode", "polar_build", "polar_sim_tx",
+    "polar_scl_decode",
     "LAYERED_MINSUM", "LAYERED_SPA", "FLOOD_MINSUM", "FLOOD_SPA", "MSG_F32", "MSG_F16", "MSG_FIX6",
     "DEMAP_EXACT", "DEMAP_MAXLOG",
 ]
@@ -96,6 +97,11 @@ _SIGS = {
     "demap_points_backward": ([_vp, _vp, _i64, _i64, _i64, _i, _vp, _f, _vp, _vp, _vp, _vp], _i),
     "map_points_backward": ([_vp, _vp, _i64, _i, _vp, _vp, _vp], _i),
     "llr_bce": ([_vp, _i64, _i64, _vp, _i64, _i64, _f, _vp, _vp, _vp], _i),
+    "polar_build": ([_i, _i, _f, _u64, _i, C.POINTER(_vp)], _i),
+    "polar_free": ([_vp], _i),
+    "polar_info": ([_vp, C.POINTER(_i), C.POINTER(_i), C.POINTER(_i), _vp], _i),
+    "polar_sim_tx": ([_vp, _u64, _u64, _i64, _vp, _i64, _vp, _vp, _vp], _i),
+    "polar_scl_decode": ([_vp, _vp, _i64, _i, _vp, _vp, _vp], _i),
     "ldpc_bp_workspace": ([_vp, _i64, C.POINTER(DecodeOpts), C.POINTER(_sz)], _i),
     "ldpc_bp_decode": ([_vp, _vp, _i64, C.POINTER(DecodeOpts), _vp, _vp, _vp, _vp, _sz, _vp], _i),
     "sim_count": ([_vp, _vp, _vp, _i64, _i, _vp, _vp], _i),
@@ -390,6 +396,67 @@ def llr_bce(llr, bits, bit_off: int = 0, *, scale: float = 1.0, grad=True, strea
     _check(load_library().llr_bce(_ptr(llr), B, N, _ptr(bits), bits.shape[1], bit_off, scale, _ptr(acc), _ptr(g),
                                   _stream(stream)), "llr_bce")
     return acc, g
+
+
+class PolarCode:
+    """Owner of an ldpcx_polar_t: N = 2^n, K information positions (data + CRC)."""
+
+    def __init__(self, handle):
+        import numpy as np
+        self.handle = handle
+        N, K, r = C.c_int(0), C.c_int(0), C.c_int(0)
+        _check(load_library().polar_info(handle, C.byref(N), C.byref(K), C.byref(r), None), "polar_info")
+        self.N, self.K, self.crc_r = N.value, K.value, r.value
+        self.n = self.N.bit_length() - 1
+        self.k_data = self.K - self.crc_r
+        info = np.zeros(self.K, dtype=np.int32)
+        _check(load_library().polar_info(handle, None, None, None, info.ctypes.data), "polar_info")
+        self.info = info
+
+    def close(self):
+        if self.handle:
+            load_library().polar_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def polar_build(n: int, K: int, design_esn0_db: float = 0.0, crc_poly: int = 0, crc_r: int = 0) -> PolarCode:
+    h = C.c_void_p()
+    _check(load_library().polar_build(n, K, design_esn0_db, crc_poly, crc_r, C.byref(h)), "polar_build")
+    return PolarCode(h.value)
+
+
+def polar_sim_tx(code: PolarCode, seed: int, cw0: int, B: int, no, y_out=None, data_out=None, stream=None):
+    """Data bits, CRC, encoder, BPSK and AWGN: (y [B, N], packed data bits [B, ceil(k_data/32)])."""
+    import torch
+    _cuda_f32(no, "no")
+    if y_out is None:
+        y_out = torch.empty((B, code.N), dtype=torch.float32, device=no.device)
+    if data_out is None:
+        data_out = torch.empty((B, (code.k_data + 31) // 32), dtype=torch.int32, device=no.device)
+    stride = 0 if no.numel() == 1 else 1
+    _check(load_library().polar_sim_tx(code.handle, seed, cw0, B, _ptr(no), stride, _ptr(y_out), _ptr(data_out),
+                                       _stream(stream)), "polar_sim_tx")
+    return y_out, data_out
+
+
+def polar_scl_decode(code: PolarCode, llr, L: int = 8, data_out=None, pm_out=None, stream=None):
+    """CRC-aided SCL (L = 1: SC) of llr [B, N]: (packed data bits [B, ceil(k_data/32)], path metrics [B])."""
+    import torch
+    _cuda_f32(llr, "llr")
+    B = llr.shape[0]
+    if data_out is None:
+        data_out = torch.empty((B, (code.k_data + 31) // 32), dtype=torch.int32, device=llr.device)
+    if pm_out is None:
+        pm_out = torch.empty(B, dtype=torch.float32, device=llr.device)
+    _check(load_library().polar_scl_decode(code.handle, _ptr(llr), B, L, _ptr(data_out), _ptr(pm_out),
+                                           _stream(stream)), "polar_scl_decode")
+    return data_out, pm_out
 
 
 # --------------------------------------------------------------------------- decoder

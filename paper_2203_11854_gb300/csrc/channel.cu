@@ -36,15 +36,6 @@ __device__ __forceinline__ int pam_level(const uint8_t *c, int h) {
     return inner;
 }
 
-// Box-Muller on one Philox word pair: u1 = ((a>>9)+0.5) 2^-23, u2 = (b>>8) 2^-24.
-__device__ __forceinline__ float2 box_muller(uint32_t a, uint32_t b) {
-    const float u1 = ((float)(a >> 9) + 0.5f) * (1.0f / 8388608.0f);
-    const float u2 = (float)(b >> 8) * (1.0f / 16777216.0f);
-    const float r = sqrtf(-2.0f * logf(u1));
-    float s, c;
-    sincospif(2.0f * u2, &s, &c);
-    return make_float2(r * c, r * s);
-}
 
 __global__ void __launch_bounds__(kMaxThreads) k_tx(const TxParams p) {
     extern __shared__ __align__(16) unsigned char smem[];

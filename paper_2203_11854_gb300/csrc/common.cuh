@@ -91,4 +91,14 @@ __device__ __forceinline__ uint4 draw(uint64_t seed, uint64_t cw, uint32_t strea
                          make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
 }
 
+// Box-Muller on one Philox word pair: u1 = ((a>>9)+0.5) 2^-23, u2 = (b>>8) 2^-24.
+__device__ __forceinline__ float2 box_muller(uint32_t a, uint32_t b) {
+    const float u1 = ((float)(a >> 9) + 0.5f) * (1.0f / 8388608.0f);
+    const float u2 = (float)(b >> 8) * (1.0f / 16777216.0f);
+    const float r = sqrtf(-2.0f * logf(u1));
+    float s, c;
+    sincospif(2.0f * u2, &s, &c);
+    return make_float2(r * c, r * s);
+}
+
 }  // namespace ldpcx
