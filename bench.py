@@ -309,6 +309,7 @@ def run_gpu(args):
             variants["mixed_batch"] = measure_mixed(lx, stream, args)
             variants["sweep_256qam"] = measure_sweep(lx, code, pk)
             variants["grad_step"] = measure_grad_step(lx)
+            variants["polar_scl"] = measure_polar(lx)
         e2e = measure_e2e(lx, code, y, info, n0, dec, stream, args, dev)
         cpu = None if (world > 1 or args.no_cpu) else cpu_baseline(args.cpu_seconds)
         result = {
@@ -461,6 +462,31 @@ def measure_grad_step(lx):
     return {"ms_per_step": ms, "codewords_per_s": B / (ms * 1e-3),
             "edge_updates_per_s": 2 * B * code.edges * iters / (ms * 1e-3),
             "workload": "BG2-shaped Z=64, batch 2048, 10 flooding SPA iterations, forward + adjoint"}
+
+
+def measure_polar(lx):
+    """CRC-aided SCL of polar codes (next row): N = 1024, K = 512 (504 data bits + CRC-8 0x107), list 8
+    and SC, 16384 codewords at Eb/N0 = 2 dB (BPSK, AWGN)."""
+    import torch
+    code = lx.polar_build(10, 512, 1.0, 0x107, 8)
+    B = 16384
+    n0 = torch.tensor([10 ** (-2.0 / 10) / (code.k_data / code.N)], device="cuda")
+    y, data = lx.polar_sim_tx(code, 5, 0, B, n0)
+    llr = ((4.0 / n0) * y).contiguous()
+    out = {"code": "N=1024, K=512 (504 data + CRC-8), Bhattacharyya design at 1 dB Es/N0", "codewords": B}
+    for L in (1, 8):
+        bits, pm = lx.polar_scl_decode(code, llr, L)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(3):
+            lx.polar_scl_decode(code, llr, L, data_out=bits, pm_out=pm)
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / 3
+        out[f"L{L}"] = {"ms": ms, "codewords_per_s": B / (ms * 1e-3), "data_gbps": B * code.k_data / (ms * 1e-3) / 1e9,
+                        "bler_2dB": float((bits != data).any(dim=1).float().mean())}
+    return out
 
 
 def measure_mixed(lx, stream, args):
