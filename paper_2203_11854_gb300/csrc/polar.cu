@@ -162,163 +162,208 @@ __host__ __device__ inline size_t scl_smem(int N, int L) {
            + sizeof(float) * (size_t)L * (N - 1)           // alpha per slot
            + (size_t)L * (N - 1)                           // beta per slot
            + 2 * (size_t)L * N                             // u and combine buffer per slot
+           + (size_t)N + 16 + sizeof(int) * ((size_t)N + 3)  // frozen flags, information positions
            + sizeof(float) * 3 * kPolarMaxL * 2            // pm, candidate metrics, leaf LLRs
            + sizeof(int) * 4 * kPolarMaxL * 2 + 64;        // slots, selection
 }
 
+// Phases of the leaf loop touch cur * s elements (cur paths, node size s = 2^ls).
+// Phases of at most 32 elements run in warp 0 alone, separated by __syncwarp;
+// larger ones use the whole CTA, separated by __syncthreads. `cta` records
+// whether the last phase was CTA-wide, which decides the barrier a phase needs
+// before it reads what the previous one wrote. Every such decision depends on
+// (i, s, cur, L) only, so all threads take the same barriers.
 __global__ void __launch_bounds__(kPolarThreads) k_polar_scl(const PolarScl p) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int N = p.N, L = p.L, T = blockDim.x;
+    const bool w0 = threadIdx.x < 32;
+    const int lane = threadIdx.x & 31;
     float *ch = reinterpret_cast<float *>(smem);
     float *alpha = ch + N;                                              // [L][N-1]
     uint8_t *beta = reinterpret_cast<uint8_t *>(alpha + (size_t)L * (N - 1));  // [L][N-1]
     uint8_t *ubuf = beta + (size_t)L * (N - 1);                         // [L][N]
     uint8_t *tmp = ubuf + (size_t)L * N;                                // [L][N]
-    float *pm = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(tmp + (size_t)L * N) + 15) & ~(uintptr_t)15);
+    uint8_t *fz = tmp + (size_t)L * N;                                  // [N] frozen flags
+    int *s_info = reinterpret_cast<int *>((reinterpret_cast<uintptr_t>(fz + N) + 15) & ~(uintptr_t)15);  // [K]
+    float *pm = reinterpret_cast<float *>(s_info + ((p.K + 3) & ~3));
     float *cm = pm + kPolarMaxL;          // [2 L] candidate metrics
-    float *lam = cm + 2 * kPolarMaxL;     // [L] leaf LLR per logical path
-    int *slot = reinterpret_cast<int *>(lam + kPolarMaxL);  // [L] logical -> physical
-    int *nslot = slot + kPolarMaxL;       // [L] new logical -> physical
-    int *src = nslot + kPolarMaxL;        // [L] new logical -> old physical to copy from (-1: none)
-    int *keep_c = src + kPolarMaxL;       // [2 L] survive flags, then [L] new bits at 2 kPolarMaxL
-    __shared__ int s_cur, s_best;
+    int *slot = reinterpret_cast<int *>(cm + 2 * kPolarMaxL);  // [L] logical -> physical
+    int *cpy_to = slot + kPolarMaxL;      // [L] copy destinations of this leaf
+    int *cpy_from = cpy_to + kPolarMaxL;  // [L] and sources
+    int *keep_c = cpy_from + kPolarMaxL;  // [L] CRC flags at the end
+    __shared__ int s_cur, s_ncopy, s_best;
 
     const int64_t b = blockIdx.x;
-    for (int j = threadIdx.x; j < N; j += T) ch[j] = p.llr[b * N + j];
+    for (int j = threadIdx.x; j < N; j += T) {
+        ch[j] = p.llr[b * N + j];
+        fz[j] = p.frozen[j];
+    }
+    for (int j = threadIdx.x; j < p.K; j += T) s_info[j] = p.info[j];
     if (threadIdx.x == 0) {
         s_cur = 1;
         pm[0] = 0.0f;
         slot[0] = 0;
     }
     __syncthreads();
+    bool cta = true;  // everything above is synchronised
+    int cur = 1;      // equal in every thread: it changes only at info leaves, after a barrier
+
+    auto sync_for = [&](bool wide) {
+        if (wide || cta) __syncthreads();
+        else if (w0) __syncwarp();
+        cta = wide;
+    };
+    const int n = p.n;
 
     for (int i = 0; i < N; ++i) {
-        const int cur = s_cur;
         // A: LLRs of the nodes that start at leaf i, from the largest down to the leaf
-        const int low = i == 0 ? N / 2 : min(i & -i, N / 2);
-        for (int s = low; s >= 1; s >>= 1) {
-            const bool right = (i / s) & 1;
-            for (int idx = threadIdx.x; idx < cur * s; idx += T) {
-                const int k = idx / s, j = idx - k * s;
+        const int llow = i == 0 ? n - 1 : min(__ffs(i) - 1, n - 1);
+        for (int ls = llow; ls >= 0; --ls) {
+            const int sz = 1 << ls;
+            const bool wide = (cur << ls) > 32;
+            sync_for(wide);
+            if (!wide && !w0) continue;
+            const bool right = (i >> ls) & 1;
+            for (int idx = wide ? threadIdx.x : lane; idx < (cur << ls); idx += wide ? T : 32) {
+                const int k = idx >> ls, j = idx & (sz - 1);
                 const int ph = slot[k];
                 float *a = alpha + (size_t)ph * (N - 1);
-                const float *P = (2 * s == N) ? ch : a + (N - 4 * s);  // parent, size 2s
-                const float x = P[j], y = P[j + s];
+                const float *P = (2 * sz == N) ? ch : a + (N - 4 * sz);  // parent, size 2s
+                const float x = P[j], y = P[j + sz];
                 if (!right) {
-                    a[N - 2 * s + j] = f_min(x, y);
+                    a[N - 2 * sz + j] = f_min(x, y);
                 } else {
-                    const uint8_t ps = beta[(size_t)ph * (N - 1) + N - 2 * s + j];
-                    a[N - 2 * s + j] = ps ? y - x : y + x;
+                    const uint8_t ps = beta[(size_t)ph * (N - 1) + N - 2 * sz + j];
+                    a[N - 2 * sz + j] = ps ? y - x : y + x;
                 }
             }
-            __syncthreads();
         }
-        // B: decision at leaf i
-        if (threadIdx.x < cur) lam[threadIdx.x] = alpha[(size_t)slot[threadIdx.x] * (N - 1) + N - 2];
-        __syncthreads();
-        if (p.frozen[i]) {
-            if (threadIdx.x < cur) {
-                const int k = threadIdx.x;
-                if (lam[k] < 0.0f) pm[k] = pm[k] + fabsf(lam[k]);
-                ubuf[(size_t)slot[k] * N + i] = 0;
+        // B: decision at leaf i, in warp 0
+        sync_for(false);
+        if (fz[i]) {
+            if (w0 && lane < cur) {
+                const int ph = slot[lane];
+                const float l = alpha[(size_t)ph * (N - 1) + N - 2];
+                if (l < 0.0f) pm[lane] = pm[lane] + fabsf(l);
+                ubuf[(size_t)ph * N + i] = 0;
             }
-            __syncthreads();
+        } else if (L == 1) {
+            // one path: the decision agrees with the sign (a tie at L = 0 keeps bit 0, the smaller c)
+            if (threadIdx.x == 0) {
+                const float l = alpha[(size_t)slot[0] * (N - 1) + N - 2];
+                ubuf[(size_t)slot[0] * N + i] = l < 0.0f ? 1 : 0;
+            }
         } else {
             const int nc = 2 * cur, keep = min(nc, L);
-            if (threadIdx.x < nc) {
-                const int c = threadIdx.x, k = c >> 1, bit = c & 1;
-                const int h = lam[k] < 0.0f ? 1 : 0;
-                cm[c] = (bit == h) ? pm[k] : pm[k] + fabsf(lam[k]);
-            }
-            __syncthreads();
-            if (threadIdx.x < nc) {
-                const int c = threadIdx.x;
-                int rank = 0;
-                for (int c2 = 0; c2 < nc; ++c2) rank += (cm[c2] < cm[c] || (cm[c2] == cm[c] && c2 < c)) ? 1 : 0;
-                keep_c[c] = rank < keep ? 1 : 0;
-            }
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                // survivors in ascending c; the first child of a path keeps its slot, a second child
-                // takes a slot of a path with no survivor (or an unused one) and is copied there
-                int used[kPolarMaxL];
-                for (int q = 0; q < L; ++q) used[q] = 0;
-                for (int k = 0; k < cur; ++k)
-                    if (keep_c[2 * k] || keep_c[2 * k + 1]) used[slot[k]] = 1;
-                int nk = 0, freeq = 0;
-                for (int c = 0; c < nc; ++c) {
-                    if (!keep_c[c]) continue;
-                    const int k = c >> 1;
-                    const bool first = (c & 1) == 0 || !keep_c[c - 1];
-                    if (first) {
-                        nslot[nk] = slot[k];
-                        src[nk] = -1;
-                    } else {
-                        while (used[freeq]) ++freeq;
-                        used[freeq] = 1;
-                        nslot[nk] = freeq;
-                        src[nk] = slot[k];
+            if (w0) {
+                // candidates c = lane and lane + 32: metric, survival (the keep smallest (PM, c))
+                float m[2];
+                bool sv[2];
+                int oslot = lane < cur ? slot[lane] : 0;
+                for (int h = 0; h < 2; ++h) {
+                    const int c = lane + 32 * h;
+                    m[h] = 0.0f;
+                    if (c < nc) {
+                        const int k = c >> 1, bit = c & 1;
+                        const float l = alpha[(size_t)slot[k] * (N - 1) + N - 2];
+                        const int hd = l < 0.0f ? 1 : 0;
+                        m[h] = (bit == hd) ? pm[k] : pm[k] + fabsf(l);
+                        cm[c] = m[h];
                     }
-                    lam[nk] = cm[c];           // reuse: the new metric
-                    keep_c[2 * kPolarMaxL + nk] = c & 1;  // the new bit
-                    ++nk;
+                }
+                __syncwarp();
+                for (int h = 0; h < 2; ++h) {
+                    const int c = lane + 32 * h;
+                    int rank = 0;
+                    if (c < nc)
+                        for (int c2 = 0; c2 < nc; ++c2) rank += (cm[c2] < m[h] || (cm[c2] == m[h] && c2 < c)) ? 1 : 0;
+                    sv[h] = c < nc && rank < keep;
+                }
+                const unsigned s0 = __ballot_sync(0xFFFFFFFFu, sv[0]), s1 = __ballot_sync(0xFFFFFFFFu, sv[1]);
+                const unsigned long long smask = (unsigned long long)s0 | ((unsigned long long)s1 << 32);
+                // duplicated paths (both children survive) and the slots in use after the selection
+                const bool dup = lane < cur && ((smask >> (2 * lane)) & 3ull) == 3ull;
+                const bool any = lane < cur && ((smask >> (2 * lane)) & 3ull) != 0ull;
+                const unsigned used = __reduce_or_sync(0xFFFFFFFFu, any ? (1u << oslot) : 0u);
+                const unsigned dmask = __ballot_sync(0xFFFFFFFFu, dup);
+                const unsigned freem = ~used & (L == 32 ? 0xFFFFFFFFu : ((1u << L) - 1u));
+                int srcs[2];  // old slot of each candidate's path, fetched by every lane
+                for (int h = 0; h < 2; ++h) srcs[h] = __shfl_sync(0xFFFFFFFFu, oslot, (lane + 32 * h) >> 1);
+                __syncwarp();
+                for (int h = 0; h < 2; ++h) {
+                    const int c = lane + 32 * h;
+                    if (!sv[h]) continue;
+                    const int k = c >> 1;
+                    const int nk = __popcll(smask & ((1ull << c) - 1ull));
+                    int ns;
+                    const bool second = (c & 1) && ((smask >> (c - 1)) & 1ull);
+                    const int srcslot = srcs[h];
+                    if (!second) {
+                        ns = srcslot;
+                    } else {
+                        const int t = __popc(dmask & ((1u << k) - 1u));  // duplicates before this one
+                        ns = __fns(freem, 0, t + 1);
+                        cpy_to[t] = ns;
+                        cpy_from[t] = srcslot;
+                    }
+                    slot[nk] = ns;
+                    pm[nk] = m[h];
+                    ubuf[(size_t)ns * N + i] = (uint8_t)(c & 1);  // position i is not copied
+                }
+                if (lane == 0) {
+                    s_ncopy = __popc(dmask);
+                    s_cur = keep;
                 }
             }
+            // the copies: all threads, after the selection of warp 0
             __syncthreads();
-            // copy the duplicated paths' state
-            for (int k = 0; k < keep; ++k) {
-                if (src[k] < 0) continue;
-                const int from = src[k], to = nslot[k];
+            cur = s_cur;
+            const int ncopy = s_ncopy;
+            for (int q = 0; q < ncopy; ++q) {
+                const int from = cpy_from[q], to = cpy_to[q];
                 for (int j = threadIdx.x; j < N - 1; j += T) {
                     alpha[(size_t)to * (N - 1) + j] = alpha[(size_t)from * (N - 1) + j];
                     beta[(size_t)to * (N - 1) + j] = beta[(size_t)from * (N - 1) + j];
                 }
                 for (int j = threadIdx.x; j < i; j += T) ubuf[(size_t)to * N + j] = ubuf[(size_t)from * N + j];
             }
-            __syncthreads();
-            if (threadIdx.x < keep) {
-                const int k = threadIdx.x;
-                slot[k] = nslot[k];
-                pm[k] = lam[k];
-                ubuf[(size_t)nslot[k] * N + i] = (uint8_t)keep_c[2 * kPolarMaxL + k];
-            }
-            if (threadIdx.x == 0) s_cur = keep;
-            __syncthreads();
+            cta = true;
         }
         // C: partial sums: leaf i closes the nodes whose last leaf it is
-        const int cur2 = s_cur;
-        if (threadIdx.x < cur2) tmp[(size_t)slot[threadIdx.x] * N] = ubuf[(size_t)slot[threadIdx.x] * N + i];
-        __syncthreads();
-        for (int s = 1; s < N; s <<= 1) {
-            const bool right = (i / s) & 1;
-            for (int idx = threadIdx.x; idx < cur2 * s; idx += T) {
-                const int k = idx / s, j = idx - k * s;
-                const int ph = slot[k];
-                uint8_t *t = tmp + (size_t)ph * N;
-                uint8_t *bt = beta + (size_t)ph * (N - 1) + N - 2 * s;
-                if (!right) {
-                    bt[j] = t[j];  // a completed left node: kept for its right sibling
-                } else {
-                    const uint8_t v = t[j];
-                    t[s + j] = v;
-                    t[j] = v ^ bt[j];
+        for (int ls = 0; ls < n; ++ls) {
+            const int sz = 1 << ls;
+            const bool wide = (cur << ls) > 32;
+            sync_for(wide);
+            const bool right = (i >> ls) & 1;
+            if (wide || w0) {
+                for (int idx = wide ? threadIdx.x : lane; idx < (cur << ls); idx += wide ? T : 32) {
+                    const int k = idx >> ls, j = idx & (sz - 1);
+                    const int ph = slot[k];
+                    uint8_t *t = tmp + (size_t)ph * N;
+                    uint8_t *bt = beta + (size_t)ph * (N - 1) + N - 2 * sz;
+                    const uint8_t v = (ls == 0) ? ubuf[(size_t)ph * N + i] : t[j];
+                    if (!right) {
+                        bt[j] = v;  // a completed left node: kept for its right sibling
+                    } else {
+                        t[sz + j] = v;
+                        t[j] = v ^ bt[j];
+                    }
                 }
             }
-            __syncthreads();
             if (!right) break;
         }
     }
 
     // CRC-aided selection and output
-    const int cur = s_cur;
+    __syncthreads();
     if (threadIdx.x < cur) {
         const int k = threadIdx.x;
         const uint8_t *uk = ubuf + (size_t)slot[k] * N;
         int ok = 1;
         if (p.r > 0) {
             const int Kd = p.K - p.r;
-            const uint64_t rem = crc_of([&](int q) { return uk[p.info[q]]; }, Kd, p.g, p.r);
-            for (int q = 0; q < p.r; ++q) ok &= ((rem >> (p.r - 1 - q)) & 1ull) == uk[p.info[Kd + q]];
+            const uint64_t rem = crc_of([&](int q) { return uk[s_info[q]]; }, Kd, p.g, p.r);
+            for (int q = 0; q < p.r; ++q) ok &= ((rem >> (p.r - 1 - q)) & 1ull) == uk[s_info[Kd + q]];
         }
         keep_c[k] = ok;
     }
@@ -336,10 +381,10 @@ __global__ void __launch_bounds__(kPolarThreads) k_polar_scl(const PolarScl p) {
     __syncthreads();
     const uint8_t *ub = ubuf + (size_t)slot[s_best] * N;
     const int Kd = p.K - p.r, kw = (Kd + 31) >> 5;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = T >> 5;
+    const int warp = threadIdx.x >> 5, nwarps = T >> 5;
     for (int w = warp; w < kw; w += nwarps) {
         const int q = 32 * w + lane;
-        const unsigned word = __ballot_sync(0xFFFFFFFFu, q < Kd && ub[p.info[q]] != 0);
+        const unsigned word = __ballot_sync(0xFFFFFFFFu, q < Kd && ub[s_info[q]] != 0);
         if (lane == 0) p.data[b * kw + w] = word;
     }
 }
@@ -449,6 +494,8 @@ extern "C" int polar_scl_decode(ldpcx_polar_t c, const float *llr, int64_t B, in
     p.B = B;
     if (cudaFuncSetAttribute(k_polar_scl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return LDPCX_E_CUDA;
-    k_polar_scl<<<(unsigned)B, kPolarThreads, smem, (cudaStream_t)stream>>>(p);
+    // small lists run mostly in warp 0: fewer threads per CTA leave room for more CTAs per SM
+    const int threads = L <= 2 ? 64 : L <= 8 ? 128 : kPolarThreads;
+    k_polar_scl<<<(unsigned)B, threads, smem, (cudaStream_t)stream>>>(p);
     return cuda_status(cudaGetLastError());
 }
