@@ -321,9 +321,11 @@ def run_gpu(args):
             "codewords_per_s": world * B / (ms_per_step * 1e-3),
             "ber": c[1] / c[0] if c[0] else None, "bler": c[3] / c[2] if c[2] else None,
             "decode_ms_per_launch": dec_mean,
+            "decode_ms_median": statistics.median(dec_ms),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
                          "frac": achieved / pk["hbm_gbs"],
                          "traffic": None if traffic_cw is None else traffic_cw * B,
+                         "dram_gbs_from_profile": None if traffic_cw is None else traffic_cw * B / (dec_mean * 1e-3) / 1e9,
                          "kernel": "k_layered_cns_sched<BG1, fp16, Z=384>" if cn_state else "k_layered<20, min-sum, fp16>",
                          "message_format": "check-node state" if cn_state else "per-edge messages",
                          "message_bytes_per_codeword_iteration": msg_cw,
