@@ -58,14 +58,18 @@ __device__ __forceinline__ uint4 (&ring(uint4 (&a)[K], uint4 (&b)[K], uint4 (&c)
     else return c;
 }
 
-// Geometry of one codeword's state: region bytes of a core and of an extension row.
+// Geometry of one codeword's state: region bytes of a core and of an extension
+// row, and (one check node per thread) the thread's slot in core row 0 and in
+// extension row 0.
 struct SchedGeo {
     int Lc, Le;
+    unsigned char *core_z, *ext_z;
     __device__ __forceinline__ int off(int r) const { return r < 4 ? r * Lc : 4 * Lc + (r - 4) * Le; }
 };
 
 // Layered min-sum update of the K check nodes zk[0..K) of a row of exact
-// degree D (the rule of cns_update, pass by pass over the K nodes).
+// degree D (the rule of cns_update, pass by pass over the K nodes). The state
+// slot of node k is row + zk[k] * slot bytes, or row itself when K = 1.
 template <int D, int PREC, int K>
 __device__ __forceinline__ void cns_update_k(const Params &p, float *app, const int2 *at, const int (&zk)[K],
                                              const uint4 (&s_old)[K], unsigned char *row, bool store) {
@@ -112,35 +116,49 @@ __device__ __forceinline__ void cns_update_k(const Params &p, float *app, const 
     }
     if (store) {
 #pragma unroll
-        for (int k = 0; k < K; ++k) cns_store(row + zk[k] * SB, SB, cns_pack<PREC>(mn[k], eq[k], neg[k], D));
+        for (int k = 0; k < K; ++k)
+            cns_store(K == 1 ? row : row + zk[k] * SB, SB, cns_pack<PREC>(mn[k], eq[k], neg[k], D));
     }
 }
 
 // One layer step of degree D on row r (blocks from b0, slots from off):
 // prefetch the state of layer r + 2 into s_far, update from s_cur, barrier.
+// With K = 1 the slot addresses come from two per-thread bases (core and
+// extension rows), so a step adds one row offset instead of recomputing
+// z * slot bytes; the state loaded is the same.
 template <int D, int BG, int PREC, int K>
 __device__ __forceinline__ void sched_step(const Params &p, const int2 *s_at, float *app, unsigned char *st,
                                            const int (&zk)[K], int t, int r, int b0, int off, const SchedGeo &geo,
                                            bool done, const uint4 (&s_cur)[K], uint4 (&s_far)[K]) {
     using S = Sched<BG>;
     using L = SchedLayout<BG, PREC>;
-    int r2 = r + 2, t2 = t;
-    if (r2 >= S::rows) {
-        r2 -= S::rows;
-        ++t2;
-    }
+    const bool wrap = r + 2 >= S::rows;  // the state two layers on is the next iteration's
+    const int r2 = wrap ? r + 2 - S::rows : r + 2;
+    const int t2 = wrap ? t + 1 : t;
     if (t2 == 0) {
 #pragma unroll
         for (int k = 0; k < K; ++k) s_far[k] = make_uint4(0u, 0u, 0u, 0u);  // iteration 0: zero messages
     } else if (!done && t2 < p.iters) {
-        const unsigned char *row2 = st + geo.off(r2);
+        if constexpr (K == 1) {
+            if (r2 < 4) s_far[0] = cns_load(geo.core_z + r2 * geo.Lc, L::sb_core);
+            else s_far[0] = cns_load(geo.ext_z + (r2 - 4) * geo.Le, L::sb_ext);
+        } else {
+            const unsigned char *row2 = st + geo.off(r2);
 #pragma unroll
-        for (int k = 0; k < K; ++k) {
-            if (r2 < 4) s_far[k] = cns_load(row2 + zk[k] * L::sb_core, L::sb_core);
-            else s_far[k] = cns_load(row2 + zk[k] * L::sb_ext, L::sb_ext);
+            for (int k = 0; k < K; ++k) {
+                if (r2 < 4) s_far[k] = cns_load(row2 + zk[k] * L::sb_core, L::sb_core);
+                else s_far[k] = cns_load(row2 + zk[k] * L::sb_ext, L::sb_ext);
+            }
         }
     }
-    if (!done) cns_update_k<D, PREC, K>(p, app, s_at + b0, zk, s_cur, st + off, t + 1 < p.iters);
+    if (!done) {
+        if constexpr (K == 1) {
+            unsigned char *slot = (r < 4 ? geo.core_z : geo.ext_z - 4 * geo.Lc) + off;
+            cns_update_k<D, PREC, K>(p, app, s_at + b0, zk, s_cur, slot, t + 1 < p.iters);
+        } else {
+            cns_update_k<D, PREC, K>(p, app, s_at + b0, zk, s_cur, st + off, t + 1 < p.iters);
+        }
+    }
     __syncthreads();
 }
 
@@ -202,6 +220,8 @@ __global__ void __launch_bounds__(kMaxThreads / K, 2)
     SchedGeo geo;
     geo.Lc = (L::sb_core * ZV + 15) / 16 * 16;
     geo.Le = (L::sb_ext * ZV + 15) / 16 * 16;
+    geo.core_z = st + zk[0] * L::sb_core;
+    geo.ext_z = st + 4 * geo.Lc + zk[0] * L::sb_ext;
     __syncthreads();
 
     uint4 a[K], b[K], c[K];
