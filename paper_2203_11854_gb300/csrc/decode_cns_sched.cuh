@@ -80,13 +80,21 @@ __device__ __forceinline__ void cns_update_k(const Params &p, float *app, const 
     for (int k = 0; k < K; ++k) cns_unpack<PREC>(s_old[k], D, mo[k], eqo[k], nego[k]);
     float T[K][D];
     int vi[K][D];
+    // the old neg bits walked down through bit 31 of wn (edges in descending order: the row's updates
+    // touch distinct APP entries, and the two-minimum rule does not depend on the order)
+    unsigned wn[K];
 #pragma unroll
-    for (int j = 0; j < D; ++j) {
+    for (int k = 0; k < K; ++k) wn[k] = nego[k] << (32 - D);
+#pragma unroll
+    for (int j = D - 1; j >= 0; --j) {
         const int2 a = at[j];
 #pragma unroll
         for (int k = 0; k < K; ++k) {
             vi[k][j] = vn_off_fma(p, a, zk[k]);
-            T[k][j] = __fsub_rn(app_at(app, vi[k][j]), mo[k].msg((eqo[k] >> j) & 1u, (nego[k] >> j) & 1u));
+            const float m = ((eqo[k] >> j) & 1u) ? mo[k].r2 : mo[k].r1;
+            const float old = __uint_as_float(__float_as_uint(m) | (wn[k] & 0x80000000u));
+            wn[k] *= p.k_two;
+            T[k][j] = __fsub_rn(app_at(app, vi[k][j]), old);
         }
     }
     FastMinSum<D> cn[K];
@@ -107,11 +115,11 @@ __device__ __forceinline__ void cns_update_k(const Params &p, float *app, const 
 #pragma unroll
         for (int k = 0; k < K; ++k) {
             const bool e = fabsf(T[k][j]) == cn[k].m1;
+            // sign of the new message: bit 31 of U = bits(T) + the product's sign bit (a flip of bit 31)
             const unsigned U = __float_as_uint(T[k][j]) * p.k_one + sxs[k];
-            const unsigned n = __umulhi(U, p.k_two);
-            neg[k] = neg[k] * p.k_two + n;
+            neg[k] = __funnelshift_l(U, neg[k], 1);  // (neg << 1) | (U >> 31)
             if (e) eq[k] |= 1u << j;
-            app_at(app, vi[k][j]) = __fadd_rn(T[k][j], __uint_as_float(n * p.k_two31 + (e ? b2[k] : b1[k])));
+            app_at(app, vi[k][j]) = __fadd_rn(T[k][j], __uint_as_float((U & 0x80000000u) | (e ? b2[k] : b1[k])));
         }
     }
     if (store) {
