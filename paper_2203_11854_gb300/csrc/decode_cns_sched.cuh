@@ -90,7 +90,7 @@ __device__ __forceinline__ void cns_update_k(const Params &p, float *app, const 
         const int2 a = at[j];
 #pragma unroll
         for (int k = 0; k < K; ++k) {
-            vi[k][j] = vn_off_fma(p, a, zk[k]);
+            vi[k][j] = vn_off_mixed(p, a, zk[k]);
             const float m = ((eqo[k] >> j) & 1u) ? mo[k].r2 : mo[k].r1;
             const float old = __uint_as_float(__float_as_uint(m) | (wn[k] & 0x80000000u));
             wn[k] *= p.k_two;
