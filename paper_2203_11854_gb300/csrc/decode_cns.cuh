@@ -194,13 +194,13 @@ __device__ __forceinline__ float &app_at(float *app, int off) {
 // the old state, T = APP - R_old, check-node rule, APP = T + R_new, store the
 // new state.
 //
-// Integer work is balanced between the ALU and FMA pipes: the APP offset by
-// vn_off_fma; in the second pass the sign of the new message is bit 31 of U =
+// Integer work is balanced between the ALU and FMA pipes. Both passes visit
+// the edges in descending order (the updates of one row touch distinct APP
+// entries, and the two-minimum rule does not depend on the order). In the
+// first pass the old neg bits walk down through bit 31 of a word doubled by
+// multiply-adds; in the second the sign of the new message is bit 31 of U =
 // bits(T) + (sign bit of the product), an addition modulo 2^32 that flips
-// exactly bit 31; n = U >> 31 as a high-word product with 2; the message bits
-// are n 2^31 + bits(magnitude); the neg mask is built by Horner's rule over the
-// edges in descending order (the updates of one row touch distinct APP
-// entries, so their order changes no result).
+// exactly bit 31, and one funnel shift appends it to the neg mask.
 template <int D, int DM, int PREC, int ZC>
 __device__ __forceinline__ void cns_update(const Params &p, int deg, float *app, const int2 *at, int z,
                                            const uint4 &s_old, unsigned char *slot, int sbytes, bool store) {
@@ -211,13 +211,17 @@ __device__ __forceinline__ void cns_update(const Params &p, int deg, float *app,
     cns_unpack<PREC>(s_old, d, mo, eqo, nego);
     float T[N];
     int vi[D ? N : 1];
+    unsigned wn = d ? nego << (32 - d) : 0u;  // old neg bits walked down through bit 31 (descending edges)
 #pragma unroll
-    for (int j = 0; j < N; ++j) {
+    for (int j = N - 1; j >= 0; --j) {
         T[j] = 0.0f;
         if (D || j < d) {
-            const int v = vn_off_fma(p, at[j], z);
+            const int v = vn_off_mixed(p, at[j], z);
             if constexpr (D != 0) vi[j] = v;
-            T[j] = __fsub_rn(app_at(app, v), mo.msg((eqo >> j) & 1u, (nego >> j) & 1u));
+            const float m = ((eqo >> j) & 1u) ? mo.r2 : mo.r1;
+            const float old = __uint_as_float(__float_as_uint(m) | (wn & 0x80000000u));
+            wn *= p.k_two;
+            T[j] = __fsub_rn(app_at(app, v), old);
         }
     }
     FastMinSum<N> cn;
@@ -232,13 +236,12 @@ __device__ __forceinline__ void cns_update(const Params &p, int deg, float *app,
         if (D || j < d) {
             const bool e = fabsf(T[j]) == cn.m1;
             const unsigned U = __float_as_uint(T[j]) * p.k_one + sxs;
-            const unsigned n = __umulhi(U, p.k_two);
-            neg = neg * p.k_two + n;
+            neg = __funnelshift_l(U, neg, 1);  // (neg << 1) | (U >> 31)
             if (e) eq |= 1u << j;
             int v;
             if constexpr (D != 0) v = vi[j];
-            else v = vn_off_fma(p, at[j], z);
-            app_at(app, v) = __fadd_rn(T[j], __uint_as_float(n * p.k_two31 + (e ? b2 : b1)));
+            else v = vn_off_mixed(p, at[j], z);
+            app_at(app, v) = __fadd_rn(T[j], __uint_as_float((U & 0x80000000u) | (e ? b2 : b1)));
         }
     }
     if (store) cns_store(slot, sbytes, cns_pack<PREC>(mn, eq, neg, d));
