@@ -246,10 +246,11 @@ int ldpc_bp_decode(ldpcx_code_t code, const float *llr_ch, int64_t B, const ldpc
  * sign bits instead of one stored message per edge (4, 8 or 16 bytes per check
  * node); every message is rebuilt exactly, so results are identical. Used when
  * the state fits the per-edge workspace. 0 = per-edge messages.
- * LDPCX_TUNE_SCHEDULE: 1 (default) = with check-node state, a code whose row
- * degrees are those of a full base graph of its shape (every code of
- * qc_ldpc_build with rows_kept = 0) runs a kernel with that layer schedule
- * compiled in; 0 = the kernel that reads the schedule from the row table.
+ * LDPCX_TUNE_SCHEDULE: 1 (default) = a code whose row degrees are those of
+ * its shape's base graph (every code of qc_ldpc_build: full, or truncated by
+ * rows_kept) runs a kernel with that layer schedule compiled in -- min-sum
+ * with check-node state for full and truncated codes, sum-product for full
+ * codes; 0 = the kernels that read the schedule from the row table.
  * Knobs change speed only, never results. */
 #define LDPCX_TUNE_L2_PREFETCH 1
 #define LDPCX_TUNE_ZPT 2

@@ -19,10 +19,11 @@ std::atomic<int> g_specialised{1};  // use compile-time-Z kernels when built
 std::atomic<int> g_cns{1};          // layered min-sum keeps check-node state instead of per-edge messages
 std::atomic<int> g_sched{1};        // ... with the full base graph's layer schedule compiled in
 
-// Row degrees of c equal those of the full base graph of shape bg.
+// Row degrees of c equal those of the first c->rows rows of the full base
+// graph of shape bg (a full or row-truncated code of qc_ldpc_build).
 template <int BG> bool sched_matches(const ldpcx_code *c) {
     using S = Sched<BG>;
-    if (c->rows != S::rows) return false;
+    if (c->rows < 4 || c->rows > S::rows) return false;
     for (int r = 0; r < c->rows; ++r) {
         const int d = c->row_ptr[r + 1] - c->row_ptr[r];
         const int want = r == 0 ? S::dc0 : r == 1 ? S::dc1 : r == 2 ? S::dc2 : r == 3 ? S::dc3
@@ -219,7 +220,9 @@ int decode_impl(ldpcx_code_t c, const float *llr_ch, int64_t B, const ldpcx_deco
     size_t smem = smem_bytes(p, layered ? 1 : 2);
     // layered sum-product on a full base graph: per-edge messages, compiled-in schedule
     if (layered && algo == kSpa && zpt == 1 && g_sched.load()) {
-        const int bg = sched_shape(c);
+        // the per-edge kernel compiles the full schedule: truncated codes take the row table
+        int bg = sched_shape(c);
+        if (bg && c->rows != (bg == 1 ? Sched<1>::rows : Sched<2>::rows)) bg = 0;
         SchedFn sf = bg && c->nnz <= kSchedMaxBlocks
                          ? layered_edge_sched_kernel(bg, algo, o->msg_prec, g_specialised.load() ? c->Z : 0)
                          : nullptr;
@@ -229,8 +232,10 @@ int decode_impl(ldpcx_code_t c, const float *llr_ch, int64_t B, const ldpcx_deco
         cns_bytes(c, o->msg_prec) <= p.msg_stride * p.msg_size) {
         const int zs = g_specialised.load() ? c->Z : 0;
         const int bg = g_sched.load() ? sched_shape(c) : 0;
-        const int kpt = g_zpt.load() == 2 && c->Z % 2 == 0 ? 2 : 1;  // check nodes per thread
-        SchedFn sf = bg && c->nnz <= kSchedMaxBlocks ? layered_cns_sched_kernel(bg, o->msg_prec, zs, kpt) : nullptr;
+        const bool trunc = bg && c->rows != (bg == 1 ? Sched<1>::rows : Sched<2>::rows);
+        const int kpt = !trunc && g_zpt.load() == 2 && c->Z % 2 == 0 ? 2 : 1;  // check nodes per thread
+        SchedFn sf = bg && c->nnz <= kSchedMaxBlocks ? layered_cns_sched_kernel(bg, o->msg_prec, zs, kpt, trunc)
+                                                     : nullptr;
         if (sf) return launch_sched(sf, c, p, B, kpt, stream);
         KernelFn f = layered_cns_kernel(c->max_deg, o->msg_prec, zs);
         if (f) {

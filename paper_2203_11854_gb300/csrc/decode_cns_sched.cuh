@@ -1,5 +1,5 @@
-// Layered min-sum with check-node state on the full 5G-shaped base graphs,
-// with the layer schedule compiled in.
+// Layered min-sum with check-node state on the 5G-shaped base graphs (full or
+// truncated to their first rows), with the layer schedule compiled in.
 //
 // The row degrees of a full base graph depend on its shape alone (the seed
 // moves blocks within a row, never changes how many there are): four core
@@ -134,14 +134,14 @@ __device__ __forceinline__ void cns_update_k(const Params &p, float *app, const 
 // With K = 1 the slot addresses come from two per-thread bases (core and
 // extension rows), so a step adds one row offset instead of recomputing
 // z * slot bytes; the state loaded is the same.
-template <int D, int BG, int PREC, int K>
+template <int D, int BG, int PREC, int K, bool TRUNC>
 __device__ __forceinline__ void sched_step(const Params &p, const int2 *s_at, float *app, unsigned char *st,
                                            const int (&zk)[K], int t, int r, int b0, int off, const SchedGeo &geo,
                                            bool done, const uint4 (&s_cur)[K], uint4 (&s_far)[K]) {
-    using S = Sched<BG>;
     using L = SchedLayout<BG, PREC>;
-    const bool wrap = r + 2 >= S::rows;  // the state two layers on is the next iteration's
-    const int r2 = wrap ? r + 2 - S::rows : r + 2;
+    const int rows = TRUNC ? p.rows : Sched<BG>::rows;
+    const bool wrap = r + 2 >= rows;  // the state two layers on is the next iteration's
+    const int r2 = wrap ? r + 2 - rows : r + 2;
     const int t2 = wrap ? t + 1 : t;
     if (t2 == 0) {
 #pragma unroll
@@ -171,7 +171,7 @@ __device__ __forceinline__ void sched_step(const Params &p, const int2 *s_at, fl
 }
 
 // COUNT consecutive rows of degree D from row r0, the first at ring phase PH.
-template <int D, int COUNT, int PH, int BG, int PREC, int K>
+template <int D, int COUNT, int PH, int BG, int PREC, int K, bool TRUNC = false>
 __device__ __forceinline__ void sched_run(const Params &p, const int2 *s_at, float *app, unsigned char *st,
                                           const int (&zk)[K], int t, int r0, int b0, int off0, int Lrow,
                                           const SchedGeo &geo, bool done, uint4 (&a)[K], uint4 (&b)[K],
@@ -179,26 +179,68 @@ __device__ __forceinline__ void sched_run(const Params &p, const int2 *s_at, flo
     int r = r0, bb = b0, off = off0;
 #pragma unroll 1
     for (int i = 0; i < COUNT / 3; ++i) {
-        sched_step<D, BG, PREC, K>(p, s_at, app, st, zk, t, r, bb, off, geo, done, ring<PH, K>(a, b, c),
+        sched_step<D, BG, PREC, K, TRUNC>(p, s_at, app, st, zk, t, r, bb, off, geo, done, ring<PH, K>(a, b, c),
                                    ring<PH + 2, K>(a, b, c));
-        sched_step<D, BG, PREC, K>(p, s_at, app, st, zk, t, r + 1, bb + D, off + Lrow, geo, done,
+        sched_step<D, BG, PREC, K, TRUNC>(p, s_at, app, st, zk, t, r + 1, bb + D, off + Lrow, geo, done,
                                    ring<PH + 1, K>(a, b, c), ring<PH + 3, K>(a, b, c));
-        sched_step<D, BG, PREC, K>(p, s_at, app, st, zk, t, r + 2, bb + 2 * D, off + 2 * Lrow, geo, done,
+        sched_step<D, BG, PREC, K, TRUNC>(p, s_at, app, st, zk, t, r + 2, bb + 2 * D, off + 2 * Lrow, geo, done,
                                    ring<PH + 2, K>(a, b, c), ring<PH + 4, K>(a, b, c));
         r += 3;
         bb += 3 * D;
         off += 3 * Lrow;
     }
     if constexpr (COUNT % 3 >= 1)
-        sched_step<D, BG, PREC, K>(p, s_at, app, st, zk, t, r, bb, off, geo, done, ring<PH, K>(a, b, c),
+        sched_step<D, BG, PREC, K, TRUNC>(p, s_at, app, st, zk, t, r, bb, off, geo, done, ring<PH, K>(a, b, c),
                                    ring<PH + 2, K>(a, b, c));
     if constexpr (COUNT % 3 == 2)
-        sched_step<D, BG, PREC, K>(p, s_at, app, st, zk, t, r + 1, bb + D, off + Lrow, geo, done,
+        sched_step<D, BG, PREC, K, TRUNC>(p, s_at, app, st, zk, t, r + 1, bb + D, off + Lrow, geo, done,
                                    ring<PH + 1, K>(a, b, c), ring<PH + 3, K>(a, b, c));
 }
 
-// K check nodes per thread: G codewords per CTA of G Z / K threads.
-template <int BG, int PREC, int ZC = 0, int K = 1>
+// `count` (run-time) consecutive rows of degree D from row r0, starting at
+// ring phase 0; the ring is rotated afterwards so that the next run starts at
+// phase 0 again.
+template <int D, int BG, int PREC, int K>
+__device__ __forceinline__ void sched_run_n(const Params &p, const int2 *s_at, float *app, unsigned char *st,
+                                            const int (&zk)[K], int t, int r0, int b0, int off0, int Lrow,
+                                            int count, const SchedGeo &geo, bool done, uint4 (&a)[K],
+                                            uint4 (&b)[K], uint4 (&c)[K]) {
+    int r = r0, bb = b0, off = off0;
+#pragma unroll 1
+    for (int i = 0; i < count / 3; ++i) {
+        sched_step<D, BG, PREC, K, true>(p, s_at, app, st, zk, t, r, bb, off, geo, done, a, c);
+        sched_step<D, BG, PREC, K, true>(p, s_at, app, st, zk, t, r + 1, bb + D, off + Lrow, geo, done, b, a);
+        sched_step<D, BG, PREC, K, true>(p, s_at, app, st, zk, t, r + 2, bb + 2 * D, off + 2 * Lrow, geo, done, c, b);
+        r += 3;
+        bb += 3 * D;
+        off += 3 * Lrow;
+    }
+    const int rem = count - 3 * (count / 3);
+    if (rem >= 1) sched_step<D, BG, PREC, K, true>(p, s_at, app, st, zk, t, r, bb, off, geo, done, a, c);
+    if (rem == 2) sched_step<D, BG, PREC, K, true>(p, s_at, app, st, zk, t, r + 1, bb + D, off + Lrow, geo, done, b, a);
+    if (rem == 1) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const uint4 x = a[k];
+            a[k] = b[k];
+            b[k] = c[k];
+            c[k] = x;
+        }
+    } else if (rem == 2) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const uint4 x = c[k];
+            c[k] = b[k];
+            b[k] = a[k];
+            a[k] = x;
+        }
+    }
+}
+
+// K check nodes per thread: G codewords per CTA of G Z / K threads. The code
+// is the full base graph of shape BG or a truncation of it to its first p.rows
+// rows (the extension rows in order), so the runs have run-time lengths.
+template <int BG, int PREC, int ZC = 0, int K = 1, bool TRUNC = false>
 __global__ void __launch_bounds__(kMaxThreads / K, 2)
     k_layered_cns_sched(const Params p, const __grid_constant__ SchedTab tab) {
     using S = Sched<BG>;
@@ -232,35 +274,53 @@ __global__ void __launch_bounds__(kMaxThreads / K, 2)
     geo.ext_z = st + 4 * geo.Lc + zk[0] * L::sb_ext;
     __syncthreads();
 
+    const int n_hi = min(S::n_hi, p.rows - 4), n_lo = p.rows - 4 - n_hi;
     uint4 a[K], b[K], c[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) a[k] = b[k] = c[k] = make_uint4(0u, 0u, 0u, 0u);
     for (int t = 0; t < p.iters; ++t) {
-        sched_run<S::dc0, 1, 0, BG, PREC, K>(p, s_at, app, st, zk, t, 0, 0, 0, geo.Lc, geo, done, a, b, c);
-        sched_run<S::dc1, 1, 1, BG, PREC, K>(p, s_at, app, st, zk, t, 1, S::dc0, geo.Lc, geo.Lc, geo, done, a, b,
-                                             c);
-        sched_run<S::dc2, 1, 2, BG, PREC, K>(p, s_at, app, st, zk, t, 2, S::dc0 + S::dc1, 2 * geo.Lc, geo.Lc, geo,
-                                             done, a, b, c);
-        sched_run<S::dc3, 1, 3, BG, PREC, K>(p, s_at, app, st, zk, t, 3, S::dc0 + S::dc1 + S::dc2, 3 * geo.Lc,
-                                             geo.Lc, geo, done, a, b, c);
-        sched_run<S::d_hi, S::n_hi, 4, BG, PREC, K>(p, s_at, app, st, zk, t, 4, L::b_hi, 4 * geo.Lc, geo.Le, geo,
-                                                    done, a, b, c);
-        sched_run<S::d_lo, S::rows - 4 - S::n_hi, 4 + S::n_hi, BG, PREC, K>(
-            p, s_at, app, st, zk, t, 4 + S::n_hi, L::b_lo, 4 * geo.Lc + S::n_hi * geo.Le, geo.Le, geo, done, a, b, c);
-        // the next iteration's first step finds its state at phase rows mod 3
+        sched_run<S::dc0, 1, 0, BG, PREC, K, TRUNC>(p, s_at, app, st, zk, t, 0, 0, 0, geo.Lc, geo, done, a, b, c);
+        sched_run<S::dc1, 1, 1, BG, PREC, K, TRUNC>(p, s_at, app, st, zk, t, 1, S::dc0, geo.Lc, geo.Lc, geo, done,
+                                                    a, b, c);
+        sched_run<S::dc2, 1, 2, BG, PREC, K, TRUNC>(p, s_at, app, st, zk, t, 2, S::dc0 + S::dc1, 2 * geo.Lc, geo.Lc,
+                                                    geo, done, a, b, c);
+        sched_run<S::dc3, 1, 3, BG, PREC, K, TRUNC>(p, s_at, app, st, zk, t, 3, S::dc0 + S::dc1 + S::dc2,
+                                                    3 * geo.Lc, geo.Lc, geo, done, a, b, c);
+        if constexpr (!TRUNC) {
+            // the full graph: run lengths known here, phases follow on
+            sched_run<S::d_hi, S::n_hi, 4, BG, PREC, K>(p, s_at, app, st, zk, t, 4, L::b_hi, 4 * geo.Lc, geo.Le,
+                                                        geo, done, a, b, c);
+            sched_run<S::d_lo, S::rows - 4 - S::n_hi, 4 + S::n_hi, BG, PREC, K>(
+                p, s_at, app, st, zk, t, 4 + S::n_hi, L::b_lo, 4 * geo.Lc + S::n_hi * geo.Le, geo.Le, geo, done, a,
+                b, c);
+            // the next iteration's first step finds its state at phase rows mod 3
 #pragma unroll
-        for (int k = 0; k < K; ++k) {
-            if constexpr (S::rows % 3 == 1) {
+            for (int k = 0; k < K; ++k) {
+                if constexpr (S::rows % 3 == 1) {
+                    const uint4 x = a[k];
+                    a[k] = b[k];
+                    b[k] = c[k];
+                    c[k] = x;
+                } else if constexpr (S::rows % 3 == 2) {
+                    const uint4 x = c[k];
+                    c[k] = b[k];
+                    b[k] = a[k];
+                    a[k] = x;
+                }
+            }
+        } else {
+            // a truncation: four core steps end at phase 1; rotate so that each run starts at phase 0
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
                 const uint4 x = a[k];
                 a[k] = b[k];
                 b[k] = c[k];
                 c[k] = x;
-            } else if constexpr (S::rows % 3 == 2) {
-                const uint4 x = c[k];
-                c[k] = b[k];
-                b[k] = a[k];
-                a[k] = x;
             }
+            sched_run_n<S::d_hi, BG, PREC, K>(p, s_at, app, st, zk, t, 4, L::b_hi, 4 * geo.Lc, geo.Le, n_hi, geo,
+                                              done, a, b, c);
+            sched_run_n<S::d_lo, BG, PREC, K>(p, s_at, app, st, zk, t, 4 + S::n_hi, L::b_lo,
+                                              4 * geo.Lc + S::n_hi * geo.Le, geo.Le, n_lo, geo, done, a, b, c);
         }
         if (!done) iters_run = t + 1;
         if (p.early_stop) {
@@ -281,9 +341,10 @@ __global__ void __launch_bounds__(kMaxThreads / K, 2)
 
 using SchedFn = void (*)(Params, SchedTab);
 
-// Kernel for a code whose row degrees follow the full base graph of shape bg
-// (1 or 2) with k check nodes per thread (1, or 2 when Z is even), or nullptr.
-SchedFn layered_cns_sched_kernel(int bg, int prec, int Z, int k);
+// Kernel for a code whose row degrees follow the base graph of shape bg (1 or
+// 2), full (k check nodes per thread: 1, or 2 when Z is even) or truncated
+// (trunc, one check node per thread), or nullptr.
+SchedFn layered_cns_sched_kernel(int bg, int prec, int Z, int k, bool trunc);
 
 }  // namespace dec
 }  // namespace ldpcx

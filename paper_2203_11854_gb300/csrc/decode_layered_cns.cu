@@ -12,14 +12,14 @@ KernelFn cns_for(int dmax, int Z) {
     return dmax <= 12 ? k_layered_cns<12, PREC, 0> : k_layered_cns<20, PREC, 0>;
 }
 
-SchedFn cns_sched_f32(int bg, int Z, int k);
-SchedFn cns_sched_f16(int bg, int Z, int k);
-SchedFn cns_sched_fix6(int bg, int Z, int k);
+SchedFn cns_sched_f32(int bg, int Z, int k, bool trunc);
+SchedFn cns_sched_f16(int bg, int Z, int k, bool trunc);
+SchedFn cns_sched_fix6(int bg, int Z, int k, bool trunc);
 
-SchedFn layered_cns_sched_kernel(int bg, int prec, int Z, int k) {
-    if (prec == kF32) return cns_sched_f32(bg, Z, k);
-    if (prec == kF16) return cns_sched_f16(bg, Z, k);
-    return cns_sched_fix6(bg, Z, k);
+SchedFn layered_cns_sched_kernel(int bg, int prec, int Z, int k, bool trunc) {
+    if (prec == kF32) return cns_sched_f32(bg, Z, k, trunc);
+    if (prec == kF16) return cns_sched_f16(bg, Z, k, trunc);
+    return cns_sched_fix6(bg, Z, k, trunc);
 }
 
 KernelFn layered_cns_kernel(int dmax, int prec, int Z) {

@@ -47,12 +47,19 @@ CODES = {
     "bg1_z384": (1, 384, 0, 2, 5),
     "bg1_z128_r13": (1, 128, 13, 2, 9),
     "bg2_z200": (2, 200, 0, 0, 3),
+    # truncations of both shapes at rate points of the mixed workload (rows 24, 5, 7, 4); the two
+    # shortest send every column (with 2Z punctured, two punctured columns can share each of their
+    # few rows and then never resolve, so no codeword would stop early)
+    "bg1_z64_r24": (1, 64, 24, 2, 7),
+    "bg1_z32_r5": (1, 32, 5, 0, 11),
+    "bg2_z64_r7": (2, 64, 7, 2, 5),
+    "bg2_z16_r4": (2, 16, 4, 0, 13),
 }
 
 
 # channel strength per code for the early-stop cases: the truncated high-rate
 # code needs a stronger channel to converge within a few iterations
-STRONG = {"bg1_z128_r13": 5.0}
+STRONG = {"bg1_z128_r13": 5.0, "bg1_z64_r24": 4.0, "bg1_z32_r5": 7.0, "bg2_z64_r7": 6.0, "bg2_z16_r4": 7.0}
 
 
 def make_case(orc, name, mean, seed):
@@ -295,7 +302,8 @@ def test_repeat_calls_are_deterministic(lx, orc):
     assert np.array_equal(a, b)
 
 
-@pytest.mark.parametrize("name", ["bg2_z64", "bg1_z384", "bg2_z200", "bg1_z128_r13"])
+@pytest.mark.parametrize("name", ["bg2_z64", "bg1_z384", "bg2_z200", "bg1_z128_r13", "bg1_z64_r24", "bg1_z32_r5",
+                                  "bg2_z64_r7", "bg2_z16_r4"])
 @pytest.mark.parametrize("prec", [0, 1, 2])
 def test_kernel_variants_agree(lx, orc, name, prec):
     """Per-edge messages, check-node state with the row table, check-node state
