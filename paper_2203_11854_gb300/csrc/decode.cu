@@ -19,25 +19,7 @@ std::atomic<int> g_specialised{1};  // use compile-time-Z kernels when built
 std::atomic<int> g_cns{1};          // layered min-sum keeps check-node state instead of per-edge messages
 std::atomic<int> g_sched{1};        // ... with the full base graph's layer schedule compiled in
 
-// Row degrees of c equal those of the first c->rows rows of the full base
-// graph of shape bg (a full or row-truncated code of qc_ldpc_build).
-template <int BG> bool sched_matches(const ldpcx_code *c) {
-    using S = Sched<BG>;
-    if (c->rows < 4 || c->rows > S::rows) return false;
-    for (int r = 0; r < c->rows; ++r) {
-        const int d = c->row_ptr[r + 1] - c->row_ptr[r];
-        const int want = r == 0 ? S::dc0 : r == 1 ? S::dc1 : r == 2 ? S::dc2 : r == 3 ? S::dc3
-                       : r < 4 + S::n_hi ? S::d_hi : S::d_lo;
-        if (d != want) return false;
-    }
-    return true;
-}
-
-int sched_shape(const ldpcx_code *c) {
-    if (c->params.bg_shape == 1 && sched_matches<1>(c)) return 1;
-    if (c->params.bg_shape == 2 && sched_matches<2>(c)) return 2;
-    return 0;
-}
+int sched_shape(const ldpcx_code *c) { return sched_shape_of(c->row_ptr.data(), c->rows, c->params.bg_shape); }
 
 // Bytes of the check-node state of one codeword in format prec.
 int64_t cns_bytes(const ldpcx_code *c, int prec) {

@@ -240,22 +240,22 @@ __device__ __forceinline__ void sched_run_n(const Params &p, const int2 *s_at, f
 // K check nodes per thread: G codewords per CTA of G Z / K threads. The code
 // is the full base graph of shape BG or a truncation of it to its first p.rows
 // rows (the extension rows in order), so the runs have run-time lengths.
-template <int BG, int PREC, int ZC = 0, int K = 1, bool TRUNC = false>
-__global__ void __launch_bounds__(kMaxThreads / K, 2)
-    k_layered_cns_sched(const Params p, const __grid_constant__ SchedTab tab) {
+// The codewords cw_base .. cw_base+G-1 of p by the whole CTA; block table
+// s_at (constant bank or shared memory); the state of codeword cw at msg +
+// (cw - msg_cw0) * msg_stride * msg_size.
+template <int BG, int PREC, int ZC, int K, bool TRUNC>
+__device__ __forceinline__ void cns_sched_tile(const Params &p, int64_t cw_base, int64_t msg_cw0,
+                                               unsigned char *smem, const int2 *s_at) {
     using S = Sched<BG>;
     using L = SchedLayout<BG, PREC>;
-    extern __shared__ __align__(16) unsigned char smem[];
     const int ZV = ZC ? ZC : p.Z;
     const int H = ZV / K;  // threads per codeword
     float *s_app_all = reinterpret_cast<float *>(smem);
     uint32_t *s_vb = reinterpret_cast<uint32_t *>(s_app_all + (size_t)p.G * p.n);
     int32_t *s_rp = reinterpret_cast<int32_t *>(s_vb + p.nnz);
     int *s_flag = reinterpret_cast<int *>(s_rp + p.rows + 1);
-    const int2 *s_at = tab.at;
 
     load_tables(p, s_vb, s_rp);  // for the syndrome check
-    const int64_t cw_base = (int64_t)blockIdx.x * p.G;
     load_channel(p, s_app_all, cw_base);
     const int g = threadIdx.x / H, z = threadIdx.x - g * H;
     int zk[K];
@@ -264,7 +264,8 @@ __global__ void __launch_bounds__(kMaxThreads / K, 2)
     const int64_t cw = cw_base + g;
     const bool active = g < p.G && cw < p.B;
     float *app = s_app_all + (size_t)(active ? g : 0) * p.n;
-    unsigned char *st = reinterpret_cast<unsigned char *>(p.msg) + (active ? cw : 0) * p.msg_stride * p.msg_size;
+    unsigned char *st =
+        reinterpret_cast<unsigned char *>(p.msg) + (active ? cw - msg_cw0 : 0) * p.msg_stride * p.msg_size;
     bool done = !active;
     int iters_run = 0;
     SchedGeo geo;
@@ -337,6 +338,32 @@ __global__ void __launch_bounds__(kMaxThreads / K, 2)
     }
     __syncthreads();
     write_outputs(p, s_app_all, cw_base, iters_run, g, active, z);
+}
+
+template <int BG, int PREC, int ZC = 0, int K = 1, bool TRUNC = false>
+__global__ void __launch_bounds__(kMaxThreads / K, 2)
+    k_layered_cns_sched(const Params p, const __grid_constant__ SchedTab tab) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    cns_sched_tile<BG, PREC, ZC, K, TRUNC>(p, (int64_t)blockIdx.x * p.G, 0, smem, tab.at);
+}
+
+// Host: the shape (1, 2) whose base graph's first `rows` row degrees the row
+// table has, or 0.
+inline int sched_shape_of(const int32_t *row_ptr, int rows, int bg_shape) {
+    auto match = [&](auto tag) {
+        using S = decltype(tag);
+        if (rows < 4 || rows > S::rows) return false;
+        for (int r = 0; r < rows; ++r) {
+            const int d = row_ptr[r + 1] - row_ptr[r];
+            const int want = r == 0 ? S::dc0 : r == 1 ? S::dc1 : r == 2 ? S::dc2 : r == 3 ? S::dc3
+                           : r < 4 + S::n_hi ? S::d_hi : S::d_lo;
+            if (d != want) return false;
+        }
+        return true;
+    };
+    if (bg_shape == 1 && match(Sched<1>{})) return 1;
+    if (bg_shape == 2 && match(Sched<2>{})) return 2;
+    return 0;
 }
 
 using SchedFn = void (*)(Params, SchedTab);

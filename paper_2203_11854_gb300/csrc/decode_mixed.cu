@@ -1,14 +1,16 @@
 // Mixed-size batch in one persistent launch: resident CTAs pull work items
 // (up to G codewords of one code) from a device queue, longest first, and run
-// a layered tile on each: the check-node-state tile (decode_cns.cuh) for
-// min-sum, the per-edge tile (decode_kernels.cuh) otherwise. Message scratch
+// a layered tile on each: for min-sum the compiled-schedule check-node-state
+// tile (decode_cns_sched.cuh) when the code is one of the 5G shapes, full or
+// truncated, else the row-table one (decode_cns.cuh); the per-edge tile
+// (decode_kernels.cuh) for sum-product. Message scratch
 // is one slot per resident CTA, sized for the largest item.
 #include <math.h>
 
 #include <algorithm>
 #include <vector>
 
-#include "decode_cns.cuh"
+#include "decode_cns_sched.cuh"
 
 namespace ldpcx {
 namespace {
@@ -20,6 +22,7 @@ struct GroupDesc {
     const int32_t *row_ptr;
     int Z, rows, nnz, n, k, n_tx, p0, G;
     int cns;  // min-sum with check-node state in the message slot
+    int bg;   // 1 or 2: the rows follow that shape's base graph (compiled schedule); 0: row table
     int64_t B, stride;
     const float *llr;
     float *llr_out;
@@ -90,8 +93,22 @@ __global__ void __launch_bounds__(kMaxThreads, 2) k_mixed(const MixedParams m) {
         p.k_two31 = m.k_two31;
         p.k_neg4z = (unsigned)(-4 * gd.Z) * m.k_one;
         if constexpr (ALGO == kMinSum) {
-            if (gd.cns) cns_tile<DMAX, PREC, 0>(p, item.cw_base, item.cw_base, smem);
-            else layered_tile<DMAX, ALGO, PREC, 1>(p, item.cw_base, item.cw_base, smem);
+            if (gd.cns && gd.bg) {
+                // block table {4 (col Z + shift), Z - shift} in shared memory past the tile's own tables
+                int2 *s_at = reinterpret_cast<int2 *>(
+                    (reinterpret_cast<uintptr_t>(smem + smem_bytes(p, 1)) + 7) & ~(uintptr_t)7);
+                for (int i = threadIdx.x; i < p.nnz; i += blockDim.x) {
+                    const uint32_t bk = p.blk[i];
+                    const int sh = (int)(bk & 0xFFFFu);
+                    s_at[i] = make_int2(4 * ((int)(bk >> 16) * p.Z + sh), p.Z - sh);
+                }
+                if (gd.bg == 1) cns_sched_tile<1, PREC, 0, 1, true>(p, item.cw_base, item.cw_base, smem, s_at);
+                else cns_sched_tile<2, PREC, 0, 1, true>(p, item.cw_base, item.cw_base, smem, s_at);
+            } else if (gd.cns) {
+                cns_tile<DMAX, PREC, 0>(p, item.cw_base, item.cw_base, smem);
+            } else {
+                layered_tile<DMAX, ALGO, PREC, 1>(p, item.cw_base, item.cw_base, smem);
+            }
         } else {
             layered_tile<DMAX, ALGO, PREC, 1>(p, item.cw_base, item.cw_base, smem);
         }
@@ -240,6 +257,8 @@ extern "C" int ldpc_bp_decode_mixed(const ldpcx_batch_group *groups, int n_group
         gd.G = group_G(c);
         gd.B = g.B;
         gd.stride = stride_of(c);
+        gd.bg = sched_shape_of(c->row_ptr.data(), c->rows, c->params.bg_shape);
+        if (gd.bg && c->nnz > kSchedMaxBlocks) gd.bg = 0;
         gd.cns = o->algo == LDPCX_LAYERED_MINSUM &&
                  cns_fits(c, o->msg_prec, gd.stride * (int64_t)(o->msg_prec == LDPCX_MSG_F32   ? 4
                                                                 : o->msg_prec == LDPCX_MSG_F16 ? 2
