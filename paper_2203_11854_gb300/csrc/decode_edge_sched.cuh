@@ -32,7 +32,7 @@ __device__ __forceinline__ void edge_update(const Params &p, float *app, const i
         float old;
         if constexpr (kSparse) old = Rc[j];
         else old = load ? msg_load<PREC>(ml + (size_t)j * p.Z) : 0.0f;
-        const int v = vn_off_fma(p, at[j], z);
+        const int v = vn_off_mixed(p, at[j], z);
         if constexpr (kSparse) vi[j] = v;
         T[j] = __fsub_rn(app_at(app, v), old);
     }
@@ -48,7 +48,7 @@ __device__ __forceinline__ void edge_update(const Params &p, float *app, const i
         MsgVec<PREC, 1>::round_store(ml + (size_t)j * p.Z, r, rq, store);
         int v;
         if constexpr (kSparse) v = vi[j];
-        else v = vn_off_fma(p, at[j], z);
+        else v = vn_off_mixed(p, at[j], z);
         app_at(app, v) = __fadd_rn(T[j], rq[0]);
     }
 }
