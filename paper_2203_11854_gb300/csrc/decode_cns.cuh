@@ -181,9 +181,9 @@ __device__ __forceinline__ int vn_off_fma(const Params &p, const int2 at, int z)
 // The same offset in three instructions, one multiply-add and two ALU
 // operations: off = 4z + at.x, less 4Z when z >= at.y.
 __device__ __forceinline__ int vn_off_mixed(const Params &p, const int2 at, int z) {
-    int off = (int)((unsigned)z * p.k_four + (unsigned)at.x);
-    if (z >= at.y) off += (int)p.k_neg4z;
-    return off;
+    unsigned off = (unsigned)z * p.k_four + (unsigned)at.x;
+    if (z >= at.y) off = off * p.k_one + p.k_neg4z;  // a predicated multiply-add: the FMA pipe
+    return (int)off;
 }
 __device__ __forceinline__ float &app_at(float *app, int off) {
     return *reinterpret_cast<float *>(reinterpret_cast<char *>(app) + off);

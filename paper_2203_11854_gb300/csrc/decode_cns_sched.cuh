@@ -118,7 +118,7 @@ __device__ __forceinline__ void cns_update_k(const Params &p, float *app, const 
             // sign of the new message: bit 31 of U = bits(T) + the product's sign bit (a flip of bit 31)
             const unsigned U = __float_as_uint(T[k][j]) * p.k_one + sxs[k];
             neg[k] = __funnelshift_l(U, neg[k], 1);  // (neg << 1) | (U >> 31)
-            if (e) eq[k] |= 1u << j;
+            if (e) eq[k] = (1u << j) * p.k_one + eq[k];  // bit j is clear: add on the FMA pipe
             app_at(app, vi[k][j]) = __fadd_rn(T[k][j], __uint_as_float((U & 0x80000000u) | (e ? b2[k] : b1[k])));
         }
     }
