@@ -229,28 +229,42 @@ def run_gpu(args):
     kw = (code.k + 31) // 32
     r = code.k / code.n_tx
     n0 = torch.tensor([1.0 / (r * M * 10 ** (EBN0 / 10))], dtype=torch.float32, device=dev)
-    y = torch.empty((B, S, 2), dtype=torch.float32, device=dev)
-    info = torch.empty((B, kw), dtype=torch.int32, device=dev)
-    llr = torch.empty((B, code.n_tx), dtype=torch.float32, device=dev)
-    bits = torch.empty((B, kw), dtype=torch.int32, device=dev)
-    its = torch.empty((B,), dtype=torch.int32, device=dev)
+    # two buffer sets: step i + 1's transmitter and demapper run on their own stream while step i decodes
+    bufs = [dict(y=torch.empty((B, S, 2), dtype=torch.float32, device=dev),
+                 info=torch.empty((B, kw), dtype=torch.int32, device=dev),
+                 llr=torch.empty((B, code.n_tx), dtype=torch.float32, device=dev),
+                 bits=torch.empty((B, kw), dtype=torch.int32, device=dev),
+                 its=torch.empty((B,), dtype=torch.int32, device=dev)) for _ in range(2)]
+    y, info, llr, bits, its = (bufs[0][key] for key in ("y", "info", "llr", "bits", "its"))
     counts = torch.zeros(5, dtype=torch.int64, device=dev)
     dec = dict(algo=lx.LAYERED_MINSUM, iters=ITERS, msg_prec=lx.MSG_F16, offset=OFFSET, clamp=CLAMP)
     ws = torch.empty(lx.ldpc_bp_workspace(code, B, **dec), dtype=torch.uint8, device=dev)
     from paper_2203_11854_gb300 import multi
     cw_base = multi.rank_cw_base(rank)  # disjoint codeword (Philox counter) ranges per rank
 
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    # The decoder's stream has the higher priority, so its CTAs are dispatched first and the transmitter and
+    # demapper of the next step only take the SM slots that the decoder's last, partial wave leaves idle
+    # (4096 codewords on 2 x 152 slots: 13.5 waves). Every step still runs all four kernels.
+    dec_stream = torch.cuda.Stream(device=dev, priority=-1)
+    tx_stream = torch.cuda.Stream(device=dev, priority=0)
+    ev_rx = [torch.cuda.Event() for _ in range(2)]    # demapper output of buffer j is ready
+    ev_free = [torch.cuda.Event() for _ in range(2)]  # the error count has consumed buffer j
 
     def step(i, timed_decode=None):
-        lx.sim_tx(code, SEED, cw_base + i * B, B, M, n0, y_out=y, info_out=info, stream=stream)
-        lx.demap_app(y, n0, M, method=lx.DEMAP_MAXLOG, clamp=CLAMP, llr_out=llr, stream=stream)
+        b = bufs[i & 1]
+        tx_stream.wait_event(ev_free[i & 1])
+        lx.sim_tx(code, SEED, cw_base + i * B, B, M, n0, y_out=b["y"], info_out=b["info"], stream=tx_stream)
+        lx.demap_app(b["y"], n0, M, method=lx.DEMAP_MAXLOG, clamp=CLAMP, llr_out=b["llr"], stream=tx_stream)
+        ev_rx[i & 1].record(tx_stream)
+        dec_stream.wait_event(ev_rx[i & 1])
         if timed_decode is not None:
-            timed_decode[0].record(stream)
-        lx.ldpc_bp_decode(code, llr, **dec, llr_out=False, bits_out=bits, iters_out=its, ws=ws, stream=stream)
+            timed_decode[0].record(dec_stream)
+        lx.ldpc_bp_decode(code, b["llr"], **dec, llr_out=False, bits_out=b["bits"], iters_out=b["its"], ws=ws,
+                          stream=dec_stream)
         if timed_decode is not None:
-            timed_decode[1].record(stream)
-        lx.sim_count(info, bits, its, code.k, counts, stream=stream)
+            timed_decode[1].record(dec_stream)
+        lx.sim_count(b["info"], b["bits"], b["its"], code.k, counts, stream=dec_stream)
+        ev_free[i & 1].record(dec_stream)
 
     for i in range(args.warmup):
         step(i)
@@ -262,8 +276,6 @@ def run_gpu(args):
 
     clocks = Clocks(local)
     dec_ms = []
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     dec_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     clocks.start()
     if dist:
@@ -272,12 +284,11 @@ def run_gpu(args):
     clocks.begin()
     t_start = torch.cuda.Event(enable_timing=True)
     t_end = torch.cuda.Event(enable_timing=True)
-    t_start.record(stream)
+    t_start.record(dec_stream)
+    tx_stream.wait_event(t_start)  # no transmitter work of a timed step starts before the timed region
     for i in range(args.steps):
-        starts[i].record(stream)
         step(args.warmup + i, dec_ev[i])
-        ends[i].record(stream)
-    t_end.record(stream)
+    t_end.record(dec_stream)  # the last count follows every kernel of every step on both streams
     torch.cuda.synchronize()
     clocks.end()
     if dist:
@@ -540,45 +551,57 @@ def measure_mixed(lx, stream, args):
 
 def measure_e2e(lx, code, y_dev, info_dev, n0, dec, stream, args, dev):
     """The receiver through the public API from host memory: pinned y -> device, demap, decode, bits -> host.
-    Double-buffered: the copies run on a second stream, so step i + 1's symbols move in and step i - 1's bits
-    move out while step i decodes. Every step's copies lie inside the timed region."""
+    Double-buffered: the copies run on their own stream and the demapper on a lower-priority one, so step
+    i + 1's symbols move in and are demapped, and step i - 1's bits move out, while step i decodes. Every
+    step's copies lie inside the timed region."""
     import torch
     kw = (code.k + 31) // 32
     y_host = y_dev.cpu().pin_memory()
     bits_host = [torch.empty((B, kw), dtype=torch.int32).pin_memory() for _ in range(2)]
     y_d = [torch.empty_like(y_dev) for _ in range(2)]
-    llr = torch.empty((B, code.n_tx), dtype=torch.float32, device=dev)
+    llr = [torch.empty((B, code.n_tx), dtype=torch.float32, device=dev) for _ in range(2)]
     bits = [torch.empty((B, kw), dtype=torch.int32, device=dev) for _ in range(2)]
     ws = torch.empty(lx.ldpc_bp_workspace(code, B, **dec), dtype=torch.uint8, device=dev)
     copy = torch.cuda.Stream(device=dev)
+    rx = torch.cuda.Stream(device=dev, priority=0)
+    dec_s = torch.cuda.Stream(device=dev, priority=-1)
     ev_in = [torch.cuda.Event() for _ in range(2)]    # symbols of buffer j are on the device
-    ev_used = [torch.cuda.Event() for _ in range(2)]  # demap has consumed buffer j
+    ev_used = [torch.cuda.Event() for _ in range(2)]  # the demapper has consumed symbols j
+    ev_rx = [torch.cuda.Event() for _ in range(2)]    # LLRs of buffer j are ready
+    ev_llr = [torch.cuda.Event() for _ in range(2)]   # the decoder has consumed LLRs j
     ev_dec = [torch.cuda.Event() for _ in range(2)]   # bits of buffer j are ready
     ev_out = [torch.cuda.Event() for _ in range(2)]   # bits of buffer j have reached the host buffer
 
-    def h2d(j):
+    def front(j):
+        copy.wait_event(ev_used[j])
         with torch.cuda.stream(copy):
-            copy.wait_event(ev_used[j])
             y_d[j].copy_(y_host, non_blocking=True)
-            ev_in[j].record(copy)
+        ev_in[j].record(copy)
+        rx.wait_event(ev_in[j])
+        rx.wait_event(ev_llr[j])
+        lx.demap_app(y_d[j], n0, M, method=lx.DEMAP_MAXLOG, clamp=CLAMP, llr_out=llr[j], stream=rx)
+        ev_used[j].record(rx)
+        ev_rx[j].record(rx)
 
     def run(steps):
-        h2d(0)
+        for s_ in (copy, rx, dec_s):
+            s_.wait_stream(stream)
+        front(0)
         for i in range(steps):
             j = i & 1
             if i + 1 < steps:
-                h2d(1 - j)
-            stream.wait_event(ev_in[j])
-            lx.demap_app(y_d[j], n0, M, method=lx.DEMAP_MAXLOG, clamp=CLAMP, llr_out=llr, stream=stream)
-            ev_used[j].record(stream)
-            stream.wait_event(ev_out[j])
-            lx.ldpc_bp_decode(code, llr, **dec, bits_out=bits[j], iters_out=False, ws=ws, stream=stream)
-            ev_dec[j].record(stream)
+                front(1 - j)
+            dec_s.wait_event(ev_rx[j])
+            dec_s.wait_event(ev_out[j])
+            lx.ldpc_bp_decode(code, llr[j], **dec, bits_out=bits[j], iters_out=False, ws=ws, stream=dec_s)
+            ev_llr[j].record(dec_s)
+            ev_dec[j].record(dec_s)
+            copy.wait_event(ev_dec[j])
             with torch.cuda.stream(copy):
-                copy.wait_event(ev_dec[j])
                 bits_host[j].copy_(bits[j], non_blocking=True)
-                ev_out[j].record(copy)
-        stream.wait_stream(copy)
+            ev_out[j].record(copy)
+        dec_s.wait_stream(copy)
+        stream.wait_stream(dec_s)
 
     run(2)
     torch.cuda.synchronize()
@@ -592,8 +615,8 @@ def measure_e2e(lx, code, y_dev, info_dev, n0, dec, stream, args, dev):
     return {"value": B * code.k / (ms * 1e-3) / 1e9, "unit": "Gbit/s",
             "h2d_bytes_per_step": y_host.numel() * 4, "d2h_bytes_per_step": bits_host[0].numel() * 4,
             "ms_per_step": ms,
-            "path": "pinned host y -> demap_app -> ldpc_bp_decode -> host bits; copies on a second stream, "
-                    "double-buffered against the previous step's decode"}
+            "path": "pinned host y -> demap_app -> ldpc_bp_decode -> host bits; copies on their own stream and "
+                    "the demapper on a lower-priority one, double-buffered against the previous step's decode"}
 
 
 def main():

@@ -13,7 +13,7 @@ __device__ unsigned int g_status;
 struct TxParams {
     const uint32_t *blk;
     const int32_t *row_ptr;
-    int Z, rows, kb, n, k, n_tx, p0;
+    int Z, rows, kb, n, k, n_tx, p0, nnz;
     int m;
     float scale;         // 1/sqrt(2(4^h-1)/3): unit average symbol energy
     uint64_t seed, cw0;
@@ -37,15 +37,30 @@ __device__ __forceinline__ int pam_level(const uint8_t *c, int h) {
 }
 
 
+// Shared-memory layout of k_tx, per CTA: [G][ns] codeword bytes (ns = n rounded
+// up to 4), [G][4 nq] packed source words, then the block table and row
+// pointers of the code.
+__host__ __device__ inline int tx_ns(int n) { return (n + 3) & ~3; }
+__host__ __device__ inline size_t tx_smem(int G, int n, int k, int nnz, int rows) {
+    const int nq = (((k + 31) >> 5) + 3) >> 2;
+    return (size_t)G * tx_ns(n) + (size_t)G * 16 * nq + 4 * (size_t)nnz + 4 * (size_t)(rows + 1);
+}
+
 __global__ void __launch_bounds__(kMaxThreads) k_tx(const TxParams p) {
     extern __shared__ __align__(16) unsigned char smem[];
-    uint8_t *s_c = smem;  // [G][n] codeword bits, one byte each
+    const int ns = tx_ns(p.n);
     const int kw = (p.k + 31) >> 5;
     const int nq = (kw + 3) >> 2;  // Philox blocks of source bits per codeword
+    uint8_t *s_c = smem;           // [G][ns] codeword bits, one byte each
+    uint32_t *s_w = reinterpret_cast<uint32_t *>(smem + (size_t)p.G * ns);  // [G][4 nq] source words
+    uint32_t *s_blk = s_w + (size_t)p.G * 4 * nq;
+    int32_t *s_rp = reinterpret_cast<int32_t *>(s_blk + p.nnz);
     const int64_t cw_base = (int64_t)blockIdx.x * p.G;
     const uint64_t cw0 = p.cw0 + (p.cw0_dev ? *p.cw0_dev : 0ull);
 
-    // a2: source bits (Philox stream 0), written packed and unpacked to smem
+    for (int i = threadIdx.x; i < p.nnz; i += blockDim.x) s_blk[i] = p.blk[i];
+    for (int i = threadIdx.x; i <= p.rows; i += blockDim.x) s_rp[i] = p.row_ptr[i];
+    // a2: source bits (Philox stream 0), written packed to the output and to shared memory
     for (int i = threadIdx.x; i < p.G * nq; i += blockDim.x) {
         const int gg = i / nq, q = i - gg * nq;
         const int64_t cw = cw_base + gg;
@@ -60,16 +75,26 @@ __global__ void __launch_bounds__(kMaxThreads) k_tx(const TxParams p) {
             const int valid = min(32, p.k - 32 * w);
             if (valid < 32) word &= (1u << valid) - 1u;
             if (p.info) p.info[cw * kw + w] = word;
-            uint8_t *dst = s_c + (size_t)gg * p.n + 32 * w;
-            for (int b = 0; b < valid; ++b) dst[b] = (uint8_t)((word >> b) & 1u);
+            s_w[(size_t)gg * 4 * nq + w] = word;
         }
+    }
+    __syncthreads();
+    // one byte per bit, four bits per 32-bit store: nibble * 0x00204081 moves bit j to bit 8j (the four
+    // shifted copies of the nibble do not overlap). Bytes past k belong to parity column kb and are
+    // overwritten below.
+    const int k4 = (p.k + 3) >> 2;
+    for (int i = threadIdx.x; i < p.G * k4; i += blockDim.x) {
+        const int gg = i / k4, j = i - gg * k4;
+        if (cw_base + gg >= p.B) continue;
+        const uint32_t nib = (s_w[(size_t)gg * 4 * nq + (j >> 3)] >> (4 * (j & 7))) & 0xFu;
+        *reinterpret_cast<uint32_t *>(s_c + (size_t)gg * ns + 4 * j) = (nib * 0x00204081u) & 0x01010101u;
     }
     __syncthreads();
 
     // a3: systematic encoding, one thread per (codeword, z)
     const int g = threadIdx.x / p.Z, z = threadIdx.x - g * p.Z;
     const bool active = g < p.G && cw_base + g < p.B;
-    uint8_t *c = s_c + (size_t)(active ? g : 0) * p.n;
+    uint8_t *c = s_c + (size_t)(active ? g : 0) * ns;
     const int Z = p.Z;
     auto at = [&](uint32_t b) -> uint8_t {
         const int col = (int)(b >> 16);
@@ -82,8 +107,8 @@ __global__ void __launch_bounds__(kMaxThreads) k_tx(const TxParams p) {
         // lambda_r = sum over the systematic blocks of core row r
         for (int r = 0; r < 4; ++r) {
             uint8_t acc = 0;
-            for (int b = p.row_ptr[r]; b < p.row_ptr[r + 1]; ++b) {
-                const uint32_t bb = p.blk[b];
+            for (int b = s_rp[r]; b < s_rp[r + 1]; ++b) {
+                const uint32_t bb = s_blk[b];
                 if ((int)(bb >> 16) < p.kb) acc ^= at(bb);
             }
             lam[r] = acc;
@@ -106,8 +131,8 @@ __global__ void __launch_bounds__(kMaxThreads) k_tx(const TxParams p) {
         for (int r = 4; r < p.rows; ++r) {
             uint8_t acc = 0;
             const int own = p.kb + r;
-            for (int b = p.row_ptr[r]; b < p.row_ptr[r + 1]; ++b) {
-                const uint32_t bb = p.blk[b];
+            for (int b = s_rp[r]; b < s_rp[r + 1]; ++b) {
+                const uint32_t bb = s_blk[b];
                 if ((int)(bb >> 16) != own) acc ^= at(bb);
             }
             c[own * Z + z] = acc;
@@ -123,7 +148,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_tx(const TxParams p) {
             const int gg = w / nw, ww = w - gg * nw;
             const int64_t cw = cw_base + gg;
             const int pos = ww * 32 + lane;
-            const bool bit = cw < p.B && pos < p.n && s_c[(size_t)gg * p.n + pos] != 0;
+            const bool bit = cw < p.B && pos < p.n && s_c[(size_t)gg * ns + pos] != 0;
             const unsigned word = __ballot_sync(0xFFFFFFFFu, bit);
             if (lane == 0 && cw < p.B) p.cw_out[cw * nw + ww] = word;
         }
@@ -142,7 +167,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_tx(const TxParams p) {
             const uint4 x = draw(p.seed, cw0 + (uint64_t)cw, 1u, (uint32_t)q);
             const float2 g01 = box_muller(x.x, x.y), g23 = box_muller(x.z, x.w);
             const float gs[4] = {g01.x, g01.y, g23.x, g23.y};
-            const uint8_t *cb = s_c + (size_t)gg * p.n + p.p0;
+            const uint8_t *cb = s_c + (size_t)gg * ns + p.p0;
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
                 const int s = 4 * q + e;
@@ -158,7 +183,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_tx(const TxParams p) {
             const float sd = sqrtf(p.no[cw * p.no_stride] * 0.5f);
             const uint4 x = draw(p.seed, cw0 + (uint64_t)cw, 1u, (uint32_t)q);
             const float2 gn[2] = {box_muller(x.x, x.y), box_muller(x.z, x.w)};
-            const uint8_t *cb = s_c + (size_t)gg * p.n + p.p0;
+            const uint8_t *cb = s_c + (size_t)gg * ns + p.p0;
 #pragma unroll
             for (int e = 0; e < 2; ++e) {
                 const int s = 2 * q + e;
@@ -699,11 +724,12 @@ int launch_tx(ldpcx_code_t c, uint64_t seed, uint64_t cw0, const uint64_t *cw0_d
     p.cw_out = cw_out;
     p.points = reinterpret_cast<const float2 *>(points);
     p.B = B;
+    p.nnz = c->nnz;
     int G = kMaxThreads / c->Z;
     if (G < 1) G = 1;
-    while (G > 1 && (size_t)G * c->n > 96 * 1024) --G;
+    while (G > 1 && tx_smem(G, c->n, c->k, c->nnz, c->rows) > 96 * 1024) --G;
     p.G = G;
-    const size_t smem = (size_t)G * c->n;
+    const size_t smem = tx_smem(G, c->n, c->k, c->nnz, c->rows);
     if (smem > 48 * 1024 &&
         cudaFuncSetAttribute(k_tx, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return LDPCX_E_CUDA;
