@@ -129,39 +129,65 @@ __device__ __forceinline__ void cns_update_k(const Params &p, float *app, const 
     }
 }
 
+// Where a step's row and the row it prefetches lie, when that is known at
+// compile time (full base graphs): core row 0..3, an extension row whose row
+// r + 2 is in the same iteration, or one of the last two rows, whose r + 2 is
+// row 0 or 1 of the next iteration. kStepAny decides at run time (truncated
+// codes, whose row count is a parameter).
+constexpr int kStepExt = 4, kStepExtWrap = 5, kStepAny = 6;
+
 // One layer step of degree D on row r (blocks from b0, slots from off):
 // prefetch the state of layer r + 2 into s_far, update from s_cur, barrier.
 // With K = 1 the slot addresses come from two per-thread bases (core and
 // extension rows), so a step adds one row offset instead of recomputing
 // z * slot bytes; the state loaded is the same.
-template <int D, int BG, int PREC, int K, bool TRUNC>
+template <int D, int BG, int PREC, int K, bool TRUNC, int MODE>
 __device__ __forceinline__ void sched_step(const Params &p, const int2 *s_at, float *app, unsigned char *st,
                                            const int (&zk)[K], int t, int r, int b0, int off, const SchedGeo &geo,
                                            bool done, const uint4 (&s_cur)[K], uint4 (&s_far)[K]) {
     using L = SchedLayout<BG, PREC>;
+    static_assert(MODE == kStepAny || !TRUNC, "truncated codes place their rows at run time");
     const int rows = TRUNC ? p.rows : Sched<BG>::rows;
-    const bool wrap = r + 2 >= rows;  // the state two layers on is the next iteration's
-    const int r2 = wrap ? r + 2 - rows : r + 2;
-    const int t2 = wrap ? t + 1 : t;
-    if (t2 == 0) {
+    // the row two layers on, its iteration, and whether it is a core row
+    int r2, t2;
+    bool core2;
+    if constexpr (MODE == kStepAny) {
+        const bool wrap = r + 2 >= rows;  // the state two layers on is the next iteration's
+        r2 = wrap ? r + 2 - rows : r + 2;
+        t2 = wrap ? t + 1 : t;
+        core2 = r2 < 4;
+    } else if constexpr (MODE == kStepExtWrap) {
+        r2 = r + 2 - rows;
+        t2 = t + 1;
+        core2 = true;
+    } else {
+        r2 = r + 2;
+        t2 = t;
+        core2 = MODE < 2;
+    }
+    // t2 == 0 only without a wrap, and t2 < p.iters holds without one (t < p.iters)
+    const bool zero = MODE == kStepExtWrap ? false : t2 == 0;
+    const bool fetch = MODE == kStepAny ? t2 < p.iters : MODE == kStepExtWrap ? t + 1 < p.iters : true;
+    if (zero) {
 #pragma unroll
         for (int k = 0; k < K; ++k) s_far[k] = make_uint4(0u, 0u, 0u, 0u);  // iteration 0: zero messages
-    } else if (!done && t2 < p.iters) {
+    } else if (!done && fetch) {
         if constexpr (K == 1) {
-            if (r2 < 4) s_far[0] = cns_load(geo.core_z + r2 * geo.Lc, L::sb_core);
+            if (core2) s_far[0] = cns_load(geo.core_z + r2 * geo.Lc, L::sb_core);
             else s_far[0] = cns_load(geo.ext_z + (r2 - 4) * geo.Le, L::sb_ext);
         } else {
             const unsigned char *row2 = st + geo.off(r2);
 #pragma unroll
             for (int k = 0; k < K; ++k) {
-                if (r2 < 4) s_far[k] = cns_load(row2 + zk[k] * L::sb_core, L::sb_core);
+                if (core2) s_far[k] = cns_load(row2 + zk[k] * L::sb_core, L::sb_core);
                 else s_far[k] = cns_load(row2 + zk[k] * L::sb_ext, L::sb_ext);
             }
         }
     }
     if (!done) {
         if constexpr (K == 1) {
-            unsigned char *slot = (r < 4 ? geo.core_z : geo.ext_z - 4 * geo.Lc) + off;
+            const bool core = MODE == kStepAny ? r < 4 : MODE < 4;
+            unsigned char *slot = (core ? geo.core_z : geo.ext_z - 4 * geo.Lc) + off;
             cns_update_k<D, PREC, K>(p, app, s_at + b0, zk, s_cur, slot, t + 1 < p.iters);
         } else {
             cns_update_k<D, PREC, K>(p, app, s_at + b0, zk, s_cur, st + off, t + 1 < p.iters);
@@ -170,31 +196,46 @@ __device__ __forceinline__ void sched_step(const Params &p, const int2 *s_at, fl
     __syncthreads();
 }
 
-// COUNT consecutive rows of degree D from row r0, the first at ring phase PH.
-template <int D, int COUNT, int PH, int BG, int PREC, int K, bool TRUNC = false>
+// COUNT consecutive rows of degree D from row r0, the first at ring phase PH
+// (= r0 for full graphs). LAST: the run ends the iteration of a full graph, so
+// its last two steps prefetch the next iteration's rows 0 and 1.
+template <int D, int COUNT, int PH, int BG, int PREC, int K, bool TRUNC = false, bool LAST = false>
 __device__ __forceinline__ void sched_run(const Params &p, const int2 *s_at, float *app, unsigned char *st,
                                           const int (&zk)[K], int t, int r0, int b0, int off0, int Lrow,
                                           const SchedGeo &geo, bool done, uint4 (&a)[K], uint4 (&b)[K],
                                           uint4 (&c)[K]) {
+    constexpr int M = TRUNC ? kStepAny : PH < 4 ? PH : kStepExt;
+    constexpr int NW = LAST ? COUNT - 2 : COUNT;  // steps without a wrap
+    static_assert(!LAST || (COUNT >= 2 && !TRUNC && PH >= 4), "the last run is an extension run of a full graph");
     int r = r0, bb = b0, off = off0;
 #pragma unroll 1
-    for (int i = 0; i < COUNT / 3; ++i) {
-        sched_step<D, BG, PREC, K, TRUNC>(p, s_at, app, st, zk, t, r, bb, off, geo, done, ring<PH, K>(a, b, c),
-                                   ring<PH + 2, K>(a, b, c));
-        sched_step<D, BG, PREC, K, TRUNC>(p, s_at, app, st, zk, t, r + 1, bb + D, off + Lrow, geo, done,
-                                   ring<PH + 1, K>(a, b, c), ring<PH + 3, K>(a, b, c));
-        sched_step<D, BG, PREC, K, TRUNC>(p, s_at, app, st, zk, t, r + 2, bb + 2 * D, off + 2 * Lrow, geo, done,
-                                   ring<PH + 2, K>(a, b, c), ring<PH + 4, K>(a, b, c));
+    for (int i = 0; i < NW / 3; ++i) {
+        sched_step<D, BG, PREC, K, TRUNC, M>(p, s_at, app, st, zk, t, r, bb, off, geo, done, ring<PH, K>(a, b, c),
+                                             ring<PH + 2, K>(a, b, c));
+        sched_step<D, BG, PREC, K, TRUNC, M>(p, s_at, app, st, zk, t, r + 1, bb + D, off + Lrow, geo, done,
+                                             ring<PH + 1, K>(a, b, c), ring<PH + 3, K>(a, b, c));
+        sched_step<D, BG, PREC, K, TRUNC, M>(p, s_at, app, st, zk, t, r + 2, bb + 2 * D, off + 2 * Lrow, geo, done,
+                                             ring<PH + 2, K>(a, b, c), ring<PH + 4, K>(a, b, c));
         r += 3;
         bb += 3 * D;
         off += 3 * Lrow;
     }
-    if constexpr (COUNT % 3 >= 1)
-        sched_step<D, BG, PREC, K, TRUNC>(p, s_at, app, st, zk, t, r, bb, off, geo, done, ring<PH, K>(a, b, c),
-                                   ring<PH + 2, K>(a, b, c));
-    if constexpr (COUNT % 3 == 2)
-        sched_step<D, BG, PREC, K, TRUNC>(p, s_at, app, st, zk, t, r + 1, bb + D, off + Lrow, geo, done,
-                                   ring<PH + 1, K>(a, b, c), ring<PH + 3, K>(a, b, c));
+    if constexpr (NW % 3 >= 1)
+        sched_step<D, BG, PREC, K, TRUNC, M>(p, s_at, app, st, zk, t, r, bb, off, geo, done, ring<PH, K>(a, b, c),
+                                             ring<PH + 2, K>(a, b, c));
+    if constexpr (NW % 3 == 2)
+        sched_step<D, BG, PREC, K, TRUNC, M>(p, s_at, app, st, zk, t, r + 1, bb + D, off + Lrow, geo, done,
+                                             ring<PH + 1, K>(a, b, c), ring<PH + 3, K>(a, b, c));
+    if constexpr (LAST) {
+        constexpr int Q = PH + NW;  // ring phase of the first wrapping step
+        r += NW % 3;
+        bb += (NW % 3) * D;
+        off += (NW % 3) * Lrow;
+        sched_step<D, BG, PREC, K, TRUNC, kStepExtWrap>(p, s_at, app, st, zk, t, r, bb, off, geo, done,
+                                                        ring<Q, K>(a, b, c), ring<Q + 2, K>(a, b, c));
+        sched_step<D, BG, PREC, K, TRUNC, kStepExtWrap>(p, s_at, app, st, zk, t, r + 1, bb + D, off + Lrow, geo,
+                                                        done, ring<Q + 1, K>(a, b, c), ring<Q + 3, K>(a, b, c));
+    }
 }
 
 // `count` (run-time) consecutive rows of degree D from row r0, starting at
@@ -208,16 +249,16 @@ __device__ __forceinline__ void sched_run_n(const Params &p, const int2 *s_at, f
     int r = r0, bb = b0, off = off0;
 #pragma unroll 1
     for (int i = 0; i < count / 3; ++i) {
-        sched_step<D, BG, PREC, K, true>(p, s_at, app, st, zk, t, r, bb, off, geo, done, a, c);
-        sched_step<D, BG, PREC, K, true>(p, s_at, app, st, zk, t, r + 1, bb + D, off + Lrow, geo, done, b, a);
-        sched_step<D, BG, PREC, K, true>(p, s_at, app, st, zk, t, r + 2, bb + 2 * D, off + 2 * Lrow, geo, done, c, b);
+        sched_step<D, BG, PREC, K, true, kStepAny>(p, s_at, app, st, zk, t, r, bb, off, geo, done, a, c);
+        sched_step<D, BG, PREC, K, true, kStepAny>(p, s_at, app, st, zk, t, r + 1, bb + D, off + Lrow, geo, done, b, a);
+        sched_step<D, BG, PREC, K, true, kStepAny>(p, s_at, app, st, zk, t, r + 2, bb + 2 * D, off + 2 * Lrow, geo, done, c, b);
         r += 3;
         bb += 3 * D;
         off += 3 * Lrow;
     }
     const int rem = count - 3 * (count / 3);
-    if (rem >= 1) sched_step<D, BG, PREC, K, true>(p, s_at, app, st, zk, t, r, bb, off, geo, done, a, c);
-    if (rem == 2) sched_step<D, BG, PREC, K, true>(p, s_at, app, st, zk, t, r + 1, bb + D, off + Lrow, geo, done, b, a);
+    if (rem >= 1) sched_step<D, BG, PREC, K, true, kStepAny>(p, s_at, app, st, zk, t, r, bb, off, geo, done, a, c);
+    if (rem == 2) sched_step<D, BG, PREC, K, true, kStepAny>(p, s_at, app, st, zk, t, r + 1, bb + D, off + Lrow, geo, done, b, a);
     if (rem == 1) {
 #pragma unroll
         for (int k = 0; k < K; ++k) {
@@ -291,7 +332,7 @@ __device__ __forceinline__ void cns_sched_tile(const Params &p, int64_t cw_base,
             // the full graph: run lengths known here, phases follow on
             sched_run<S::d_hi, S::n_hi, 4, BG, PREC, K>(p, s_at, app, st, zk, t, 4, L::b_hi, 4 * geo.Lc, geo.Le,
                                                         geo, done, a, b, c);
-            sched_run<S::d_lo, S::rows - 4 - S::n_hi, 4 + S::n_hi, BG, PREC, K>(
+            sched_run<S::d_lo, S::rows - 4 - S::n_hi, 4 + S::n_hi, BG, PREC, K, false, true>(
                 p, s_at, app, st, zk, t, 4 + S::n_hi, L::b_lo, 4 * geo.Lc + S::n_hi * geo.Le, geo.Le, geo, done, a,
                 b, c);
             // the next iteration's first step finds its state at phase rows mod 3
