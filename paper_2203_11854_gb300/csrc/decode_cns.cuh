@@ -47,20 +47,20 @@ template <> struct CnsMag<kF32> {
     }
 };
 template <> struct CnsMag<kF16> {
-    unsigned short h1, h2;
+    unsigned w;  // the two binary16 magnitudes, r1 in the low half
     float r1, r2;
     __device__ __forceinline__ void set(float v1, float v2) {
-        const __half a = __float2half_rn(v1), b = __float2half_rn(v2);
-        h1 = __half_as_ushort(a);
-        h2 = __half_as_ushort(b);
-        r1 = __half2float(a);
-        r2 = __half2float(b);
+        const __half2 h = __floats2half2_rn(v1, v2);  // each rounded to nearest even
+        w = *reinterpret_cast<const unsigned *>(&h);
+        const float2 f = __half22float2(h);
+        r1 = f.x;
+        r2 = f.y;
     }
-    __device__ __forceinline__ void from_bits(unsigned w) {
-        h1 = (unsigned short)(w & 0xFFFFu);
-        h2 = (unsigned short)(w >> 16);
-        r1 = __half2float(__ushort_as_half(h1));
-        r2 = __half2float(__ushort_as_half(h2));
+    __device__ __forceinline__ void from_bits(unsigned bits) {
+        w = bits;
+        const float2 f = __half22float2(*reinterpret_cast<const __half2 *>(&bits));
+        r1 = f.x;
+        r2 = f.y;
     }
     __device__ __forceinline__ float msg(unsigned eq, unsigned neg) const {
         const float m = eq ? r2 : r1;
@@ -105,9 +105,8 @@ __device__ __forceinline__ uint4 cns_pack(const CnsMag<PREC> &m, unsigned eq, un
     if constexpr (PREC == kF32) {
         return make_uint4(__float_as_uint(m.r1), __float_as_uint(m.r2), eq, neg);
     } else if constexpr (PREC == kF16) {
-        const unsigned w0 = (unsigned)m.h1 | ((unsigned)m.h2 << 16);
-        if (d <= 16) return make_uint4(w0, eq | (neg << 16), 0u, 0u);
-        return make_uint4(w0, eq, neg, 0u);
+        if (d <= 16) return make_uint4(m.w, neg | (eq << 16), 0u, 0u);
+        return make_uint4(m.w, eq, neg, 0u);
     } else {
         if (d <= 11) return make_uint4((unsigned)m.q1 | ((unsigned)m.q2 << 5) | (eq << 10) | (neg << 21), 0u, 0u, 0u);
         if (d <= 22) return make_uint4((unsigned)m.q1 | ((unsigned)m.q2 << 5) | (eq << 10), neg, 0u, 0u);
@@ -125,8 +124,8 @@ __device__ __forceinline__ void cns_unpack(const uint4 &s, int d, CnsMag<PREC> &
     } else if constexpr (PREC == kF16) {
         m.from_bits(s.x);
         if (d <= 16) {
-            eq = s.y & 0xFFFFu;
-            neg = s.y >> 16;
+            eq = s.y >> 16;
+            neg = s.y & 0xFFFFu;
         } else {
             eq = s.y;
             neg = s.z;
@@ -149,6 +148,56 @@ __device__ __forceinline__ void cns_unpack(const uint4 &s, int d, CnsMag<PREC> &
             neg = s.z;
         }
         m.values();
+    }
+}
+
+// The same layouts as a compile-time-degree update walks them: eq bit j of a
+// state is bit j + cns_eq_pos of the word eqw, and neg bit D-1 is bit 31 of wn
+// with the lower neg bits below it (the bits further down are never shifted
+// up to bit 31 within D steps). So neither mask is extracted.
+template <int PREC, int D> constexpr int cns_eq_pos() {
+    return (PREC == kF16 && D <= 16) ? 16 : (PREC == kFix6 && D <= 22) ? 10 : 0;
+}
+template <int PREC, int D>
+__device__ __forceinline__ void cns_unpack_walk(const uint4 &s, CnsMag<PREC> &m, unsigned &eqw, unsigned &wn) {
+    if constexpr (PREC == kF32) {
+        m.r1 = __uint_as_float(s.x);
+        m.r2 = __uint_as_float(s.y);
+        eqw = s.z;
+        wn = s.w << (32 - D);
+    } else if constexpr (PREC == kF16) {
+        m.from_bits(s.x);
+        eqw = s.y;
+        if constexpr (D <= 16) wn = s.y << (32 - D);  // neg in bits 0..15, eq above
+        else wn = s.z << (32 - D);
+    } else {
+        if constexpr (D <= 22) {
+            m.q1 = (int)(s.x & 31u);
+            m.q2 = (int)((s.x >> 5) & 31u);
+            eqw = s.x;
+            if constexpr (D <= 11) wn = s.x << (11 - D);  // neg in bits 21..31
+            else wn = s.y << (32 - D);
+        } else {
+            m.q1 = (int)(s.x & 0xFFu);
+            m.q2 = (int)((s.x >> 8) & 0xFFu);
+            eqw = s.y;
+            wn = s.z << (32 - D);
+        }
+        m.values();
+    }
+}
+// Pack with the new eq mask already at bit j + cns_eq_pos.
+template <int PREC, int D>
+__device__ __forceinline__ uint4 cns_pack_walk(const CnsMag<PREC> &m, unsigned eqw, unsigned neg) {
+    if constexpr (PREC == kF32) {
+        return make_uint4(__float_as_uint(m.r1), __float_as_uint(m.r2), eqw, neg);
+    } else if constexpr (PREC == kF16) {
+        if constexpr (D <= 16) return make_uint4(m.w, eqw | neg, 0u, 0u);
+        else return make_uint4(m.w, eqw, neg, 0u);
+    } else {
+        if constexpr (D <= 11) return make_uint4((unsigned)m.q1 | ((unsigned)m.q2 << 5) | eqw | (neg << 21), 0u, 0u, 0u);
+        else if constexpr (D <= 22) return make_uint4((unsigned)m.q1 | ((unsigned)m.q2 << 5) | eqw, neg, 0u, 0u);
+        else return make_uint4((unsigned)m.q1 | ((unsigned)m.q2 << 8), eqw, neg, 0u);
     }
 }
 

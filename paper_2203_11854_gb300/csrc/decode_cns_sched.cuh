@@ -74,24 +74,22 @@ template <int D, int PREC, int K>
 __device__ __forceinline__ void cns_update_k(const Params &p, float *app, const int2 *at, const int (&zk)[K],
                                              const uint4 (&s_old)[K], unsigned char *row, bool store) {
     constexpr int SB = cns_slot_bytes<PREC>(D);
+    constexpr int EP = cns_eq_pos<PREC, D>();
     CnsMag<PREC> mo[K];
-    unsigned eqo[K], nego[K];
-#pragma unroll
-    for (int k = 0; k < K; ++k) cns_unpack<PREC>(s_old[k], D, mo[k], eqo[k], nego[k]);
-    float T[K][D];
-    int vi[K][D];
     // the old neg bits walked down through bit 31 of wn (edges in descending order: the row's updates
     // touch distinct APP entries, and the two-minimum rule does not depend on the order)
-    unsigned wn[K];
+    unsigned eqo[K], wn[K];
 #pragma unroll
-    for (int k = 0; k < K; ++k) wn[k] = nego[k] << (32 - D);
+    for (int k = 0; k < K; ++k) cns_unpack_walk<PREC, D>(s_old[k], mo[k], eqo[k], wn[k]);
+    float T[K][D];
+    int vi[K][D];
 #pragma unroll
     for (int j = D - 1; j >= 0; --j) {
         const int2 a = at[j];
 #pragma unroll
         for (int k = 0; k < K; ++k) {
             vi[k][j] = vn_off_mixed(p, a, zk[k]);
-            const float m = ((eqo[k] >> j) & 1u) ? mo[k].r2 : mo[k].r1;
+            const float m = ((eqo[k] >> (j + EP)) & 1u) ? mo[k].r2 : mo[k].r1;
             const float old = __uint_as_float(__float_as_uint(m) | (wn[k] & 0x80000000u));
             wn[k] *= p.k_two;
             T[k][j] = __fsub_rn(app_at(app, vi[k][j]), old);
@@ -118,14 +116,14 @@ __device__ __forceinline__ void cns_update_k(const Params &p, float *app, const 
             // sign of the new message: bit 31 of U = bits(T) + the product's sign bit (a flip of bit 31)
             const unsigned U = __float_as_uint(T[k][j]) * p.k_one + sxs[k];
             neg[k] = __funnelshift_l(U, neg[k], 1);  // (neg << 1) | (U >> 31)
-            if (e) eq[k] = (1u << j) * p.k_one + eq[k];  // bit j is clear: add on the FMA pipe
+            if (e) eq[k] = (1u << (j + EP)) * p.k_one + eq[k];  // the bit is clear: add on the FMA pipe
             app_at(app, vi[k][j]) = __fadd_rn(T[k][j], __uint_as_float((U & 0x80000000u) | (e ? b2[k] : b1[k])));
         }
     }
     if (store) {
 #pragma unroll
         for (int k = 0; k < K; ++k)
-            cns_store(K == 1 ? row : row + zk[k] * SB, SB, cns_pack<PREC>(mn[k], eq[k], neg[k], D));
+            cns_store(K == 1 ? row : row + zk[k] * SB, SB, cns_pack_walk<PREC, D>(mn[k], eq[k], neg[k]));
     }
 }
 
