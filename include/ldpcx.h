@@ -99,6 +99,7 @@ typedef struct {
     int max_row_deg;         /* largest check-node degree */
     int n, k, n_tx, p0;      /* codeword, info and transmitted bits; p0 = first transmitted position */
     int64_t edges;           /* nnz * Z */
+    int encodable;           /* 1 when the transmitter can encode the code (see qc_ldpc_build_base) */
 } ldpcx_code_info;
 
 /* Build the code on the host (no device work; device tables are uploaded on
@@ -113,6 +114,58 @@ int qc_ldpc_info(ldpcx_code_t code, ldpcx_code_info *info);
 /* Copy the base matrix (row-major int16, -1 = zero block) into host memory
  * S_out of `capacity` entries (>= rows*cols, else LDPCX_E_INVAL). */
 int qc_ldpc_base(ldpcx_code_t code, int16_t *S_out, int capacity);
+
+/* A quasi-cyclic code from a caller-supplied base matrix (the paper's
+ * Section III lists LDPC codes from user parity-check matrices, with alist
+ * import, next to the 5G codes). S: host, rows x cols row-major, -1 = all-zero
+ * block, s in [0, Z) = identity cyclically shifted by s (block (r,c) joins
+ * check node r*Z+z to variable node c*Z + (z+s) mod Z, as for the seeded
+ * codes); copied, the caller keeps ownership. The first kb columns are the
+ * systematic ones (k = kb*Z); transmission as for qc_ldpc_build (punct_cols
+ * systematic columns not sent, then n_tx bits; n_tx = 0: all the rest).
+ * Every decoder accepts the code (within its limits: row degree <= 20,
+ * n <= 65535, else LDPCX_E_UNSUPPORTED at decode time). The transmitter
+ * (sim_tx, sim_codewords, sim_run) also needs cols = kb + rows >= kb + 4,
+ * core rows 0..3 with no block past column kb+3, extension row r >= 4 with,
+ * past column kb+3, exactly one block, at its own column kb+r (any shift), and
+ * an invertible core parity part (rows 0..3 x columns kb..kb+3, 4Z x 4Z over
+ * GF(2)); ldpcx_code_info.encodable says whether it holds, and the
+ * transmitter returns LDPCX_E_UNSUPPORTED when it does not. The 5G
+ * dual-diagonal core [[P1 I - -] [I I I -] [- - I I] [P1 - - I]] is encoded
+ * by its recursion, any other invertible core through its inverse (computed
+ * here by Gauss-Jordan elimination). Errors: LDPCX_E_INVAL for a null
+ * pointer, Z outside [2, 384], rows or cols outside [1, 4096] / [2, 4096],
+ * kb outside [1, cols), a shift outside [-1, Z), a row with fewer than two
+ * blocks, or a bad puncturing / n_tx. */
+typedef struct {
+    int rows, cols;   /* base matrix shape */
+    int kb;           /* systematic columns */
+    int Z;            /* lifting size, 2..384 */
+    const int16_t *S; /* host [rows][cols] */
+    int punct_cols;   /* 0..kb */
+    int n_tx;         /* 0 = every bit after the punctured ones */
+} ldpcx_base_params;
+int qc_ldpc_build_base(const ldpcx_base_params *params, ldpcx_code_t *out);
+
+/* Parse a parity-check matrix in alist text (MacKay's format: "N M", the
+ * largest column and row weights, the N column weights, the M row weights,
+ * then N lines of 1-based row indices, one line per column, and M lines of
+ * 1-based column indices, one per row; zeros pad a line and are skipped) into
+ * the base matrix of lifting size Z. text: host, len bytes (a NUL ends it
+ * early). The matrix must consist of Z x Z blocks that are zero or cyclically
+ * shifted identities, and the column lists must give the same entries as the
+ * row lists. Writes *rows_out = M/Z, *cols_out = N/Z, and, when S_out is
+ * not NULL, the base matrix to S_out (capacity >= rows*cols entries; -1 =
+ * zero block). Errors: LDPCX_E_INVAL for malformed text, inconsistent
+ * lists, a non-circulant block, N or M not a multiple of Z, or a small
+ * capacity. */
+int qc_alist_parse(const char *text, size_t len, int Z, int16_t *S_out, int capacity, int *rows_out,
+                   int *cols_out);
+/* The code's parity-check matrix as alist text (the format above, lines
+ * padded with zeros to the largest weight), NUL-terminated in buf (cap bytes).
+ * *len_out = the text length without the NUL, always; buf = NULL is a size
+ * query. Errors: LDPCX_E_INVAL for a null code or len_out, or cap <= len. */
+int qc_ldpc_alist(ldpcx_code_t code, char *buf, size_t cap, size_t *len_out);
 
 /* ------------------------------------------------ transmitter (a2 .. a5) */
 /* Monte-Carlo transmitter for codewords cw0 .. cw0+B-1 (BinarySource,
@@ -133,7 +186,10 @@ int qc_ldpc_base(ldpcx_code_t code, int16_t *S_out, int capacity);
  * no: device float, N0 of codeword b at no[b * no_stride] (stride 0 or 1).
  * y_out (device): m = 1 -> [B][n_tx] float; else [B][n_tx/m][2] float (re, im).
  * info_out (device, or NULL): [B][ceil(k/32)] packed information bits.
- * m in {1,2,4,6,8} and n_tx divisible by m, else LDPCX_E_INVAL. */
+ * m in {1,2,4,6,8} and n_tx divisible by m, else LDPCX_E_INVAL. A code the
+ * transmitter cannot encode (ldpcx_code_info.encodable = 0; only codes of
+ * qc_ldpc_build_base) gives LDPCX_E_UNSUPPORTED, here and in sim_codewords,
+ * sim_tx_points and sim_run. */
 int sim_tx(ldpcx_code_t code, uint64_t seed, uint64_t cw0, int64_t B, int m,
            const float *no, int64_t no_stride, float *y_out, uint32_t *info_out, void *stream);
 

@@ -22,7 +22,7 @@ __all__ = [
     "ldpc_bp_backward", "ldpcx_phi", "sim_codewords", "demap_app_prior", "llr_apriori", "llr_mutual_info",
     "ldpc_extrinsic", "DEMAP_OUT_APP", "DEMAP_OUT_EXTRINSIC", "sim_tx_points", "demap_points",
     "demap_points_backward", "map_points_backward", "llr_bce", "PolarCode", "polar_build", "polar_sim_tx",
-    "polar_scl_decode",
+    "polar_scl_decode", "qc_ldpc_build_base", "qc_alist_parse", "qc_ldpc_alist",
     "LAYERED_MINSUM", "LAYERED_SPA", "FLOOD_MINSUM", "FLOOD_SPA", "MSG_F32", "MSG_F16", "MSG_FIX6",
     "DEMAP_EXACT", "DEMAP_MAXLOG",
 ]
@@ -49,7 +49,12 @@ class CodeParams(C.Structure):
 class CodeInfo(C.Structure):
     _fields_ = [("Z", C.c_int), ("rows", C.c_int), ("cols", C.c_int), ("kb", C.c_int), ("nnz", C.c_int),
                 ("max_row_deg", C.c_int), ("n", C.c_int), ("k", C.c_int), ("n_tx", C.c_int), ("p0", C.c_int),
-                ("edges", C.c_int64)]
+                ("edges", C.c_int64), ("encodable", C.c_int)]
+
+
+class BaseParams(C.Structure):
+    _fields_ = [("rows", C.c_int), ("cols", C.c_int), ("kb", C.c_int), ("Z", C.c_int), ("S", C.c_void_p),
+                ("punct_cols", C.c_int), ("n_tx", C.c_int)]
 
 
 class DecodeOpts(C.Structure):
@@ -85,6 +90,9 @@ _SIGS = {
     "qc_ldpc_free": ([_vp], _i),
     "qc_ldpc_info": ([_vp, C.POINTER(CodeInfo)], _i),
     "qc_ldpc_base": ([_vp, _vp, _i], _i),
+    "qc_ldpc_build_base": ([C.POINTER(BaseParams), C.POINTER(_vp)], _i),
+    "qc_alist_parse": ([C.c_char_p, _sz, _i, _vp, _i, C.POINTER(_i), C.POINTER(_i)], _i),
+    "qc_ldpc_alist": ([_vp, _vp, _sz, C.POINTER(_sz)], _i),
     "sim_tx": ([_vp, _u64, _u64, _i64, _i, _vp, _i64, _vp, _vp, _vp], _i),
     "demap_app": ([_vp, _vp, _i64, _i64, _i64, _i, _i, _f, _vp, _vp], _i),
     "sim_codewords": ([_vp, _u64, _u64, _i64, _vp, _vp], _i),
@@ -216,6 +224,41 @@ def qc_ldpc_build(bg_shape: int, Z: int, seed: int | None = None, rows_kept: int
     h = C.c_void_p()
     _check(load_library().qc_ldpc_build(C.byref(p), C.byref(h)), "qc_ldpc_build")
     return Code(h.value)
+
+
+def qc_ldpc_build_base(S, Z: int, kb: int, punct_cols: int = 0, n_tx: int = 0) -> Code:
+    """Code from a caller-supplied base matrix S ([rows][cols], -1 = zero block, else the shift)."""
+    import numpy as np
+    S = np.ascontiguousarray(S, dtype=np.int16)
+    if S.ndim != 2:
+        raise ValueError("S must be a 2-D base matrix")
+    p = BaseParams(S.shape[0], S.shape[1], kb, Z, S.ctypes.data, punct_cols, n_tx)
+    h = C.c_void_p()
+    _check(load_library().qc_ldpc_build_base(C.byref(p), C.byref(h)), "qc_ldpc_build_base")
+    return Code(h.value)
+
+
+def qc_alist_parse(text: str, Z: int):
+    """Base matrix ([rows][cols] int16, -1 = zero block) of an alist parity-check matrix of lifting size Z."""
+    import numpy as np
+    raw = text.encode("ascii")
+    rows, cols = _i(), _i()
+    lib = load_library()
+    _check(lib.qc_alist_parse(raw, len(raw), Z, None, 0, C.byref(rows), C.byref(cols)), "qc_alist_parse")
+    S = np.empty((rows.value, cols.value), dtype=np.int16)
+    _check(lib.qc_alist_parse(raw, len(raw), Z, S.ctypes.data, S.size, C.byref(rows), C.byref(cols)),
+           "qc_alist_parse")
+    return S
+
+
+def qc_ldpc_alist(code: Code) -> str:
+    """The code's parity-check matrix as alist text."""
+    lib = load_library()
+    n = _sz()
+    _check(lib.qc_ldpc_alist(code.handle, None, 0, C.byref(n)), "qc_ldpc_alist")
+    buf = C.create_string_buffer(n.value + 1)
+    _check(lib.qc_ldpc_alist(code.handle, buf, n.value + 1, C.byref(n)), "qc_ldpc_alist")
+    return buf.value.decode("ascii")
 
 
 def qc_ldpc_free(code: Code) -> None:

@@ -14,6 +14,8 @@ struct TxParams {
     const uint32_t *blk;
     const int32_t *row_ptr;
     int Z, rows, kb, n, k, n_tx, p0, nnz;
+    const uint32_t *core_inv;  // [4Z][inv_words] inverse of the core parity part, or null (dual diagonal)
+    int inv_words;
     int m;
     float scale;         // 1/sqrt(2(4^h-1)/3): unit average symbol energy
     uint64_t seed, cw0;
@@ -41,9 +43,10 @@ __device__ __forceinline__ int pam_level(const uint8_t *c, int h) {
 // up to 4), [G][4 nq] packed source words, then the block table and row
 // pointers of the code.
 __host__ __device__ inline int tx_ns(int n) { return (n + 3) & ~3; }
-__host__ __device__ inline size_t tx_smem(int G, int n, int k, int nnz, int rows) {
+__host__ __device__ inline size_t tx_smem(int G, int n, int k, int nnz, int rows, int inv_words) {
     const int nq = (((k + 31) >> 5) + 3) >> 2;
-    return (size_t)G * tx_ns(n) + (size_t)G * 16 * nq + 4 * (size_t)nnz + 4 * (size_t)(rows + 1);
+    return (size_t)G * tx_ns(n) + (size_t)G * 16 * nq + 4 * (size_t)nnz + 4 * (size_t)(rows + 1) +
+           4 * (size_t)G * inv_words;
 }
 
 __global__ void __launch_bounds__(kMaxThreads) k_tx(const TxParams p) {
@@ -55,11 +58,13 @@ __global__ void __launch_bounds__(kMaxThreads) k_tx(const TxParams p) {
     uint32_t *s_w = reinterpret_cast<uint32_t *>(smem + (size_t)p.G * ns);  // [G][4 nq] source words
     uint32_t *s_blk = s_w + (size_t)p.G * 4 * nq;
     int32_t *s_rp = reinterpret_cast<int32_t *>(s_blk + p.nnz);
+    uint32_t *s_lam = reinterpret_cast<uint32_t *>(s_rp + p.rows + 1);  // [G][inv_words] packed lambda
     const int64_t cw_base = (int64_t)blockIdx.x * p.G;
     const uint64_t cw0 = p.cw0 + (p.cw0_dev ? *p.cw0_dev : 0ull);
 
     for (int i = threadIdx.x; i < p.nnz; i += blockDim.x) s_blk[i] = p.blk[i];
     for (int i = threadIdx.x; i <= p.rows; i += blockDim.x) s_rp[i] = p.row_ptr[i];
+    for (int i = threadIdx.x; i < p.G * p.inv_words; i += blockDim.x) s_lam[i] = 0u;
     // a2: source bits (Philox stream 0), written packed to the output and to shared memory
     for (int i = threadIdx.x; i < p.G * nq; i += blockDim.x) {
         const int gg = i / nq, q = i - gg * nq;
@@ -113,10 +118,28 @@ __global__ void __launch_bounds__(kMaxThreads) k_tx(const TxParams p) {
             }
             lam[r] = acc;
         }
-        c[p.kb * Z + z] = lam[0] ^ lam[1] ^ lam[2] ^ lam[3];  // p_a: the core rows sum to [I 0 0 0]
+        if (p.core_inv) {
+            // lambda as a 4Z-bit vector, bit r Z + z = lambda_r[z]
+            uint32_t *lw = s_lam + (size_t)g * p.inv_words;
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+                if (lam[r]) atomicOr(&lw[(r * Z + z) >> 5], 1u << ((r * Z + z) & 31));
+        } else {
+            c[p.kb * Z + z] = lam[0] ^ lam[1] ^ lam[2] ^ lam[3];  // p_a: the core rows sum to [I 0 0 0]
+        }
     }
     __syncthreads();
-    if (active) {
+    if (active && p.core_inv) {
+        // core parity p = H_core^-1 lambda: bit r Z + z is the parity of (row r Z + z of the inverse) & lambda
+        const uint32_t *lw = s_lam + (size_t)g * p.inv_words;
+#pragma unroll 1
+        for (int r = 0; r < 4; ++r) {
+            const uint32_t *row = p.core_inv + (size_t)(r * Z + z) * p.inv_words;
+            uint32_t x = 0u;
+            for (int w = 0; w < p.inv_words; ++w) x ^= __ldg(row + w) & lw[w];
+            c[(p.kb + r) * Z + z] = (uint8_t)(__popc(x) & 1);
+        }
+    } else if (active) {
         const uint8_t pa = c[p.kb * Z + z];
         const uint8_t pb = lam[0] ^ c[p.kb * Z + (z + 1 == Z ? 0 : z + 1)];  // row 0: P^1 p_a + p_b
         const uint8_t pc = lam[1] ^ pa ^ pb;                                  // row 1: p_a + p_b + p_c
@@ -131,11 +154,16 @@ __global__ void __launch_bounds__(kMaxThreads) k_tx(const TxParams p) {
         for (int r = 4; r < p.rows; ++r) {
             uint8_t acc = 0;
             const int own = p.kb + r;
+            int s_own = 0;
             for (int b = s_rp[r]; b < s_rp[r + 1]; ++b) {
                 const uint32_t bb = s_blk[b];
                 if ((int)(bb >> 16) != own) acc ^= at(bb);
+                else s_own = (int)(bb & 0xFFFFu);
             }
-            c[own * Z + z] = acc;
+            // check z holds own-column bit (z + s_own) mod Z
+            int zz = z + s_own;
+            zz -= (zz >= Z) ? Z : 0;
+            c[own * Z + zz] = acc;
         }
     }
     __syncthreads();
@@ -724,12 +752,15 @@ int launch_tx(ldpcx_code_t c, uint64_t seed, uint64_t cw0, const uint64_t *cw0_d
     p.cw_out = cw_out;
     p.points = reinterpret_cast<const float2 *>(points);
     p.B = B;
+    if (c->enc == kEncNone) return LDPCX_E_UNSUPPORTED;
     p.nnz = c->nnz;
+    p.core_inv = c->enc == kEncCoreInv ? d.core_inv : nullptr;
+    p.inv_words = c->enc == kEncCoreInv ? c->inv_words : 0;
     int G = kMaxThreads / c->Z;
     if (G < 1) G = 1;
-    while (G > 1 && tx_smem(G, c->n, c->k, c->nnz, c->rows) > 96 * 1024) --G;
+    while (G > 1 && tx_smem(G, c->n, c->k, c->nnz, c->rows, p.inv_words) > 96 * 1024) --G;
     p.G = G;
-    const size_t smem = tx_smem(G, c->n, c->k, c->nnz, c->rows);
+    const size_t smem = tx_smem(G, c->n, c->k, c->nnz, c->rows, p.inv_words);
     if (smem > 48 * 1024 &&
         cudaFuncSetAttribute(k_tx, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return LDPCX_E_CUDA;

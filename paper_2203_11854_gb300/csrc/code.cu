@@ -4,6 +4,8 @@
 
 #include <algorithm>
 #include <new>
+#include <string>
+#include <vector>
 
 #include "common.cuh"
 
@@ -71,6 +73,127 @@ void seeded_base(const Shape &sh, int Z, uint64_t seed, std::vector<int16_t> &S,
             if (drawn[(size_t)r * C + c]) S[(size_t)r * C + c] = (int16_t)rng.below((uint32_t)Z);
 }
 
+// Block table, row pointers and largest row degree from c->S.
+void index_blocks(ldpcx_code *c) {
+    c->blk.clear();
+    c->row_ptr.assign(c->rows + 1, 0);
+    c->max_deg = 0;
+    for (int r = 0; r < c->rows; ++r) {
+        int deg = 0;
+        for (int col = 0; col < c->cols; ++col) {
+            const int s = c->S[(size_t)r * c->cols + col];
+            if (s < 0) continue;
+            c->blk.push_back(((uint32_t)col << 16) | (uint32_t)s);
+            ++deg;
+        }
+        c->row_ptr[r + 1] = c->row_ptr[r] + deg;
+        c->max_deg = std::max(c->max_deg, deg);
+    }
+    c->nnz = (int)c->blk.size();
+}
+
+// GF(2) inverse of the core parity part H_core (rows 0..3, columns kb..kb+3,
+// a 4Z x 4Z matrix: block (r, kb+j) with shift s has ones at (rZ + z,
+// jZ + (z+s) mod Z)) by Gauss-Jordan elimination on [H_core | I]. Row i of the
+// inverse is written to inv[i * nw ..], bit j of word j/32 = entry (i, j).
+// False when H_core is singular.
+bool core_inverse(const ldpcx_code *c, std::vector<uint32_t> &inv, int &nw) {
+    const int Z = c->Z, N = 4 * Z;
+    nw = (N + 31) / 32;
+    const int W = 2 * nw;  // words per augmented row
+    std::vector<uint32_t> a((size_t)N * W, 0u);
+    auto set = [&](int row, int col) { a[(size_t)row * W + (col >> 5)] ^= 1u << (col & 31); };
+    for (int r = 0; r < 4; ++r)
+        for (int j = 0; j < 4; ++j) {
+            const int s = c->S[(size_t)r * c->cols + c->kb + j];
+            if (s < 0) continue;
+            for (int z = 0; z < Z; ++z) set(r * Z + z, j * Z + (z + s) % Z);
+        }
+    for (int i = 0; i < N; ++i) a[(size_t)i * W + nw + (i >> 5)] |= 1u << (i & 31);
+    for (int col = 0; col < N; ++col) {
+        const int w = col >> 5;
+        const uint32_t bit = 1u << (col & 31);
+        int piv = -1;
+        for (int i = col; i < N; ++i)
+            if (a[(size_t)i * W + w] & bit) {
+                piv = i;
+                break;
+            }
+        if (piv < 0) return false;
+        if (piv != col)
+            for (int k = 0; k < W; ++k) std::swap(a[(size_t)piv * W + k], a[(size_t)col * W + k]);
+        for (int i = 0; i < N; ++i)
+            if (i != col && (a[(size_t)i * W + w] & bit))
+                for (int k = 0; k < W; ++k) a[(size_t)i * W + k] ^= a[(size_t)col * W + k];
+    }
+    inv.assign((size_t)N * nw, 0u);
+    for (int i = 0; i < N; ++i)
+        for (int k = 0; k < nw; ++k) inv[(size_t)i * nw + k] = a[(size_t)i * W + nw + k];
+    return true;
+}
+
+// Which encoder the transmitter can use for c (ldpcx::kEnc*), with the core
+// inverse when it needs one.
+void analyse_encoder(ldpcx_code *c) {
+    c->enc = ldpcx::kEncNone;
+    c->core_inv.clear();
+    c->inv_words = 0;
+    const int kb = c->kb, C = c->cols;
+    if (c->rows < 4 || C != kb + c->rows) return;
+    auto S = [&](int r, int col) { return (int)c->S[(size_t)r * C + col]; };
+    for (int r = 0; r < c->rows; ++r)
+        for (int col = kb + 4; col < C; ++col)
+            if (S(r, col) >= 0 && !(r >= 4 && col == kb + r)) return;  // a parity column out of order
+    for (int r = 4; r < c->rows; ++r)
+        if (S(r, kb + r) < 0) return;  // extension row without its own parity block
+    static const int dual[4][4] = {{1, 0, -1, -1}, {0, 0, 0, -1}, {-1, -1, 0, 0}, {1, -1, -1, 0}};
+    bool is_dual = true;
+    for (int r = 0; r < 4; ++r)
+        for (int j = 0; j < 4; ++j) is_dual = is_dual && S(r, kb + j) == dual[r][j];
+    if (is_dual) {
+        c->enc = ldpcx::kEncDualDiag;
+        return;
+    }
+    int nw = 0;
+    if (core_inverse(c, c->core_inv, nw)) {
+        c->enc = ldpcx::kEncCoreInv;
+        c->inv_words = nw;
+    }
+}
+
+// Lines of text split into integer tokens (empty lines kept); false on any
+// other token.
+bool int_lines(const char *text, size_t len, std::vector<std::vector<long>> &lines) {
+    lines.clear();
+    std::vector<long> cur;
+    size_t i = 0;
+    auto flush = [&]() {
+        lines.push_back(cur);
+        cur.clear();
+    };
+    while (i < len && text[i] != '\0') {
+        const char ch = text[i];
+        if (ch == '\n') {
+            flush();
+            ++i;
+        } else if (ch == ' ' || ch == '\t' || ch == '\r') {
+            ++i;
+        } else if (ch >= '0' && ch <= '9') {
+            long v = 0;
+            while (i < len && text[i] >= '0' && text[i] <= '9') {
+                v = v * 10 + (text[i] - '0');
+                if (v > 100000000L) return false;
+                ++i;
+            }
+            cur.push_back(v);
+        } else {
+            return false;
+        }
+    }
+    flush();
+    return true;
+}
+
 }  // namespace
 
 extern "C" const char *ldpcx_status_str(int status) {
@@ -136,21 +259,179 @@ extern "C" int qc_ldpc_build(const ldpcx_code_params *p, ldpcx_code_t *out) {
     c->S.resize((size_t)rows * c->cols);
     for (int r = 0; r < rows; ++r)
         for (int col = 0; col < c->cols; ++col) c->S[(size_t)r * c->cols + col] = full[(size_t)r * C + col];
-    c->row_ptr.assign(rows + 1, 0);
-    c->max_deg = 0;
-    for (int r = 0; r < rows; ++r) {
-        int deg = 0;
-        for (int col = 0; col < c->cols; ++col) {
-            const int s = c->S[(size_t)r * c->cols + col];
-            if (s < 0) continue;
-            c->blk.push_back(((uint32_t)col << 16) | (uint32_t)s);
-            ++deg;
-        }
-        c->row_ptr[r + 1] = c->row_ptr[r] + deg;
-        c->max_deg = std::max(c->max_deg, deg);
-    }
-    c->nnz = (int)c->blk.size();
+    index_blocks(c);
+    analyse_encoder(c);
     *out = c;
+    return LDPCX_OK;
+}
+
+extern "C" int qc_ldpc_build_base(const ldpcx_base_params *p, ldpcx_code_t *out) {
+    if (!p || !out || !p->S) return LDPCX_E_INVAL;
+    if (p->Z < 2 || p->Z > ldpcx::kMaxZ) return LDPCX_E_INVAL;
+    if (p->rows < 1 || p->rows > 4096 || p->cols < 2 || p->cols > 4096) return LDPCX_E_INVAL;
+    if (p->kb < 1 || p->kb >= p->cols) return LDPCX_E_INVAL;
+    if (p->punct_cols < 0 || p->punct_cols > p->kb) return LDPCX_E_INVAL;
+    for (int r = 0; r < p->rows; ++r) {
+        int deg = 0;
+        for (int col = 0; col < p->cols; ++col) {
+            const int s = p->S[(size_t)r * p->cols + col];
+            if (s < -1 || s >= p->Z) return LDPCX_E_INVAL;
+            deg += s >= 0;
+        }
+        if (deg < 2) return LDPCX_E_INVAL;  // every check node needs two edges
+    }
+    ldpcx_code *c = new (std::nothrow) ldpcx_code();
+    if (!c) return LDPCX_E_NOMEM;
+    c->params = ldpcx_code_params{0, p->Z, 0ull, 0, p->punct_cols, p->n_tx};
+    c->Z = p->Z;
+    c->rows = p->rows;
+    c->cols = p->cols;
+    c->kb = p->kb;
+    c->n = c->cols * c->Z;
+    c->k = c->kb * c->Z;
+    c->p0 = p->punct_cols * c->Z;
+    c->n_tx = p->n_tx == 0 ? c->n - c->p0 : p->n_tx;
+    if (c->n_tx < 1 || c->p0 + c->n_tx > c->n) {
+        delete c;
+        return LDPCX_E_INVAL;
+    }
+    c->S.assign(p->S, p->S + (size_t)p->rows * p->cols);
+    index_blocks(c);
+    analyse_encoder(c);
+    *out = c;
+    return LDPCX_OK;
+}
+
+extern "C" int qc_alist_parse(const char *text, size_t len, int Z, int16_t *S_out, int capacity, int *rows_out,
+                              int *cols_out) {
+    if (!text || !rows_out || !cols_out || Z < 1 || Z > ldpcx::kMaxZ) return LDPCX_E_INVAL;
+    std::vector<std::vector<long>> all, L;
+    if (!int_lines(text, len, all)) return LDPCX_E_INVAL;
+    // the header: the first four non-empty lines
+    size_t at = 0;
+    while (L.size() < 4 && at < all.size()) {
+        if (!all[at].empty()) L.push_back(all[at]);
+        ++at;
+    }
+    if (L.size() < 4 || L[0].size() != 2 || L[1].size() != 2) return LDPCX_E_INVAL;
+    const long N = L[0][0], M = L[0][1];
+    if (N < 1 || M < 1 || N % Z || M % Z || N / Z > 4096 || M / Z > 4096) return LDPCX_E_INVAL;
+    if ((long)L[2].size() != N || (long)L[3].size() != M) return LDPCX_E_INVAL;
+    // the N + M lists: the non-empty lines that follow, or, when a list is
+    // empty (a weight-0 column or row written without padding), every line
+    // that follows up to the trailing empty ones
+    std::vector<std::vector<long>> rest(all.begin() + (long)at, all.end());
+    while (!rest.empty() && rest.back().empty()) rest.pop_back();
+    long nonempty = 0;
+    for (const auto &ln : rest) nonempty += !ln.empty();
+    if (nonempty == N + M) {
+        for (const auto &ln : rest)
+            if (!ln.empty()) L.push_back(ln);
+    } else if ((long)rest.size() == N + M) {
+        L.insert(L.end(), rest.begin(), rest.end());
+    } else {
+        return LDPCX_E_INVAL;
+    }
+    // the row lists give the entries; the column lists must give the same ones
+    std::vector<std::vector<int>> by_col((size_t)N);
+    long entries = 0;
+    for (long i = 0; i < M; ++i) {
+        long cnt = 0;
+        for (long v : L[4 + N + i]) {
+            if (v == 0) continue;  // padding
+            if (v > N) return LDPCX_E_INVAL;
+            by_col[(size_t)(v - 1)].push_back((int)i);
+            ++cnt;
+        }
+        if (cnt != L[3][(size_t)i]) return LDPCX_E_INVAL;
+        entries += cnt;
+    }
+    long col_entries = 0;
+    for (long j = 0; j < N; ++j) {
+        std::vector<int> listed;
+        for (long v : L[4 + j]) {
+            if (v == 0) continue;
+            if (v > M) return LDPCX_E_INVAL;
+            listed.push_back((int)(v - 1));
+        }
+        if ((long)listed.size() != L[2][(size_t)j]) return LDPCX_E_INVAL;
+        std::vector<int> have = by_col[(size_t)j];
+        std::sort(listed.begin(), listed.end());
+        std::sort(have.begin(), have.end());
+        if (listed != have) return LDPCX_E_INVAL;
+        col_entries += (long)listed.size();
+    }
+    if (col_entries != entries) return LDPCX_E_INVAL;
+    const int rows = (int)(M / Z), cols = (int)(N / Z);
+    *rows_out = rows;
+    *cols_out = cols;
+    if (!S_out) return LDPCX_OK;  // size query
+    if (capacity < rows * cols) return LDPCX_E_INVAL;
+    // every Z x Z block must be zero or a cyclically shifted identity: entry (z, (z + s) mod Z)
+    std::vector<int> shift((size_t)rows * cols, -1), count((size_t)rows * cols, 0);
+    for (long j = 0; j < N; ++j)
+        for (int i : by_col[(size_t)j]) {
+            const int br = i / Z, z = i % Z, bc = (int)(j / Z), w = (int)(j % Z);
+            const int s = (w - z + Z) % Z;
+            const size_t b = (size_t)br * cols + bc;
+            if (shift[b] >= 0 && shift[b] != s) return LDPCX_E_INVAL;
+            shift[b] = s;
+            ++count[b];
+        }
+    for (size_t b = 0; b < shift.size(); ++b) {
+        if (count[b] != 0 && count[b] != Z) return LDPCX_E_INVAL;
+        S_out[b] = (int16_t)shift[b];
+    }
+    return LDPCX_OK;
+}
+
+extern "C" int qc_ldpc_alist(ldpcx_code_t c, char *buf, size_t cap, size_t *len_out) {
+    if (!c || !len_out) return LDPCX_E_INVAL;
+    const int Z = c->Z, R = c->rows, C = c->cols;
+    std::vector<int> col_deg(C, 0);
+    for (int r = 0; r < R; ++r)
+        for (int col = 0; col < C; ++col) col_deg[col] += c->S[(size_t)r * C + col] >= 0;
+    const int max_c = *std::max_element(col_deg.begin(), col_deg.end());
+    std::string t;
+    t.reserve((size_t)c->nnz * Z * 14 + 64);
+    auto num = [&](long v, char end) {
+        t += std::to_string(v);
+        t += end;
+    };
+    num((long)C * Z, ' ');
+    num((long)R * Z, '\n');
+    num(max_c, ' ');
+    num(c->max_deg, '\n');
+    for (int col = 0; col < C; ++col)
+        for (int w = 0; w < Z; ++w) num(col_deg[col], col == C - 1 && w == Z - 1 ? '\n' : ' ');
+    for (int r = 0; r < R; ++r)
+        for (int z = 0; z < Z; ++z) num(c->row_ptr[r + 1] - c->row_ptr[r], r == R - 1 && z == Z - 1 ? '\n' : ' ');
+    // variable (col, w): check rows r Z + (w - s) mod Z of the blocks in base column col, ascending
+    for (int col = 0; col < C; ++col)
+        for (int w = 0; w < Z; ++w) {
+            int k = 0;
+            for (int r = 0; r < R; ++r) {
+                const int s = c->S[(size_t)r * C + col];
+                if (s < 0) continue;
+                num((long)r * Z + (w - s + Z) % Z + 1, ++k == max_c ? '\n' : ' ');
+            }
+            for (; k < max_c;) num(0, ++k == max_c ? '\n' : ' ');
+        }
+    // check (r, z): variables col Z + (z + s) mod Z of the row's blocks, ascending
+    for (int r = 0; r < R; ++r)
+        for (int z = 0; z < Z; ++z) {
+            int k = 0;
+            for (int b = c->row_ptr[r]; b < c->row_ptr[r + 1]; ++b) {
+                const int col = (int)(c->blk[b] >> 16), s = (int)(c->blk[b] & 0xFFFFu);
+                num((long)col * Z + (z + s) % Z + 1, ++k == c->max_deg ? '\n' : ' ');
+            }
+            for (; k < c->max_deg;) num(0, ++k == c->max_deg ? '\n' : ' ');
+        }
+    *len_out = t.size();
+    if (!buf) return LDPCX_OK;  // size query
+    if (cap < t.size() + 1) return LDPCX_E_INVAL;
+    memcpy(buf, t.data(), t.size());
+    buf[t.size()] = '\0';
     return LDPCX_OK;
 }
 
@@ -180,6 +461,7 @@ extern "C" int qc_ldpc_info(ldpcx_code_t c, ldpcx_code_info *info) {
     info->n_tx = c->n_tx;
     info->p0 = c->p0;
     info->edges = (int64_t)c->nnz * c->Z;
+    info->encodable = c->enc != ldpcx::kEncNone;
     return LDPCX_OK;
 }
 
@@ -202,13 +484,16 @@ int code_device(ldpcx_code_t c, DevCode *out) {
     if (!c->d_tables) {
         const size_t nb = sizeof(uint32_t) * c->blk.size();
         const size_t nr = sizeof(int32_t) * c->row_ptr.size();
+        const size_t ni = sizeof(uint32_t) * c->core_inv.size();
+        const size_t oi = (nb + nr + 15) / 16 * 16;
         void *p = nullptr;
-        if (cudaMalloc(&p, nb + nr) != cudaSuccess) {
+        if (cudaMalloc(&p, oi + ni) != cudaSuccess) {
             cudaGetLastError();
             return LDPCX_E_NOMEM;
         }
         if (cudaMemcpy(p, c->blk.data(), nb, cudaMemcpyHostToDevice) != cudaSuccess ||
-            cudaMemcpy((char *)p + nb, c->row_ptr.data(), nr, cudaMemcpyHostToDevice) != cudaSuccess) {
+            cudaMemcpy((char *)p + nb, c->row_ptr.data(), nr, cudaMemcpyHostToDevice) != cudaSuccess ||
+            (ni && cudaMemcpy((char *)p + oi, c->core_inv.data(), ni, cudaMemcpyHostToDevice) != cudaSuccess)) {
             cudaFree(p);
             return LDPCX_E_CUDA;
         }
@@ -216,6 +501,7 @@ int code_device(ldpcx_code_t c, DevCode *out) {
         c->dev = dev;
         c->d.blk = (const uint32_t *)p;
         c->d.row_ptr = (const int32_t *)((char *)p + nb);
+        c->d.core_inv = ni ? (const uint32_t *)((char *)p + oi) : nullptr;
     }
     *out = c->d;
     return LDPCX_OK;

@@ -20,9 +20,17 @@ constexpr int kMaxThreads = 384;
 
 // Device-side view of a code's tables.
 struct DevCode {
-    const uint32_t *blk;    // [nnz] (col << 16) | shift, sorted by base row, then column
-    const int32_t *row_ptr; // [rows + 1] first block of each base row
+    const uint32_t *blk;      // [nnz] (col << 16) | shift, sorted by base row, then column
+    const int32_t *row_ptr;   // [rows + 1] first block of each base row
+    const uint32_t *core_inv; // [4Z][inv_words] GF(2) inverse of the core parity part, or null
 };
+
+// Encoder structure of a code: the transmitter handles base matrices whose
+// core rows 0..3 touch only the systematic and the four core parity columns
+// and whose extension row r touches, past those, only its own column kb + r.
+constexpr int kEncNone = 0;      // not encodable by the transmitter
+constexpr int kEncDualDiag = 1;  // the 5G dual-diagonal core: the recursion
+constexpr int kEncCoreInv = 2;   // any invertible core: its inverse
 
 }  // namespace ldpcx
 
@@ -33,6 +41,9 @@ struct ldpcx_code {
     std::vector<int16_t> S;        // rows x cols base matrix, -1 = zero block
     std::vector<uint32_t> blk;     // nonzero blocks in row-major order
     std::vector<int32_t> row_ptr;  // rows + 1
+    int enc = 0;                   // ldpcx::kEnc*
+    int inv_words = 0;             // words per row of core_inv
+    std::vector<uint32_t> core_inv;  // [4Z][inv_words] (kEncCoreInv)
     std::mutex mu;
     int dev = -1;                  // device the tables live on
     void *d_tables = nullptr;

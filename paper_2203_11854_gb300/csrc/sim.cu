@@ -22,6 +22,7 @@ size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 int layout(const ldpcx_sim_config *c, SimLayout *L) {
     if (!c || !c->code) return LDPCX_E_INVAL;
     const ldpcx_code *code = c->code;
+    if (code->enc == ldpcx::kEncNone) return LDPCX_E_UNSUPPORTED;  // the transmitter cannot encode it
     if (!(c->m == 1 || c->m == 2 || c->m == 4 || c->m == 6 || c->m == 8)) return LDPCX_E_INVAL;
     if (code->n_tx % c->m) return LDPCX_E_INVAL;
     if (c->batch < 1 || c->max_batches < 1 || c->n_snr < 0 || c->min_bit_errors < 0) return LDPCX_E_INVAL;
