@@ -14,7 +14,12 @@
 //   gw   += gV_e (APP^t_v - C^(t-1)_e),  gA^t_v += w gV_e,  carry_e = -w gV_e
 //   dLoss/dL = sum_t gA^t (through the channel clamp).
 // APP^t is recomputed from the checkpointed C^(t-1) in the forward's row order,
-// so it equals the forward's value bit for bit.
+// so it equals the forward's value bit for bit. phi and phi' are evaluated with
+// the hardware exponential, reciprocal and logarithm (phi_fast, dphi_fast:
+// within about 2e-5 and 1e-6 relative), the exclusive sums S_e as in the
+// forward's check node (the largest term left out of the running sum) and the
+// exclusive sums of u from prefix and suffix sums: O(d) per check node. dL/dL
+// accumulates in grad_llr itself, iteration by iteration.
 #include <math.h>
 
 #include "decode_kernels.cuh"
@@ -39,8 +44,19 @@ struct BwdParams {
     int G;
 };
 
-__device__ __forceinline__ float phi_f(float x) { return log1pf(__fdiv_rn(2.0f, expm1f(x))); }
-__device__ __forceinline__ float dphi_f(float x) { return -1.0f / sinhf(x); }
+// phi'(x) = -1/sinh(x) from the hardware exponential; below x = 1/16, where
+// e^x - e^-x would cancel, from the Taylor series sinh x = x (1 + x^2/6 (1 +
+// x^2/20 (1 + x^2/42))) (truncation below 1e-12 relative there). Above it
+// e - 1/e >= 0.125 loses at most a factor 16 of the exponential's relative
+// error: about 1e-6 relative overall.
+__device__ __forceinline__ float dphi_fast(float x) {
+    if (x < 0.0625f) {
+        const float x2 = x * x;
+        return -__fdividef(1.0f, x * (1.0f + x2 * (1.0f / 6.0f) * (1.0f + x2 * (1.0f / 20.0f) * (1.0f + x2 * (1.0f / 42.0f)))));
+    }
+    const float e = __expf(x);
+    return -__fdividef(2.0f, e - __fdividef(1.0f, e));
+}
 
 __device__ __forceinline__ int vn_of(uint32_t vb, int z, int Z) {
     int zz = z + (int)(vb & 0xFFFFu);
@@ -57,15 +73,26 @@ __device__ __forceinline__ float placed_llr(const BwdParams &p, int64_t cw, int 
     return fminf(fmaxf(x, -p.clamp), p.clamp);
 }
 
-template <int DMAX>
-__global__ void __launch_bounds__(kMaxThreads, 1) k_backward(const BwdParams p) {
+// Sum over the TPC adjacent lanes of one check node (TPC a power of two <= 32).
+template <int TPC> __device__ __forceinline__ float group_sum(float x) {
+#pragma unroll
+    for (int o = 1; o < TPC; o <<= 1) x += __shfl_xor_sync(0xFFFFFFFFu, x, o);
+    return x;
+}
+
+// TPC threads per check node: thread q of node z takes the edges j = q, q +
+// TPC, ... of the row (DPT of them at most), and the row-wide quantities (the
+// sign parity, the largest phi term and the sums) are combined by shuffles
+// among the node's TPC adjacent lanes. Threads: G Z TPC per CTA.
+template <int DMAX, int TPC>
+__global__ void __launch_bounds__(512, TPC == 4 ? 2 : 1) k_backward(const BwdParams p) {
+    constexpr int DPT = (DMAX + TPC - 1) / TPC;
     extern __shared__ __align__(16) unsigned char smem[];
     const size_t gn = (size_t)p.G * p.n;
     float *s_app = reinterpret_cast<float *>(smem);
     float *s_gin = s_app + gn;   // gA^(t+1)
     float *s_gout = s_gin + gn;  // gA^t (accumulated)
-    float *s_gl = s_gout + gn;   // dLoss/dL
-    float *s_gw = s_gl + gn;     // [nnz] weight gradient of this iteration
+    float *s_gw = s_gout + gn;   // [nnz] weight gradient of this iteration
     uint32_t *s_vb = reinterpret_cast<uint32_t *>(s_gw + p.nnz);
     int32_t *s_rp = reinterpret_cast<int32_t *>(s_vb + p.nnz);
 
@@ -78,12 +105,13 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_backward(const BwdParams p) 
     const int64_t cw_base = (int64_t)blockIdx.x * p.G;
     for (int gg = 0; gg < p.G; ++gg) {
         const int64_t c2 = cw_base + gg;
-        for (int v = threadIdx.x; v < p.n; v += blockDim.x) {
+        for (int v = threadIdx.x; v < p.n; v += blockDim.x)
             s_gin[(size_t)gg * p.n + v] = c2 < p.B ? p.grad_out[c2 * p.n + v] : 0.0f;
-            s_gl[(size_t)gg * p.n + v] = 0.0f;
-        }
+        if (c2 < p.B)
+            for (int t = threadIdx.x; t < p.n_tx; t += blockDim.x) p.grad_llr[c2 * p.n_tx + t] = 0.0f;
     }
-    const int g = threadIdx.x / p.Z, z = threadIdx.x - g * p.Z;
+    const int node = threadIdx.x / TPC, q = threadIdx.x - node * TPC;
+    const int g = node / p.Z, z = node - g * p.Z;
     const int64_t cw = cw_base + g;
     const bool active = g < p.G && cw < p.B;
     const size_t off = (size_t)(active ? g : 0) * p.n;
@@ -101,84 +129,110 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_backward(const BwdParams p) 
         if (ck) {
             for (int r = 0; r < p.rows; ++r) {
                 if (active)
-                    for (int b = s_rp[r]; b < s_rp[r + 1]; ++b) {
+                    for (int b = s_rp[r] + q; b < s_rp[r + 1]; b += TPC) {
                         const int v = vn_of(s_vb[b], z, p.Z);
                         s_app[off + v] = __fadd_rn(s_app[off + v], ck[(size_t)b * p.Z]);
                     }
                 __syncthreads();
             }
         }
-        // dLoss/dL collects every gA^(t+1); gA^t starts from zero
-        for (size_t i = threadIdx.x; i < gn; i += blockDim.x) {
-            s_gl[i] += gin[i];
-            gout[i] = 0.0f;
+        // dLoss/dL collects every gA^(t+1) (transmitted positions only); gA^t starts from zero
+        for (int gg = 0; gg < p.G; ++gg) {
+            const int64_t c2 = cw_base + gg;
+            if (c2 >= p.B) break;
+            for (int tt = threadIdx.x; tt < p.n_tx; tt += blockDim.x)
+                p.grad_llr[c2 * p.n_tx + tt] += gin[(size_t)gg * p.n + p.p0 + tt];
         }
+        for (size_t i = threadIdx.x; i < gn; i += blockDim.x) gout[i] = 0.0f;
         __syncthreads();
         const float *w_t = p.weights ? p.weights + (size_t)t * p.nnz : nullptr;
         const bool has_carry = t + 1 < p.iters;
         for (int r = 0; r < p.rows; ++r) {
             const int b0 = s_rp[r], deg = s_rp[r + 1] - b0;
-            float gw[DMAX];
+            float gw[DPT];
+            float V[DPT], d[DPT], f[DPT], u[DPT];
+            int vi[DPT];
+            // this thread's edges: the sign parity, its largest phi term and their sum
+            unsigned par = 0;
+            float fmax = -1.0f;
+            int im = -1;
 #pragma unroll
-            for (int j = 0; j < DMAX; ++j) gw[j] = 0.0f;
-            if (active) {
-                float V[DMAX], d[DMAX], f[DMAX], u[DMAX];
-                int vi[DMAX];
-                unsigned neg = 0;
-#pragma unroll
-                for (int j = 0; j < DMAX; ++j) {
-                    V[j] = d[j] = f[j] = u[j] = 0.0f;
-                    vi[j] = 0;
-                    if (j < deg) {
-                        vi[j] = vn_of(s_vb[b0 + j], z, p.Z);
-                        const float cold = ck ? ck[(size_t)(b0 + j) * p.Z] : 0.0f;
-                        d[j] = __fsub_rn(s_app[off + vi[j]], cold);
-                        V[j] = w_t ? __fmul_rn(w_t[b0 + j], d[j]) : d[j];
-                        f[j] = phi_f(fminf(fmaxf(fabsf(V[j]), lo), hi));
-                        neg |= (V[j] < 0.0f ? 1u : 0u) << j;
-                    }
-                }
-                const unsigned par = __popc(neg) & 1u;
-                // u_e = gC_e s_e phi'(x_e) [lo < S_e < hi]
-#pragma unroll
-                for (int j = 0; j < DMAX; ++j) {
-                    if (j < deg) {
-                        float S = 0.0f;
-#pragma unroll
-                        for (int i = 0; i < DMAX; ++i)
-                            if (i < deg && i != j) S += f[i];
-                        const float gC = gin[off + vi[j]] + (has_carry ? carry[(size_t)(b0 + j) * p.Z] : 0.0f);
-                        const float s = ((par ^ (neg >> j)) & 1u) ? -1.0f : 1.0f;
-                        u[j] = (S > lo && S < hi) ? gC * s * dphi_f(S) : 0.0f;
-                    }
-                }
-                // gV_e = phi'(a_e) sgn(V_e) [lo <= |V_e| <= hi] sum_{e' != e} u_e'
-#pragma unroll
-                for (int j = 0; j < DMAX; ++j) {
-                    if (j < deg) {
-                        float U = 0.0f;
-#pragma unroll
-                        for (int i = 0; i < DMAX; ++i)
-                            if (i < deg && i != j) U += u[i];
-                        const float a = fabsf(V[j]);
-                        const bool inside = a >= lo && a <= hi;
-                        const float gV = inside ? dphi_f(a) * (V[j] < 0.0f ? -1.0f : 1.0f) * U : 0.0f;
-                        const float w = w_t ? w_t[b0 + j] : 1.0f;
-                        gw[j] = gV * d[j];
-                        gout[off + vi[j]] += w * gV;
-                        carry[(size_t)(b0 + j) * p.Z] = -w * gV;
+            for (int i = 0; i < DPT; ++i) {
+                const int j = q + TPC * i;
+                gw[i] = V[i] = d[i] = f[i] = u[i] = 0.0f;
+                vi[i] = 0;
+                if (active && j < deg) {
+                    vi[i] = vn_of(s_vb[b0 + j], z, p.Z);
+                    const float cold = ck ? ck[(size_t)(b0 + j) * p.Z] : 0.0f;
+                    d[i] = __fsub_rn(s_app[off + vi[i]], cold);
+                    V[i] = w_t ? __fmul_rn(w_t[b0 + j], d[i]) : d[i];
+                    f[i] = dec::phi_fast(fminf(fmaxf(fabsf(V[i]), lo), hi));
+                    par ^= V[i] < 0.0f ? 1u : 0u;
+                    if (f[i] > fmax) {
+                        fmax = f[i];
+                        im = i;
                     }
                 }
             }
-            // weight gradient: every lane of a warp is at the same block b0 + j
+            // the row's largest term (ties: the lowest edge index) leaves the running sum, as in the forward
+            float rmax = fmax;
+            int jmax = im >= 0 ? q + TPC * im : DMAX;
+#pragma unroll
+            for (int o = 1; o < TPC; o <<= 1) {
+                const float om = __shfl_xor_sync(0xFFFFFFFFu, rmax, o);
+                const int oj = __shfl_xor_sync(0xFFFFFFFFu, jmax, o);
+                if (om > rmax || (om == rmax && oj < jmax)) {
+                    rmax = om;
+                    jmax = oj;
+                }
+            }
+#pragma unroll
+            for (int o = 1; o < TPC; o <<= 1) par ^= __shfl_xor_sync(0xFFFFFFFFu, par, o);
+            float part = 0.0f;
+#pragma unroll
+            for (int i = 0; i < DPT; ++i)
+                if (q + TPC * i < deg && q + TPC * i != jmax) part += f[i];
+            const float s_rest = group_sum<TPC>(part);
+            const float s_all = s_rest + rmax;
+            // u_e = gC_e s_e phi'(x_e) [lo < S_e < hi]
+            float usum = 0.0f;
+#pragma unroll
+            for (int i = 0; i < DPT; ++i) {
+                const int j = q + TPC * i;
+                if (active && j < deg) {
+                    const float S = j == jmax ? s_rest : s_all - f[i];
+                    const float gC = gin[off + vi[i]] + (has_carry ? carry[(size_t)(b0 + j) * p.Z] : 0.0f);
+                    const float sg = (par ^ (V[i] < 0.0f ? 1u : 0u)) ? -1.0f : 1.0f;
+                    u[i] = (S > lo && S < hi) ? gC * sg * dphi_fast(S) : 0.0f;
+                    usum += u[i];
+                }
+            }
+            const float U_all = group_sum<TPC>(usum);
+            // gV_e = phi'(a_e) sgn(V_e) [lo <= |V_e| <= hi] sum_{e' != e} u_e'
+#pragma unroll
+            for (int i = 0; i < DPT; ++i) {
+                const int j = q + TPC * i;
+                if (active && j < deg) {
+                    const float U = U_all - u[i];
+                    const float a = fabsf(V[i]);
+                    const bool inside = a >= lo && a <= hi;
+                    const float gV = inside ? dphi_fast(a) * (V[i] < 0.0f ? -1.0f : 1.0f) * U : 0.0f;
+                    const float w = w_t ? w_t[b0 + j] : 1.0f;
+                    gw[i] = gV * d[i];
+                    gout[off + vi[i]] += w * gV;
+                    carry[(size_t)(b0 + j) * p.Z] = -w * gV;
+                }
+            }
+            // weight gradient: the lanes of a warp with the same q are at the same blocks b0 + q + TPC i
             if (p.grad_w) {
 #pragma unroll
-                for (int j = 0; j < DMAX; ++j) {
-                    if (j < deg) {
-                        float x = gw[j];
+                for (int i = 0; i < DPT; ++i) {
+                    if (TPC * i < deg) {  // warp-uniform: some lane of the warp has an edge in slot i
+                        float x = gw[i];
 #pragma unroll
-                        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xFFFFFFFFu, x, o);
-                        if ((threadIdx.x & 31) == 0 && x != 0.0f) atomicAdd(&s_gw[b0 + j], x);
+                        for (int o = TPC; o < 32; o <<= 1) x += __shfl_xor_sync(0xFFFFFFFFu, x, o);
+                        const int j = q + TPC * i;
+                        if ((threadIdx.x & 31) < TPC && j < deg && x != 0.0f) atomicAdd(&s_gw[b0 + j], x);
                     }
                 }
             }
@@ -195,22 +249,21 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_backward(const BwdParams p) 
         gout = tmp;
         __syncthreads();
     }
-    // dLoss/dL += gA^0, then through the channel clamp to the transmitted positions
-    for (size_t i = threadIdx.x; i < gn; i += blockDim.x) s_gl[i] += gin[i];
-    __syncthreads();
+    // dLoss/dL += gA^0, then through the channel clamp (each thread revisits only its own entries)
     for (int gg = 0; gg < p.G; ++gg) {
         const int64_t c2 = cw_base + gg;
         if (c2 >= p.B) break;
         for (int t = threadIdx.x; t < p.n_tx; t += blockDim.x) {
             const float x = p.llr[c2 * p.n_tx + t];
             const bool pass = (x == x) && fabsf(x) <= p.clamp;
-            p.grad_llr[c2 * p.n_tx + t] = pass ? s_gl[(size_t)gg * p.n + p.p0 + t] : 0.0f;
+            const float gsum = p.grad_llr[c2 * p.n_tx + t] + gin[(size_t)gg * p.n + p.p0 + t];
+            p.grad_llr[c2 * p.n_tx + t] = pass ? gsum : 0.0f;
         }
     }
 }
 
 size_t bwd_smem(int G, int n, int nnz, int rows) {
-    return sizeof(float) * (4 * (size_t)G * n + nnz) + sizeof(uint32_t) * nnz + sizeof(int32_t) * (rows + 1);
+    return sizeof(float) * (3 * (size_t)G * n + nnz) + sizeof(uint32_t) * nnz + sizeof(int32_t) * (rows + 1);
 }
 
 int64_t stride_of(const ldpcx_code *c) {
@@ -277,15 +330,20 @@ extern "C" int ldpc_bp_backward(ldpcx_code_t c, const float *llr_ch, int64_t B, 
     p.grad_w = grad_weights;
     p.carry = (float *)ws;
     p.B = B;
-    int G = kMaxThreads / c->Z;
+    // threads per check node: as many as keep a CTA within 512 threads
+    const int tpc = c->Z <= 128 ? 4 : c->Z <= 256 ? 2 : 1;
+    int G = 512 / (c->Z * tpc);
     if (G < 1) G = 1;
-    while (G > 1 && bwd_smem(G, c->n, c->nnz, c->rows) > 216 * 1024) --G;
+    const size_t cap = tpc == 4 ? 112 * 1024 : 216 * 1024;  // two CTAs per SM with four threads per node
+    while (G > 1 && bwd_smem(G, c->n, c->nnz, c->rows) > cap) --G;
     p.G = G;
     const size_t smem = bwd_smem(G, c->n, c->nnz, c->rows);
-    auto fn = c->max_deg <= 12 ? k_backward<12> : k_backward<20>;
+    void (*fn)(BwdParams) = nullptr;
+    if (c->max_deg <= 12) fn = tpc == 4 ? k_backward<12, 4> : tpc == 2 ? k_backward<12, 2> : k_backward<12, 1>;
+    else fn = tpc == 4 ? k_backward<20, 4> : tpc == 2 ? k_backward<20, 2> : k_backward<20, 1>;
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return LDPCX_E_CUDA;
-    const int threads = (G * c->Z + 31) / 32 * 32;
+    const int threads = (G * c->Z * tpc + 31) / 32 * 32;
     const int64_t grid = (B + G - 1) / G;
     fn<<<(unsigned)grid, threads, smem, (cudaStream_t)stream>>>(p);
     return cudaGetLastError() == cudaSuccess ? LDPCX_OK : LDPCX_E_CUDA;

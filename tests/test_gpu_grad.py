@@ -41,7 +41,7 @@ def gpu_grads(lx, gcode, L, cw, w, iters):
     out = LdpcBP.apply(Lt, wt, gcode, iters, 20.0)
     loss = torch.nn.functional.binary_cross_entropy_with_logits(-out, torch.from_numpy(cw).cuda().float())
     loss.backward()
-    return float(loss), Lt.grad.cpu().numpy(), wt.grad.cpu().numpy(), out.detach().cpu().numpy()
+    return float(loss.detach()), Lt.grad.cpu().numpy(), wt.grad.cpu().numpy(), out.detach().cpu().numpy()
 
 
 def test_ckpt_forward_equals_plain_decode(lx, orc):
@@ -54,7 +54,9 @@ def test_ckpt_forward_equals_plain_decode(lx, orc):
     assert ckpt.numel() == lx.ldpc_bp_ckpt_bytes(g, 10, iters=8)
 
 
-@pytest.mark.parametrize("bg,Z,B,iters", [(2, 64, 4, 10), (2, 8, 12, 6)])
+# Z <= 128 runs four threads per check node in the adjoint, 129..256 two, larger Z one; BG1 rows reach degree 19
+@pytest.mark.parametrize("bg,Z,B,iters", [(2, 64, 4, 10), (2, 8, 12, 6), (1, 16, 3, 5), (2, 160, 2, 4),
+                                          (2, 288, 1, 3)])
 def test_gradients_match_autograd_oracle(lx, orc, bg, Z, B, iters):
     from oracle import grad
     code, cw, L, w = make(orc, bg, Z, B, 1.0, iters, 17)
