@@ -30,7 +30,7 @@ int64_t cns_bytes(const ldpcx_code *c, int prec) {
 }
 
 KernelFn pick_kernel(int max_deg, bool layered, int algo, int prec, int zpt, int Z) {
-    if (!layered) return flooding_kernel(max_deg, algo, prec);
+    if (!layered) return flooding_kernel(max_deg, algo, prec, flood_tpc(Z));
     if (zpt == 1 && g_specialised.load()) {
         KernelFn f = prec == kF32 ? layered_kernel_zc_f32(max_deg, algo, Z)
                    : prec == kF16 ? layered_kernel_zc_f16(max_deg, algo, Z)
@@ -68,12 +68,14 @@ std::atomic<int> g_pf_dist{0};
 std::atomic<int> g_zpt{0};
 std::atomic<int> g_cw_per_cta{0};  // 0 = automatic
 
-// Codewords per CTA: enough check-node threads to fill ~384 threads, bounded
-// by the shared memory that keeps two CTAs per SM (layered) or one (flooding).
+// Codewords per CTA: enough check-node threads to fill ~384 threads (layered)
+// or up to 512 threads of TPC per check node (flooding), bounded by the shared
+// memory that keeps two CTAs per SM (layered; flooding with TPC > 1) or one.
 int pick_G(const ldpcx_code *c, bool layered) {
     const size_t per_cw = sizeof(float) * (size_t)c->n * (layered ? 1 : 2);
-    const size_t budget = layered ? 105 * 1024 : 210 * 1024;
-    int G = kMaxThreads / c->Z;
+    const int tpc = layered ? 1 : flood_tpc(c->Z);
+    const size_t budget = layered || tpc > 1 ? 105 * 1024 : 210 * 1024;
+    int G = layered ? kMaxThreads / c->Z : 512 / (c->Z * tpc);
     if (G < 1) G = 1;
     while (G > 1 && per_cw * G > budget) --G;
     const int want = g_cw_per_cta.load();
@@ -228,7 +230,7 @@ int decode_impl(ldpcx_code_t c, const float *llr_ch, int64_t B, const ldpcx_deco
     if (smem > 227 * 1024) return LDPCX_E_UNSUPPORTED;
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return LDPCX_E_CUDA;
-    int threads = p.G * (p.Z / zpt);
+    int threads = layered ? p.G * (p.Z / zpt) : p.G * p.Z * flood_tpc(p.Z);
     threads = (threads + 31) / 32 * 32;
     const int64_t grid = (B + p.G - 1) / p.G;
     if (grid > 0x7FFFFFFF) return LDPCX_E_INVAL;

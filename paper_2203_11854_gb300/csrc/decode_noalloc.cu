@@ -71,8 +71,9 @@ size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 // bounded by two CTAs per SM (layered) or one (flooding).
 int codewords_per_cta(const ldpcx_code *c, bool layered) {
     const size_t per_cw = sizeof(float) * (size_t)c->n * (layered ? 1 : 2);
-    const size_t budget = layered ? 105 * 1024 : 210 * 1024;
-    int G = kMaxThreads / c->Z;
+    const int tpc = layered ? 1 : flood_tpc(c->Z);
+    const size_t budget = layered || tpc > 1 ? 105 * 1024 : 210 * 1024;
+    int G = layered ? kMaxThreads / c->Z : 512 / (c->Z * tpc);
     if (G < 1) G = 1;
     while (G > 1 && per_cw * G > budget) --G;
     return G;
@@ -101,7 +102,7 @@ extern "C" int ldpc_bp_decode_noalloc(ldpcx_code_t c, const float *llr_ch, int64
     const bool layered = o->algo == LDPCX_LAYERED_MINSUM || o->algo == LDPCX_LAYERED_SPA;
     const int algo = (o->algo == LDPCX_LAYERED_MINSUM || o->algo == LDPCX_FLOOD_MINSUM) ? kMinSum : kSpa;
     KernelFn fn = nullptr;
-    if (!layered) fn = flooding_kernel(c->max_deg, algo, o->msg_prec);
+    if (!layered) fn = flooding_kernel(c->max_deg, algo, o->msg_prec, flood_tpc(c->Z));
     else if (o->msg_prec == kF32) fn = layered_kernel_f32(c->max_deg, algo, 1);
     else if (o->msg_prec == kF16) fn = layered_kernel_f16(c->max_deg, algo, 1);
     else fn = layered_kernel_fix6(c->max_deg, algo, 1);
@@ -149,7 +150,7 @@ extern "C" int ldpc_bp_decode_noalloc(ldpcx_code_t c, const float *llr_ch, int64
     if (smem > 227 * 1024) return LDPCX_E_UNSUPPORTED;
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return LDPCX_E_CUDA;
-    const int threads = (p.G * p.Z + 31) / 32 * 32;
+    const int threads = (p.G * p.Z * (layered ? 1 : flood_tpc(p.Z)) + 31) / 32 * 32;
     const int64_t grid = (B + p.G - 1) / p.G;
     fn<<<(unsigned)grid, threads, smem, s>>>(p);
     return cudaGetLastError() == cudaSuccess ? LDPCX_OK : LDPCX_E_CUDA;

@@ -94,7 +94,8 @@ def test_layered_minsum_bit_exact(lx, orc, name, prec, early_stop):
         assert oits.min() < 8  # some codewords stop early: the path is exercised
 
 
-@pytest.mark.parametrize("name", ["bg2_z8", "bg2_z64", "bg1_z128_r13"])
+# flooding runs four threads per check node up to Z = 128, two up to 256, one above
+@pytest.mark.parametrize("name", ["bg2_z8", "bg2_z64", "bg1_z128_r13", "bg2_z200", "bg1_z384"])
 @pytest.mark.parametrize("prec", [0, 1, 2])
 @pytest.mark.parametrize("weighted", [False, True])
 def test_flooding_minsum_bit_exact(lx, orc, name, prec, weighted):
@@ -119,7 +120,7 @@ def spa_close(gpu, ref, rel=1e-3):
     return np.abs(g - r) <= rel * np.maximum(np.abs(r), 1.0)
 
 
-@pytest.mark.parametrize("name", ["bg2_z8", "bg2_z64", "bg1_z384"])
+@pytest.mark.parametrize("name", ["bg2_z8", "bg2_z64", "bg2_z200", "bg1_z384"])
 @pytest.mark.parametrize("schedule", ["layered", "flooding"])
 def test_spa_fp32_within_tolerance(lx, orc, name, schedule):
     ocode, u, cw, L_tx = make_case(orc, name, 3.0, 29)
