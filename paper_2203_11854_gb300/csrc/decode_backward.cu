@@ -73,6 +73,19 @@ __device__ __forceinline__ float placed_llr(const BwdParams &p, int64_t cw, int 
     return fminf(fmaxf(x, -p.clamp), p.clamp);
 }
 
+// The values src[(b0 + j) Z] of this thread's edges j = q + TPC i of a row
+// (zero where it has none): loaded one row ahead of their use, so that the
+// global loads of the next row overlap the current row's arithmetic.
+template <int DPT, int TPC>
+__device__ __forceinline__ void row_values(const float *src, bool on, int b0, int deg, int q, int Z,
+                                           float (&out)[DPT]) {
+#pragma unroll
+    for (int i = 0; i < DPT; ++i) {
+        const int j = q + TPC * i;
+        out[i] = (on && TPC * i < deg && j < deg) ? src[(size_t)(b0 + j) * Z] : 0.0f;
+    }
+}
+
 // Sum over the TPC adjacent lanes of one check node (TPC a power of two <= 32).
 template <int TPC> __device__ __forceinline__ float group_sum(float x) {
 #pragma unroll
@@ -127,12 +140,22 @@ __global__ void __launch_bounds__(512, TPC == 4 ? 2 : 1) k_backward(const BwdPar
         __syncthreads();
         const float *ck = t >= 1 ? p.ckpt + (size_t)(t - 1) * p.tstride + (active ? cw : 0) * p.stride + z : nullptr;
         if (ck) {
+            float cn[DPT];
+            row_values<DPT, TPC>(ck, active, s_rp[0], s_rp[1] - s_rp[0], q, p.Z, cn);
             for (int r = 0; r < p.rows; ++r) {
-                if (active)
-                    for (int b = s_rp[r] + q; b < s_rp[r + 1]; b += TPC) {
-                        const int v = vn_of(s_vb[b], z, p.Z);
-                        s_app[off + v] = __fadd_rn(s_app[off + v], ck[(size_t)b * p.Z]);
+                const int b0 = s_rp[r], deg = s_rp[r + 1] - b0;
+                float cc[DPT];
+#pragma unroll
+                for (int i = 0; i < DPT; ++i) cc[i] = cn[i];
+                if (r + 1 < p.rows) row_values<DPT, TPC>(ck, active, s_rp[r + 1], s_rp[r + 2] - s_rp[r + 1], q, p.Z, cn);
+#pragma unroll
+                for (int i = 0; i < DPT; ++i) {
+                    const int j = q + TPC * i;
+                    if (TPC * i < deg && active && j < deg) {
+                        const int v = vn_of(s_vb[b0 + j], z, p.Z);
+                        s_app[off + v] = __fadd_rn(s_app[off + v], cc[i]);
                     }
+                }
                 __syncthreads();
             }
         }
@@ -147,8 +170,22 @@ __global__ void __launch_bounds__(512, TPC == 4 ? 2 : 1) k_backward(const BwdPar
         __syncthreads();
         const float *w_t = p.weights ? p.weights + (size_t)t * p.nnz : nullptr;
         const bool has_carry = t + 1 < p.iters;
+        float ckn[DPT], cyn[DPT];  // the next row's checkpointed messages and carries
+        row_values<DPT, TPC>(ck, active && ck, s_rp[0], s_rp[1] - s_rp[0], q, p.Z, ckn);
+        row_values<DPT, TPC>(carry, active && has_carry, s_rp[0], s_rp[1] - s_rp[0], q, p.Z, cyn);
         for (int r = 0; r < p.rows; ++r) {
             const int b0 = s_rp[r], deg = s_rp[r + 1] - b0;
+            float ckc[DPT], cyc[DPT];
+#pragma unroll
+            for (int i = 0; i < DPT; ++i) {
+                ckc[i] = ckn[i];
+                cyc[i] = cyn[i];
+            }
+            if (r + 1 < p.rows) {
+                const int b1 = s_rp[r + 1], d1 = s_rp[r + 2] - b1;
+                row_values<DPT, TPC>(ck, active && ck, b1, d1, q, p.Z, ckn);
+                row_values<DPT, TPC>(carry, active && has_carry, b1, d1, q, p.Z, cyn);
+            }
             float gw[DPT];
             float V[DPT], d[DPT], f[DPT], u[DPT];
             int vi[DPT];
@@ -161,10 +198,9 @@ __global__ void __launch_bounds__(512, TPC == 4 ? 2 : 1) k_backward(const BwdPar
                 const int j = q + TPC * i;
                 gw[i] = V[i] = d[i] = f[i] = u[i] = 0.0f;
                 vi[i] = 0;
-                if (active && j < deg) {
+                if (TPC * i < deg && active && j < deg) {  // the first test is warp-uniform
                     vi[i] = vn_of(s_vb[b0 + j], z, p.Z);
-                    const float cold = ck ? ck[(size_t)(b0 + j) * p.Z] : 0.0f;
-                    d[i] = __fsub_rn(s_app[off + vi[i]], cold);
+                    d[i] = __fsub_rn(s_app[off + vi[i]], ckc[i]);
                     V[i] = w_t ? __fmul_rn(w_t[b0 + j], d[i]) : d[i];
                     f[i] = dec::phi_fast(fminf(fmaxf(fabsf(V[i]), lo), hi));
                     par ^= V[i] < 0.0f ? 1u : 0u;
@@ -199,9 +235,9 @@ __global__ void __launch_bounds__(512, TPC == 4 ? 2 : 1) k_backward(const BwdPar
 #pragma unroll
             for (int i = 0; i < DPT; ++i) {
                 const int j = q + TPC * i;
-                if (active && j < deg) {
+                if (TPC * i < deg && active && j < deg) {  // the first test is warp-uniform
                     const float S = j == jmax ? s_rest : s_all - f[i];
-                    const float gC = gin[off + vi[i]] + (has_carry ? carry[(size_t)(b0 + j) * p.Z] : 0.0f);
+                    const float gC = gin[off + vi[i]] + cyc[i];
                     const float sg = (par ^ (V[i] < 0.0f ? 1u : 0u)) ? -1.0f : 1.0f;
                     u[i] = (S > lo && S < hi) ? gC * sg * dphi_fast(S) : 0.0f;
                     usum += u[i];
@@ -212,7 +248,7 @@ __global__ void __launch_bounds__(512, TPC == 4 ? 2 : 1) k_backward(const BwdPar
 #pragma unroll
             for (int i = 0; i < DPT; ++i) {
                 const int j = q + TPC * i;
-                if (active && j < deg) {
+                if (TPC * i < deg && active && j < deg) {  // the first test is warp-uniform
                     const float U = U_all - u[i];
                     const float a = fabsf(V[i]);
                     const bool inside = a >= lo && a <= hi;
