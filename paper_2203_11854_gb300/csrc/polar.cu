@@ -389,6 +389,91 @@ __global__ void __launch_bounds__(kPolarThreads) k_polar_scl(const PolarScl p) {
     }
 }
 
+// Successive cancellation (list of one) with one warp per codeword and
+// kScWarps codewords per CTA: the same node order, f / g arithmetic, partial
+// sums and path metric as k_polar_scl with L = 1 (so the same bits), but every
+// phase is a warp loop separated by __syncwarp, with no CTA barrier inside the
+// leaf loop. The channel LLRs are read from global memory where they are used
+// (the two halves of the root, at leaves 0 and N/2). Per warp in shared
+// memory: node LLRs [N-1] (node of size s at N - 2s), left-node partial sums
+// [N-1], combine buffer [N], decisions [N]; per CTA: frozen flags [N] and
+// information positions [K].
+constexpr int kScWarps = 4;
+__host__ __device__ inline size_t sc_warp_bytes(int N) {
+    return ((sizeof(float) * ((size_t)N - 1) + 3 * (size_t)N + 15) / 16) * 16;
+}
+__host__ __device__ inline size_t sc_smem(int N, int K) {
+    return kScWarps * sc_warp_bytes(N) + (((size_t)N + 15) / 16) * 16 + sizeof(int) * (size_t)K;
+}
+
+__global__ void __launch_bounds__(32 * kScWarps) k_polar_sc(const PolarScl p) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int N = p.N, n = p.n, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint8_t *fz = smem + kScWarps * sc_warp_bytes(N);
+    int *s_info = reinterpret_cast<int *>(fz + ((N + 15) / 16) * 16);
+    for (int j = threadIdx.x; j < N; j += blockDim.x) fz[j] = p.frozen[j];
+    for (int j = threadIdx.x; j < p.K; j += blockDim.x) s_info[j] = p.info[j];
+    __syncthreads();
+    const int64_t b = (int64_t)blockIdx.x * kScWarps + warp;
+    if (b >= p.B) return;  // a whole warp leaves; no CTA barrier follows
+    unsigned char *w = smem + warp * sc_warp_bytes(N);
+    const float *ch = p.llr + b * N;
+    float *a = reinterpret_cast<float *>(w);                   // [N-1]
+    uint8_t *beta = reinterpret_cast<uint8_t *>(a + (N - 1));  // [N-1]
+    uint8_t *t = beta + (N - 1);                               // [N]
+    uint8_t *u = t + N;                                        // [N]
+    float pm = 0.0f;  // equal in every lane
+    for (int i = 0; i < N; ++i) {
+        // LLRs of the nodes that start at leaf i, from the largest down to the leaf
+        const int llow = i == 0 ? n - 1 : min(__ffs(i) - 1, n - 1);
+        for (int ls = llow; ls >= 0; --ls) {
+            const int sz = 1 << ls;
+            const bool right = (i >> ls) & 1;
+            const float *P = (2 * sz == N) ? ch : a + (N - 4 * sz);  // parent, size 2s
+            for (int j = lane; j < sz; j += 32) {
+                const float x = (2 * sz == N) ? __ldg(P + j) : P[j], y = (2 * sz == N) ? __ldg(P + j + sz) : P[j + sz];
+                if (!right) a[N - 2 * sz + j] = f_min(x, y);
+                else a[N - 2 * sz + j] = beta[N - 2 * sz + j] ? y - x : y + x;
+            }
+            __syncwarp();
+        }
+        // decision at leaf i (every lane reads the same leaf LLR)
+        const float l = a[N - 2];
+        uint8_t ui;
+        if (fz[i]) {
+            ui = 0;
+            if (l < 0.0f) pm = pm + fabsf(l);
+        } else {
+            ui = l < 0.0f ? 1 : 0;  // a tie at 0 keeps bit 0
+        }
+        if (lane == 0) u[i] = ui;
+        // partial sums: leaf i closes the nodes whose last leaf it is
+        for (int ls = 0; ls < n; ++ls) {
+            const int sz = 1 << ls;
+            const bool right = (i >> ls) & 1;
+            uint8_t *bt = beta + N - 2 * sz;
+            for (int j = lane; j < sz; j += 32) {
+                const uint8_t v = (ls == 0) ? ui : t[j];
+                if (!right) {
+                    bt[j] = v;  // a completed left node: kept for its right sibling
+                } else {
+                    t[sz + j] = v;
+                    t[j] = v ^ bt[j];
+                }
+            }
+            __syncwarp();
+            if (!right) break;
+        }
+    }
+    if (p.pm_out && lane == 0) p.pm_out[b] = pm;
+    const int Kd = p.K - p.r, kw = (Kd + 31) >> 5;
+    for (int q0 = 0; q0 < kw; ++q0) {
+        const int q = 32 * q0 + lane;
+        const unsigned word = __ballot_sync(0xFFFFFFFFu, q < Kd && u[s_info[q]] != 0);
+        if (lane == 0) p.data[b * kw + q0] = word;
+    }
+}
+
 }  // namespace
 }  // namespace ldpcx
 
@@ -492,6 +577,16 @@ extern "C" int polar_scl_decode(ldpcx_polar_t c, const float *llr, int64_t B, in
     p.data = data_out;
     p.pm_out = pm_out;
     p.B = B;
+    if (L == 1) {
+        // a list of one: one warp per codeword
+        const size_t ssm = sc_smem(c->N, c->K);
+        if (ssm > 48 * 1024 &&
+            cudaFuncSetAttribute(k_polar_sc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm) != cudaSuccess)
+            return LDPCX_E_CUDA;
+        const int64_t grid = (B + kScWarps - 1) / kScWarps;
+        k_polar_sc<<<(unsigned)grid, 32 * kScWarps, ssm, (cudaStream_t)stream>>>(p);
+        return cuda_status(cudaGetLastError());
+    }
     if (cudaFuncSetAttribute(k_polar_scl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return LDPCX_E_CUDA;
     // small lists run mostly in warp 0: fewer threads per CTA leave room for more CTAs per SM
