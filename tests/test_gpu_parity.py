@@ -241,9 +241,10 @@ def test_sim_run_ber_matches_oracle_statistically(lx, orc):
     assert abs(g_err - o_err) <= 0.02 * max(g_err, o_err) + 20
 
 
-def test_full_size_launch_sampled(lx, orc):
-    """The bench launch: BG1-shaped Z=384, B=4096, layered min-sum, FP16 messages,
-    20 iterations; six sampled codewords against the oracle's FP32 replay."""
+@pytest.mark.parametrize("prec", [1, 0, 2])
+def test_full_size_launch_sampled(lx, orc, prec):
+    """The bench launch: BG1-shaped Z=384, B=4096, layered min-sum, 20 iterations, FP16 messages (the
+    headline) and the FP32 / 6-bit variants; six sampled codewords against the oracle's FP32 replay."""
     bg, Z, B = 1, 384, 4096
     ocode = orc.Code(bg, Z, punct_cols=2)
     code = lx.qc_ldpc_build(bg, Z, punct_cols=2)
@@ -255,10 +256,10 @@ def test_full_size_launch_sampled(lx, orc):
     cw[sample] = ocode.encoder.encode(u)
     L = inputs.gaussian_llrs(cw, 2.0, 10)
     L_tx = np.ascontiguousarray(L[:, ocode.p0:ocode.p0 + ocode.n_tx])
-    llr, bits, its = lx.ldpc_bp_decode(code, cuda(L_tx), algo=lx.LAYERED_MINSUM, iters=20, msg_prec=lx.MSG_F16,
+    llr, bits, its = lx.ldpc_bp_decode(code, cuda(L_tx), algo=lx.LAYERED_MINSUM, iters=20, msg_prec=prec,
                                        llr_out=True)
     app, hard, oits = orc.decode(ocode.graph, orc.place_llr(L_tx[sample], ocode.p0, ocode.n), algo=0, iters=20,
-                                 prec=1, store=1)
+                                 prec=1, store=prec)
     assert np.array_equal(llr[torch.from_numpy(sample).cuda()].cpu().numpy(), app.astype(np.float32))
     assert np.array_equal(unpack(bits.cpu().numpy()[sample], ocode.k), hard[:, :ocode.k])
     assert (its.cpu().numpy() == 20).all()
