@@ -555,8 +555,13 @@ int polar_scl_decode(ldpcx_polar_t code, const float *llr, int64_t B, int L, uin
  * r = k/n_tx. A point ends after max_batches batches or once it has
  * min_bit_errors bit errors (checked between batches when > 0); the sweep
  * ends early after a point whose BER is below stop_ber (> 0). With
- * use_graph, one batch is captured once as a CUDA graph and replayed.
- * The sweep synchronises `stream` first and then runs on a private stream of
+ * use_graph, a batch runs as two captured CUDA graphs, a front (transmitter,
+ * demapper) and a back (decoder, count), over two buffer sets: the next
+ * batch's front runs on a lower-priority stream while the current batch
+ * decodes (a front started for a batch that does not follow -- after an
+ * early end of a point or of the sweep -- is discarded); the counts equal
+ * those of eager mode (use_graph = 0: one stream, launch by launch).
+ * The sweep synchronises `stream` first and then runs on private streams of
  * its own; it returns after all its work has finished. */
 typedef struct {
     ldpcx_code_t code;
@@ -579,7 +584,8 @@ typedef struct {
     int64_t bits, bit_errors, blocks, block_errors, iter_sum;
 } ldpcx_sim_counts;
 
-/* Workspace bytes sim_run needs for cfg (batch buffers + decoder messages). */
+/* Workspace bytes sim_run needs for cfg (two sets of batch buffers + decoder
+ * messages). */
 int sim_workspace(const ldpcx_sim_config *cfg, size_t *ws_bytes);
 /* Run the sweep. out: host [n_snr] counts (points not run are zero);
  * *points_run = points executed. Synchronises `stream` once per batch check

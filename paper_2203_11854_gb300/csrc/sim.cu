@@ -1,8 +1,20 @@
 // Monte-Carlo BER/BLER sweep (the loop around the paper's Listing 1): for each
 // Eb/N0 point, batches of codewords run transmitter -> demapper -> decoder ->
-// error count on the device. The codeword index lives in device memory and is
-// advanced by a kernel at the end of each batch, so one captured CUDA graph of
-// a batch replays for every batch of every point.
+// error count on the device.
+//
+// Each batch's N0 and first codeword index are written by the host into the
+// device copy its transmitter reads. Eager mode runs the four launches of a
+// batch one after another on one stream. Graph mode splits a batch into a front (transmitter + demapper into one of
+// two buffer sets, with that set's N0 and first codeword index written by the
+// host) and a back (decoder + error count from that set), captured once per
+// set as four CUDA graphs. The front of the next batch runs on a second,
+// lower-priority stream while the current batch decodes, so it fills the SM
+// slots the decoder's last wave leaves idle. The next batch is guessed before
+// the host has read the current counts (the same point, or the next point after
+// its last batch); a wrong guess (a point ended by min_bit_errors or a sweep
+// ended by stop_ber) discards that front and runs the right one. Codeword
+// indices follow the batches actually counted, so both modes give the same
+// counts.
 #include <math.h>
 
 #include <vector>
@@ -12,7 +24,8 @@
 namespace {
 
 struct SimLayout {
-    size_t y, llr, ref, hat, iters, no, cw0, acc, dec, total;
+    size_t y[2], llr[2], ref[2], no[2], cw0[2];
+    size_t hat, iters, acc, dec, total;
     int64_t S, kw;
     size_t dec_bytes;
 };
@@ -43,34 +56,79 @@ int layout(const ldpcx_sim_config *c, SimLayout *L) {
         return at;
     };
     L->dec = take(dec);
-    L->y = take(sizeof(float) * (size_t)B * L->S * (c->m == 1 ? 1 : 2));
-    L->llr = take(sizeof(float) * (size_t)B * code->n_tx);
-    L->ref = take(sizeof(uint32_t) * (size_t)B * L->kw);
+    for (int s = 0; s < 2; ++s) {
+        L->y[s] = take(sizeof(float) * (size_t)B * L->S * (c->m == 1 ? 1 : 2));
+        L->llr[s] = take(sizeof(float) * (size_t)B * code->n_tx);
+        L->ref[s] = take(sizeof(uint32_t) * (size_t)B * L->kw);
+        L->no[s] = take(sizeof(float));
+        L->cw0[s] = take(sizeof(uint64_t));
+    }
     L->hat = take(sizeof(uint32_t) * (size_t)B * L->kw);
     L->iters = take(sizeof(int32_t) * (size_t)B);
-    L->no = take(sizeof(float));
-    L->cw0 = take(sizeof(uint64_t));
     L->acc = take(sizeof(int64_t) * 5);
     L->dec_bytes = dec;
     L->total = off;
     return LDPCX_OK;
 }
 
-// One batch: transmitter, demapper, decoder, counter, advance of the codeword index.
-int run_batch(const ldpcx_sim_config *c, const SimLayout &L, char *ws, cudaStream_t s) {
-    const ldpcx_code *code = c->code;
-    const int64_t B = c->batch;
-    float *y = (float *)(ws + L.y), *llr = (float *)(ws + L.llr), *no = (float *)(ws + L.no);
-    uint32_t *ref = (uint32_t *)(ws + L.ref), *hat = (uint32_t *)(ws + L.hat);
+// Front of a batch into buffer set s: transmitter (codewords from the set's
+// device index) and demapper.
+int run_front(const ldpcx_sim_config *c, const SimLayout &L, char *ws, int s, cudaStream_t st) {
+    float *y = (float *)(ws + L.y[s]), *llr = (float *)(ws + L.llr[s]), *no = (float *)(ws + L.no[s]);
+    uint32_t *ref = (uint32_t *)(ws + L.ref[s]);
+    const uint64_t *cw0 = (const uint64_t *)(ws + L.cw0[s]);
+    int r = ldpcx::launch_tx(c->code, c->seed, 0, cw0, c->batch, c->m, no, 0, y, ref, st);
+    if (!r) r = demap_app(y, no, 0, c->batch, L.S, c->m, c->demap_method, c->demap_clamp, llr, st);
+    return r;
+}
+
+// Back of a batch from buffer set s: decoder and error count into the point's counters.
+int run_back(const ldpcx_sim_config *c, const SimLayout &L, char *ws, int s, cudaStream_t st) {
+    float *llr = (float *)(ws + L.llr[s]);
+    uint32_t *ref = (uint32_t *)(ws + L.ref[s]), *hat = (uint32_t *)(ws + L.hat);
     int32_t *iters = (int32_t *)(ws + L.iters);
-    uint64_t *cw0 = (uint64_t *)(ws + L.cw0);
-    int64_t *acc = (int64_t *)(ws + L.acc);
-    int st = ldpcx::launch_tx(c->code, c->seed, 0, cw0, B, c->m, no, 0, y, ref, s);
-    if (!st) st = demap_app(y, no, 0, B, L.S, c->m, c->demap_method, c->demap_clamp, llr, s);
-    if (!st) st = ldpc_bp_decode(c->code, llr, B, &c->dec, nullptr, hat, iters, ws + L.dec, L.dec_bytes, s);
-    if (!st) st = sim_count(ref, hat, iters, B, code->k, acc, s);
-    if (!st) st = ldpcx::launch_advance(cw0, (uint64_t)B, s);
-    return st;
+    int r = ldpc_bp_decode(c->code, llr, c->batch, &c->dec, nullptr, hat, iters, ws + L.dec, L.dec_bytes, st);
+    if (!r) r = sim_count(ref, hat, iters, c->batch, c->code->k, (int64_t *)(ws + L.acc), st);
+    return r;
+}
+
+float n0_of(const ldpcx_sim_config *c, int point) {
+    const double r = (double)c->code->k / (double)c->code->n_tx;
+    return (float)(1.0 / (r * (double)c->m * pow(10.0, c->ebn0_db[point] / 10.0)));
+}
+
+// Owner of the streams, events and graphs of one sweep.
+struct Runtime {
+    cudaStream_t back = nullptr, front = nullptr;
+    cudaEvent_t fdone[2] = {nullptr, nullptr}, bdone[2] = {nullptr, nullptr};
+    cudaGraphExec_t fexec[2] = {nullptr, nullptr}, bexec[2] = {nullptr, nullptr};
+    ~Runtime() {
+        if (back) cudaStreamSynchronize(back);  // nothing of the sweep is left in flight
+        if (front) cudaStreamSynchronize(front);
+        for (int s = 0; s < 2; ++s) {
+            if (fexec[s]) cudaGraphExecDestroy(fexec[s]);
+            if (bexec[s]) cudaGraphExecDestroy(bexec[s]);
+            if (fdone[s]) cudaEventDestroy(fdone[s]);
+            if (bdone[s]) cudaEventDestroy(bdone[s]);
+        }
+        if (back) cudaStreamDestroy(back);
+        if (front) cudaStreamDestroy(front);
+    }
+};
+
+// Capture fn(s, stream) into an executable graph.
+template <typename F> int capture(cudaStream_t st, cudaGraphExec_t *exec, F fn) {
+    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed) != cudaSuccess) return LDPCX_E_CUDA;
+    const int cs = fn();
+    cudaGraph_t g = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(st, &g);
+    if (cs || ce != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return cs ? cs : LDPCX_E_CUDA;
+    }
+    const cudaError_t ie = cudaGraphInstantiate(exec, g, 0);
+    cudaGraphDestroy(g);
+    return ie == cudaSuccess ? LDPCX_OK : LDPCX_E_CUDA;
 }
 
 }  // namespace
@@ -91,60 +149,112 @@ extern "C" int sim_run(const ldpcx_sim_config *c, ldpcx_sim_counts *out, int *po
     if (st) return st;
     if (!out) return LDPCX_E_INVAL;
     if (!ws_v || ws_bytes < L.total || ((uintptr_t)ws_v & 255u)) return LDPCX_E_WORKSPACE;
-    // Work runs on a private non-blocking stream (the legacy NULL stream cannot
+    // Work runs on private non-blocking streams (the legacy NULL stream cannot
     // be captured into a graph), ordered after the caller's stream.
-    cudaStream_t caller = (cudaStream_t)stream, s = nullptr;
-    if (cudaStreamSynchronize(caller) != cudaSuccess) return LDPCX_E_CUDA;
-    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return LDPCX_E_CUDA;
+    if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return LDPCX_E_CUDA;
+    Runtime rt;
+    int lo = 0, hi = 0;
+    cudaDeviceGetStreamPriorityRange(&lo, &hi);  // hi: the numerically smallest, highest priority
+    if (cudaStreamCreateWithPriority(&rt.back, cudaStreamNonBlocking, hi) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&rt.front, cudaStreamNonBlocking, lo) != cudaSuccess)
+        return LDPCX_E_CUDA;
+    for (int s = 0; s < 2; ++s)
+        if (cudaEventCreateWithFlags(&rt.fdone[s], cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&rt.bdone[s], cudaEventDisableTiming) != cudaSuccess)
+            return LDPCX_E_CUDA;
     char *ws = (char *)ws_v;
     ldpcx::DevCode d;
     st = ldpcx::code_device(c->code, &d);  // upload tables before any capture
-    if (st) {
-        cudaStreamDestroy(s);
-        return st;
-    }
+    if (st) return st;
     for (int i = 0; i < c->n_snr; ++i) out[i] = ldpcx_sim_counts{0, 0, 0, 0, 0};
     if (points_run) *points_run = 0;
+    const bool graph = c->use_graph != 0;
+    const int64_t B = c->batch;
 
-    uint64_t cw_start = c->cw0;
-    if (cudaMemcpyAsync(ws + L.cw0, &cw_start, sizeof(cw_start), cudaMemcpyHostToDevice, s) != cudaSuccess) {
-        cudaStreamDestroy(s);
-        return LDPCX_E_CUDA;
-    }
-
-    cudaGraphExec_t exec = nullptr;
-    cudaGraph_t graph = nullptr;
-    const double r = (double)c->code->k / (double)c->code->n_tx;
+    // Launch the front of batch (point, index cw) into set s: N0 and the first
+    // codeword index are written on the front stream, after the set's last back.
+    std::vector<float> n0_host(2);
+    std::vector<uint64_t> cw_host(2);
+    auto front = [&](int s, int point, uint64_t cw) -> int {
+        cudaStream_t fs = graph ? rt.front : rt.back;
+        n0_host[s] = n0_of(c, point);
+        cw_host[s] = cw;
+        if (graph && cudaStreamWaitEvent(fs, rt.bdone[s], 0) != cudaSuccess) return LDPCX_E_CUDA;
+        if (cudaMemcpyAsync(ws + L.no[s], &n0_host[s], sizeof(float), cudaMemcpyHostToDevice, fs) != cudaSuccess ||
+            cudaMemcpyAsync(ws + L.cw0[s], &cw_host[s], sizeof(uint64_t), cudaMemcpyHostToDevice, fs) != cudaSuccess)
+            return LDPCX_E_CUDA;
+        int r;
+        if (graph) {
+            if (!rt.fexec[s]) {
+                if (cudaStreamSynchronize(fs) != cudaSuccess) return LDPCX_E_CUDA;
+                r = capture(fs, &rt.fexec[s], [&] { return run_front(c, L, ws, s, fs); });
+                if (r) return r;
+            }
+            r = cudaGraphLaunch(rt.fexec[s], fs) == cudaSuccess ? LDPCX_OK : LDPCX_E_CUDA;
+        } else {
+            r = run_front(c, L, ws, s, fs);
+        }
+        if (!r && cudaEventRecord(rt.fdone[s], fs) != cudaSuccess) r = LDPCX_E_CUDA;
+        return r;
+    };
+    auto back = [&](int s) -> int {
+        if (graph && cudaStreamWaitEvent(rt.back, rt.fdone[s], 0) != cudaSuccess) return LDPCX_E_CUDA;
+        int r;
+        if (graph) {
+            if (!rt.bexec[s]) {
+                if (cudaStreamSynchronize(rt.back) != cudaSuccess) return LDPCX_E_CUDA;
+                r = capture(rt.back, &rt.bexec[s], [&] { return run_back(c, L, ws, s, rt.back); });
+                if (r) return r;
+            }
+            r = cudaGraphLaunch(rt.bexec[s], rt.back) == cudaSuccess ? LDPCX_OK : LDPCX_E_CUDA;
+        } else {
+            r = run_back(c, L, ws, s, rt.back);
+        }
+        if (!r && cudaEventRecord(rt.bdone[s], rt.back) != cudaSuccess) r = LDPCX_E_CUDA;
+        return r;
+    };
+    // Pending front: the set it fills and the batch it holds (point, index in point).
+    struct Pending {
+        bool on = false;
+        int set = 0, point = 0;
+        int64_t b = 0;
+    } pend;
+    uint64_t cw_next = c->cw0;  // index of the next batch's first codeword
+    int set = 0;
     int result = LDPCX_OK;
     for (int i = 0; i < c->n_snr && result == LDPCX_OK; ++i) {
-        const float n0 = (float)(1.0 / (r * (double)c->m * pow(10.0, c->ebn0_db[i] / 10.0)));
-        if (cudaMemcpyAsync(ws + L.no, &n0, sizeof(n0), cudaMemcpyHostToDevice, s) != cudaSuccess ||
-            cudaMemsetAsync(ws + L.acc, 0, sizeof(int64_t) * 5, s) != cudaSuccess) {
+        if (cudaMemsetAsync(ws + L.acc, 0, sizeof(int64_t) * 5, rt.back) != cudaSuccess) {
             result = LDPCX_E_CUDA;
             break;
         }
         int64_t counts[5] = {0, 0, 0, 0, 0};
         for (int64_t b = 0; b < c->max_batches; ++b) {
-            if (c->use_graph) {
-                if (!exec) {
-                    if (cudaStreamSynchronize(s) != cudaSuccess) { result = LDPCX_E_CUDA; break; }
-                    if (cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
-                        result = LDPCX_E_CUDA;
-                        break;
-                    }
-                    int cs = run_batch(c, L, ws, s);
-                    cudaError_t ce = cudaStreamEndCapture(s, &graph);
-                    if (cs || ce != cudaSuccess) { result = cs ? cs : LDPCX_E_CUDA; break; }
-                    if (cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) { result = LDPCX_E_CUDA; break; }
-                }
-                if (cudaGraphLaunch(exec, s) != cudaSuccess) { result = LDPCX_E_CUDA; break; }
-            } else {
-                result = run_batch(c, L, ws, s);
+            // the front of this batch: pending if the guess was right, else launched now
+            if (!(pend.on && pend.point == i && pend.b == b)) {
+                set = pend.on ? 1 - pend.set : set;  // a wrong guess leaves its set to finish in the background
+                result = front(set, i, cw_next);
                 if (result) break;
+            } else {
+                set = pend.set;
+            }
+            pend.on = false;
+            cw_next += (uint64_t)B;
+            result = back(set);
+            if (result) break;
+            // guess the next batch and start its front into the other set while this one decodes (submitted
+            // after the back, so the decoder's CTAs are dispatched first)
+            if (graph) {
+                const bool more = b + 1 < c->max_batches;
+                if (more || i + 1 < c->n_snr) {
+                    pend = Pending{true, 1 - set, more ? i : i + 1, more ? b + 1 : 0};
+                    result = front(pend.set, pend.point, cw_next);
+                    if (result) break;
+                }
             }
             if (c->min_bit_errors > 0) {
-                if (cudaMemcpyAsync(counts, ws + L.acc, sizeof(counts), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-                    cudaStreamSynchronize(s) != cudaSuccess) {
+                if (cudaMemcpyAsync(counts, ws + L.acc, sizeof(counts), cudaMemcpyDeviceToHost, rt.back) !=
+                        cudaSuccess ||
+                    cudaStreamSynchronize(rt.back) != cudaSuccess) {
                     result = LDPCX_E_CUDA;
                     break;
                 }
@@ -152,8 +262,8 @@ extern "C" int sim_run(const ldpcx_sim_config *c, ldpcx_sim_counts *out, int *po
             }
         }
         if (result) break;
-        if (cudaMemcpyAsync(counts, ws + L.acc, sizeof(counts), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-            cudaStreamSynchronize(s) != cudaSuccess) {
+        if (cudaMemcpyAsync(counts, ws + L.acc, sizeof(counts), cudaMemcpyDeviceToHost, rt.back) != cudaSuccess ||
+            cudaStreamSynchronize(rt.back) != cudaSuccess) {
             result = LDPCX_E_CUDA;
             break;
         }
@@ -161,9 +271,7 @@ extern "C" int sim_run(const ldpcx_sim_config *c, ldpcx_sim_counts *out, int *po
         if (points_run) *points_run = i + 1;
         if (c->stop_ber > 0.0 && counts[0] > 0 && (double)counts[1] / (double)counts[0] < c->stop_ber) break;
     }
-    if (exec) cudaGraphExecDestroy(exec);
-    if (graph) cudaGraphDestroy(graph);
-    if (cudaStreamSynchronize(s) != cudaSuccess && result == LDPCX_OK) result = LDPCX_E_CUDA;
-    cudaStreamDestroy(s);
+    if (cudaStreamSynchronize(rt.front) != cudaSuccess && result == LDPCX_OK) result = LDPCX_E_CUDA;
+    if (cudaStreamSynchronize(rt.back) != cudaSuccess && result == LDPCX_OK) result = LDPCX_E_CUDA;
     return result;
 }

@@ -226,6 +226,21 @@ def test_sim_run_equals_stepwise_chain(lx):
         assert [res_g[i][f] for f in ("bits", "bit_errors", "blocks", "block_errors", "iter_sum")] == c
 
 
+@pytest.mark.parametrize("kw", [dict(max_batches=4, min_bit_errors=300), dict(max_batches=2, stop_ber=2e-2),
+                                dict(max_batches=3, min_bit_errors=50, stop_ber=1e-1)])
+def test_sim_run_graph_equals_eager_with_early_ends(lx, kw):
+    # graph mode starts the next batch's front before the host reads the counts; a point ended by its
+    # error count or a sweep ended by stop_ber discards that front, so the counts must still match eager mode
+    code = lx.qc_ldpc_build(2, 32)
+    base = dict(m=4, demap_method=lx.DEMAP_MAXLOG, algo=lx.LAYERED_MINSUM, iters=8, msg_prec=lx.MSG_F16,
+                seed=17, cw0=5, batch=200)
+    ebn0 = [0.0, 1.0, 2.0, 3.0, 4.0]
+    res_g = lx.sim_run(code, ebn0, use_graph=True, **base, **kw)
+    res_e = lx.sim_run(code, ebn0, use_graph=False, **base, **kw)
+    assert res_g == res_e
+    assert sum(p["blocks"] for p in res_g) > 0
+
+
 def test_sim_run_ber_matches_oracle_statistically(lx, orc):
     code = lx.qc_ldpc_build(2, 8)
     ocode = orc.Code(2, 8)
