@@ -19,7 +19,7 @@ struct TxParams {
     int m;
     float scale;         // 1/sqrt(2(4^h-1)/3): unit average symbol energy
     uint64_t seed, cw0;
-    const uint64_t *cw0_dev;  // when set, *cw0_dev is added to cw0 (graph replays)
+    const uint64_t *cw0_dev;  // when set, *cw0_dev is added to cw0 (graph replays: the host writes it per batch)
     const float *no;
     int64_t no_stride;
     float *y;            // [B][S][2] or [B][S]
@@ -698,7 +698,6 @@ __global__ void __launch_bounds__(256) k_count(const uint32_t *__restrict__ ref,
     }
 }
 
-__global__ void k_advance(uint64_t *cw0_dev, uint64_t inc) { *cw0_dev += inc; }
 
 bool valid_m(int m) { return m == 1 || m == 2 || m == 4 || m == 6 || m == 8; }
 
@@ -770,10 +769,6 @@ int launch_tx(ldpcx_code_t c, uint64_t seed, uint64_t cw0, const uint64_t *cw0_d
     return cuda_status(cudaGetLastError());
 }
 
-int launch_advance(uint64_t *cw0_dev, uint64_t inc, cudaStream_t stream) {
-    k_advance<<<1, 1, 0, stream>>>(cw0_dev, inc);
-    return cuda_status(cudaGetLastError());
-}
 
 }  // namespace ldpcx
 

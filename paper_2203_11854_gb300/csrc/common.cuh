@@ -69,8 +69,6 @@ unsigned int take_status_channel(cudaStream_t s);
 int launch_tx(ldpcx_code_t c, uint64_t seed, uint64_t cw0, const uint64_t *cw0_dev, int64_t B, int m,
               const float *no, int64_t no_stride, float *y_out, uint32_t *info_out, cudaStream_t stream,
               uint32_t *cw_out = nullptr, const float *points = nullptr);
-// *cw0_dev += inc on the device.
-int launch_advance(uint64_t *cw0_dev, uint64_t inc, cudaStream_t stream);
 
 // Per-device cached attribute: SM count.
 int sm_count();
