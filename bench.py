@@ -152,6 +152,22 @@ def profile_traffic():
         return None, digest
 
 
+def host_cpu():
+    """Architecture and, where the kernel reports one, the model name of the host CPU."""
+    import platform
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu model", "hardware"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return f"{platform.machine()}" + (f", {model}" if model else "")
+
+
 def cpu_baseline(seconds=12.0, ebn0=EBN0):
     """The oracle as it stands (FP64, layered min-sum with the FP16 message store), whole chain, on all
     host cores, for a bounded sample of codewords of the same workload."""
@@ -169,6 +185,7 @@ def cpu_baseline(seconds=12.0, ebn0=EBN0):
         done += chunk
     k = code.k
     return {"value": done * k / t_total / 1e9, "unit": "Gbit/s", "cores": cores, "kind": "oracle",
+            "cpu": host_cpu(),
             "sample": f"{done} codewords of the workload (FP64 oracle chain: source, GF(2) encoder, mapper, AWGN, "
                       f"max-log demapper, layered min-sum with FP16 message store, 20 iterations), {t_total:.1f} s",
             "codewords_per_s": done / t_total}
@@ -206,7 +223,7 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": workload_config(),
-            "cpu_baseline": {"value": value, "unit": "Gbit/s", "cores": cores, "kind": "oracle",
+            "cpu_baseline": {"value": value, "unit": "Gbit/s", "cores": cores, "kind": "oracle", "cpu": host_cpu(),
                              "sample": f"{per_step} codewords per step of the workload through the FP64 oracle chain"},
             "e2e": {"value": value, "unit": "Gbit/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
