@@ -40,13 +40,16 @@ __device__ __forceinline__ int pam_level(const uint8_t *c, int h) {
 
 
 // Shared-memory layout of k_tx, per CTA: [G][ns] codeword bytes (ns = n rounded
-// up to 4), [G][4 nq] packed source words, then the block table and row
-// pointers of the code.
+// up to 4), [G][4 nq] packed source words, then (8-byte aligned) the block
+// table as {col Z + shift, Z - shift} pairs, the row pointers and the packed
+// lambda words of the general core.
 __host__ __device__ inline int tx_ns(int n) { return (n + 3) & ~3; }
-__host__ __device__ inline size_t tx_smem(int G, int n, int k, int nnz, int rows, int inv_words) {
+__host__ __device__ inline size_t tx_enc_off(int G, int n, int k) {
     const int nq = (((k + 31) >> 5) + 3) >> 2;
-    return (size_t)G * tx_ns(n) + (size_t)G * 16 * nq + 4 * (size_t)nnz + 4 * (size_t)(rows + 1) +
-           4 * (size_t)G * inv_words;
+    return ((size_t)G * tx_ns(n) + (size_t)G * 16 * nq + 7) & ~(size_t)7;
+}
+__host__ __device__ inline size_t tx_smem(int G, int n, int k, int nnz, int rows, int inv_words) {
+    return tx_enc_off(G, n, k) + 8 * (size_t)nnz + 4 * (size_t)(rows + 1) + 4 * (size_t)G * inv_words;
 }
 
 __global__ void __launch_bounds__(kMaxThreads) k_tx(const TxParams p) {
@@ -56,13 +59,17 @@ __global__ void __launch_bounds__(kMaxThreads) k_tx(const TxParams p) {
     const int nq = (kw + 3) >> 2;  // Philox blocks of source bits per codeword
     uint8_t *s_c = smem;           // [G][ns] codeword bits, one byte each
     uint32_t *s_w = reinterpret_cast<uint32_t *>(smem + (size_t)p.G * ns);  // [G][4 nq] source words
-    uint32_t *s_blk = s_w + (size_t)p.G * 4 * nq;
-    int32_t *s_rp = reinterpret_cast<int32_t *>(s_blk + p.nnz);
+    int2 *s_enc = reinterpret_cast<int2 *>(smem + tx_enc_off(p.G, p.n, p.k));  // [nnz] {col Z + s, Z - s}
+    int32_t *s_rp = reinterpret_cast<int32_t *>(s_enc + p.nnz);
     uint32_t *s_lam = reinterpret_cast<uint32_t *>(s_rp + p.rows + 1);  // [G][inv_words] packed lambda
     const int64_t cw_base = (int64_t)blockIdx.x * p.G;
     const uint64_t cw0 = p.cw0 + (p.cw0_dev ? *p.cw0_dev : 0ull);
 
-    for (int i = threadIdx.x; i < p.nnz; i += blockDim.x) s_blk[i] = p.blk[i];
+    for (int i = threadIdx.x; i < p.nnz; i += blockDim.x) {
+        const uint32_t bb = p.blk[i];
+        const int sh = (int)(bb & 0xFFFFu);
+        s_enc[i] = make_int2((int)(bb >> 16) * p.Z + sh, p.Z - sh);
+    }
     for (int i = threadIdx.x; i <= p.rows; i += blockDim.x) s_rp[i] = p.row_ptr[i];
     for (int i = threadIdx.x; i < p.G * p.inv_words; i += blockDim.x) s_lam[i] = 0u;
     // a2: source bits (Philox stream 0), written packed to the output and to shared memory
@@ -101,20 +108,23 @@ __global__ void __launch_bounds__(kMaxThreads) k_tx(const TxParams p) {
     const bool active = g < p.G && cw_base + g < p.B;
     uint8_t *c = s_c + (size_t)(active ? g : 0) * ns;
     const int Z = p.Z;
-    auto at = [&](uint32_t b) -> uint8_t {
-        const int col = (int)(b >> 16);
-        int zz = z + (int)(b & 0xFFFFu);
-        zz -= (zz >= Z) ? Z : 0;
-        return c[col * Z + zz];
+    // bit of check z in block e: codeword position col Z + (z + s) mod Z; blocks of columns below
+    // `lim` Z are those with e.x < lim Z (s < Z)
+    auto at = [&](const int2 e) -> uint8_t {
+        int v = e.x + z;
+        if (z >= e.y) v -= Z;
+        return c[v];
     };
     uint8_t lam[4] = {0, 0, 0, 0};
     if (active) {
         // lambda_r = sum over the systematic blocks of core row r
+        const int kbZ = p.kb * Z;
         for (int r = 0; r < 4; ++r) {
             uint8_t acc = 0;
+#pragma unroll 4
             for (int b = s_rp[r]; b < s_rp[r + 1]; ++b) {
-                const uint32_t bb = s_blk[b];
-                if ((int)(bb >> 16) < p.kb) acc ^= at(bb);
+                const int2 e = s_enc[b];
+                if (e.x < kbZ) acc ^= at(e);
             }
             lam[r] = acc;
         }
@@ -153,17 +163,18 @@ __global__ void __launch_bounds__(kMaxThreads) k_tx(const TxParams p) {
         // extension rows only read columns < kb + 4, so they are independent
         for (int r = 4; r < p.rows; ++r) {
             uint8_t acc = 0;
-            const int own = p.kb + r;
-            int s_own = 0;
+            const int ownZ = (p.kb + r) * Z;  // the row's own parity column; every other block lies below it
+            int2 eo = make_int2(ownZ, Z);
+#pragma unroll 4
             for (int b = s_rp[r]; b < s_rp[r + 1]; ++b) {
-                const uint32_t bb = s_blk[b];
-                if ((int)(bb >> 16) != own) acc ^= at(bb);
-                else s_own = (int)(bb & 0xFFFFu);
+                const int2 e = s_enc[b];
+                if (e.x < ownZ) acc ^= at(e);
+                else eo = e;
             }
             // check z holds own-column bit (z + s_own) mod Z
-            int zz = z + s_own;
-            zz -= (zz >= Z) ? Z : 0;
-            c[own * Z + zz] = acc;
+            int v = eo.x + z;
+            if (z >= eo.y) v -= Z;
+            c[v] = acc;
         }
     }
     __syncthreads();
