@@ -463,7 +463,7 @@ def measure_sweep(lx, code, pk):
 
 
 def measure_grad_step(lx):
-    """Config 4's training step: weighted flooding sum-product, BG2-shaped Z=64, batch 2048, 10 iterations,
+    """The weighted-BP training step: weighted flooding sum-product, BG2-shaped Z=64, batch 2048, 10 iterations,
     forward with checkpoints plus the hand-written adjoint (ldpc_bp_decode_ckpt + ldpc_bp_backward)."""
     import torch
     from paper_2203_11854_gb300.autograd import LdpcBP
@@ -495,7 +495,7 @@ def measure_grad_step(lx):
 
 
 def measure_polar(lx):
-    """CRC-aided SCL of polar codes (next row): N = 1024, K = 512 (504 data bits + CRC-8 0x107), list 8
+    """CRC-aided SCL of polar codes: N = 1024, K = 512 (504 data bits + CRC-8 0x107), list 8
     and SC, 16384 codewords at Eb/N0 = 2 dB (BPSK, AWGN)."""
     import torch
     code = lx.polar_build(10, 512, 1.0, 0x107, 8)

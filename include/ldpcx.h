@@ -60,7 +60,7 @@ const char *ldpcx_status_str(int status);
  * otherwise. flags may be NULL. */
 int ldpcx_sync_status(void *stream, unsigned int *flags);
 
-/* ------------------------------------------------------------ code (a1) */
+/* ------------------------------------------------------------ code */
 /* A seeded quasi-cyclic LDPC code with the 5G-NR base-graph shape (the
  * paper's "5G LDPC codes", Sec. III-B; LDPC5GEncoder in Listing 1). The 3GPP
  * TS 38.212 shift tables are not used: the base matrix S (rows x cols, -1 =
@@ -167,7 +167,7 @@ int qc_alist_parse(const char *text, size_t len, int Z, int16_t *S_out, int capa
  * query. Errors: LDPCX_E_INVAL for a null code or len_out, or cap <= len. */
 int qc_ldpc_alist(ldpcx_code_t code, char *buf, size_t cap, size_t *len_out);
 
-/* ------------------------------------------------ transmitter (a2 .. a5) */
+/* ------------------------------------------------ transmitter */
 /* Monte-Carlo transmitter for codewords cw0 .. cw0+B-1 (BinarySource,
  * LDPC5GEncoder, Mapper, AWGN of Listing 1), all on the device:
  *  - info bit j of codeword w = bit (j mod 32) of output word (j mod 128)/32
@@ -193,7 +193,7 @@ int qc_ldpc_alist(ldpcx_code_t code, char *buf, size_t cap, size_t *len_out);
 int sim_tx(ldpcx_code_t code, uint64_t seed, uint64_t cw0, int64_t B, int m,
            const float *no, int64_t no_stride, float *y_out, uint32_t *info_out, void *stream);
 
-/* ----------------------------------------------------------- demap (a6) */
+/* ----------------------------------------------------------- demap */
 /* APP demapper (Demapper("app"), Listing 1) for Gray square QAM on AWGN:
  *   L_i = ln sum_{x: b_i(x)=0} exp(-|y-x|^2/N0) - ln sum_{x: b_i(x)=1} exp(...)
  * computed per I/Q dimension (exact for Gray square QAM on a circular AWGN
@@ -209,7 +209,7 @@ int sim_tx(ldpcx_code_t code, uint64_t seed, uint64_t cw0, int64_t B, int m,
 int demap_app(const float *y, const float *no, int64_t no_stride, int64_t B, int64_t syms_per_cw,
               int m, int method, float clamp, float *llr_out, void *stream);
 
-/* ------------------------------------------------ BP decoding (a7 .. a10) */
+/* ------------------------------------------------ BP decoding */
 /* Belief-propagation decoding (LDPC5GDecoder, "BP decoder and variants",
  * Sec. III-B; min-sum BP as the custom CUDA op of Sec. IV-A). Messages
  * R = check-to-variable; for the variable-to-check inputs T_i of a check:
@@ -340,7 +340,7 @@ int ldpcx_tune_get(int key, int *value);
 int ldpc_bp_decode_noalloc(ldpcx_code_t code, const float *llr_ch, int64_t B, const ldpcx_decode_opts *opts,
                            float *llr_out, uint32_t *bits_out, int32_t *iters_out, void *stream);
 
-/* -------------------------------------------- mixed-size batch (a12) */
+/* -------------------------------------------- mixed-size batch */
 /* One persistent launch decodes a batch mixing codes of different lifting
  * sizes, base-graph shapes and rates -- the per-example differing execution
  * the paper names as the reason for custom CUDA ops (Sec. III-D, Sec. IV-A).
@@ -368,7 +368,7 @@ int ldpc_bp_mixed_workspace(const ldpcx_batch_group *groups, int n_groups, const
 int ldpc_bp_decode_mixed(const ldpcx_batch_group *groups, int n_groups, const ldpcx_decode_opts *opts, void *ws,
                          size_t ws_bytes, void *stream);
 
-/* ------------------------------------------- differentiable BP (a11) */
+/* ------------------------------------------- differentiable BP */
 /* Gradients through the unrolled decoder ("gradients can be specified" for a
  * custom op, Sec. IV-A; end-to-end learning with a binary cross-entropy loss,
  * Sec. III-C, Listing 2). Supported for weighted flooding sum-product
@@ -401,7 +401,7 @@ int ldpc_bp_backward(ldpcx_code_t code, const float *llr_ch, int64_t B, const ld
                      const void *ckpt, size_t ckpt_bytes, const float *grad_llr_out, float *grad_llr_ch,
                      float *grad_weights, void *ws, size_t ws_bytes, void *stream);
 
-/* ------------------------------------------------------ error count (a10) */
+/* ------------------------------------------------------ error count */
 /* compute_ber of Listing 1: for each codeword, bit errors = popcount over
  * the k information bits of ref XOR hat; block error = any bit error.
  * counts (device int64[5]) accumulates {info bits, bit errors, blocks,
@@ -410,7 +410,7 @@ int ldpc_bp_backward(ldpcx_code_t code, const float *llr_ch, int64_t B, const ld
 int sim_count(const uint32_t *ref, const uint32_t *hat, const int32_t *iters, int64_t B, int k,
               int64_t *counts, void *stream);
 
-/* ------------------------- demapper with prior, EXIT charts (next row 1) */
+/* ------------------------- demapper with prior, EXIT charts */
 /* The feature list of the paper names a demapper with prior and EXIT chart
  * simulations (Section III, list of FEC features). These entry points close
  * the bit-interleaved coded modulation loop with iterative demapping and
@@ -464,7 +464,7 @@ int llr_mutual_info(const float *llr, int64_t B, int64_t N, const uint32_t *bits
 int ldpc_extrinsic(ldpcx_code_t code, const float *app, const float *llr_in, int64_t B, float clamp, float *out,
                    void *stream);
 
-/* --------------- trainable constellation, end-to-end gradients (next row 3) */
+/* --------------- trainable constellation, end-to-end gradients */
 /* Listing 2 of the paper makes the constellation trainable and learns it
  * end to end through mapper, AWGN and demapper with a binary cross-entropy
  * loss. These entry points run that chain and its adjoint with a constellation
@@ -510,7 +510,7 @@ int map_points_backward(ldpcx_code_t code, const uint32_t *cw, int64_t B, int m,
 int llr_bce(const float *llr, int64_t B, int64_t N, const uint32_t *bits, int64_t bits_stride, int64_t bit_off,
             float scale, double *loss_acc, float *grad_llr, void *stream);
 
-/* ----------------------------------- polar codes, SC/SCL decoding (next row 4) */
+/* ----------------------------------- polar codes, SC/SCL decoding */
 /* The paper lists polar codes with SC, SCL and SCL-CRC decoders among its FEC
  * features (Section III) and names the polar SCL decoder as a custom CUDA
  * kernel case (Section IV-A). Conventions:
@@ -547,7 +547,7 @@ int polar_sim_tx(ldpcx_polar_t code, uint64_t seed, uint64_t cw0, int64_t B, con
 int polar_scl_decode(ldpcx_polar_t code, const float *llr, int64_t B, int L, uint32_t *data_out, float *pm_out,
                      void *stream);
 
-/* -------------------------------------------------- Monte-Carlo run (a13) */
+/* -------------------------------------------------- Monte-Carlo run */
 /* A BER/BLER sweep over Eb/N0 points (the loop around Listing 1): for each
  * point, batches of `batch` codewords run sim_tx -> demap_app -> ldpc_bp_decode
  * -> sim_count on the device; codeword indices continue across batches and

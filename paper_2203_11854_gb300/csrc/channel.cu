@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_tx(const TxParams p) {
     }
     for (int i = threadIdx.x; i <= p.rows; i += blockDim.x) s_rp[i] = p.row_ptr[i];
     for (int i = threadIdx.x; i < p.G * p.inv_words; i += blockDim.x) s_lam[i] = 0u;
-    // a2: source bits (Philox stream 0), written packed to the output and to shared memory
+    // source bits (Philox stream 0), written packed to the output and to shared memory
     for (int i = threadIdx.x; i < p.G * nq; i += blockDim.x) {
         const int gg = i / nq, q = i - gg * nq;
         const int64_t cw = cw_base + gg;
@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_tx(const TxParams p) {
     }
     __syncthreads();
 
-    // a3: systematic encoding, one thread per (codeword, z)
+    // systematic encoding, one thread per (codeword, z)
     const int g = threadIdx.x / p.Z, z = threadIdx.x - g * p.Z;
     const bool active = g < p.G && cw_base + g < p.B;
     uint8_t *c = s_c + (size_t)(active ? g : 0) * ns;
@@ -194,7 +194,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_tx(const TxParams p) {
     }
     if (!p.y) return;  // codewords only: no barrier follows
 
-    // a4 + a5: Gray mapping and AWGN (Philox stream 1)
+    // Gray mapping and AWGN (Philox stream 1)
     const int m = p.m, S = p.n_tx / m;
     if (m == 1) {
         const int nqs = (S + 3) >> 2;
