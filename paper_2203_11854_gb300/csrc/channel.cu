@@ -293,9 +293,9 @@ __global__ void __launch_bounds__(256) k_demap(const float *__restrict__ y, cons
                                                float scale, float *__restrict__ llr) {
     const int64_t total = B * S;
     bool bad = false;
+    const float inv_shared = no_stride ? 0.0f : 1.0f / no[0];  // one N0 for all: no per-symbol division
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t b = i / S;
-        const float inv_n0 = 1.0f / no[b * no_stride];
+        const float inv_n0 = no_stride ? 1.0f / no[i / S] : inv_shared;
         if constexpr (M == 1) {
             float v = y[i];
             float L = 4.0f * v * inv_n0;
@@ -387,9 +387,9 @@ __global__ void __launch_bounds__(256) k_demap_prior(const float *__restrict__ y
                                                      float *__restrict__ llr) {
     const int64_t total = B * S;
     bool bad = false;
+    const float inv_shared = no_stride ? 0.0f : 1.0f / no[0];  // one N0 for all: no per-symbol division
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t b = i / S;
-        const float inv_n0 = 1.0f / no[b * no_stride];
+        const float inv_n0 = no_stride ? 1.0f / no[i / S] : inv_shared;
         if constexpr (M == 1) {
             const float v = y[i], la = prior ? prior[i] : 0.0f;
             float L = 4.0f * v * inv_n0;
