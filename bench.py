@@ -184,8 +184,19 @@ def cpu_baseline(seconds=12.0, ebn0=EBN0):
         t_total += time.perf_counter() - t0
         done += chunk
     k = code.k
+    # the same chain on one core, a shorter sample
+    t1, done1 = 0.0, 0
+    while t1 < seconds / 4 and done1 < 2000:
+        t0 = time.perf_counter()
+        oracle.sim(code, seed=SEED, cw0=cw0 + done + done1, B=2, ebn0_db=ebn0, m=M,
+                   demap_method=oracle.DEMAP_MAXLOG, algo=oracle.ALGO_MINSUM, iters=ITERS, prec=0,
+                   store=oracle.STORE_F16, offset=OFFSET, clamp=CLAMP, nthreads=1)
+        t1 += time.perf_counter() - t0
+        done1 += 2
     return {"value": done * k / t_total / 1e9, "unit": "Gbit/s", "cores": cores, "kind": "oracle",
             "cpu": host_cpu(),
+            "one_core": {"value": done1 * k / t1 / 1e9, "unit": "Gbit/s", "codewords": done1,
+                         "seconds": round(t1, 2)},
             "sample": f"{done} codewords of the workload (FP64 oracle chain: source, GF(2) encoder, mapper, AWGN, "
                       f"max-log demapper, layered min-sum with FP16 message store, 20 iterations), {t_total:.1f} s",
             "codewords_per_s": done / t_total}
