@@ -547,6 +547,31 @@ int polar_sim_tx(ldpcx_polar_t code, uint64_t seed, uint64_t cw0, int64_t B, con
 int polar_scl_decode(ldpcx_polar_t code, const float *llr, int64_t B, int L, uint32_t *data_out, float *pm_out,
                      void *stream);
 
+/* ------------------------------------------------------- rate matching */
+/* Circular-buffer rate matching (the paper's Section III lists 5G LDPC with
+ * rate matching among its FEC features), as the parameterised procedure of
+ * the 5G NR LDPC chain; the start position per redundancy version is the
+ * caller's (k0), so no standard table is built in:
+ *   buffer w = codeword bits [p0, p0 + ncb) (p0 = the code's punctured
+ *   systematic bits, ldpcx_code_info.p0); selection e_k = w[(k0 + k) mod ncb],
+ *   k = 0 .. E-1 (E > ncb repeats, E < ncb punctures); interleaving over qm
+ *   rows of E/qm columns, written by rows and read by columns:
+ *   f[i qm + j] = e[j (E/qm) + i].
+ * rate_match: cw (device) [B][ceil(n/32)] packed codeword bits (bit v of
+ *   codeword b = bit v mod 32 of word v/32, as sim_codewords writes them) ->
+ *   out (device) [B][ceil(E/32)] packed transmitted bits f.
+ * rate_recover (soft combining): llr (device) [B][E] received LLRs in
+ *   transmission order -> out (device) [B][ncb]: buffer position p holds the
+ *   sum, in increasing k, of the e_k that came from it (0 where none did).
+ *   A code built with n_tx = ncb and the same punct_cols decodes it directly.
+ * Errors: LDPCX_E_INVAL for a null pointer with B > 0, B < 0, ncb outside
+ * [1, n - p0], k0 outside [0, ncb), E < 1, qm not in {1,2,4,6,8} or not
+ * dividing E. */
+int rate_match(ldpcx_code_t code, const uint32_t *cw, int64_t B, int k0, int ncb, int E, int qm,
+               uint32_t *out, void *stream);
+int rate_recover(ldpcx_code_t code, const float *llr, int64_t B, int k0, int ncb, int E, int qm,
+                 float *out, void *stream);
+
 /* -------------------------------------------------- Monte-Carlo run */
 /* A BER/BLER sweep over Eb/N0 points (the loop around Listing 1): for each
  * point, batches of `batch` codewords run sim_tx -> demap_app -> ldpc_bp_decode

@@ -22,7 +22,7 @@ __all__ = [
     "ldpc_bp_backward", "ldpcx_phi", "sim_codewords", "demap_app_prior", "llr_apriori", "llr_mutual_info",
     "ldpc_extrinsic", "DEMAP_OUT_APP", "DEMAP_OUT_EXTRINSIC", "sim_tx_points", "demap_points",
     "demap_points_backward", "map_points_backward", "llr_bce", "PolarCode", "polar_build", "polar_sim_tx",
-    "polar_scl_decode", "qc_ldpc_build_base", "qc_alist_parse", "qc_ldpc_alist",
+    "polar_scl_decode", "qc_ldpc_build_base", "qc_alist_parse", "qc_ldpc_alist", "rate_match", "rate_recover",
     "LAYERED_MINSUM", "LAYERED_SPA", "FLOOD_MINSUM", "FLOOD_SPA", "MSG_F32", "MSG_F16", "MSG_FIX6",
     "DEMAP_EXACT", "DEMAP_MAXLOG",
 ]
@@ -93,6 +93,8 @@ _SIGS = {
     "qc_ldpc_build_base": ([C.POINTER(BaseParams), C.POINTER(_vp)], _i),
     "qc_alist_parse": ([C.c_char_p, _sz, _i, _vp, _i, C.POINTER(_i), C.POINTER(_i)], _i),
     "qc_ldpc_alist": ([_vp, _vp, _sz, C.POINTER(_sz)], _i),
+    "rate_match": ([_vp, _vp, _i64, _i, _i, _i, _i, _vp, _vp], _i),
+    "rate_recover": ([_vp, _vp, _i64, _i, _i, _i, _i, _vp, _vp], _i),
     "sim_tx": ([_vp, _u64, _u64, _i64, _i, _vp, _i64, _vp, _vp, _vp], _i),
     "demap_app": ([_vp, _vp, _i64, _i64, _i64, _i, _i, _f, _vp, _vp], _i),
     "sim_codewords": ([_vp, _u64, _u64, _i64, _vp, _vp], _i),
@@ -259,6 +261,29 @@ def qc_ldpc_alist(code: Code) -> str:
     buf = C.create_string_buffer(n.value + 1)
     _check(lib.qc_ldpc_alist(code.handle, buf, n.value + 1, C.byref(n)), "qc_ldpc_alist")
     return buf.value.decode("ascii")
+
+
+def rate_match(code: Code, cw, k0: int, ncb: int, E: int, qm: int, out=None, stream=None):
+    """Packed transmitted bits [B, ceil(E/32)] (int32) of packed codewords cw [B, ceil(n/32)] (int32, CUDA)."""
+    import torch
+    B = cw.shape[0]
+    if out is None:
+        out = torch.empty((B, (E + 31) // 32), dtype=torch.int32, device=cw.device)
+    _check(load_library().rate_match(code.handle, _ptr(cw), B, k0, ncb, E, qm, _ptr(out), _stream(stream)),
+           "rate_match")
+    return out
+
+
+def rate_recover(code: Code, llr, k0: int, ncb: int, qm: int, out=None, stream=None):
+    """Soft buffer [B, ncb] (float32) of received LLRs llr [B, E] (float32, CUDA, transmission order)."""
+    import torch
+    _cuda_f32(llr, "llr")
+    B, E = llr.shape
+    if out is None:
+        out = torch.empty((B, ncb), dtype=torch.float32, device=llr.device)
+    _check(load_library().rate_recover(code.handle, _ptr(llr), B, k0, ncb, E, qm, _ptr(out), _stream(stream)),
+           "rate_recover")
+    return out
 
 
 def qc_ldpc_free(code: Code) -> None:
