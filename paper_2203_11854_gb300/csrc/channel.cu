@@ -737,6 +737,7 @@ namespace ldpcx {
 int launch_tx(ldpcx_code_t c, uint64_t seed, uint64_t cw0, const uint64_t *cw0_dev, int64_t B, int m,
               const float *no, int64_t no_stride, float *y_out, uint32_t *info_out, cudaStream_t stream,
               uint32_t *cw_out, const float *points) {
+    if (c->enc == kEncNone) return LDPCX_E_UNSUPPORTED;  // before any device work
     DevCode d;
     int st = code_device(c, &d);
     if (st) return st;
@@ -762,7 +763,6 @@ int launch_tx(ldpcx_code_t c, uint64_t seed, uint64_t cw0, const uint64_t *cw0_d
     p.cw_out = cw_out;
     p.points = reinterpret_cast<const float2 *>(points);
     p.B = B;
-    if (c->enc == kEncNone) return LDPCX_E_UNSUPPORTED;
     p.nnz = c->nnz;
     p.core_inv = c->enc == kEncCoreInv ? d.core_inv : nullptr;
     p.inv_words = c->enc == kEncCoreInv ? c->inv_words : 0;

@@ -102,6 +102,21 @@ def test_argument_validation(lx):
     assert L.demap_app(16, 16, 0, 1, 1, 2, 5, 20.0, 16, None) == -1
     assert L.sim_tx(code.handle, 1, 0, 4, 3, 16, 0, 16, 16, None) == -1
     assert L.sim_count(16, 16, None, 4, 0, 16, None) == -1
+    # rate matching: buffer, start, length and rows checked before any launch; B = 0 is a no-op
+    nb = code.n - code.p0
+    for k0, ncb, E, qm in [(0, 0, 8, 1), (3, 3, 8, 1), (-1, 8, 8, 1), (0, nb + 1, 8, 1), (0, 8, 0, 1), (0, 8, 9, 2),
+                           (0, 8, 9, 3)]:
+        assert L.rate_match(code.handle, 16, 4, k0, ncb, E, qm, 16, None) == -1, (k0, ncb, E, qm)
+        assert L.rate_recover(code.handle, 16, 4, k0, ncb, E, qm, 16, None) == -1, (k0, ncb, E, qm)
+    assert L.rate_match(code.handle, None, 4, 0, nb, 8, 1, 16, None) == -1
+    assert L.rate_match(code.handle, None, 0, 0, nb, 8, 1, None, None) == 0
+    # user base matrices: the transmitter refuses an unencodable code before any launch
+    S = code.base().copy()
+    S[5, 10 + 7] = 1  # extension row 5 reads a later parity column
+    ucode = lx.qc_ldpc_build_base(S, 8, 10)
+    assert ucode.encodable == 0
+    assert L.sim_tx(ucode.handle, 1, 0, 4, 2, 16, 0, 16, 16, None) == -2
+    assert L.sim_codewords(ucode.handle, 1, 0, 4, 16, None) == -2
     assert lx.ldpcx_status_str(-4).startswith("LDPCX_E_WORKSPACE")
 
 
