@@ -428,9 +428,18 @@ def measure_variants(lx, code, llr, bits, its, stream, args, pk):
         del ws
     lx.ldpcx_tune_set(lx.TUNE_CN_STATE, 1)
     if "minsum_f32" in out and "minsum_f16" in out:
-        out["f16_over_f32"] = out["minsum_f32"]["decode_ms"] / out["minsum_f16"]["decode_ms"]
-        out["f16_over_f32_per_edge_plain_path"] = (out["minsum_f32_per_edge"]["decode_ms"]
-                                                   / out["minsum_f16"]["decode_ms"])
+        # FP16 >= 1.6x FP32 throughput, like for like: the same storage format at both precisions
+        cns = out["minsum_f32"]["decode_ms"] / out["minsum_f16"]["decode_ms"]
+        edge = out["minsum_f32_per_edge"]["decode_ms"] / out["minsum_f16_per_edge"]["decode_ms"]
+        out["f16_over_f32"] = cns
+        out["f16_over_f32_per_edge"] = edge
+        out["f16_over_f32_target"] = {
+            "target": 1.6, "met": bool(cns >= 1.6 and edge >= 1.6),
+            "reason": "both formats keep a resident CTA's messages in L2, so the decoder is bound by instruction "
+                      "issue, not by the message width; FP16 and FP32 run the same instructions"}
+        # not a precision ratio: FP16 check-node state against FP32 per-edge messages (format and precision)
+        out["f16_state_over_f32_per_edge_format_and_precision"] = (out["minsum_f32_per_edge"]["decode_ms"]
+                                                                   / out["minsum_f16"]["decode_ms"])
     try:
         os.remove(cache)
     except OSError:
@@ -647,6 +656,98 @@ def measure_e2e(lx, code, y_dev, info_dev, n0, dec, stream, args, dev):
                     "the demapper on a lower-priority one, double-buffered against the previous step's decode"}
 
 
+CASES = ("minsum_f16", "minsum_f32", "minsum_fix6", "spa_f16", "spa_f32", "grad", "mixed", "flood_spa_z8")
+
+
+def run_case(args):
+    """One kernel's launches alone, for timing and for small-case ncu captures: W untimed launches, then K
+    launches between CUDA events on the launching stream. Prints one JSON line with the mean launch time.
+    minsum_* / spa_*: ldpc_bp_decode of the BG1-shaped Z=384 code (20 iterations, no early stop) on --batch
+    codewords of the 16-QAM workload; grad: the weighted flooding sum-product forward with checkpoints and
+    its adjoint (BG2-shaped Z=64, 10 iterations, --batch codewords); mixed: the persistent mixed-code launch
+    (8192 codewords); flood_spa_z8: flooding sum-product FP32, BG2-shaped Z=8, 20 iterations."""
+    import torch
+    import paper_2203_11854_gb300 as lx
+    lx.load_library()
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    Bc = args.batch
+    name = args.case
+    info = {}
+    if name.startswith(("minsum_", "spa_")):
+        algo = lx.LAYERED_MINSUM if name.startswith("minsum_") else lx.LAYERED_SPA
+        prec = {"f16": lx.MSG_F16, "f32": lx.MSG_F32, "fix6": lx.MSG_FIX6}[name.split("_")[1]]
+        code = lx.qc_ldpc_build(BG, Z, punct_cols=PUNCT)
+        r = code.k / code.n_tx
+        n0 = torch.tensor([1.0 / (r * M * 10 ** (EBN0 / 10))], dtype=torch.float32, device=dev)
+        y, _ = lx.sim_tx(code, SEED, 0, Bc, M, n0)
+        llr = lx.demap_app(y, n0, M, method=lx.DEMAP_MAXLOG, clamp=CLAMP)
+        dec = dict(algo=algo, iters=ITERS, msg_prec=prec, offset=OFFSET, clamp=CLAMP)
+        ws = torch.empty(lx.ldpc_bp_workspace(code, Bc, **dec), dtype=torch.uint8, device=dev)
+        kw = (code.k + 31) // 32
+        bits = torch.empty((Bc, kw), dtype=torch.int32, device=dev)
+        its = torch.empty((Bc,), dtype=torch.int32, device=dev)
+        cn_state, msg_cw = lx.ldpc_bp_msg_format(code, algo=algo, iters=ITERS, msg_prec=prec)
+        info = {"codewords": Bc, "edges": code.edges, "iters": ITERS, "message_bytes_per_codeword_iteration": msg_cw,
+                "message_format": "check-node state" if cn_state else "per-edge messages",
+                "algorithmic_bytes_per_launch": Bc * (msg_cw * 2 * (ITERS - 1) + 4 * code.n_tx + code.k / 8)}
+
+        def fn():
+            lx.ldpc_bp_decode(code, llr, **dec, bits_out=bits, iters_out=its, ws=ws, stream=stream)
+    elif name == "flood_spa_z8":
+        code = lx.qc_ldpc_build(2, 8)
+        n0 = torch.tensor([1.0 / (code.k / code.n_tx * 2 * 10 ** (2.0 / 10))], dtype=torch.float32, device=dev)
+        y, _ = lx.sim_tx(code, SEED, 0, Bc, 2, n0)
+        llr = lx.demap_app(y, n0, 2, method=lx.DEMAP_EXACT, clamp=CLAMP)
+        dec = dict(algo=lx.FLOOD_SPA, iters=ITERS, msg_prec=lx.MSG_F32, clamp=CLAMP)
+        ws = torch.empty(lx.ldpc_bp_workspace(code, Bc, **dec), dtype=torch.uint8, device=dev)
+        info = {"codewords": Bc, "edges": code.edges, "iters": ITERS}
+
+        def fn():
+            lx.ldpc_bp_decode(code, llr, **dec, ws=ws, stream=stream)
+    elif name == "grad":
+        code = lx.qc_ldpc_build(2, 64)
+        iters = 10
+        g = torch.Generator(device=dev)
+        g.manual_seed(3)
+        llr = (2.0 + 2.0 * torch.randn((Bc, code.n_tx), device=dev, generator=g)).float().contiguous()
+        w = torch.ones((iters, code.nnz), device=dev)
+        ckpt = torch.empty(lx.ldpc_bp_ckpt_bytes(code, Bc, iters=iters, weights=w), dtype=torch.uint8, device=dev)
+        gw = torch.zeros_like(w)
+        gout = torch.ones((Bc, code.n), dtype=torch.float32, device=dev)
+        info = {"codewords": Bc, "edges": code.edges, "iters": iters}
+
+        def fn():
+            lx.ldpc_bp_decode_ckpt(code, llr, iters=iters, weights=w, ckpt=ckpt, stream=stream)
+            lx.ldpc_bp_backward(code, llr, ckpt, gout, iters=iters, weights=w, grad_weights=gw, stream=stream)
+    elif name == "mixed":
+        from paper_2203_11854_gb300 import workloads
+        groups, _, desc = workloads.mixed_batch(8192, seed=11)
+        dec = dict(algo=lx.LAYERED_MINSUM, iters=20, msg_prec=lx.MSG_F16, early_stop=True)
+        ws = torch.empty(lx.ldpc_bp_mixed_workspace(groups, **dec), dtype=torch.uint8, device=dev)
+        info = {"codewords": 8192}
+
+        def fn():
+            lx.ldpc_bp_decode_mixed(groups, **dec, ws=ws, stream=stream)
+    else:
+        raise SystemExit(f"unknown case {name}; one of {', '.join(CASES)}")
+    for _ in range(args.warmup):
+        fn()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(args.steps):
+        fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    st, _ = lx.ldpcx_sync_status()
+    if st != 0:
+        raise SystemExit(f"device status: {lx.ldpcx_status_str(st)}")
+    ms = a.elapsed_time(b) / args.steps
+    print(json.dumps({"case": name, "ms_per_launch": ms, "steps": args.steps, "warmup": args.warmup, **info}),
+          flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -657,7 +758,14 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--batch", type=int, default=B, help="codewords per step (4096 for the headline workload)")
+    ap.add_argument("--case", default=None, choices=CASES,
+                    help="time one kernel's launches alone (for profiling) instead of the Monte-Carlo step")
     args = ap.parse_args()
+    if args.case:
+        if args.warmup < 1 or args.steps < 1:
+            raise SystemExit("--case needs --warmup >= 1 and --steps >= 1")
+        run_case(args)
+        return
     globals()["B"] = args.batch
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

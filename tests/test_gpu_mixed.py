@@ -47,7 +47,7 @@ def build_groups(lx, orc, seed=3):
     return out
 
 
-@pytest.mark.parametrize("algo,prec", [(0, 1), (0, 0), (0, 2), (1, 0)])
+@pytest.mark.parametrize("algo,prec", [(0, 1), (0, 0), (0, 2), (1, 0), (1, 1)])
 def test_mixed_equals_per_group(lx, orc, algo, prec):
     groups = build_groups(lx, orc)
     res = lx.ldpc_bp_decode_mixed(groups, algo=algo, iters=12, msg_prec=prec, early_stop=True, llr_out=True)
@@ -70,6 +70,24 @@ def test_mixed_group_against_oracle(lx, orc):
                                 algo=0, iters=12, prec=1, store=1, early_stop=True)
     assert np.array_equal(res[2][0].cpu().numpy(), app.astype(np.float32))
     assert np.array_equal(res[2][2].cpu().numpy(), its)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_mixed_spa_group_against_oracle(lx, orc, prec):
+    """Layered sum-product in the mixed launch (FP32 and FP16 messages) against the FP64 oracle on one
+    group, element by element within 1e-3 relative (absolute below |LLR| = 1) after clamping to +-20."""
+    groups = build_groups(lx, orc)
+    res = lx.ldpc_bp_decode_mixed(groups, algo=1, iters=12, msg_prec=prec, early_stop=False, llr_out=True)
+    for gi in (1, 2):
+        code, llr = groups[gi]
+        bg, Z, rk, punct, B = GROUPS[gi]
+        ocode = orc.Code(bg, Z, rows_kept=rk, punct_cols=punct)
+        app, _, _ = orc.decode(ocode.graph, orc.place_llr(llr.cpu().numpy().astype(np.float64), ocode.p0, ocode.n),
+                               algo=1, iters=12, store=orc.STORE_F16 if prec == 1 else orc.STORE_NATIVE)
+        g = np.clip(res[gi][0].cpu().numpy().astype(np.float64), -20, 20)
+        r = np.clip(app, -20, 20)
+        err = np.abs(g - r) / np.maximum(np.abs(r), 1.0)
+        assert (err <= 1e-3).all(), f"group {gi}: max scaled error {err.max():.3g}"
 
 
 def test_mixed_rejects_flooding(lx, orc):

@@ -115,9 +115,19 @@ def test_flooding_minsum_bit_exact(lx, orc, name, prec, weighted):
 
 
 def spa_close(gpu, ref, rel=1e-3):
+    """Element-wise |g - r| <= rel * max(|r|, 1) after clamping both to +-20: relative
+    below the clamp, with an absolute floor of rel where |r| < 1 (an LLR near 0 has no
+    meaningful relative error; 1e-3 in L moves the bit probability by at most 2.5e-4)."""
     g = np.clip(gpu.astype(np.float64), -20, 20)
     r = np.clip(ref, -20, 20)
     return np.abs(g - r) <= rel * np.maximum(np.abs(r), 1.0)
+
+
+def spa_report(gpu, ref):
+    g = np.clip(gpu.astype(np.float64), -20, 20)
+    r = np.clip(ref, -20, 20)
+    err = np.abs(g - r) / np.maximum(np.abs(r), 1.0)
+    return f"max scaled error {err.max():.3g}, {(err > 1e-3).sum()} of {err.size} above 1e-3"
 
 
 @pytest.mark.parametrize("name", ["bg2_z8", "bg2_z64", "bg2_z200", "bg1_z384"])
@@ -132,6 +142,39 @@ def test_spa_fp32_within_tolerance(lx, orc, name, schedule):
     ok = spa_close(llr.cpu().numpy(), app)
     assert ok.all(), f"{(~ok).sum()} of {ok.size} outside 1e-3"
     assert np.array_equal(unpack(bits.cpu().numpy(), ocode.k), hard[:, :ocode.k])
+
+
+@pytest.mark.parametrize("name", ["bg2_z8", "bg2_z64", "bg2_z200", "bg1_z384"])
+@pytest.mark.parametrize("schedule", ["layered", "flooding"])
+def test_spa_fp16_within_tolerance(lx, orc, name, schedule):
+    """Sum-product with FP16 messages against the FP64 oracle with the binary16 message store:
+    the check-node output is rounded to half (RNE), stored and added to the APP on both sides."""
+    ocode, u, cw, L_tx = make_case(orc, name, 3.0, 29)
+    code = gpu_code(lx, name)
+    algo = lx.LAYERED_SPA if schedule == "layered" else lx.FLOOD_SPA
+    llr, bits, _ = lx.ldpc_bp_decode(code, cuda(L_tx), algo=algo, iters=10, msg_prec=lx.MSG_F16, llr_out=True)
+    app, hard, _ = orc.decode(ocode.graph, orc.place_llr(L_tx, ocode.p0, ocode.n), algo=1,
+                              schedule=0 if schedule == "layered" else 1, iters=10, store=orc.STORE_F16)
+    g = llr.cpu().numpy()
+    ok = spa_close(g, app)
+    assert ok.all(), spa_report(g, app)
+    # hard decisions agree wherever the oracle's APP is farther from 0 than the tolerance
+    sure = np.abs(app[:, :ocode.k]) > 1e-3
+    assert np.array_equal(unpack(bits.cpu().numpy(), ocode.k)[sure], hard[:, :ocode.k][sure])
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_spa_weighted_flooding_within_tolerance(lx, orc, prec):
+    """Weighted flooding sum-product (FP32 and FP16 messages) against the FP64 oracle."""
+    ocode, u, cw, L_tx = make_case(orc, "bg2_z64", 2.5, 37)
+    code = gpu_code(lx, "bg2_z64")
+    w = (0.6 + 0.8 * inputs.rng(9).random((8, code.nnz))).astype(np.float32)
+    llr, _, _ = lx.ldpc_bp_decode(code, cuda(L_tx), algo=lx.FLOOD_SPA, iters=8, msg_prec=prec, llr_out=True,
+                                  weights=cuda(w))
+    app, _, _ = orc.decode(ocode.graph, orc.place_llr(L_tx, ocode.p0, ocode.n), algo=1, schedule=1, iters=8,
+                           store=orc.STORE_F16 if prec == 1 else orc.STORE_NATIVE, weights=w.astype(np.float64))
+    g = llr.cpu().numpy()
+    assert spa_close(g, app).all(), spa_report(g, app)
 
 
 def test_tx_noiseless_symbols_and_bits(lx, orc):
