@@ -152,6 +152,52 @@ def profile_traffic():
         return None, digest
 
 
+def profile_sections(name):
+    """Per-kernel figures of a committed ncu summary under profiles/: a list of dicts (one per "### " section, or
+    the whole file), each with "current" = True when the sources it names hash as they did at capture time."""
+    try:
+        text = open(os.path.join(ROOT, "profiles", name)).read()
+    except OSError:
+        return []
+    secs, cur = [], {}
+    for line in text.splitlines():
+        if line.startswith("### "):
+            if cur:
+                secs.append(cur)
+            cur = {"kernel": line[4:].strip().strip("`")}
+        elif ": " in line and line.strip().startswith("- "):
+            k, v = line.strip()[2:].split(": ", 1)
+            cur[k.strip()] = v.strip().strip("`")
+    if cur:
+        secs.append(cur)
+    src = os.path.join(ROOT, "paper_2203_11854_gb300", "csrc")
+    for sec in secs:
+        files = sec.get("kernel sources hashed", "").split(" (")[0].split(" + ")
+        try:
+            blob = b"".join(open(os.path.join(src, f.strip()), "rb").read() for f in files if f.strip())
+            sec["current"] = bool(blob) and hashlib.sha256(blob).hexdigest()[:16] == sec.get("kernel sources sha256[:16]")
+        except OSError:
+            sec["current"] = False
+    return secs
+
+
+def issue_peak():
+    """Warp instructions per second the GPU can issue: SMs x 4 schedulers x the maximum SM clock."""
+    import torch
+    pk, _ = peaks()
+    return torch.cuda.get_device_properties(0).multi_processor_count * 4 * pk.get("sm_max_mhz", 2070.0) * 1e6
+
+
+def inst_per_32_edges(profile, kernel_sub=None):
+    """Warp instructions per 32 edge updates from a current ncu summary, or None."""
+    for sec in profile_sections(profile):
+        if kernel_sub and kernel_sub not in sec.get("kernel", ""):
+            continue
+        if sec.get("current") and "warp instructions per 32 edge updates" in sec:
+            return float(sec["warp instructions per 32 edge updates"])
+    return None
+
+
 def host_cpu():
     """Architecture and, where the kernel reports one, the model name of the host CPU."""
     import platform
@@ -339,15 +385,18 @@ def run_gpu(args):
     pk, pk_kind = peaks()
     achieved = alg_bytes / (dec_mean * 1e-3) / 1e9
     traffic_cw, _ = profile_traffic()
+    ipe = inst_per_32_edges("decode_layered_minsum_f16_bg1_z384.md") if cn_state else None
+    issue_frac = None if ipe is None else ipe * B * code.edges * ITERS / (dec_mean * 1e-3) / 32 / issue_peak()
 
     result = None
     if rank == 0:
         variants = {}
         if not args.quick:
             variants = measure_variants(lx, code, llr, bits, its, stream, args, pk)
-            variants["mixed_batch"] = measure_mixed(lx, stream, args)
+            variants["mixed_batch"] = measure_mixed(lx, stream, args, pk)
             variants["sweep_256qam"] = measure_sweep(lx, code, pk)
             variants["grad_step"] = measure_grad_step(lx)
+            variants["flood_spa_z8"] = measure_flood_z8(lx)
             variants["polar_scl"] = measure_polar(lx)
         e2e = measure_e2e(lx, code, y, info, n0, dec, stream, args, dev)
         cpu = None if (world > 1 or args.no_cpu) else cpu_baseline(args.cpu_seconds)
@@ -369,7 +418,9 @@ def run_gpu(args):
                          "message_format": "check-node state" if cn_state else "per-edge messages",
                          "message_bytes_per_codeword_iteration": msg_cw,
                          "peak_kind": f"{pk_kind} HBM copy bandwidth",
-                         "algorithmic_bytes_per_launch": alg_bytes},
+                         "algorithmic_bytes_per_launch": alg_bytes,
+                         # the ceiling that binds: warp instructions (ncu, same sources) over the issue rate
+                         "issue_frac": issue_frac, "warp_inst_per_32_edge_updates": ipe},
             "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
             "gpu_launches": 4 * args.steps,
             "variants": variants,
@@ -423,6 +474,14 @@ def measure_variants(lx, code, llr, bits, its, stream, args, pk):
             # results per clock per SM (4 per sub-partition) at the 2070 MHz maximum SM clock
             mufu_peak = 16 * torch.cuda.get_device_properties(0).multi_processor_count * 2.07e9
             out[name]["mufu_frac"] = 6 * B * code.edges * ITERS / (ms * 1e-3) / mufu_peak
+        # instruction-issue fraction: warp instructions per 32 edge updates (ncu, same kernel sources) times
+        # the edge updates per second, over SMs x 4 schedulers x the maximum SM clock
+        prof = {"minsum_f16": ("decode_layered_minsum_f16_bg1_z384.md", None),
+                "spa_f16": ("decode_layered_spa_f16_bg1_z384.md", None)}.get(name)
+        ipe = inst_per_32_edges(*prof) if prof else None
+        if ipe is not None:
+            out[name]["issue_frac"] = ipe * (B * code.edges * ITERS / (ms * 1e-3)) / 32 / issue_peak()
+            out[name]["warp_inst_per_32_edge_updates"] = ipe
         for key in (lx.TUNE_L2_PREFETCH, lx.TUNE_CW_PER_CTA, lx.TUNE_ZPT):
             lx.ldpcx_tune_set(key, 0)
         del ws
@@ -482,6 +541,30 @@ def measure_sweep(lx, code, pk):
     return out
 
 
+def measure_flood_z8(lx):
+    """The tiny plain-method configuration: BG2-shaped 42x52 code, Z = 8 (n = 416, k = 80, nothing punctured),
+    QPSK, Eb/N0 0..4 dB in 0.5 dB steps, 1000 codewords per point, flooding sum-product with FP32 messages for
+    20 iterations (no early stop): the graph-captured sweep (sim_run), its BER/BLER curve and throughput."""
+    import torch
+    code = lx.qc_ldpc_build(2, 8)
+    grid = [0.5 * i for i in range(9)]
+    kw = dict(m=2, demap_method=lx.DEMAP_EXACT, algo=lx.FLOOD_SPA, iters=20, msg_prec=lx.MSG_F32, early_stop=False,
+              seed=SEED, cw0=1 << 38, batch=1000, max_batches=1, use_graph=True)
+    ws = torch.empty(lx.sim_workspace(code, grid, **kw), dtype=torch.uint8, device="cuda")
+    lx.sim_run(code, grid, ws=ws, **kw)  # warm-up: graph capture
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    pts = lx.sim_run(code, grid, ws=ws, **kw)
+    torch.cuda.synchronize()
+    sec = time.perf_counter() - t0
+    cws = sum(q["blocks"] for q in pts)
+    return {"workload": "BG2-shaped Z=8 (n=416, k=80), QPSK, 9 Eb/N0 points x 1000 codewords, flooding "
+                        "sum-product FP32, 20 iterations", "seconds": sec, "codewords": cws,
+            "codewords_per_s": cws / sec, "gbps": cws * code.k / sec / 1e9,
+            "curve": [{"ebn0_db": q["ebn0_db"], "ber": q["bit_errors"] / q["bits"],
+                       "bler": q["block_errors"] / q["blocks"]} for q in pts]}
+
+
 def measure_grad_step(lx):
     """The weighted-BP training step: weighted flooding sum-product, BG2-shaped Z=64, batch 2048, 10 iterations,
     forward with checkpoints plus the hand-written adjoint (ldpc_bp_decode_ckpt + ldpc_bp_backward)."""
@@ -509,9 +592,19 @@ def measure_grad_step(lx):
     b.record()
     torch.cuda.synchronize()
     ms = a.elapsed_time(b) / reps
-    return {"ms_per_step": ms, "codewords_per_s": B / (ms * 1e-3),
-            "edge_updates_per_s": 2 * B * code.edges * iters / (ms * 1e-3),
-            "workload": "BG2-shaped Z=64, batch 2048, 10 flooding SPA iterations, forward + adjoint"}
+    out = {"ms_per_step": ms, "codewords_per_s": B / (ms * 1e-3),
+           "edge_updates_per_s": 2 * B * code.edges * iters / (ms * 1e-3),
+           "workload": "BG2-shaped Z=64, batch 2048, 10 flooding SPA iterations, forward + adjoint"}
+    # issue-bound roofline: the two kernels' warp instructions (ncu at 1024 codewords, scaled by the batch)
+    # over the step time and the GPU's issue rate; the autograd glue adds no kernel of this library
+    f = inst_per_32_edges("flooding_spa_and_adjoint_bg2_z64.md", "k_flooding")
+    g = inst_per_32_edges("flooding_spa_and_adjoint_bg2_z64.md", "k_backward")
+    if f is not None and g is not None:
+        inst = (f + g) * B * code.edges * iters / 32
+        out["roofline"] = {"bound": "issue", "achieved": inst / (ms * 1e-3), "peak": issue_peak(),
+                           "unit": "warp instructions/s", "frac": inst / (ms * 1e-3) / issue_peak(),
+                           "warp_inst_per_32_edge_updates": {"forward": f, "adjoint": g}}
+    return out
 
 
 def measure_polar(lx):
@@ -539,14 +632,20 @@ def measure_polar(lx):
     return out
 
 
-def measure_mixed(lx, stream, args):
+def measure_mixed(lx, stream, args, pk):
     """Uneven batch (8192 codewords over 48 codes: Z 16..384, both shapes, rates 1/3..8/9, QPSK/16/64-QAM,
-    Eb/N0 within 1 dB of each waterfall), layered min-sum FP16 with early stop: one persistent launch against
-    one launch per code group."""
+    Eb/N0 within 1 dB of each waterfall), layered min-sum FP16 with early stop: one persistent launch, its
+    work-item size autotuned on this batch, against one launch per code group. Roofline: the algorithmic
+    bytes of every codeword's own storage format for the iterations it ran (state reads from its second
+    iteration on, writes in every iteration but a full run's last) plus its channel LLRs and bits, over the
+    launch time."""
     import torch
-    from paper_2203_11854_gb300 import workloads
+    from paper_2203_11854_gb300 import autotune, workloads
     groups, infos, desc = workloads.mixed_batch(8192, seed=11)
     dec = dict(algo=lx.LAYERED_MINSUM, iters=20, msg_prec=lx.MSG_F16, early_stop=True)
+    cache = f"/tmp/ldpcx_autotune_mixed_{os.getpid()}.json"
+    tuned = autotune.tune_mixed(groups, **dec, cache_path=cache)
+    autotune.apply_mixed(groups, **dec, cache_path=cache)
     ws = torch.empty(lx.ldpc_bp_mixed_workspace(groups, **dec), dtype=torch.uint8, device="cuda")
     wss = [torch.empty(max(1, lx.ldpc_bp_workspace(c, l.shape[0], **dec)), dtype=torch.uint8, device="cuda")
            for c, l in groups]
@@ -575,14 +674,31 @@ def measure_mixed(lx, stream, args):
     # decoded bits agree between the two launches, and the error counts of the batch
     counts = torch.zeros(5, dtype=torch.int64, device="cuda")
     res = persistent()
+    alg_bytes = 0.0
     for (c, l), info, (_, b_, it) in zip(groups, infos, res):
         lx.sim_count(info, b_, it, c.k, counts)
+        _, msg_cw = lx.ldpc_bp_msg_format(c, **{k: dec[k] for k in ("algo", "iters", "msg_prec")})
+        its = it.to(torch.int64)
+        reads = (its - 1).clamp(min=0).sum().item()
+        writes = torch.where(its < dec["iters"], its, its - 1).sum().item()
+        alg_bytes += msg_cw * (reads + writes) + l.shape[0] * (4 * c.n_tx + c.k / 8)
+    lx.ldpcx_tune_set(lx.TUNE_CW_PER_CTA, 0)
+    try:
+        os.remove(cache)
+    except OSError:
+        pass
     cnt = counts.cpu().tolist()
     out.update(desc)
     out["speedup"] = out["per_group"]["ms"] / out["persistent"]["ms"]
     out["ber"] = cnt[1] / cnt[0]
     out["bler"] = cnt[3] / cnt[2]
     out["mean_iters"] = cnt[4] / cnt[2]
+    out["autotune"] = {"knob": "codewords per work item (LDPCX_TUNE_CW_PER_CTA; 0 = automatic)",
+                       "best": tuned["best"], "timings": tuned["timings"]}
+    achieved = alg_bytes / (out["persistent"]["ms"] * 1e-3) / 1e9
+    out["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                       "frac": achieved / pk["hbm_gbs"], "algorithmic_bytes_per_launch": alg_bytes,
+                       "note": "each codeword's own message format (check-node state) for the iterations it ran"}
     return out
 
 

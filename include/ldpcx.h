@@ -46,6 +46,7 @@ extern "C" {
 #define LDPCX_E_NONFINITE (-6)   /* device-latched: a non-finite input was sanitised */
 #define LDPCX_E_TIMEOUT (-7)     /* device-latched: a bounded wait gave up */
 #define LDPCX_E_NODEVICE (-8)    /* no CUDA device is visible */
+#define LDPCX_E_IO (-9)          /* a checkpoint file could not be read, parsed or written */
 
 /* Device status flags latched by kernels (ldpcx_sync_status). */
 #define LDPCX_FLAG_NONFINITE 1u  /* NaN input -> treated as 0; +-inf -> +-clamp */
@@ -100,6 +101,7 @@ typedef struct {
     int n, k, n_tx, p0;      /* codeword, info and transmitted bits; p0 = first transmitted position */
     int64_t edges;           /* nnz * Z */
     int encodable;           /* 1 when the transmitter can encode the code (see qc_ldpc_build_base) */
+    int n_fill;              /* filler bits at positions k .. k + n_fill - 1 (qc_ldpc_shorten), else 0 */
 } ldpcx_code_info;
 
 /* Build the code on the host (no device work; device tables are uploaded on
@@ -114,6 +116,24 @@ int qc_ldpc_info(ldpcx_code_t code, ldpcx_code_info *info);
 /* Copy the base matrix (row-major int16, -1 = zero block) into host memory
  * S_out of `capacity` entries (>= rows*cols, else LDPCX_E_INVAL). */
 int qc_ldpc_base(ldpcx_code_t code, int16_t *S_out, int capacity);
+
+/* A code block carrying k < kb*Z information bits (the 5G code blocks of the
+ * paper's Listing 1, k = 500 bits coded into n = 1000, Sec. III-C): *out is a
+ * new code object, a copy of `code` in which systematic positions k .. kb*Z-1
+ * are filler bits. Fillers are 0, known to both ends, and never transmitted:
+ * the transmit layout (sim_tx, sim_codewords' transmitted bits, rate_match,
+ * rate_recover, the decoders' llr_ch, ldpc_extrinsic) is the list of codeword
+ * positions p0 .. p0 + n_tx + n_fill - 1 without the fillers, in increasing
+ * order, so n_tx shrinks by n_fill. The transmitter draws k source bits and
+ * encodes [u | 0 ... 0]; the decoders give the fillers the channel LLR
+ * +clamp (a known zero) and write k bits to bits_out; sim_run counts k bits
+ * per block. The base matrix, the tables and every kernel are the mother
+ * code's. Requires p0 <= k <= kb*Z, fillers inside the transmitted span
+ * (p0 + n_tx >= kb*Z) and an unshortened `code`, else LDPCX_E_INVAL. The
+ * differentiable decode (ldpc_bp_decode_ckpt, ldpc_bp_backward) accepts no
+ * shortened code (LDPCX_E_UNSUPPORTED). Free *out with qc_ldpc_free; it does
+ * not depend on `code` afterwards. */
+int qc_ldpc_shorten(ldpcx_code_t code, int k, ldpcx_code_t *out);
 
 /* A quasi-cyclic code from a caller-supplied base matrix (the paper's
  * Section III lists LDPC codes from user parity-check matrices, with alist
@@ -192,6 +212,20 @@ int qc_ldpc_alist(ldpcx_code_t code, char *buf, size_t cap, size_t *len_out);
  * sim_tx_points and sim_run. */
 int sim_tx(ldpcx_code_t code, uint64_t seed, uint64_t cw0, int64_t B, int m,
            const float *no, int64_t no_stride, float *y_out, uint32_t *info_out, void *stream);
+
+/* Mapper and AWGN on caller bits (the Mapper and AWGN layers of Listing 1
+ * applied to a rate-matched stream, Sec. III-C): bits (device)
+ * [B][ceil(E/32)] packed (bit t of row b = bit t mod 32 of word t/32), E bits
+ * per row, m in {1,2,4,6,8} dividing E. Symbol s of row b maps bits
+ * s m .. s m + m - 1 as sim_tx maps a symbol and adds the Gaussians sim_tx
+ * draws for symbol s of codeword cw0 + b, with the same arithmetic: sim_tx
+ * equals sim_codewords, then rate_match with k0 = 0, ncb = E = n_tx, qm = 1,
+ * then this call. no: device, N0 of row b at no[b * no_stride] (stride 0 or
+ * 1). y_out (device): m = 1 -> [B][E] float; else [B][E/m][2] (re, im).
+ * Errors: LDPCX_E_INVAL for B < 0, E < 1, a bad m or stride, or a null pointer
+ * with B > 0. */
+int qam_map_awgn(const uint32_t *bits, int64_t B, int E, int m, uint64_t seed, uint64_t cw0, const float *no,
+                 int64_t no_stride, float *y_out, void *stream);
 
 /* ----------------------------------------------------------- demap */
 /* APP demapper (Demapper("app"), Listing 1) for Gray square QAM on AWGN:
@@ -293,7 +327,9 @@ int ldpc_bp_decode(ldpcx_code_t code, const float *llr_ch, int64_t B, const ldpc
  * z and z + Z/2, honoured when Z is even. Other kernels use one.
  * LDPCX_TUNE_CW_PER_CTA: codewords decoded together by one CTA of
  * ldpc_bp_decode (0 = automatic: about 384 check nodes per CTA within the
- * shared-memory budget; a smaller value gives smaller CTAs, more per SM).
+ * shared-memory budget; a smaller value gives smaller CTAs, more per SM), and
+ * the cap on the codewords of one work item of ldpc_bp_decode_mixed (smaller
+ * items: a finer queue, less waiting on a tile's slowest codeword).
  * LDPCX_TUNE_SPECIALISED: 1 (default) = use the layered min-sum kernels built
  * for a compile-time lifting size when one exists for the code's Z (384);
  * 0 = always the generic kernel.
@@ -317,25 +353,45 @@ int ldpc_bp_decode(ldpcx_code_t code, const float *llr_ch, int64_t B, const ldpc
 int ldpcx_tune_set(int key, int value);
 int ldpcx_tune_get(int key, int *value);
 
+/* Host-side fault injection, for tests of the error paths (the library makes
+ * no GPU fault on purpose). kind LDPCX_FAULT_ALLOC arms a one-shot allocation
+ * failure: the allocations of the library -- a code or polar object on the host
+ * (qc_ldpc_build, qc_ldpc_build_base, qc_ldpc_shorten, polar_build), and the
+ * device tables a code or polar code uploads on its first use on a device
+ * (sim_tx, sim_codewords, sim_tx_points, ldpc_bp_decode and its variants,
+ * ldpc_bp_backward, sim_run, polar_sim_tx, polar_scl_decode) -- let `after`
+ * allocations pass and fail the next one, which then returns LDPCX_E_NOMEM
+ * with the caller's outputs untouched; the injector then disarms.
+ * LDPCX_FAULT_NONE disarms it. The environment variable LDPCX_FAULT=alloc or
+ * alloc:N (N = `after`) arms it when the library first checks it. Errors:
+ * LDPCX_E_INVAL for an unknown kind or after < 0. */
+#define LDPCX_FAULT_NONE 0
+#define LDPCX_FAULT_ALLOC 1
+int ldpcx_fault_set(int kind, int after);
+
 /* Allocation-free decode. The paper has no counterpart: this entry point
  * exists for callers that cannot call cudaMalloc -- a receiver that allocates
  * every buffer at start-up and forbids allocation on its real-time path, a host
  * thread that must never block on the device (cudaMalloc may synchronise), or
  * a component whose device memory belongs to an allocator this library cannot
  * reach. It decodes exactly like ldpc_bp_decode (same arguments and outputs,
- * same results bit for bit) but keeps its scratch -- the code tables and the
- * check-to-variable messages -- in a fixed array of LDPCX_NOALLOC_SCRATCH_BYTES
- * inside the library image, which every GPU that loads the library holds
- * until the process exits. It calls no cudaMalloc, cudaFree or allocating
- * library routine. Limits: the tables (rounded to 256 bytes) plus
- * B * round_up(edges, 128) messages must fit in the array, else
- * LDPCX_E_WORKSPACE (at Z = 384, BG1-shaped: 69 codewords with FP32
- * messages, 138 with FP16, 276 with FIX6). The first call on a device looks up
- * the array's device address (cudaGetSymbolAddress); make that first call
- * before any stream capture. Every call on a device shares the array and
- * leaves its contents behind; nothing needs clearing (tables are rewritten by
- * each call, every message is written before it is read), but calls that
- * overlap on the GPU -- on different streams -- race on it. */
+ * same kernel choice and tuning knobs, same results bit for bit) but keeps its
+ * scratch -- the code tables and the check-to-variable messages, or for
+ * layered min-sum the check-node state -- in a fixed array of
+ * LDPCX_NOALLOC_SCRATCH_BYTES inside the library image, which every GPU that
+ * loads the library holds until the process exits. It calls no cudaMalloc,
+ * cudaFree or allocating library routine. Limits: the tables (rounded to 256
+ * bytes) plus B times the per-codeword bytes of the decoder's message format
+ * must fit in the array, else LDPCX_E_WORKSPACE before any work; B is bounded
+ * before any product is formed. At Z = 384, BG1-shaped: layered min-sum
+ * (check-node state) 118 / 218 / 436 codewords with FP32 / FP16 / FIX6
+ * messages; sum-product and flooding (per-edge messages) 69 / 138. The first
+ * call on a device looks up the array's device address (cudaGetSymbolAddress);
+ * make that first call before any stream capture. Every call on a device
+ * shares the array and leaves its contents behind; nothing needs clearing
+ * (tables are rewritten by each call, every message is written before it is
+ * read), but calls that overlap on the GPU -- on different streams -- race on
+ * it. */
 #define LDPCX_NOALLOC_SCRATCH_BYTES (32u << 20)
 int ldpc_bp_decode_noalloc(ldpcx_code_t code, const float *llr_ch, int64_t B, const ldpcx_decode_opts *opts,
                            float *llr_out, uint32_t *bits_out, int32_t *iters_out, void *stream);
@@ -552,8 +608,12 @@ int polar_scl_decode(ldpcx_polar_t code, const float *llr, int64_t B, int L, uin
  * rate matching among its FEC features), as the parameterised procedure of
  * the 5G NR LDPC chain; the start position per redundancy version is the
  * caller's (k0), so no standard table is built in:
- *   buffer w = codeword bits [p0, p0 + ncb) (p0 = the code's punctured
- *   systematic bits, ldpcx_code_info.p0); selection e_k = w[(k0 + k) mod ncb],
+ *   buffer w = the first ncb bits of the transmit layout: codeword positions
+ *   p0, p0 + 1, ... (p0 = the code's punctured systematic bits,
+ *   ldpcx_code_info.p0) without the filler bits of a shortened code
+ *   (qc_ldpc_shorten); the 5G form keeps the fillers in the buffer as <NULL>
+ *   entries and skips them while reading, which selects the same bits when its
+ *   start counts the fillers before it; selection e_k = w[(k0 + k) mod ncb],
  *   k = 0 .. E-1 (E > ncb repeats, E < ncb punctures); interleaving over qm
  *   rows of E/qm columns, written by rows and read by columns:
  *   f[i qm + j] = e[j (E/qm) + i].
@@ -565,8 +625,8 @@ int polar_scl_decode(ldpcx_polar_t code, const float *llr, int64_t B, int L, uin
  *   sum, in increasing k, of the e_k that came from it (0 where none did).
  *   A code built with n_tx = ncb and the same punct_cols decodes it directly.
  * Errors: LDPCX_E_INVAL for a null pointer with B > 0, B < 0, ncb outside
- * [1, n - p0], k0 outside [0, ncb), E < 1, qm not in {1,2,4,6,8} or not
- * dividing E. */
+ * [1, n - p0 - n_fill], k0 outside [0, ncb), E < 1, qm not in {1,2,4,6,8} or
+ * not dividing E. */
 int rate_match(ldpcx_code_t code, const uint32_t *cw, int64_t B, int k0, int ncb, int E, int qm,
                uint32_t *out, void *stream);
 int rate_recover(ldpcx_code_t code, const float *llr, int64_t B, int k0, int ncb, int E, int qm,
@@ -603,6 +663,8 @@ typedef struct {
     int n_snr;
     double stop_ber;        /* 0 = never stop early */
     int use_graph;          /* capture and replay one batch as a CUDA graph */
+    const char *ckpt_path;  /* host path of the sweep's checkpoint file, or NULL (see sim_run) */
+    int max_points;         /* run at most this many points in this call (0 = no limit) */
 } ldpcx_sim_config;
 
 typedef struct {
@@ -614,7 +676,22 @@ typedef struct {
 int sim_workspace(const ldpcx_sim_config *cfg, size_t *ws_bytes);
 /* Run the sweep. out: host [n_snr] counts (points not run are zero);
  * *points_run = points executed. Synchronises `stream` once per batch check
- * and once per point. ws: device, >= sim_workspace bytes, 256-byte aligned. */
+ * and once per point. ws: device, >= sim_workspace bytes, 256-byte aligned.
+ * Checkpoint / resume: with ckpt_path set, the sweep's state is written to
+ * that file after every finished point -- the points done with their int64
+ * counts, the index of the next codeword and whether the sweep has ended --
+ * as JSON, through a temporary file renamed over the old one, so an
+ * interrupted run leaves the last complete state. A call that finds the file
+ * restores it and continues with the next point from the saved codeword
+ * index; since every draw is counter-based, the counts equal those of an
+ * uninterrupted sweep bit for bit (and a sweep already ended returns its
+ * saved counts without device work). The file carries a fingerprint of
+ * everything that fixes the counts (code, channel, decoder, seed, cw0, batch
+ * sizes, stopping rules, Eb/N0 points; not use_graph or max_points); a file
+ * of another sweep, or one this library did not write, gives LDPCX_E_IO
+ * before any device work, as does a write that fails. max_points > 0 ends
+ * the call after that many points of this call (a long sweep run in slices).
+ * out and *points_run then cover the restored and the new points. */
 int sim_run(const ldpcx_sim_config *cfg, ldpcx_sim_counts *out, int *points_run,
             void *ws, size_t ws_bytes, void *stream);
 

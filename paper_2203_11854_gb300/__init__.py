@@ -23,6 +23,7 @@ __all__ = [
     "ldpc_extrinsic", "DEMAP_OUT_APP", "DEMAP_OUT_EXTRINSIC", "sim_tx_points", "demap_points",
     "demap_points_backward", "map_points_backward", "llr_bce", "PolarCode", "polar_build", "polar_sim_tx",
     "polar_scl_decode", "qc_ldpc_build_base", "qc_alist_parse", "qc_ldpc_alist", "rate_match", "rate_recover",
+    "qc_ldpc_shorten", "qam_map_awgn", "ldpcx_fault_set", "FAULT_NONE", "FAULT_ALLOC",
     "LAYERED_MINSUM", "LAYERED_SPA", "FLOOD_MINSUM", "FLOOD_SPA", "MSG_F32", "MSG_F16", "MSG_FIX6",
     "DEMAP_EXACT", "DEMAP_MAXLOG",
 ]
@@ -33,6 +34,7 @@ DEMAP_EXACT, DEMAP_MAXLOG = 0, 1
 DEMAP_OUT_APP, DEMAP_OUT_EXTRINSIC = 0, 1
 FLAG_NONFINITE, FLAG_TIMEOUT = 1, 2
 TUNE_L2_PREFETCH, TUNE_ZPT, TUNE_CW_PER_CTA, TUNE_SPECIALISED, TUNE_CN_STATE, TUNE_SCHEDULE = 1, 2, 3, 4, 5, 6
+FAULT_NONE, FAULT_ALLOC = 0, 1
 
 
 class LdpcxError(RuntimeError):
@@ -49,7 +51,7 @@ class CodeParams(C.Structure):
 class CodeInfo(C.Structure):
     _fields_ = [("Z", C.c_int), ("rows", C.c_int), ("cols", C.c_int), ("kb", C.c_int), ("nnz", C.c_int),
                 ("max_row_deg", C.c_int), ("n", C.c_int), ("k", C.c_int), ("n_tx", C.c_int), ("p0", C.c_int),
-                ("edges", C.c_int64), ("encodable", C.c_int)]
+                ("edges", C.c_int64), ("encodable", C.c_int), ("n_fill", C.c_int)]
 
 
 class BaseParams(C.Structure):
@@ -66,7 +68,8 @@ class SimConfig(C.Structure):
     _fields_ = [("code", C.c_void_p), ("m", C.c_int), ("demap_method", C.c_int), ("demap_clamp", C.c_float),
                 ("dec", DecodeOpts), ("seed", C.c_uint64), ("cw0", C.c_uint64), ("batch", C.c_int64),
                 ("max_batches", C.c_int64), ("min_bit_errors", C.c_int64), ("ebn0_db", C.POINTER(C.c_double)),
-                ("n_snr", C.c_int), ("stop_ber", C.c_double), ("use_graph", C.c_int)]
+                ("n_snr", C.c_int), ("stop_ber", C.c_double), ("use_graph", C.c_int), ("ckpt_path", C.c_char_p),
+                ("max_points", C.c_int)]
 
 
 class BatchGroup(C.Structure):
@@ -93,6 +96,8 @@ _SIGS = {
     "qc_ldpc_build_base": ([C.POINTER(BaseParams), C.POINTER(_vp)], _i),
     "qc_alist_parse": ([C.c_char_p, _sz, _i, _vp, _i, C.POINTER(_i), C.POINTER(_i)], _i),
     "qc_ldpc_alist": ([_vp, _vp, _sz, C.POINTER(_sz)], _i),
+    "qc_ldpc_shorten": ([_vp, _i, C.POINTER(_vp)], _i),
+    "qam_map_awgn": ([_vp, _i64, _i, _i, _u64, _u64, _vp, _i64, _vp, _vp], _i),
     "rate_match": ([_vp, _vp, _i64, _i, _i, _i, _i, _vp, _vp], _i),
     "rate_recover": ([_vp, _vp, _i64, _i, _i, _i, _i, _vp, _vp], _i),
     "sim_tx": ([_vp, _u64, _u64, _i64, _i, _vp, _i64, _vp, _vp, _vp], _i),
@@ -127,6 +132,7 @@ _SIGS = {
     "ldpc_bp_backward_workspace": ([_vp, _i64, C.POINTER(DecodeOpts), C.POINTER(_sz)], _i),
     "ldpc_bp_backward": ([_vp, _vp, _i64, C.POINTER(DecodeOpts), _vp, _sz, _vp, _vp, _vp, _vp, _sz, _vp], _i),
     "ldpcx_tune_set": ([_i, _i], _i),
+    "ldpcx_fault_set": ([_i, _i], _i),
     "ldpcx_tune_get": ([_i, C.POINTER(_i)], _i),
 }
 
@@ -263,6 +269,14 @@ def qc_ldpc_alist(code: Code) -> str:
     return buf.value.decode("ascii")
 
 
+def qc_ldpc_shorten(code: Code, k: int) -> Code:
+    """A new code carrying k information bits: systematic positions k .. kb*Z-1 become filler bits
+    (known zeros, not transmitted)."""
+    h = C.c_void_p()
+    _check(load_library().qc_ldpc_shorten(code.handle, k, C.byref(h)), "qc_ldpc_shorten")
+    return Code(h.value)
+
+
 def rate_match(code: Code, cw, k0: int, ncb: int, E: int, qm: int, out=None, stream=None):
     """Packed transmitted bits [B, ceil(E/32)] (int32) of packed codewords cw [B, ceil(n/32)] (int32, CUDA)."""
     import torch
@@ -316,6 +330,20 @@ def sim_tx(code: Code, seed: int, cw0: int, B: int, m: int, no, y_out=None, info
     _check(load_library().sim_tx(code.handle, seed, cw0, B, m, _ptr(no), stride, _ptr(y_out), _ptr(info_out),
                                  _stream(stream)), "sim_tx")
     return y_out, info_out
+
+
+def qam_map_awgn(bits, E: int, m: int, seed: int, cw0: int, no, y_out=None, stream=None):
+    """Gray mapper + AWGN on packed bits [B, ceil(E/32)] (int32, CUDA): symbols and noise as sim_tx draws them
+    for codewords cw0 .. cw0+B-1. Returns y [B, E] (m = 1) or [B, E/m, 2] float32."""
+    import torch
+    _cuda_f32(no, "no")
+    B = bits.shape[0]
+    if y_out is None:
+        y_out = torch.empty((B, E) if m == 1 else (B, E // m, 2), dtype=torch.float32, device=bits.device)
+    stride = 0 if no.numel() == 1 else 1
+    _check(load_library().qam_map_awgn(_ptr(bits), B, E, m, seed, cw0, _ptr(no), stride, _ptr(y_out),
+                                       _stream(stream)), "qam_map_awgn")
+    return y_out
 
 
 # --------------------------------------------------------------------------- demapper
@@ -740,17 +768,19 @@ def sim_count(ref, hat, iters, k: int, counts, stream=None):
 
 
 def _sim_config(code: Code, ebn0_db, *, m, demap_method, demap_clamp, algo, iters, msg_prec, early_stop, offset,
-                clamp, seed, cw0, batch, max_batches, min_bit_errors, stop_ber, use_graph):
+                clamp, seed, cw0, batch, max_batches, min_bit_errors, stop_ber, use_graph, ckpt_path, max_points):
     eb = (C.c_double * len(ebn0_db))(*ebn0_db)
+    path = None if ckpt_path is None else os.fsencode(ckpt_path)
     cfg = SimConfig(code.handle, m, demap_method, demap_clamp,
                     _opts(algo, iters, msg_prec, early_stop, offset, clamp, None), seed, cw0, batch, max_batches,
-                    min_bit_errors, C.cast(eb, C.POINTER(C.c_double)), len(ebn0_db), stop_ber, int(bool(use_graph)))
-    return cfg, eb
+                    min_bit_errors, C.cast(eb, C.POINTER(C.c_double)), len(ebn0_db), stop_ber, int(bool(use_graph)),
+                    path, max_points)
+    return cfg, (eb, path)
 
 
 _SIM_DEFAULTS = dict(m=4, demap_method=DEMAP_MAXLOG, demap_clamp=20.0, algo=LAYERED_MINSUM, iters=20,
                      msg_prec=MSG_F16, early_stop=False, offset=0.5, clamp=20.0, seed=0x1DBC, cw0=0, batch=1024,
-                     max_batches=1, min_bit_errors=0, stop_ber=0.0, use_graph=True)
+                     max_batches=1, min_bit_errors=0, stop_ber=0.0, use_graph=True, ckpt_path=None, max_points=0)
 
 
 def sim_workspace(code: Code, ebn0_db, **kw) -> int:
@@ -761,7 +791,9 @@ def sim_workspace(code: Code, ebn0_db, **kw) -> int:
 
 
 def sim_run(code: Code, ebn0_db, ws=None, stream=None, device=None, **kw):
-    """Monte-Carlo sweep; returns a list of dicts (one per point run)."""
+    """Monte-Carlo sweep; returns a list of dicts (one per point run, restored points of a checkpoint included).
+    ckpt_path: the sweep's checkpoint file (written after every point, resumed from when present);
+    max_points: points to run in this call (0 = all)."""
     import torch
     args = {**_SIM_DEFAULTS, **kw}
     cfg, _keep = _sim_config(code, list(ebn0_db), **args)
@@ -779,6 +811,12 @@ def sim_run(code: Code, ebn0_db, ws=None, stream=None, device=None, **kw):
 
 def ldpcx_tune_set(key: int, value: int) -> None:
     _check(load_library().ldpcx_tune_set(key, value), "ldpcx_tune_set")
+
+
+def ldpcx_fault_set(kind: int, after: int = 0) -> None:
+    """Arm (FAULT_ALLOC: the allocation after `after` more fails once with LDPCX_E_NOMEM) or disarm (FAULT_NONE)
+    the library's host-side fault injector."""
+    _check(load_library().ldpcx_fault_set(kind, after), "ldpcx_fault_set")
 
 
 def ldpcx_tune_get(key: int) -> int:

@@ -11,6 +11,8 @@ Knobs: LDPCX_TUNE_CW_PER_CTA (codewords per CTA) everywhere; with per-edge
 messages LDPCX_TUNE_L2_PREFETCH (message-span prefetch distance of the layered
 kernels); with check-node state LDPCX_TUNE_ZPT (one or two check nodes per
 thread). Layer order is not a knob: changing it changes the decoder's results.
+tune_mixed() tunes the persistent mixed-code launch on the caller's batch (the
+cap on the codewords of one work item), keyed by the batch's code mix.
 """
 from __future__ import annotations
 
@@ -100,6 +102,58 @@ def tune(code, *, B: int = 1024, algo: int = 0, msg_prec: int = 1, iters: int = 
     cache[_key(code, algo, msg_prec, iters, early_stop)] = best
     save_cache(cache, cache_path)
     return {"best": best, "timings": timings}
+
+
+def _mixed_key(groups, algo, msg_prec, iters, early_stop):
+    """The batch's code mix: per group its shape and codeword count, in group order."""
+    dev = torch.cuda.get_device_name()
+    mix = ";".join(f"Z{c.Z}r{c.rows}c{c.cols}n{c.n_tx}f{c.n_fill}B{int(l.shape[0])}" for c, l in groups)
+    return f"{dev}|mixed|{mix}|algo{algo}|msg{msg_prec}|it{iters}|es{int(early_stop)}"
+
+
+def tune_mixed(groups, *, algo: int = 0, msg_prec: int = 1, iters: int = 20, early_stop: bool = True, reps: int = 3,
+               cache_path=None, candidates=(0, 12, 8, 6, 4, 2)) -> dict:
+    """Tune the persistent mixed-code launch (ldpc_bp_decode_mixed) on the caller's own batch: the cap on the
+    codewords of one work item (LDPCX_TUNE_CW_PER_CTA). Every candidate must give the same outputs bit for bit;
+    the fastest is cached under the batch's code mix."""
+    from . import ldpc_bp_decode_mixed, ldpc_bp_mixed_workspace
+    dec = dict(algo=algo, iters=iters, msg_prec=msg_prec, early_stop=early_stop)
+    saved = ldpcx_tune_get(TUNE_CW_PER_CTA)
+    timings, ref = [], None
+    try:
+        for g in candidates:
+            ldpcx_tune_set(TUNE_CW_PER_CTA, g)
+            ws = torch.empty(ldpc_bp_mixed_workspace(groups, **dec), dtype=torch.uint8, device="cuda")
+            out = ldpc_bp_decode_mixed(groups, **dec, llr_out=True, ws=ws)
+            flat = [t for o in out for t in o if t is not None]
+            if ref is None:
+                ref = flat
+            elif not all(torch.equal(a, b) for a, b in zip(flat, ref)):
+                raise RuntimeError(f"codewords per item {g} changed the decoder's results")
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            for _ in range(reps):
+                ldpc_bp_decode_mixed(groups, **dec, ws=ws)
+            b.record()
+            torch.cuda.synchronize()
+            timings.append({"cw_per_cta": g, "ms": a.elapsed_time(b) / reps})
+            del ws
+    finally:
+        ldpcx_tune_set(TUNE_CW_PER_CTA, saved)
+    best = dict(min(timings, key=lambda t: t["ms"]))
+    cache = load_cache(cache_path)
+    cache[_mixed_key(groups, algo, msg_prec, iters, early_stop)] = best
+    save_cache(cache, cache_path)
+    return {"best": best, "timings": timings}
+
+
+def apply_mixed(groups, *, algo: int = 0, msg_prec: int = 1, iters: int = 20, early_stop: bool = True,
+                cache_path=None):
+    """Set the cached work-item cap for this code mix (automatic when none is cached)."""
+    best = load_cache(cache_path).get(_mixed_key(groups, algo, msg_prec, iters, early_stop))
+    ldpcx_tune_set(TUNE_CW_PER_CTA, best["cw_per_cta"] if best else 0)
+    return best
 
 
 def apply(code, *, algo: int = 0, msg_prec: int = 1, iters: int = 20, early_stop: bool = False, cache_path=None):

@@ -14,6 +14,7 @@ struct TxParams {
     const uint32_t *blk;
     const int32_t *row_ptr;
     int Z, rows, kb, n, k, n_tx, p0, nnz;
+    int nf;                    // filler bits at positions k .. k + nf - 1 (0, known, not transmitted)
     const uint32_t *core_inv;  // [4Z][inv_words] inverse of the core parity part, or null (dual diagonal)
     int inv_words;
     int m;
@@ -100,6 +101,14 @@ __global__ void __launch_bounds__(kMaxThreads) k_tx(const TxParams p) {
         if (cw_base + gg >= p.B) continue;
         const uint32_t nib = (s_w[(size_t)gg * 4 * nq + (j >> 3)] >> (4 * (j & 7))) & 0xFu;
         *reinterpret_cast<uint32_t *>(s_c + (size_t)gg * ns + 4 * j) = (nib * 0x00204081u) & 0x01010101u;
+    }
+    if (p.nf > 0) {
+        // filler bits are 0; bytes k .. 4 k4 - 1 already are (the last source word is masked)
+        const int f0 = 4 * k4, f1 = p.k + p.nf, nfz = f1 > f0 ? f1 - f0 : 0;
+        for (int i = threadIdx.x; i < p.G * nfz; i += blockDim.x) {
+            const int gg = i / nfz, v = f0 + (i - gg * nfz);
+            if (cw_base + gg < p.B) s_c[(size_t)gg * ns + v] = 0;
+        }
     }
     __syncthreads();
 
@@ -206,11 +215,11 @@ __global__ void __launch_bounds__(kMaxThreads) k_tx(const TxParams p) {
             const uint4 x = draw(p.seed, cw0 + (uint64_t)cw, 1u, (uint32_t)q);
             const float2 g01 = box_muller(x.x, x.y), g23 = box_muller(x.z, x.w);
             const float gs[4] = {g01.x, g01.y, g23.x, g23.y};
-            const uint8_t *cb = s_c + (size_t)gg * ns + p.p0;
+            const uint8_t *cg = s_c + (size_t)gg * ns;
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
                 const int s = 4 * q + e;
-                if (s < S) p.y[cw * S + s] = (1.0f - 2.0f * (float)cb[s]) + sd * gs[e];
+                if (s < S) p.y[cw * S + s] = (1.0f - 2.0f * (float)cg[tx_position(s, p.p0, p.k, p.nf)]) + sd * gs[e];
             }
         }
     } else {
@@ -228,6 +237,12 @@ __global__ void __launch_bounds__(kMaxThreads) k_tx(const TxParams p) {
                 const int s = 2 * q + e;
                 if (s >= S) break;
                 const uint8_t *bits = cb + (size_t)s * m;
+                uint8_t gathered[8];
+                if (p.nf > 0) {  // a shortened code: the symbol's bits skip the fillers
+                    const uint8_t *cg = s_c + (size_t)gg * ns;
+                    for (int j = 0; j < m; ++j) gathered[j] = cg[tx_position(s * m + j, p.p0, p.k, p.nf)];
+                    bits = gathered;
+                }
                 float xi, xq;
                 if (p.points) {
                     int l = 0;
@@ -240,6 +255,53 @@ __global__ void __launch_bounds__(kMaxThreads) k_tx(const TxParams p) {
                     xq = (float)pam_level(bits + 1, h) * p.scale;
                 }
                 reinterpret_cast<float2 *>(p.y)[cw * S + s] = make_float2(xi + sd * gn[e].x, xq + sd * gn[e].y);
+            }
+        }
+    }
+}
+
+// Mapper and AWGN on caller bits: symbol s of row b takes bits s m .. s m + m - 1
+// of the row and the Gaussians k_tx draws for symbol s of codeword cw0 + b
+// (Philox stream 1; one block gives four real or two complex symbols), with the
+// same arithmetic, so the symbols equal k_tx's for the same bits.
+__global__ void __launch_bounds__(256) k_map_awgn(const uint32_t *__restrict__ bits, int64_t B, int E, int nw, int m,
+                                                  float scale, uint64_t seed, uint64_t cw0,
+                                                  const float *__restrict__ no, int64_t no_stride,
+                                                  float *__restrict__ y) {
+    const int S = E / m;
+    const int per = m == 1 ? 4 : 2;
+    const int nqs = (S + per - 1) / per;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < B * nqs; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = i / nqs;
+        const int q = (int)(i - b * nqs);
+        const float sd = sqrtf(no[b * no_stride] * 0.5f);
+        const uint4 x = draw(seed, cw0 + (uint64_t)b, 1u, (uint32_t)q);
+        const uint32_t *row = bits + b * nw;
+        if (m == 1) {
+            const float2 g01 = box_muller(x.x, x.y), g23 = box_muller(x.z, x.w);
+            const float gs[4] = {g01.x, g01.y, g23.x, g23.y};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int s = 4 * q + e;
+                if (s >= S) break;
+                const uint8_t bit = (uint8_t)((row[s >> 5] >> (s & 31)) & 1u);
+                y[b * S + s] = (1.0f - 2.0f * (float)bit) + sd * gs[e];
+            }
+        } else {
+            const int h = m >> 1;
+            const float2 gn[2] = {box_muller(x.x, x.y), box_muller(x.z, x.w)};
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const int s = 2 * q + e;
+                if (s >= S) break;
+                uint8_t lb[8];
+                for (int j = 0; j < m; ++j) {
+                    const int t = s * m + j;
+                    lb[j] = (uint8_t)((row[t >> 5] >> (t & 31)) & 1u);
+                }
+                const float xi = (float)pam_level(lb, h) * scale;
+                const float xq = (float)pam_level(lb + 1, h) * scale;
+                reinterpret_cast<float2 *>(y)[b * S + s] = make_float2(xi + sd * gn[e].x, xq + sd * gn[e].y);
             }
         }
     }
@@ -477,12 +539,12 @@ __global__ void __launch_bounds__(256) k_mutual_info(const float *__restrict__ l
 }
 
 __global__ void __launch_bounds__(256) k_extrinsic(const float *__restrict__ app, const float *__restrict__ in,
-                                                   int64_t B, int n, int p0, int n_tx, float clamp,
+                                                   int64_t B, int n, int p0, int n_tx, int k, int nf, float clamp,
                                                    float *__restrict__ out) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < B * n_tx; i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t b = i / n_tx, t = i - b * n_tx;
         const float x = fminf(fmaxf(in[i], -clamp), clamp);  // the input as the decoder clamped it
-        out[i] = fminf(fmaxf(app[b * n + p0 + t] - x, -clamp), clamp);
+        out[i] = fminf(fmaxf(app[b * n + tx_position((int)t, p0, k, nf)] - x, -clamp), clamp);
     }
 }
 
@@ -624,9 +686,9 @@ __global__ void __launch_bounds__(256) k_demap_points_bwd(const float *__restric
 }
 
 // Adjoint of the mapper: grad_points[label(b, s)] += grad_x[b][s].
-__global__ void __launch_bounds__(256) k_map_points_bwd(const uint32_t *__restrict__ cw, int64_t nw, int p0, int m,
-                                                        int64_t B, int64_t S, const float *__restrict__ gx,
-                                                        float *__restrict__ gpts) {
+__global__ void __launch_bounds__(256) k_map_points_bwd(const uint32_t *__restrict__ cw, int64_t nw, int p0, int k,
+                                                        int nf, int m, int64_t B, int64_t S,
+                                                        const float *__restrict__ gx, float *__restrict__ gpts) {
     __shared__ float s_g[512];
     const int P = 1 << m;
     for (int l = threadIdx.x; l < 2 * P; l += blockDim.x) s_g[l] = 0.0f;
@@ -635,7 +697,7 @@ __global__ void __launch_bounds__(256) k_map_points_bwd(const uint32_t *__restri
         const int64_t b = i / S, s = i - b * S;
         const uint32_t *row = cw + b * nw;
         int l = 0;
-        for (int j = 0; j < m; ++j) l = (l << 1) | (int)bit_at(row, p0 + s * m + j);
+        for (int j = 0; j < m; ++j) l = (l << 1) | (int)bit_at(row, tx_position((int)(s * m + j), p0, k, nf));
         const float2 g = reinterpret_cast<const float2 *>(gx)[i];
         atomicAdd(&s_g[2 * l], g.x);
         atomicAdd(&s_g[2 * l + 1], g.y);
@@ -751,6 +813,7 @@ int launch_tx(ldpcx_code_t c, uint64_t seed, uint64_t cw0, const uint64_t *cw0_d
     p.k = c->k;
     p.n_tx = c->n_tx;
     p.p0 = c->p0;
+    p.nf = c->n_fill;
     p.m = m;
     p.scale = qam_scale(m);
     p.seed = seed;
@@ -790,6 +853,21 @@ extern "C" int sim_tx(ldpcx_code_t c, uint64_t seed, uint64_t cw0, int64_t B, in
     if (B == 0) return LDPCX_OK;
     if (!no || !y_out) return LDPCX_E_INVAL;
     return launch_tx(c, seed, cw0, nullptr, B, m, no, no_stride, y_out, info_out, (cudaStream_t)stream);
+}
+
+extern "C" int qam_map_awgn(const uint32_t *bits, int64_t B, int E, int m, uint64_t seed, uint64_t cw0,
+                            const float *no, int64_t no_stride, float *y_out, void *stream) {
+    if (B < 0 || E < 1 || !valid_m(m) || E % m != 0 || (no_stride != 0 && no_stride != 1)) return LDPCX_E_INVAL;
+    if (B == 0) return LDPCX_OK;
+    if (!bits || !no || !y_out) return LDPCX_E_INVAL;
+    const int per = m == 1 ? 4 : 2;
+    const int64_t work = B * (int64_t)((E / m + per - 1) / per);
+    int64_t blocks = (work + 255) / 256;
+    const int64_t cap = (int64_t)sm_count() * 8;
+    if (blocks > cap) blocks = cap;
+    k_map_awgn<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(bits, B, E, (E + 31) / 32, m, qam_scale(m), seed,
+                                                                   cw0, no, no_stride, y_out);
+    return cuda_status(cudaGetLastError());
 }
 
 extern "C" int demap_app(const float *y, const float *no, int64_t no_stride, int64_t B, int64_t syms, int m,
@@ -896,8 +974,8 @@ extern "C" int ldpc_extrinsic(ldpcx_code_t c, const float *app, const float *llr
     int64_t blocks = (B * c->n_tx + 255) / 256;
     const int64_t cap = (int64_t)sm_count() * 8;
     if (blocks > cap) blocks = cap;
-    k_extrinsic<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(app, llr_in, B, c->n, c->p0, c->n_tx, clamp,
-                                                                    out);
+    k_extrinsic<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(app, llr_in, B, c->n, c->p0, c->n_tx, c->k,
+                                                                     c->n_fill, clamp, out);
     return cuda_status(cudaGetLastError());
 }
 
@@ -967,8 +1045,8 @@ extern "C" int map_points_backward(ldpcx_code_t c, const uint32_t *cw, int64_t B
     if (B == 0) return LDPCX_OK;
     if (!cw || !grad_x || !grad_points) return LDPCX_E_INVAL;
     const int64_t S = c->n_tx / m, nw = (c->n + 31) / 32;
-    k_map_points_bwd<<<grid_for(B * S, 4), 256, 0, (cudaStream_t)stream>>>(cw, nw, c->p0, m, B, S, grad_x,
-                                                                         grad_points);
+    k_map_points_bwd<<<grid_for(B * S, 4), 256, 0, (cudaStream_t)stream>>>(cw, nw, c->p0, c->k, c->n_fill, m, B, S,
+                                                                         grad_x, grad_points);
     return cuda_status(cudaGetLastError());
 }
 

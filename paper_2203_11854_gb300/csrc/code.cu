@@ -1,8 +1,11 @@
 // Code construction (seeded 5G-shaped QC-LDPC base matrices), code objects,
 // status helpers. Host code only; the device tables are uploaded lazily.
+#include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <new>
 #include <string>
 #include <vector>
@@ -207,6 +210,7 @@ extern "C" const char *ldpcx_status_str(int status) {
         case LDPCX_E_NONFINITE: return "LDPCX_E_NONFINITE: non-finite input sanitised";
         case LDPCX_E_TIMEOUT: return "LDPCX_E_TIMEOUT: bounded device wait gave up";
         case LDPCX_E_NODEVICE: return "LDPCX_E_NODEVICE: no CUDA device";
+        case LDPCX_E_IO: return "LDPCX_E_IO: checkpoint file could not be read, parsed or written";
         default: return "unknown ldpcx status";
     }
 }
@@ -238,7 +242,7 @@ extern "C" int qc_ldpc_build(const ldpcx_code_params *p, ldpcx_code_t *out) {
     if (rows < 4 || rows > M_full) return LDPCX_E_INVAL;
     if (p->punct_cols < 0 || p->punct_cols > sh.kb) return LDPCX_E_INVAL;
 
-    ldpcx_code *c = new (std::nothrow) ldpcx_code();
+    ldpcx_code *c = ldpcx::fault_alloc() ? nullptr : new (std::nothrow) ldpcx_code();
     if (!c) return LDPCX_E_NOMEM;
     c->params = *p;
     std::vector<int16_t> full;
@@ -280,7 +284,7 @@ extern "C" int qc_ldpc_build_base(const ldpcx_base_params *p, ldpcx_code_t *out)
         }
         if (deg < 2) return LDPCX_E_INVAL;  // every check node needs two edges
     }
-    ldpcx_code *c = new (std::nothrow) ldpcx_code();
+    ldpcx_code *c = ldpcx::fault_alloc() ? nullptr : new (std::nothrow) ldpcx_code();
     if (!c) return LDPCX_E_NOMEM;
     c->params = ldpcx_code_params{0, p->Z, 0ull, 0, p->punct_cols, p->n_tx};
     c->Z = p->Z;
@@ -462,6 +466,36 @@ extern "C" int qc_ldpc_info(ldpcx_code_t c, ldpcx_code_info *info) {
     info->p0 = c->p0;
     info->edges = (int64_t)c->nnz * c->Z;
     info->encodable = c->enc != ldpcx::kEncNone;
+    info->n_fill = c->n_fill;
+    return LDPCX_OK;
+}
+
+extern "C" int qc_ldpc_shorten(ldpcx_code_t code, int k, ldpcx_code_t *out) {
+    if (!code || !out) return LDPCX_E_INVAL;
+    const int K = code->kb * code->Z;
+    if (code->n_fill != 0 || k < code->p0 || k > K || code->p0 + code->n_tx < K) return LDPCX_E_INVAL;
+    if (code->n_tx - (K - k) < 1) return LDPCX_E_INVAL;
+    ldpcx_code *c = ldpcx::fault_alloc() ? nullptr : new (std::nothrow) ldpcx_code();
+    if (!c) return LDPCX_E_NOMEM;
+    c->params = code->params;
+    c->Z = code->Z;
+    c->rows = code->rows;
+    c->cols = code->cols;
+    c->kb = code->kb;
+    c->nnz = code->nnz;
+    c->max_deg = code->max_deg;
+    c->n = code->n;
+    c->p0 = code->p0;
+    c->k = k;
+    c->n_fill = K - k;
+    c->n_tx = code->n_tx - c->n_fill;
+    c->S = code->S;
+    c->blk = code->blk;
+    c->row_ptr = code->row_ptr;
+    c->enc = code->enc;
+    c->inv_words = code->inv_words;
+    c->core_inv = code->core_inv;
+    *out = c;  // device tables are uploaded on first use, as for any code
     return LDPCX_OK;
 }
 
@@ -487,7 +521,7 @@ int code_device(ldpcx_code_t c, DevCode *out) {
         const size_t ni = sizeof(uint32_t) * c->core_inv.size();
         const size_t oi = (nb + nr + 15) / 16 * 16;
         void *p = nullptr;
-        if (cudaMalloc(&p, oi + ni) != cudaSuccess) {
+        if (fault_alloc() || cudaMalloc(&p, oi + ni) != cudaSuccess) {
             cudaGetLastError();
             return LDPCX_E_NOMEM;
         }
@@ -507,6 +541,31 @@ int code_device(ldpcx_code_t c, DevCode *out) {
     return LDPCX_OK;
 }
 
+namespace {
+std::atomic<int> g_fault_kind{-1};  // -1: the environment not read yet
+std::atomic<int> g_fault_after{0};
+std::once_flag g_fault_env;
+
+void fault_from_env() {
+    const char *e = getenv("LDPCX_FAULT");
+    int kind = LDPCX_FAULT_NONE, after = 0;
+    if (e && strncmp(e, "alloc", 5) == 0 && (e[5] == 0 || (e[5] == ':' && sscanf(e + 6, "%d", &after) == 1))) {
+        kind = after >= 0 ? LDPCX_FAULT_ALLOC : LDPCX_FAULT_NONE;
+    }
+    int expect = -1;
+    g_fault_after.store(after < 0 ? 0 : after);
+    g_fault_kind.compare_exchange_strong(expect, kind);  // an ldpcx_fault_set before this wins
+}
+}  // namespace
+
+bool fault_alloc() {
+    std::call_once(g_fault_env, fault_from_env);
+    if (g_fault_kind.load() != LDPCX_FAULT_ALLOC) return false;
+    if (g_fault_after.fetch_sub(1) > 0) return false;
+    g_fault_kind.store(LDPCX_FAULT_NONE);  // one shot
+    return true;
+}
+
 int sm_count() {
     static int cached[64] = {0};
     int dev = 0;
@@ -521,3 +580,11 @@ int sm_count() {
 }
 
 }  // namespace ldpcx
+
+extern "C" int ldpcx_fault_set(int kind, int after) {
+    if ((kind != LDPCX_FAULT_NONE && kind != LDPCX_FAULT_ALLOC) || after < 0) return LDPCX_E_INVAL;
+    std::call_once(ldpcx::g_fault_env, ldpcx::fault_from_env);
+    ldpcx::g_fault_after.store(after);
+    ldpcx::g_fault_kind.store(kind);
+    return LDPCX_OK;
+}

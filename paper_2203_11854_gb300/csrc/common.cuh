@@ -38,6 +38,7 @@ constexpr int kEncCoreInv = 2;   // any invertible core: its inverse
 struct ldpcx_code {
     ldpcx_code_params params;
     int Z, rows, cols, kb, nnz, max_deg, n, k, n_tx, p0;
+    int n_fill = 0;                // filler bits at positions k .. k + n_fill - 1 (qc_ldpc_shorten)
     std::vector<int16_t> S;        // rows x cols base matrix, -1 = zero block
     std::vector<uint32_t> blk;     // nonzero blocks in row-major order
     std::vector<int32_t> row_ptr;  // rows + 1
@@ -70,10 +71,25 @@ int launch_tx(ldpcx_code_t c, uint64_t seed, uint64_t cw0, const uint64_t *cw0_d
               const float *no, int64_t no_stride, float *y_out, uint32_t *info_out, cudaStream_t stream,
               uint32_t *cw_out = nullptr, const float *points = nullptr);
 
+// Host fault injection (ldpcx_fault_set, LDPCX_FAULT): true when the armed
+// one-shot allocation failure fires for this allocation.
+bool fault_alloc();
+
+// The codewords-per-CTA tuning knob (LDPCX_TUNE_CW_PER_CTA): 0 = automatic,
+// else a cap on the codewords one CTA decodes together.
+int tune_cw_per_cta();
+
 // Per-device cached attribute: SM count.
 int sm_count();
 
 inline int cuda_status(cudaError_t e) { return e == cudaSuccess ? LDPCX_OK : LDPCX_E_CUDA; }
+
+// Codeword position of transmitted bit t: the transmit layout starts at p0 and
+// skips the n_fill filler positions k .. k + n_fill - 1 of a shortened code.
+__host__ __device__ __forceinline__ int tx_position(int t, int p0, int k, int n_fill) {
+    const int v = p0 + t;
+    return v >= k ? v + n_fill : v;
+}
 
 // Set the device status word (atomic OR) -- used for conditions only the GPU sees.
 __device__ __forceinline__ void latch(unsigned int *word, unsigned int flag) { atomicOr(word, flag); }

@@ -6,7 +6,7 @@
 #include <algorithm>
 #include <atomic>
 
-#include "decode_edge_sched.cuh"
+#include "decode_plan.cuh"
 
 namespace ldpcx {
 namespace {
@@ -87,6 +87,8 @@ int pick_G(const ldpcx_code *c, bool layered) {
 
 }  // namespace
 
+int tune_cw_per_cta() { return g_cw_per_cta.load(); }
+
 unsigned int take_status_decode(cudaStream_t s) {
     unsigned int v = 0, zero = 0;
     if (cudaMemcpyFromSymbolAsync(&v, g_status, sizeof(v), 0, cudaMemcpyDeviceToHost, s) != cudaSuccess) return 0;
@@ -154,9 +156,33 @@ int decode_impl(ldpcx_code_t c, const float *llr_ch, int64_t B, const ldpcx_deco
     DevCode d;
     st = code_device(c, &d);
     if (st) return st;
+    DecodePlan pl;
+    st = decode_plan(c, o, &pl);
+    if (st) return st;
+    // the workspace holds per-edge messages; check-node state uses the same per-codeword stride
+    const Params p = decode_params(c, d.blk, d.row_ptr, llr_ch, B, o, llr_out, bits_out, iters_out, ws,
+                                   msg_stride(c), ckpt, pl.layered);
+    if (!p.status) return LDPCX_E_CUDA;
+    return decode_launch(pl, c, p, B, stream);
+}
 
+// The adjoint supports weighted flooding sum-product with FP32 messages and a
+// fixed iteration count.
+int check_differentiable(const ldpcx_code *c, const ldpcx_decode_opts *o) {
+    int st = check_opts(c, o);
+    if (st) return st;
+    if (o->algo != LDPCX_FLOOD_SPA || o->msg_prec != LDPCX_MSG_F32 || o->early_stop) return LDPCX_E_UNSUPPORTED;
+    if (c->n_fill) return LDPCX_E_UNSUPPORTED;  // the adjoint reads the channel LLRs in the unshortened layout
+    return LDPCX_OK;
+}
+
+}  // namespace
+
+int dec::decode_plan(const ldpcx_code *c, const ldpcx_decode_opts *o, DecodePlan *pl) {
+    *pl = DecodePlan{};
     const bool layered = o->algo == LDPCX_LAYERED_MINSUM || o->algo == LDPCX_LAYERED_SPA;
     const int algo = (o->algo == LDPCX_LAYERED_MINSUM || o->algo == LDPCX_FLOOD_MINSUM) ? kMinSum : kSpa;
+    pl->layered = layered;
     int zpt = 1;
     if (layered) {
         const int want = g_zpt.load();
@@ -168,40 +194,8 @@ int decode_impl(ldpcx_code_t c, const float *llr_ch, int64_t B, const ldpcx_deco
         fn = pick_kernel(c->max_deg, layered, algo, o->msg_prec, zpt, c->Z);
     }
     if (!fn) return LDPCX_E_UNSUPPORTED;
-
-    Params p{};
-    p.blk = d.blk;
-    p.row_ptr = d.row_ptr;
-    p.Z = c->Z;
-    p.rows = c->rows;
-    p.nnz = c->nnz;
-    p.n = c->n;
-    p.k = c->k;
-    p.n_tx = c->n_tx;
-    p.p0 = c->p0;
-    p.iters = o->iters;
-    p.early_stop = o->early_stop;
-    p.offset = o->offset;
-    p.clamp = o->clamp;
-    p.phi_lo = (float)log1p(2.0 / expm1((double)o->clamp));
-    p.llr = llr_ch;
-    p.msg = ws;
-    p.msg_stride = msg_stride(c);
-    p.weights = o->weights;
-    p.ckpt = ckpt;
-    p.ckpt_tstride = B * msg_stride(c);
-    p.llr_out = llr_out;
-    p.bits_out = bits_out;
-    p.iters_out = iters_out;
-    p.B = B;
-    p.G = pick_G(c, layered);
-    p.pf_dist = layered ? g_pf_dist.load() : 0;
-    p.msg_size = (int)msg_bytes(o->msg_prec);
-    p.status = status_word_decode();
-    if (!p.status) return LDPCX_E_CUDA;
-    set_int_constants(p);
-
-    size_t smem = smem_bytes(p, layered ? 1 : 2);
+    pl->fn = fn;
+    pl->zpt = zpt;
     // layered sum-product on a full base graph: per-edge messages, compiled-in schedule
     if (layered && algo == kSpa && zpt == 1 && g_sched.load()) {
         // the per-edge kernel compiles the full schedule: truncated codes take the row table
@@ -210,44 +204,90 @@ int decode_impl(ldpcx_code_t c, const float *llr_ch, int64_t B, const ldpcx_deco
         SchedFn sf = bg && c->nnz <= kSchedMaxBlocks
                          ? layered_edge_sched_kernel(bg, algo, o->msg_prec, g_specialised.load() ? c->Z : 0)
                          : nullptr;
-        if (sf) return launch_sched(sf, c, p, B, 1, stream);
+        if (sf) {
+            pl->sf = sf;
+            pl->kpt = 1;
+            return LDPCX_OK;
+        }
     }
     if (layered && algo == kMinSum && zpt == 1 && g_cns.load() &&
-        cns_bytes(c, o->msg_prec) <= p.msg_stride * p.msg_size) {
+        cns_bytes(c, o->msg_prec) <= msg_stride(c) * (int64_t)msg_bytes(o->msg_prec)) {
         const int zs = g_specialised.load() ? c->Z : 0;
         const int bg = g_sched.load() ? sched_shape(c) : 0;
         const bool trunc = bg && c->rows != (bg == 1 ? Sched<1>::rows : Sched<2>::rows);
         const int kpt = !trunc && g_zpt.load() == 2 && c->Z % 2 == 0 ? 2 : 1;  // check nodes per thread
         SchedFn sf = bg && c->nnz <= kSchedMaxBlocks ? layered_cns_sched_kernel(bg, o->msg_prec, zs, kpt, trunc)
                                                      : nullptr;
-        if (sf) return launch_sched(sf, c, p, B, kpt, stream);
+        if (sf) {
+            pl->sf = sf;
+            pl->kpt = kpt;
+            pl->cns = true;
+            return LDPCX_OK;
+        }
         KernelFn f = layered_cns_kernel(c->max_deg, o->msg_prec, zs);
         if (f) {
-            fn = f;
-            smem = cns_smem_bytes(p);
+            pl->fn = f;
+            pl->cns = true;
         }
     }
-    if (smem > 227 * 1024) return LDPCX_E_UNSUPPORTED;
-    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-        return LDPCX_E_CUDA;
-    int threads = layered ? p.G * (p.Z / zpt) : p.G * p.Z * flood_tpc(p.Z);
-    threads = (threads + 31) / 32 * 32;
-    const int64_t grid = (B + p.G - 1) / p.G;
-    if (grid > 0x7FFFFFFF) return LDPCX_E_INVAL;
-    fn<<<(unsigned)grid, threads, smem, (cudaStream_t)stream>>>(p);
-    return cuda_status(cudaGetLastError());
-}
-
-// The adjoint supports weighted flooding sum-product with FP32 messages and a
-// fixed iteration count.
-int check_differentiable(const ldpcx_code *c, const ldpcx_decode_opts *o) {
-    int st = check_opts(c, o);
-    if (st) return st;
-    if (o->algo != LDPCX_FLOOD_SPA || o->msg_prec != LDPCX_MSG_F32 || o->early_stop) return LDPCX_E_UNSUPPORTED;
     return LDPCX_OK;
 }
 
-}  // namespace
+int64_t dec::decode_plan_bytes_per_cw(const ldpcx_code *c, const ldpcx_decode_opts *o, const DecodePlan &pl) {
+    return pl.cns ? cns_bytes(c, o->msg_prec) : msg_stride(c) * (int64_t)msg_bytes(o->msg_prec);
+}
+
+dec::Params dec::decode_params(const ldpcx_code *c, const uint32_t *blk, const int32_t *row_ptr,
+                               const float *llr_ch, int64_t B, const ldpcx_decode_opts *o, float *llr_out,
+                               uint32_t *bits_out, int32_t *iters_out, void *msg, int64_t stride, float *ckpt,
+                               bool layered) {
+    Params p{};
+    p.blk = blk;
+    p.row_ptr = row_ptr;
+    p.Z = c->Z;
+    p.rows = c->rows;
+    p.nnz = c->nnz;
+    p.n = c->n;
+    p.k = c->k;
+    p.n_tx = c->n_tx;
+    p.p0 = c->p0;
+    p.nf = c->n_fill;
+    p.iters = o->iters;
+    p.early_stop = o->early_stop;
+    p.offset = o->offset;
+    p.clamp = o->clamp;
+    p.phi_lo = (float)log1p(2.0 / expm1((double)o->clamp));
+    p.llr = llr_ch;
+    p.msg = msg;
+    p.msg_stride = stride;
+    p.weights = o->weights;
+    p.ckpt = ckpt;
+    p.ckpt_tstride = B * stride;
+    p.llr_out = llr_out;
+    p.bits_out = bits_out;
+    p.iters_out = iters_out;
+    p.B = B;
+    p.G = pick_G(c, layered);
+    p.pf_dist = layered ? g_pf_dist.load() : 0;
+    p.msg_size = (int)msg_bytes(o->msg_prec);
+    p.status = status_word_decode();
+    set_int_constants(p);
+    return p;
+}
+
+int dec::decode_launch(const DecodePlan &pl, const ldpcx_code *c, const Params &p, int64_t B, void *stream) {
+    if (pl.sf) return launch_sched(pl.sf, c, p, B, pl.kpt, stream);
+    const size_t smem = pl.cns ? cns_smem_bytes(p) : smem_bytes(p, pl.layered ? 1 : 2);
+    if (smem > 227 * 1024) return LDPCX_E_UNSUPPORTED;
+    if (cudaFuncSetAttribute(pl.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return LDPCX_E_CUDA;
+    int threads = pl.layered ? p.G * (p.Z / pl.zpt) : p.G * p.Z * flood_tpc(p.Z);
+    threads = (threads + 31) / 32 * 32;
+    const int64_t grid = (B + p.G - 1) / p.G;
+    if (grid > 0x7FFFFFFF) return LDPCX_E_INVAL;
+    pl.fn<<<(unsigned)grid, threads, smem, (cudaStream_t)stream>>>(p);
+    return cuda_status(cudaGetLastError());
+}
 
 size_t ckpt_bytes(const ldpcx_code *c, int64_t B, int iters) {
     return sizeof(float) * (size_t)(iters > 1 ? iters - 1 : 1) * (size_t)B * (size_t)msg_stride(c);

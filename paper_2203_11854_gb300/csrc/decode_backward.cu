@@ -312,6 +312,7 @@ int check_bwd(const ldpcx_code *c, const ldpcx_decode_opts *o) {
     int st = ldpc_bp_workspace(const_cast<ldpcx_code *>(c), 1, o, &tmp);  // validates the options
     if (st) return st;
     if (o->algo != LDPCX_FLOOD_SPA || o->msg_prec != LDPCX_MSG_F32 || o->early_stop) return LDPCX_E_UNSUPPORTED;
+    if (c->n_fill) return LDPCX_E_UNSUPPORTED;  // channel LLRs are read in the unshortened layout
     if (bwd_smem(1, c->n, c->nnz, c->rows) > 216 * 1024) return LDPCX_E_UNSUPPORTED;
     return LDPCX_OK;
 }

@@ -155,13 +155,8 @@ __global__ void __launch_bounds__(512, TPC > 1 ? 2 : 1) k_flooding(const Params 
             for (int gg = 0; gg < p.G; ++gg) {
                 const int64_t c2 = cw_base + gg;
                 const bool keep = s_done[gg] != 0;
-                for (int v = threadIdx.x; v < p.n; v += blockDim.x) {
-                    float x = 0.0f;
-                    const int tt = v - p.p0;
-                    if (keep) x = cur[(size_t)gg * p.n + v];
-                    else if (c2 < p.B && tt >= 0 && tt < p.n_tx) x = clamp_llr(p.llr[c2 * p.n_tx + tt], p.clamp, bad);
-                    nxt[(size_t)gg * p.n + v] = x;
-                }
+                for (int v = threadIdx.x; v < p.n; v += blockDim.x)
+                    nxt[(size_t)gg * p.n + v] = keep ? cur[(size_t)gg * p.n + v] : channel_llr(p, c2, v, bad);
             }
         }
         __syncthreads();

@@ -98,6 +98,7 @@ struct Params {
     const uint32_t *blk;
     const int32_t *row_ptr;
     int Z, rows, nnz, n, k, n_tx, p0;
+    int nf;                       // filler bits at positions k .. k + nf - 1 (known zeros, not transmitted)
     int iters, early_stop;
     float offset, clamp, phi_lo;  // phi_lo = phi(clamp)
     const float *llr;             // [B][n_tx]
@@ -151,12 +152,22 @@ __device__ __forceinline__ float4 clamp_llr4(float4 x, float c, bool &bad) {
                        clamp_llr(x.w, c, bad) + 0.0f);
 }
 
+// Channel LLR of codeword position v (clamped; +0.0 for -0.0): punctured and
+// untransmitted positions 0, filler bits of a shortened code +clamp (a known
+// zero), the rest from the transmit layout.
+__device__ __forceinline__ float channel_llr(const Params &p, int64_t cw, int v, bool &bad) {
+    if (v >= p.k && v < p.k + p.nf) return p.clamp;
+    const int t = v - p.p0 - (v >= p.k ? p.nf : 0);
+    if (cw < p.B && v >= p.p0 && t < p.n_tx) return clamp_llr(p.llr[cw * p.n_tx + t], p.clamp, bad) + 0.0f;
+    return 0.0f;
+}
+
 // Load the channel LLRs of the CTA's codewords into app (placed: punctured and
 // untransmitted positions are 0). When the row layout allows, 16-byte loads,
 // four per thread in flight (streaming: the LLRs are read once).
 __device__ inline void load_channel(const Params &p, float *app, int64_t cw_base) {
     bool bad = false;
-    if (((p.p0 | p.n_tx | p.n) & 3) == 0 && (reinterpret_cast<uintptr_t>(p.llr) & 15u) == 0) {
+    if (p.nf == 0 && ((p.p0 | p.n_tx | p.n) & 3) == 0 && (reinterpret_cast<uintptr_t>(p.llr) & 15u) == 0) {
         const int bd = blockDim.x, n4 = p.n_tx >> 2;
         for (int g = 0; g < p.G; ++g) {
             const int64_t cw = cw_base + g;
@@ -185,12 +196,7 @@ __device__ inline void load_channel(const Params &p, float *app, int64_t cw_base
     }
     for (int g = 0; g < p.G; ++g) {
         const int64_t cw = cw_base + g;
-        for (int v = threadIdx.x; v < p.n; v += blockDim.x) {
-            float x = 0.0f;
-            const int t = v - p.p0;
-            if (cw < p.B && t >= 0 && t < p.n_tx) x = clamp_llr(p.llr[cw * p.n_tx + t], p.clamp, bad);
-            app[(size_t)g * p.n + v] = x + 0.0f;  // -0.0 -> +0.0 (same value)
-        }
+        for (int v = threadIdx.x; v < p.n; v += blockDim.x) app[(size_t)g * p.n + v] = channel_llr(p, cw, v, bad);
     }
     if (bad) latch(p.status, LDPCX_FLAG_NONFINITE);
 }

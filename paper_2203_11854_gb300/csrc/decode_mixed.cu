@@ -21,6 +21,7 @@ struct GroupDesc {
     const uint32_t *blk;
     const int32_t *row_ptr;
     int Z, rows, nnz, n, k, n_tx, p0, G;
+    int nf;   // filler bits of a shortened code
     int cns;  // min-sum with check-node state in the message slot
     int bg;   // 1 or 2: the rows follow that shape's base graph (compiled schedule); 0: row table
     int64_t B, stride;
@@ -70,6 +71,7 @@ __global__ void __launch_bounds__(kMaxThreads, 2) k_mixed(const MixedParams m) {
         p.k = gd.k;
         p.n_tx = gd.n_tx;
         p.p0 = gd.p0;
+        p.nf = gd.nf;
         p.iters = m.iters;
         p.early_stop = m.early_stop;
         p.offset = m.offset;
@@ -134,12 +136,15 @@ MixedFn pick_mixed(int dmax, int algo, int prec) {
 
 size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
-// Codewords per CTA for a code (same rule as ldpc_bp_decode's layered path).
+// Codewords per CTA for a code (same rule as ldpc_bp_decode's layered path,
+// including the LDPCX_TUNE_CW_PER_CTA cap): the codewords of one work item.
 int group_G(const ldpcx_code *c) {
     const size_t per_cw = sizeof(float) * (size_t)c->n;
     int G = kMaxThreads / c->Z;
     if (G < 1) G = 1;
     while (G > 1 && per_cw * G > 105 * 1024) --G;
+    const int want = tune_cw_per_cta();
+    if (want > 0 && want < G) G = want;
     return G;
 }
 
@@ -254,6 +259,7 @@ extern "C" int ldpc_bp_decode_mixed(const ldpcx_batch_group *groups, int n_group
         gd.k = c->k;
         gd.n_tx = c->n_tx;
         gd.p0 = c->p0;
+        gd.nf = c->n_fill;
         gd.G = group_G(c);
         gd.B = g.B;
         gd.stride = stride_of(c);

@@ -16,7 +16,7 @@
 
 #include <mutex>
 
-#include "decode_kernels.cuh"
+#include "decode_plan.cuh"
 
 namespace {
 
@@ -67,46 +67,33 @@ int scratch_address(unsigned char **out) {
 
 size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
-// Codewords per CTA (same rule as ldpc_bp_decode): ~384 check-node threads,
-// bounded by two CTAs per SM (layered) or one (flooding).
-int codewords_per_cta(const ldpcx_code *c, bool layered) {
-    const size_t per_cw = sizeof(float) * (size_t)c->n * (layered ? 1 : 2);
-    const int tpc = layered ? 1 : flood_tpc(c->Z);
-    const size_t budget = layered || tpc > 1 ? 105 * 1024 : 210 * 1024;
-    int G = layered ? kMaxThreads / c->Z : 512 / (c->Z * tpc);
-    if (G < 1) G = 1;
-    while (G > 1 && per_cw * G > budget) --G;
-    return G;
-}
-
 }  // namespace
 
 extern "C" int ldpc_bp_decode_noalloc(ldpcx_code_t c, const float *llr_ch, int64_t B, const ldpcx_decode_opts *o,
                                       float *llr_out, uint32_t *bits_out, int32_t *iters_out, void *stream) {
     if (!c || B < 0 || (B > 0 && !llr_ch)) return LDPCX_E_INVAL;
-    size_t msg_bytes = 0;
-    int st = ldpc_bp_workspace(c, B, o, &msg_bytes);  // validates the options
+    size_t ws_unused = 0;
+    int st = ldpc_bp_workspace(c, 0, o, &ws_unused);  // validates the options
     if (st) return st;
     if (B == 0) return LDPCX_OK;
     const int words = c->nnz + c->rows + 1;
     if (words > kMaxTableWords) return LDPCX_E_UNSUPPORTED;
+    // the kernel ldpc_bp_decode would run, and the bytes each codeword's messages (or check-node state) take
+    DecodePlan pl;
+    st = decode_plan(c, o, &pl);
+    if (st) return st;
+    const int64_t per_cw = decode_plan_bytes_per_cw(c, o, pl);
+    const int msg_size = o->msg_prec == LDPCX_MSG_F32 ? 4 : o->msg_prec == LDPCX_MSG_F16 ? 2 : 1;
     const size_t table_bytes = align256(sizeof(uint32_t) * (size_t)words);
-    if (msg_bytes > (size_t)LDPCX_NOALLOC_SCRATCH_BYTES - table_bytes) return LDPCX_E_WORKSPACE;
+    // B is bounded by the array before any product is formed
+    const int64_t capacity =
+        per_cw > 0 ? (int64_t)(((size_t)LDPCX_NOALLOC_SCRATCH_BYTES - table_bytes) / (size_t)per_cw) : 0;
+    if (B > capacity) return LDPCX_E_WORKSPACE;
+    if (per_cw % 16 != 0) return LDPCX_E_UNSUPPORTED;  // every codeword's state starts on a 16-byte boundary
 
     unsigned char *scratch = nullptr;
     st = scratch_address(&scratch);
     if (st) return st;
-    unsigned int *status = status_word_decode();
-    if (!status) return LDPCX_E_CUDA;
-
-    const bool layered = o->algo == LDPCX_LAYERED_MINSUM || o->algo == LDPCX_LAYERED_SPA;
-    const int algo = (o->algo == LDPCX_LAYERED_MINSUM || o->algo == LDPCX_FLOOD_MINSUM) ? kMinSum : kSpa;
-    KernelFn fn = nullptr;
-    if (!layered) fn = flooding_kernel(c->max_deg, algo, o->msg_prec, flood_tpc(c->Z));
-    else if (o->msg_prec == kF32) fn = layered_kernel_f32(c->max_deg, algo, 1);
-    else if (o->msg_prec == kF16) fn = layered_kernel_f16(c->max_deg, algo, 1);
-    else fn = layered_kernel_fix6(c->max_deg, algo, 1);
-    if (!fn) return LDPCX_E_UNSUPPORTED;
 
     cudaStream_t s = (cudaStream_t)stream;
     TablesByValue t;
@@ -117,41 +104,10 @@ extern "C" int ldpc_bp_decode_noalloc(ldpcx_code_t c, const float *llr_ch, int64
     k_put_tables<<<1, 256, 0, s>>>(t, tables);
     if (cudaGetLastError() != cudaSuccess) return LDPCX_E_CUDA;
 
-    const int64_t E = (int64_t)c->nnz * c->Z;
-    Params p{};
-    p.blk = tables;
-    p.row_ptr = reinterpret_cast<const int32_t *>(tables + c->nnz);
-    p.Z = c->Z;
-    p.rows = c->rows;
-    p.nnz = c->nnz;
-    p.n = c->n;
-    p.k = c->k;
-    p.n_tx = c->n_tx;
-    p.p0 = c->p0;
-    p.iters = o->iters;
-    p.early_stop = o->early_stop;
-    p.offset = o->offset;
-    p.clamp = o->clamp;
-    p.phi_lo = (float)log1p(2.0 / expm1((double)o->clamp));
-    p.llr = llr_ch;
-    p.msg = scratch + table_bytes;
-    p.msg_stride = (E + 127) / 128 * 128;
-    p.weights = o->weights;
-    p.llr_out = llr_out;
-    p.bits_out = bits_out;
-    p.iters_out = iters_out;
-    p.B = B;
-    p.G = codewords_per_cta(c, layered);
-    p.pf_dist = 0;
-    p.msg_size = o->msg_prec == kF32 ? 4 : o->msg_prec == kF16 ? 2 : 1;
-    p.status = status;
-
-    const size_t smem = smem_bytes(p, layered ? 1 : 2);
-    if (smem > 227 * 1024) return LDPCX_E_UNSUPPORTED;
-    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-        return LDPCX_E_CUDA;
-    const int threads = (p.G * p.Z * (layered ? 1 : flood_tpc(p.Z)) + 31) / 32 * 32;
-    const int64_t grid = (B + p.G - 1) / p.G;
-    fn<<<(unsigned)grid, threads, smem, s>>>(p);
-    return cudaGetLastError() == cudaSuccess ? LDPCX_OK : LDPCX_E_CUDA;
+    // messages packed at the plan's own per-codeword size (check-node state for layered min-sum)
+    const Params p = decode_params(c, tables, reinterpret_cast<const int32_t *>(tables + c->nnz), llr_ch, B, o,
+                                   llr_out, bits_out, iters_out, scratch + table_bytes, per_cw / msg_size, nullptr,
+                                   pl.layered);
+    if (!p.status) return LDPCX_E_CUDA;
+    return decode_launch(pl, c, p, B, stream);
 }

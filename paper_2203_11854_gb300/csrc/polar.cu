@@ -46,7 +46,10 @@ int polar_device(ldpcx_polar *c, const int32_t **info, const uint8_t **frozen) {
         }
         void *mem = nullptr;
         const size_t bi = sizeof(int32_t) * (size_t)std::max(1, c->K), bf = (size_t)c->N;
-        if (cudaMalloc(&mem, bi + bf) != cudaSuccess) return LDPCX_E_NOMEM;
+        if (fault_alloc() || cudaMalloc(&mem, bi + bf) != cudaSuccess) {
+            cudaGetLastError();
+            return LDPCX_E_NOMEM;
+        }
         c->d_info = (int32_t *)mem;
         c->d_frozen = (uint8_t *)mem + bi;
         if (cudaMemcpy(c->d_info, c->info.data(), sizeof(int32_t) * c->K, cudaMemcpyHostToDevice) != cudaSuccess ||
@@ -482,7 +485,7 @@ using namespace ldpcx;
 extern "C" int polar_build(int n, int K, float design_esn0_db, uint64_t crc_poly, int crc_r, ldpcx_polar_t *out) {
     if (!out || n < 2 || n > 10 || K < 1 || K > (1 << n) || crc_r < 0 || crc_r >= K || crc_r > 32) return LDPCX_E_INVAL;
     if (crc_r > 0 && !((crc_poly >> crc_r) & 1ull)) return LDPCX_E_INVAL;  // the x^r term
-    ldpcx_polar *c = new (std::nothrow) ldpcx_polar();
+    ldpcx_polar *c = fault_alloc() ? nullptr : new (std::nothrow) ldpcx_polar();
     if (!c) return LDPCX_E_NOMEM;
     c->n = n;
     c->N = 1 << n;

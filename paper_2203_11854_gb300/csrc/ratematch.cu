@@ -1,6 +1,7 @@
 // Circular-buffer rate matching of codewords and soft recovery of received
 // LLRs (the rate matching of the 5G NR LDPC chain, with the start position and
-// buffer size given by the caller). Both are index work: one thread per output
+// buffer size given by the caller). The buffer is the transmit layout: codeword
+// positions from p0 on, without a shortened code's filler bits. Both are index work: one thread per output
 // bit (ballot-packed per warp) and one thread per buffer position (a gather in
 // increasing k, so no atomics and the sums run in a fixed order).
 #include "common.cuh"
@@ -11,6 +12,7 @@ namespace {
 struct RmParams {
     int64_t B;
     int p0, ncb, k0, E, qm, C;  // C = E / qm columns of the interleaver
+    int k, nf;                  // a shortened code's filler positions k .. k + nf - 1 are not in the buffer
     int nw_in, nw_out;          // packed words per codeword in / out
 };
 
@@ -30,7 +32,7 @@ __global__ void __launch_bounds__(256) k_rate_match(const RmParams p, const uint
         if (f < p.E) {
             const int i = f / p.qm, j = f - i * p.qm;  // f = i qm + j  <-  k = j C + i
             const int64_t k = (int64_t)j * p.C + i;
-            const int pos = p.p0 + (int)((p.k0 + k) % p.ncb);
+            const int pos = tx_position((int)((p.k0 + k) % p.ncb), p.p0, p.k, p.nf);
             bit = (cw[b * p.nw_in + (pos >> 5)] >> (pos & 31)) & 1u;
         }
         const unsigned word = __ballot_sync(0xFFFFFFFFu, bit);
@@ -55,7 +57,7 @@ __global__ void __launch_bounds__(256) k_rate_recover(const RmParams p, const fl
 
 int rm_check(const ldpcx_code *c, int64_t B, int k0, int ncb, int E, int qm) {
     if (!c || B < 0) return LDPCX_E_INVAL;
-    if (ncb < 1 || ncb > c->n - c->p0 || k0 < 0 || k0 >= ncb || E < 1) return LDPCX_E_INVAL;
+    if (ncb < 1 || ncb > c->n - c->p0 - c->n_fill || k0 < 0 || k0 >= ncb || E < 1) return LDPCX_E_INVAL;
     if (!(qm == 1 || qm == 2 || qm == 4 || qm == 6 || qm == 8) || E % qm) return LDPCX_E_INVAL;
     return LDPCX_OK;
 }
@@ -64,6 +66,8 @@ RmParams rm_params(const ldpcx_code *c, int64_t B, int k0, int ncb, int E, int q
     RmParams p{};
     p.B = B;
     p.p0 = c->p0;
+    p.k = c->k;
+    p.nf = c->n_fill;
     p.ncb = ncb;
     p.k0 = k0;
     p.E = E;

@@ -15,13 +15,135 @@
 // ended by stop_ber) discards that front and runs the right one. Codeword
 // indices follow the batches actually counted, so both modes give the same
 // counts.
+#include <errno.h>
+#include <inttypes.h>
 #include <math.h>
+#include <stdio.h>
+#include <string.h>
 
+#include <string>
 #include <vector>
 
 #include "common.cuh"
 
 namespace {
+
+// ---------------------------------------------------------------- checkpoints
+// FNV-1a (64 bit) over everything that fixes a sweep's counts.
+struct Fnv {
+    uint64_t h = 0xcbf29ce484222325ull;
+    void bytes(const void *p, size_t n) {
+        const unsigned char *b = (const unsigned char *)p;
+        for (size_t i = 0; i < n; ++i) {
+            h ^= b[i];
+            h *= 0x100000001b3ull;
+        }
+    }
+    template <typename T> void put(const T &v) { bytes(&v, sizeof(v)); }
+};
+
+uint64_t fingerprint(const ldpcx_sim_config *c) {
+    Fnv f;
+    const ldpcx_code *code = c->code;
+    const int shape[] = {code->Z, code->rows, code->cols, code->kb, code->n, code->k, code->n_tx, code->p0,
+                         code->n_fill};
+    f.bytes(shape, sizeof(shape));
+    f.bytes(code->S.data(), sizeof(int16_t) * code->S.size());
+    f.put(c->m);
+    f.put(c->demap_method);
+    f.put(c->demap_clamp);
+    f.put(c->dec.algo);
+    f.put(c->dec.iters);
+    f.put(c->dec.msg_prec);
+    f.put(c->dec.early_stop);
+    f.put(c->dec.offset);
+    f.put(c->dec.clamp);
+    f.put(c->seed);
+    f.put(c->cw0);
+    f.put(c->batch);
+    f.put(c->max_batches);
+    f.put(c->min_bit_errors);
+    f.put(c->stop_ber);
+    f.put(c->n_snr);
+    for (int i = 0; i < c->n_snr; ++i) f.put(c->ebn0_db[i]);
+    return f.h;
+}
+
+struct Ckpt {
+    uint64_t fp = 0, next_cw = 0;
+    int next_point = 0, finished = 0;
+    std::vector<ldpcx_sim_counts> pts;
+};
+
+const char *kCkptFormat = "ldpcx-sim-checkpoint";
+
+// Write the state as JSON, one item per line, to path + ".tmp", then rename it
+// over path (atomic on POSIX file systems: a reader sees the old or the new state).
+int write_ckpt(const char *path, const ldpcx_sim_config *c, const Ckpt &k) {
+    const std::string tmp = std::string(path) + ".tmp";
+    FILE *f = fopen(tmp.c_str(), "w");
+    if (!f) return LDPCX_E_IO;
+    bool ok = fprintf(f, "{\n \"format\": \"%s\",\n \"version\": 1,\n \"fingerprint\": \"%016" PRIx64 "\",\n",
+                      kCkptFormat, k.fp) > 0;
+    ok = ok && fprintf(f, " \"next_point\": %d,\n \"next_cw\": %" PRIu64 ",\n \"finished\": %d,\n \"points\": [\n",
+                       k.next_point, k.next_cw, k.finished) > 0;
+    for (int i = 0; ok && i < k.next_point; ++i) {
+        const ldpcx_sim_counts &q = k.pts[(size_t)i];
+        ok = fprintf(f,
+                     "  {\"ebn0_db\": %.17g, \"bits\": %" PRId64 ", \"bit_errors\": %" PRId64 ", \"blocks\": %" PRId64
+                     ", \"block_errors\": %" PRId64 ", \"iter_sum\": %" PRId64 "}%s\n",
+                     c->ebn0_db[i], q.bits, q.bit_errors, q.blocks, q.block_errors, q.iter_sum,
+                     i + 1 < k.next_point ? "," : "") > 0;
+    }
+    ok = ok && fprintf(f, " ]\n}\n") > 0;
+    ok = (fflush(f) == 0) && ok;
+    ok = (fclose(f) == 0) && ok;
+    if (!ok || rename(tmp.c_str(), path) != 0) {
+        remove(tmp.c_str());
+        return LDPCX_E_IO;
+    }
+    return LDPCX_OK;
+}
+
+// Read a checkpoint this library wrote for the sweep with fingerprint fp:
+// LDPCX_OK (loaded), 1 (no file), LDPCX_E_IO (unreadable, malformed or of another sweep).
+int read_ckpt(const char *path, const ldpcx_sim_config *c, uint64_t fp, Ckpt *k) {
+    FILE *f = fopen(path, "r");
+    if (!f) return errno == ENOENT ? 1 : LDPCX_E_IO;
+    std::vector<std::string> lines;
+    char buf[512];
+    while (fgets(buf, sizeof(buf), f)) lines.emplace_back(buf);
+    fclose(f);
+    if (lines.size() < 9) return LDPCX_E_IO;
+    char fmt[64] = {0};
+    int version = 0;
+    unsigned long long fpv = 0, ncw = 0;
+    if (lines[0] != "{\n" || sscanf(lines[1].c_str(), " \"format\": \"%63[^\"]\",", fmt) != 1 || strcmp(fmt, kCkptFormat) ||
+        sscanf(lines[2].c_str(), " \"version\": %d,", &version) != 1 || version != 1 ||
+        sscanf(lines[3].c_str(), " \"fingerprint\": \"%16llx\",", &fpv) != 1 || fpv != fp ||
+        sscanf(lines[4].c_str(), " \"next_point\": %d,", &k->next_point) != 1 ||
+        sscanf(lines[5].c_str(), " \"next_cw\": %llu,", &ncw) != 1 ||
+        sscanf(lines[6].c_str(), " \"finished\": %d,", &k->finished) != 1 || lines[7] != " \"points\": [\n")
+        return LDPCX_E_IO;
+    if (k->next_point < 0 || k->next_point > c->n_snr || (k->finished != 0 && k->finished != 1)) return LDPCX_E_IO;
+    if (lines.size() != (size_t)k->next_point + 10) return LDPCX_E_IO;
+    k->fp = fpv;
+    k->next_cw = ncw;
+    k->pts.assign((size_t)k->next_point, ldpcx_sim_counts{0, 0, 0, 0, 0});
+    for (int i = 0; i < k->next_point; ++i) {
+        double eb = 0.0;
+        long long v[5] = {0, 0, 0, 0, 0};
+        if (sscanf(lines[(size_t)8 + i].c_str(),
+                   "  {\"ebn0_db\": %lf, \"bits\": %lld, \"bit_errors\": %lld, \"blocks\": %lld, \"block_errors\": %lld, "
+                   "\"iter_sum\": %lld}",
+                   &eb, &v[0], &v[1], &v[2], &v[3], &v[4]) != 6 ||
+            eb != c->ebn0_db[i])
+            return LDPCX_E_IO;
+        k->pts[(size_t)i] = ldpcx_sim_counts{v[0], v[1], v[2], v[3], v[4]};
+    }
+    if (lines[(size_t)8 + k->next_point] != " ]\n" || lines[(size_t)9 + k->next_point] != "}\n") return LDPCX_E_IO;
+    return LDPCX_OK;
+}
 
 struct SimLayout {
     size_t y[2], llr[2], ref[2], no[2], cw0[2];
@@ -147,8 +269,31 @@ extern "C" int sim_run(const ldpcx_sim_config *c, ldpcx_sim_counts *out, int *po
     SimLayout L;
     int st = layout(c, &L);
     if (st) return st;
-    if (!out) return LDPCX_E_INVAL;
+    if (!out || c->max_points < 0) return LDPCX_E_INVAL;
     if (!ws_v || ws_bytes < L.total || ((uintptr_t)ws_v & 255u)) return LDPCX_E_WORKSPACE;
+    // a saved state of this sweep: read it before any device work
+    Ckpt ck;
+    ck.fp = c->ckpt_path ? fingerprint(c) : 0;
+    int first = 0;
+    uint64_t cw_next = c->cw0;  // index of the next batch's first codeword
+    auto restore = [&]() {
+        for (int i = 0; i < c->n_snr; ++i) out[i] = i < ck.next_point ? ck.pts[(size_t)i] : ldpcx_sim_counts{0, 0, 0, 0, 0};
+        if (points_run) *points_run = ck.next_point;
+    };
+    if (c->ckpt_path) {
+        Ckpt saved;
+        const int rs = read_ckpt(c->ckpt_path, c, ck.fp, &saved);
+        if (rs < 0) return rs;
+        if (rs == LDPCX_OK) {
+            ck = saved;
+            if (ck.finished || ck.next_point >= c->n_snr) {  // nothing left to run
+                restore();
+                return LDPCX_OK;
+            }
+            first = ck.next_point;
+            cw_next = ck.next_cw;
+        }
+    }
     // Work runs on private non-blocking streams (the legacy NULL stream cannot
     // be captured into a graph), ordered after the caller's stream.
     if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return LDPCX_E_CUDA;
@@ -166,8 +311,7 @@ extern "C" int sim_run(const ldpcx_sim_config *c, ldpcx_sim_counts *out, int *po
     ldpcx::DevCode d;
     st = ldpcx::code_device(c->code, &d);  // upload tables before any capture
     if (st) return st;
-    for (int i = 0; i < c->n_snr; ++i) out[i] = ldpcx_sim_counts{0, 0, 0, 0, 0};
-    if (points_run) *points_run = 0;
+    restore();  // outputs: the restored points, zeros for the rest
     const bool graph = c->use_graph != 0;
     const int64_t B = c->batch;
 
@@ -219,10 +363,10 @@ extern "C" int sim_run(const ldpcx_sim_config *c, ldpcx_sim_counts *out, int *po
         int set = 0, point = 0;
         int64_t b = 0;
     } pend;
-    uint64_t cw_next = c->cw0;  // index of the next batch's first codeword
     int set = 0;
     int result = LDPCX_OK;
-    for (int i = 0; i < c->n_snr && result == LDPCX_OK; ++i) {
+    for (int i = first; i < c->n_snr && result == LDPCX_OK; ++i) {
+        if (c->max_points > 0 && i - first >= c->max_points) break;  // this call's slice is done
         if (cudaMemsetAsync(ws + L.acc, 0, sizeof(int64_t) * 5, rt.back) != cudaSuccess) {
             result = LDPCX_E_CUDA;
             break;
@@ -269,7 +413,17 @@ extern "C" int sim_run(const ldpcx_sim_config *c, ldpcx_sim_counts *out, int *po
         }
         out[i] = ldpcx_sim_counts{counts[0], counts[1], counts[2], counts[3], counts[4]};
         if (points_run) *points_run = i + 1;
-        if (c->stop_ber > 0.0 && counts[0] > 0 && (double)counts[1] / (double)counts[0] < c->stop_ber) break;
+        const bool stop = c->stop_ber > 0.0 && counts[0] > 0 && (double)counts[1] / (double)counts[0] < c->stop_ber;
+        if (c->ckpt_path) {
+            ck.pts.resize((size_t)i + 1);
+            ck.pts[(size_t)i] = out[i];
+            ck.next_point = i + 1;
+            ck.next_cw = cw_next;
+            ck.finished = stop || i + 1 == c->n_snr;
+            result = write_ckpt(c->ckpt_path, c, ck);
+            if (result) break;
+        }
+        if (stop) break;
     }
     if (cudaStreamSynchronize(rt.front) != cudaSuccess && result == LDPCX_OK) result = LDPCX_E_CUDA;
     if (cudaStreamSynchronize(rt.back) != cudaSuccess && result == LDPCX_OK) result = LDPCX_E_CUDA;

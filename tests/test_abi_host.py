@@ -132,3 +132,34 @@ def test_no_device_is_reported(lx):
     st = L.ldpc_bp_decode(code.handle, 4096, 4, C.byref(o), None, None, None, 4096 * 256, 1 << 30, None)
     assert st in (-8, -5)
     assert L.ldpcx_sync_status(None, None) == -8
+
+
+def test_shorten_host_checks(lx):
+    """qc_ldpc_shorten is host work: sizes of the derived code and its argument checks, no GPU needed."""
+    mother = lx.qc_ldpc_build(2, 52, punct_cols=2)
+    sc = lx.qc_ldpc_shorten(mother, 500)
+    assert (sc.k, sc.n_fill, sc.n_tx, sc.n, sc.p0) == (500, 20, 2580, 2704, 104)
+    assert (sc.nnz, sc.rows, sc.cols, sc.kb) == (mother.nnz, mother.rows, mother.cols, mother.kb)
+    assert (sc.base() == mother.base()).all()
+    assert lx.qc_ldpc_shorten(mother, 520).n_fill == 0
+    h = C.c_void_p()
+    L = lx.load_library()
+    for k in (103, 521, -1):  # below the punctured columns, above kb Z
+        assert L.qc_ldpc_shorten(mother.handle, k, C.byref(h)) == -1
+    assert L.qc_ldpc_shorten(sc.handle, 400, C.byref(h)) == -1  # a shortened code is not shortened again
+    assert L.qc_ldpc_shorten(None, 400, C.byref(h)) == -1
+    # fillers outside the transmitted span
+    trunc = lx.qc_ldpc_build(2, 52, punct_cols=2, n_tx=300)
+    assert L.qc_ldpc_shorten(trunc.handle, 500, C.byref(h)) == -1
+    del mother  # the derived code keeps its own copy of the tables
+    assert lx.qc_ldpc_info(sc).k == 500
+
+
+def test_qam_map_awgn_argument_checks(lx):
+    L = lx.load_library()
+    one = C.c_void_p(16)  # never dereferenced: every call below returns before device work
+    assert L.qam_map_awgn(one, 0, 8, 4, 1, 0, one, 0, one, None) == 0     # B = 0: nothing to do
+    assert L.qam_map_awgn(one, 2, 10, 4, 1, 0, one, 0, one, None) == -1   # m does not divide E
+    assert L.qam_map_awgn(one, 2, 8, 3, 1, 0, one, 0, one, None) == -1    # m not a constellation size
+    assert L.qam_map_awgn(one, 2, 8, 4, 1, 0, one, 2, one, None) == -1    # N0 stride 0 or 1
+    assert L.qam_map_awgn(None, 2, 8, 4, 1, 0, one, 0, one, None) == -1   # null bits

@@ -60,6 +60,34 @@ def test_mixed_equals_per_group(lx, orc, algo, prec):
     assert lx.ldpcx_sync_status()[0] == 0
 
 
+@pytest.mark.parametrize("cap", [1, 3, 8])
+def test_mixed_work_item_cap_keeps_results(lx, orc, cap):
+    """The tuned knob (codewords per work item) changes only how the batch is split into items."""
+    groups = build_groups(lx, orc)
+    ref = lx.ldpc_bp_decode_mixed(groups, algo=0, iters=12, msg_prec=1, early_stop=True, llr_out=True)
+    try:
+        lx.ldpcx_tune_set(lx.TUNE_CW_PER_CTA, cap)
+        got = lx.ldpc_bp_decode_mixed(groups, algo=0, iters=12, msg_prec=1, early_stop=True, llr_out=True)
+    finally:
+        lx.ldpcx_tune_set(lx.TUNE_CW_PER_CTA, 0)
+    for r, g in zip(ref, got):
+        assert all(torch.equal(a, b) for a, b in zip(r, g) if a is not None)
+
+
+def test_mixed_autotune(lx, orc, tmp_path):
+    from paper_2203_11854_gb300 import autotune
+    groups = build_groups(lx, orc)
+    path = str(tmp_path / "tune.json")
+    res = autotune.tune_mixed(groups, algo=0, msg_prec=1, iters=12, early_stop=True, cache_path=path,
+                              candidates=(0, 4, 1))
+    assert {t["cw_per_cta"] for t in res["timings"]} == {0, 4, 1}
+    try:
+        best = autotune.apply_mixed(groups, algo=0, msg_prec=1, iters=12, early_stop=True, cache_path=path)
+        assert best == res["best"] and lx.ldpcx_tune_get(lx.TUNE_CW_PER_CTA) == best["cw_per_cta"]
+    finally:
+        lx.ldpcx_tune_set(lx.TUNE_CW_PER_CTA, 0)
+
+
 def test_mixed_group_against_oracle(lx, orc):
     groups = build_groups(lx, orc)
     res = lx.ldpc_bp_decode_mixed(groups, algo=0, iters=12, msg_prec=1, early_stop=True, llr_out=True)
