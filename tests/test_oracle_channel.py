@@ -104,6 +104,23 @@ def test_uncoded_bpsk_ber(orc, ebn0):
     assert binom_ok(err, B * n, p)
 
 
+@pytest.mark.parametrize("k_over_n,ebn0", [(0.5, 2.0), (1 / 3, 4.0), (0.8, 1.0)])
+def test_n0_carries_the_code_rate(orc, k_over_n, ebn0):
+    """Reading R5: N0 = 1/(r m Eb/N0) with r = k/n_tx, so a transmitted BPSK bit sees Es/N0 = r Eb/N0 and its
+    hard-decision error rate is Q(sqrt(2 r Eb/N0)) (uncoded bits sent at the code's rate)."""
+    B, n = 200, 3000
+    k = round(k_over_n * n)
+    bits = orc.source_bits(23, 0, B, n)
+    x = orc.map_bits(bits, 1)
+    N0 = orc.n0_from_ebn0(ebn0, k, n, 1)
+    y = orc.awgn(x, 1, N0, 79, 0)
+    err = int(((y < 0) != (bits == 1)).sum())
+    p = Q(math.sqrt(2 * (k / n) * 10 ** (ebn0 / 10)))
+    assert binom_ok(err, B * n, p)
+    # and a rate-1 reading would be far off
+    assert not binom_ok(err, B * n, Q(math.sqrt(2 * 10 ** (ebn0 / 10))))
+
+
 @pytest.mark.parametrize("ebn0", [2.0, 6.0])
 def test_uncoded_16qam_maxlog_ber(orc, ebn0):
     B, n = 100, 8000
