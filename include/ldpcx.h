@@ -384,7 +384,7 @@ int ldpcx_fault_set(int kind, int after);
  * bytes) plus B times the per-codeword bytes of the decoder's message format
  * must fit in the array, else LDPCX_E_WORKSPACE before any work; B is bounded
  * before any product is formed. At Z = 384, BG1-shaped: layered min-sum
- * (check-node state) 118 / 218 / 436 codewords with FP32 / FP16 / FIX6
+ * (their state format) 118 / 153 / 436 codewords with FP32 / FP16 / FIX6
  * messages; sum-product and flooding (per-edge messages) 69 / 138. The first
  * call on a device looks up the array's device address (cudaGetSymbolAddress);
  * make that first call before any stream capture. Every call on a device

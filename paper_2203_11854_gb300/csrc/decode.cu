@@ -210,31 +210,36 @@ int dec::decode_plan(const ldpcx_code *c, const ldpcx_decode_opts *o, DecodePlan
             return LDPCX_OK;
         }
     }
-    if (layered && algo == kMinSum && zpt == 1 && g_cns.load() &&
-        cns_bytes(c, o->msg_prec) <= msg_stride(c) * (int64_t)msg_bytes(o->msg_prec)) {
+    // layered min-sum: check-node state (the compiled schedule's format, or the row-table kernel's) when it
+    // fits the per-edge workspace of a codeword
+    const int64_t ws_cw = msg_stride(c) * (int64_t)msg_bytes(o->msg_prec);
+    if (layered && algo == kMinSum && zpt == 1 && g_cns.load()) {
         const int zs = g_specialised.load() ? c->Z : 0;
         const int bg = g_sched.load() ? sched_shape(c) : 0;
         const bool trunc = bg && c->rows != (bg == 1 ? Sched<1>::rows : Sched<2>::rows);
         const int kpt = !trunc && g_zpt.load() == 2 && c->Z % 2 == 0 ? 2 : 1;  // check nodes per thread
         SchedFn sf = bg && c->nnz <= kSchedMaxBlocks ? layered_cns_sched_kernel(bg, o->msg_prec, zs, kpt, trunc)
                                                      : nullptr;
-        if (sf) {
+        const int64_t sb = bg ? sched_state_bytes(bg, o->msg_prec, kpt, c->row_ptr.data(), c->rows, c->Z) : 0;
+        if (sf && sb <= ws_cw) {
             pl->sf = sf;
             pl->kpt = kpt;
             pl->cns = true;
+            pl->state_bytes = sb;
             return LDPCX_OK;
         }
-        KernelFn f = layered_cns_kernel(c->max_deg, o->msg_prec, zs);
+        KernelFn f = cns_bytes(c, o->msg_prec) <= ws_cw ? layered_cns_kernel(c->max_deg, o->msg_prec, zs) : nullptr;
         if (f) {
             pl->fn = f;
             pl->cns = true;
+            pl->state_bytes = cns_bytes(c, o->msg_prec);
         }
     }
     return LDPCX_OK;
 }
 
 int64_t dec::decode_plan_bytes_per_cw(const ldpcx_code *c, const ldpcx_decode_opts *o, const DecodePlan &pl) {
-    return pl.cns ? cns_bytes(c, o->msg_prec) : msg_stride(c) * (int64_t)msg_bytes(o->msg_prec);
+    return pl.cns ? pl.state_bytes : msg_stride(c) * (int64_t)msg_bytes(o->msg_prec);
 }
 
 dec::Params dec::decode_params(const ldpcx_code *c, const uint32_t *blk, const int32_t *row_ptr,
@@ -323,13 +328,12 @@ extern "C" int ldpc_bp_msg_format(ldpcx_code_t c, const ldpcx_decode_opts *o, in
     if (!c || !cn_state || !bytes_per_cw) return LDPCX_E_INVAL;
     int st = ldpcx::check_opts(c, o);
     if (st) return st;
-    const bool minsum_layered = o->algo == LDPCX_LAYERED_MINSUM;
-    const int64_t edge_bytes = (int64_t)c->nnz * c->Z * (int64_t)ldpcx::msg_bytes(o->msg_prec);
-    const int64_t cns = ldpcx::cns_bytes(c, o->msg_prec);
-    const bool use = minsum_layered && ldpcx::g_cns.load() &&
-                     cns <= ldpcx::msg_stride(c) * (int64_t)ldpcx::msg_bytes(o->msg_prec);
-    *cn_state = use ? 1 : 0;
-    *bytes_per_cw = use ? cns : edge_bytes;
+    // the format the decoder would run (the same choice as ldpc_bp_decode)
+    ldpcx::dec::DecodePlan pl;
+    st = ldpcx::dec::decode_plan(c, o, &pl);
+    if (st) return st;
+    *cn_state = pl.cns ? 1 : 0;
+    *bytes_per_cw = pl.cns ? pl.state_bytes : (int64_t)c->nnz * c->Z * (int64_t)ldpcx::msg_bytes(o->msg_prec);
     return LDPCX_OK;
 }
 

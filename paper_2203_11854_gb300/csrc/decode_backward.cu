@@ -48,14 +48,15 @@ struct BwdParams {
 // e^x - e^-x would cancel, from the Taylor series sinh x = x (1 + x^2/6 (1 +
 // x^2/20 (1 + x^2/42))) (truncation below 1e-12 relative there). Above it
 // e - 1/e >= 0.125 loses at most a factor 16 of the exponential's relative
-// error: about 1e-6 relative overall.
+// error: about 1e-6 relative overall. The hardware approximations are those
+// of phi_fast (every value here is a normal binary32 number).
 __device__ __forceinline__ float dphi_fast(float x) {
     if (x < 0.0625f) {
         const float x2 = x * x;
-        return -__fdividef(1.0f, x * (1.0f + x2 * (1.0f / 6.0f) * (1.0f + x2 * (1.0f / 20.0f) * (1.0f + x2 * (1.0f / 42.0f)))));
+        return -dec::hw_rcp(x * (1.0f + x2 * (1.0f / 6.0f) * (1.0f + x2 * (1.0f / 20.0f) * (1.0f + x2 * (1.0f / 42.0f)))));
     }
-    const float e = __expf(x);
-    return -__fdividef(2.0f, e - __fdividef(1.0f, e));
+    const float e = dec::hw_exp2(x * dec::kLog2e);
+    return -2.0f * dec::hw_rcp(e - dec::hw_rcp(e));
 }
 
 __device__ __forceinline__ int vn_of(uint32_t vb, int z, int Z) {

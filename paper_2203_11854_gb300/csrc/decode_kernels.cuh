@@ -85,11 +85,32 @@ __device__ __forceinline__ float phi(float x) { return log1pf(__fdiv_rn(2.0f, ex
 // Otherwise e^x - 1 >= 0.064 loses at most a factor e^x/(e^x - 1) < 17 of the
 // exponential's relative error, and ln(1+y) >= 0.06 is taken where log2 is
 // accurate in absolute terms; the result stays within about 2e-5 relative.
+//
+// e^x = 2^(x log2 e), ln y = log2(y) ln 2 and 1/x come from the PTX ex2, lg2 and
+// rcp approximations with subnormals flushed: for phi(clamp) <= x <= clamp
+// every argument and result here (x, e^x, e^x - 1 >= x, 2/(e^x - 1) <= 2/x,
+// 1 + y) is a normal binary32 number, so the flush changes no value.
+constexpr float kLog2e = 1.44269504088896341f, kLn2 = 0.693147180559945309f;
+__device__ __forceinline__ float hw_exp2(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float hw_log2(float x) {
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float hw_rcp(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
 __device__ __forceinline__ float phi_fast(float x) {
     const float em1 = x < 0.0625f ? x * (1.0f + x * (0.5f + x * (1.0f / 6.0f + x * (1.0f / 24.0f))))
-                                  : __expf(x) - 1.0f;
-    const float y = __fdividef(2.0f, em1);
-    return y < 0.0625f ? y * (1.0f - y * (0.5f - y * (1.0f / 3.0f - y * 0.25f))) : __logf(1.0f + y);
+                                  : hw_exp2(x * kLog2e) - 1.0f;
+    const float y = 2.0f * hw_rcp(em1);
+    return y < 0.0625f ? y * (1.0f - y * (0.5f - y * (1.0f / 3.0f - y * 0.25f))) : hw_log2(1.0f + y) * kLn2;
 }
 
 template <bool FAST> __device__ __forceinline__ float phi_t(float x) { return FAST ? phi_fast(x) : phi(x); }

@@ -104,8 +104,8 @@ __global__ void __launch_bounds__(kMaxThreads, 2) k_mixed(const MixedParams m) {
                     const int sh = (int)(bk & 0xFFFFu);
                     s_at[i] = make_int2(4 * ((int)(bk >> 16) * p.Z + sh), p.Z - sh);
                 }
-                if (gd.bg == 1) cns_sched_tile<1, PREC, 0, 1, true>(p, item.cw_base, item.cw_base, smem, s_at);
-                else cns_sched_tile<2, PREC, 0, 1, true>(p, item.cw_base, item.cw_base, smem, s_at);
+                if (gd.bg == 1) cns_sched_tile1<1, PREC, 0, true>(p, item.cw_base, item.cw_base, smem, s_at);
+                else cns_sched_tile1<2, PREC, 0, true>(p, item.cw_base, item.cw_base, smem, s_at);
             } else if (gd.cns) {
                 cns_tile<DMAX, PREC, 0>(p, item.cw_base, item.cw_base, smem);
             } else {
@@ -263,12 +263,14 @@ extern "C" int ldpc_bp_decode_mixed(const ldpcx_batch_group *groups, int n_group
         gd.G = group_G(c);
         gd.B = g.B;
         gd.stride = stride_of(c);
+        const int64_t slot_cw = gd.stride * (int64_t)(o->msg_prec == LDPCX_MSG_F32   ? 4
+                                                      : o->msg_prec == LDPCX_MSG_F16 ? 2
+                                                                                     : 1);
         gd.bg = sched_shape_of(c->row_ptr.data(), c->rows, c->params.bg_shape);
         if (gd.bg && c->nnz > kSchedMaxBlocks) gd.bg = 0;
-        gd.cns = o->algo == LDPCX_LAYERED_MINSUM &&
-                 cns_fits(c, o->msg_prec, gd.stride * (int64_t)(o->msg_prec == LDPCX_MSG_F32   ? 4
-                                                                : o->msg_prec == LDPCX_MSG_F16 ? 2
-                                                                                               : 1));
+        // the compiled-schedule tile's own format must fit the codeword's slot
+        if (gd.bg && sched_state_bytes(gd.bg, o->msg_prec, 1, c->row_ptr.data(), c->rows, c->Z) > slot_cw) gd.bg = 0;
+        gd.cns = o->algo == LDPCX_LAYERED_MINSUM && cns_fits(c, o->msg_prec, slot_cw);
         gd.llr = g.llr_ch;
         gd.llr_out = g.llr_out;
         gd.bits = g.bits_out;

@@ -17,6 +17,7 @@ struct DecodePlan {
     int zpt = 1;            // check nodes per thread of fn (layered)
     bool layered = false;
     bool cns = false;       // min-sum check-node state instead of per-edge messages
+    int64_t state_bytes = 0;  // with cns: bytes of one codeword's state in the kernel's format
 };
 
 // Picks the kernel; LDPCX_E_UNSUPPORTED when none is built for the code.

@@ -47,7 +47,7 @@ def decode_noalloc_abi(lx, code, llr, opts):
 @pytest.mark.parametrize("bg,Z,punct,B,algo,prec,early,weighted", [
     (1, 384, 2, 40, 0, 1, False, False),   # BG1-shaped Z=384, FP16 min-sum (the headline decoder)
     (1, 384, 2, 24, 0, 0, True, False),    # FP32 messages, early stop
-    (1, 384, 2, 218, 0, 1, False, False),  # FP16 min-sum at the array's limit (check-node state)
+    (1, 384, 2, 153, 0, 1, False, False),  # FP16 min-sum at the array's limit (218112-byte state)
     (2, 64, 0, 150, 0, 2, False, False),   # BG2-shaped Z=64, 6-bit messages, several CTAs + ragged tail
     (1, 128, 2, 9, 0, 1, True, False),     # BG1-shaped Z=128, FP16 min-sum, early stop
     (2, 8, 0, 100, 2, 0, True, False),     # flooding min-sum
@@ -95,7 +95,7 @@ def test_noalloc_minsum_equals_oracle_replay(lx, orc, prec):
 
 
 @pytest.mark.parametrize("algo,prec,limit", [
-    (0, 1, 218),  # layered min-sum, FP16 check-node state: 153600 bytes per codeword
+    (0, 1, 153),  # layered min-sum, FP16: core-row state + per-edge extension rows, 218112 bytes per codeword
     (0, 0, 118),  # FP32 state: 282624 bytes
     (0, 2, 436),  # 6-bit state: 76800 bytes
     (1, 1, 138),  # layered sum-product, FP16 per-edge messages: 242688 bytes
