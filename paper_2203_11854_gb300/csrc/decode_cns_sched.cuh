@@ -453,7 +453,9 @@ __device__ __forceinline__ void cns_sched_tile(const Params &p, int64_t cw_base,
 // with scalar registers throughout and the slot addresses formed from two
 // per-thread bases (core and extension rows), so a step adds one row offset.
 // BG1-shaped codes with FP16 messages keep the extension rows per edge
-// (SchedLayout::edge_ext); plane B of a node lies pb bytes past its plane A.
+// (SchedLayout::edge_ext); plane B of a node lies 8 Z - 4 z bytes past its
+// plane A, an offset formed where it is used (a register held across the whole
+// kernel costs more than the multiply-add).
 
 // Layered min-sum update of check node z of a row of exact degree D from its
 // check-node state (the rule of cns_update_k for one node).
@@ -493,11 +495,12 @@ __device__ __forceinline__ void cns_update1(const Params &p, float *app, const i
 }
 
 // One layer step of degree D on row r with one check node per thread.
-template <int D, int BG, int PREC, bool TRUNC, int MODE>
-__device__ __forceinline__ void sched_step1(const Params &p, const int2 *s_at, float *app, int z, int pb, int t,
-                                            int r, int b0, int off, const SchedGeo &geo, bool done,
-                                            const uint4 &s_cur, uint4 &s_far) {
+template <int D, int BG, int PREC, int ZC, bool TRUNC, int MODE>
+__device__ __forceinline__ void sched_step1(const Params &p, const int2 *s_at, float *app, int z, int t, int r,
+                                            int b0, int off, const SchedGeo &geo, bool done, const uint4 &s_cur,
+                                            uint4 &s_far) {
     using L = SchedLayout<BG, PREC>;
+    const int pb = 8 * (ZC ? ZC : p.Z) - 4 * z;  // plane B past plane A (per-edge extension rows)
     // an extension row: the core rows of both shapes have degree 10 or more, the extension rows 6 or less
     constexpr bool ext_row = D <= 8;
     int r2, t2;
@@ -536,64 +539,64 @@ __device__ __forceinline__ uint4 &ring1(uint4 &a, uint4 &b, uint4 &c) {
 }
 
 // COUNT consecutive rows of degree D from row r0 at ring phase PH (as sched_run).
-template <int D, int COUNT, int PH, int BG, int PREC, bool TRUNC = false, bool LAST = false>
-__device__ __forceinline__ void sched_run1(const Params &p, const int2 *s_at, float *app, int z, int pb, int t,
-                                           int r0, int b0, int off0, int Lrow, const SchedGeo &geo, bool done,
-                                           uint4 &a, uint4 &b, uint4 &c) {
+template <int D, int COUNT, int PH, int BG, int PREC, int ZC, bool TRUNC = false, bool LAST = false>
+__device__ __forceinline__ void sched_run1(const Params &p, const int2 *s_at, float *app, int z, int t, int r0,
+                                           int b0, int off0, int Lrow, const SchedGeo &geo, bool done, uint4 &a,
+                                           uint4 &b, uint4 &c) {
     constexpr int M = TRUNC ? kStepAny : PH < 4 ? PH : kStepExt;
     constexpr int NW = LAST ? COUNT - 2 : COUNT;  // steps without a wrap
     static_assert(!LAST || (COUNT >= 2 && !TRUNC && PH >= 4), "the last run is an extension run of a full graph");
     int r = r0, bb = b0, off = off0;
 #pragma unroll 1
     for (int i = 0; i < NW / 3; ++i) {
-        sched_step1<D, BG, PREC, TRUNC, M>(p, s_at, app, z, pb, t, r, bb, off, geo, done, ring1<PH>(a, b, c),
+        sched_step1<D, BG, PREC, ZC, TRUNC, M>(p, s_at, app, z, t, r, bb, off, geo, done, ring1<PH>(a, b, c),
                                            ring1<PH + 2>(a, b, c));
-        sched_step1<D, BG, PREC, TRUNC, M>(p, s_at, app, z, pb, t, r + 1, bb + D, off + Lrow, geo, done,
+        sched_step1<D, BG, PREC, ZC, TRUNC, M>(p, s_at, app, z, t, r + 1, bb + D, off + Lrow, geo, done,
                                            ring1<PH + 1>(a, b, c), ring1<PH + 3>(a, b, c));
-        sched_step1<D, BG, PREC, TRUNC, M>(p, s_at, app, z, pb, t, r + 2, bb + 2 * D, off + 2 * Lrow, geo, done,
+        sched_step1<D, BG, PREC, ZC, TRUNC, M>(p, s_at, app, z, t, r + 2, bb + 2 * D, off + 2 * Lrow, geo, done,
                                            ring1<PH + 2>(a, b, c), ring1<PH + 4>(a, b, c));
         r += 3;
         bb += 3 * D;
         off += 3 * Lrow;
     }
     if constexpr (NW % 3 >= 1)
-        sched_step1<D, BG, PREC, TRUNC, M>(p, s_at, app, z, pb, t, r, bb, off, geo, done, ring1<PH>(a, b, c),
+        sched_step1<D, BG, PREC, ZC, TRUNC, M>(p, s_at, app, z, t, r, bb, off, geo, done, ring1<PH>(a, b, c),
                                            ring1<PH + 2>(a, b, c));
     if constexpr (NW % 3 == 2)
-        sched_step1<D, BG, PREC, TRUNC, M>(p, s_at, app, z, pb, t, r + 1, bb + D, off + Lrow, geo, done,
+        sched_step1<D, BG, PREC, ZC, TRUNC, M>(p, s_at, app, z, t, r + 1, bb + D, off + Lrow, geo, done,
                                            ring1<PH + 1>(a, b, c), ring1<PH + 3>(a, b, c));
     if constexpr (LAST) {
         constexpr int Q = PH + NW;  // ring phase of the first wrapping step
         r += NW % 3;
         bb += (NW % 3) * D;
         off += (NW % 3) * Lrow;
-        sched_step1<D, BG, PREC, TRUNC, kStepExtWrap>(p, s_at, app, z, pb, t, r, bb, off, geo, done,
+        sched_step1<D, BG, PREC, ZC, TRUNC, kStepExtWrap>(p, s_at, app, z, t, r, bb, off, geo, done,
                                                       ring1<Q>(a, b, c), ring1<Q + 2>(a, b, c));
-        sched_step1<D, BG, PREC, TRUNC, kStepExtWrap>(p, s_at, app, z, pb, t, r + 1, bb + D, off + Lrow, geo, done,
+        sched_step1<D, BG, PREC, ZC, TRUNC, kStepExtWrap>(p, s_at, app, z, t, r + 1, bb + D, off + Lrow, geo, done,
                                                       ring1<Q + 1>(a, b, c), ring1<Q + 3>(a, b, c));
     }
 }
 
 // `count` (run-time) consecutive rows of degree D of a truncated graph (as sched_run_n).
-template <int D, int BG, int PREC>
-__device__ __forceinline__ void sched_run_n1(const Params &p, const int2 *s_at, float *app, int z, int pb, int t,
-                                             int r0, int b0, int off0, int Lrow, int count, const SchedGeo &geo,
-                                             bool done, uint4 &a, uint4 &b, uint4 &c) {
+template <int D, int BG, int PREC, int ZC>
+__device__ __forceinline__ void sched_run_n1(const Params &p, const int2 *s_at, float *app, int z, int t, int r0,
+                                             int b0, int off0, int Lrow, int count, const SchedGeo &geo, bool done,
+                                             uint4 &a, uint4 &b, uint4 &c) {
     int r = r0, bb = b0, off = off0;
 #pragma unroll 1
     for (int i = 0; i < count / 3; ++i) {
-        sched_step1<D, BG, PREC, true, kStepAny>(p, s_at, app, z, pb, t, r, bb, off, geo, done, a, c);
-        sched_step1<D, BG, PREC, true, kStepAny>(p, s_at, app, z, pb, t, r + 1, bb + D, off + Lrow, geo, done, b, a);
-        sched_step1<D, BG, PREC, true, kStepAny>(p, s_at, app, z, pb, t, r + 2, bb + 2 * D, off + 2 * Lrow, geo,
+        sched_step1<D, BG, PREC, ZC, true, kStepAny>(p, s_at, app, z, t, r, bb, off, geo, done, a, c);
+        sched_step1<D, BG, PREC, ZC, true, kStepAny>(p, s_at, app, z, t, r + 1, bb + D, off + Lrow, geo, done, b, a);
+        sched_step1<D, BG, PREC, ZC, true, kStepAny>(p, s_at, app, z, t, r + 2, bb + 2 * D, off + 2 * Lrow, geo,
                                                  done, c, b);
         r += 3;
         bb += 3 * D;
         off += 3 * Lrow;
     }
     const int rem = count - 3 * (count / 3);
-    if (rem >= 1) sched_step1<D, BG, PREC, true, kStepAny>(p, s_at, app, z, pb, t, r, bb, off, geo, done, a, c);
+    if (rem >= 1) sched_step1<D, BG, PREC, ZC, true, kStepAny>(p, s_at, app, z, t, r, bb, off, geo, done, a, c);
     if (rem == 2)
-        sched_step1<D, BG, PREC, true, kStepAny>(p, s_at, app, z, pb, t, r + 1, bb + D, off + Lrow, geo, done, b, a);
+        sched_step1<D, BG, PREC, ZC, true, kStepAny>(p, s_at, app, z, t, r + 1, bb + D, off + Lrow, geo, done, b, a);
     if (rem == 1) {
         const uint4 x = a;
         a = b;
@@ -634,24 +637,22 @@ __device__ __forceinline__ void cns_sched_tile1(const Params &p, int64_t cw_base
     geo.Le = L::edge_ext ? (12 * ZV + 15) / 16 * 16 : (L::sb_ext * ZV + 15) / 16 * 16;
     geo.core_z = st + z * L::sb_core;
     geo.ext_z = st + 4 * geo.Lc + z * (L::edge_ext ? 8 : L::sb_ext);
-    const int pb = 8 * ZV - 4 * z;  // plane B of a node's extension-row slot, past its plane A
     __syncthreads();
 
     const int n_hi = min(S::n_hi, p.rows - 4), n_lo = p.rows - 4 - n_hi;
     uint4 a = make_uint4(0u, 0u, 0u, 0u), b = a, c = a;
     for (int t = 0; t < p.iters; ++t) {
-        sched_run1<S::dc0, 1, 0, BG, PREC, TRUNC>(p, s_at, app, z, pb, t, 0, 0, 0, geo.Lc, geo, done, a, b, c);
-        sched_run1<S::dc1, 1, 1, BG, PREC, TRUNC>(p, s_at, app, z, pb, t, 1, S::dc0, geo.Lc, geo.Lc, geo, done, a,
+        sched_run1<S::dc0, 1, 0, BG, PREC, ZC, TRUNC>(p, s_at, app, z, t, 0, 0, 0, geo.Lc, geo, done, a, b, c);
+        sched_run1<S::dc1, 1, 1, BG, PREC, ZC, TRUNC>(p, s_at, app, z, t, 1, S::dc0, geo.Lc, geo.Lc, geo, done, a,
                                                   b, c);
-        sched_run1<S::dc2, 1, 2, BG, PREC, TRUNC>(p, s_at, app, z, pb, t, 2, S::dc0 + S::dc1, 2 * geo.Lc, geo.Lc,
+        sched_run1<S::dc2, 1, 2, BG, PREC, ZC, TRUNC>(p, s_at, app, z, t, 2, S::dc0 + S::dc1, 2 * geo.Lc, geo.Lc,
                                                   geo, done, a, b, c);
-        sched_run1<S::dc3, 1, 3, BG, PREC, TRUNC>(p, s_at, app, z, pb, t, 3, S::dc0 + S::dc1 + S::dc2,
+        sched_run1<S::dc3, 1, 3, BG, PREC, ZC, TRUNC>(p, s_at, app, z, t, 3, S::dc0 + S::dc1 + S::dc2,
                                                   3 * geo.Lc, geo.Lc, geo, done, a, b, c);
         if constexpr (!TRUNC) {
-            sched_run1<S::d_hi, S::n_hi, 4, BG, PREC>(p, s_at, app, z, pb, t, 4, L::b_hi, 4 * geo.Lc, geo.Le, geo,
+            sched_run1<S::d_hi, S::n_hi, 4, BG, PREC, ZC>(p, s_at, app, z, t, 4, L::b_hi, 4 * geo.Lc, geo.Le, geo,
                                                       done, a, b, c);
-            sched_run1<S::d_lo, S::rows - 4 - S::n_hi, 4 + S::n_hi, BG, PREC, false, true>(
-                p, s_at, app, z, pb, t, 4 + S::n_hi, L::b_lo, 4 * geo.Lc + S::n_hi * geo.Le, geo.Le, geo, done, a,
+            sched_run1<S::d_lo, S::rows - 4 - S::n_hi, 4 + S::n_hi, BG, PREC, ZC, false, true>(p, s_at, app, z, t, 4 + S::n_hi, L::b_lo, 4 * geo.Lc + S::n_hi * geo.Le, geo.Le, geo, done, a,
                 b, c);
             if constexpr (S::rows % 3 == 1) {  // the next iteration's first step finds its state at phase 0
                 const uint4 x = a;
@@ -670,9 +671,9 @@ __device__ __forceinline__ void cns_sched_tile1(const Params &p, int64_t cw_base
             a = b;
             b = c;
             c = x;
-            sched_run_n1<S::d_hi, BG, PREC>(p, s_at, app, z, pb, t, 4, L::b_hi, 4 * geo.Lc, geo.Le, n_hi, geo, done,
+            sched_run_n1<S::d_hi, BG, PREC, ZC>(p, s_at, app, z, t, 4, L::b_hi, 4 * geo.Lc, geo.Le, n_hi, geo, done,
                                             a, b, c);
-            sched_run_n1<S::d_lo, BG, PREC>(p, s_at, app, z, pb, t, 4 + S::n_hi, L::b_lo,
+            sched_run_n1<S::d_lo, BG, PREC, ZC>(p, s_at, app, z, t, 4 + S::n_hi, L::b_lo,
                                             4 * geo.Lc + S::n_hi * geo.Le, geo.Le, n_lo, geo, done, a, b, c);
         }
         if (!done) iters_run = t + 1;
@@ -689,12 +690,82 @@ __device__ __forceinline__ void cns_sched_tile1(const Params &p, int64_t cw_base
     write_outputs(p, s_app_all, cw_base, iters_run, g, active, z);
 }
 
+// The kernel. For a full base graph with one check node per thread the tile
+// is written out in the kernel body: the same steps as cns_sched_tile1, which
+// (called as a function) compiles to about 8 % more instructions on sm_103a.
 template <int BG, int PREC, int ZC = 0, int K = 1, bool TRUNC = false>
 __global__ void __launch_bounds__(kMaxThreads / K, 2)
     k_layered_cns_sched(const Params p, const __grid_constant__ SchedTab tab) {
     extern __shared__ __align__(16) unsigned char smem[];
-    if constexpr (K == 1) cns_sched_tile1<BG, PREC, ZC, TRUNC>(p, (int64_t)blockIdx.x * p.G, 0, smem, tab.at);
-    else cns_sched_tile<BG, PREC, ZC, K, TRUNC>(p, (int64_t)blockIdx.x * p.G, 0, smem, tab.at);
+    if constexpr (K == 1 && !TRUNC) {
+        using S = Sched<BG>;
+        using L = SchedLayout<BG, PREC>;
+        const int ZV = ZC ? ZC : p.Z;
+        const int64_t cw_base = (int64_t)blockIdx.x * p.G;
+        const int2 *s_at = tab.at;
+        float *s_app_all = reinterpret_cast<float *>(smem);
+        uint32_t *s_vb = reinterpret_cast<uint32_t *>(s_app_all + (size_t)p.G * p.n);
+        int32_t *s_rp = reinterpret_cast<int32_t *>(s_vb + p.nnz);
+        int *s_flag = reinterpret_cast<int *>(s_rp + p.rows + 1);
+        load_tables(p, s_vb, s_rp);  // for the syndrome check
+        load_channel(p, s_app_all, cw_base);
+        const int g = threadIdx.x / ZV, z = threadIdx.x - g * ZV;
+        const int64_t cw = cw_base + g;
+        const bool active = g < p.G && cw < p.B;
+        float *app = s_app_all + (size_t)(active ? g : 0) * p.n;
+        unsigned char *st =
+            reinterpret_cast<unsigned char *>(p.msg) + (active ? cw : 0) * p.msg_stride * p.msg_size;
+        bool done = !active;
+        int iters_run = 0;
+        SchedGeo geo;
+        geo.Lc = (L::sb_core * ZV + 15) / 16 * 16;
+        geo.Le = L::edge_ext ? (12 * ZV + 15) / 16 * 16 : (L::sb_ext * ZV + 15) / 16 * 16;
+        geo.core_z = st + z * L::sb_core;
+        geo.ext_z = st + 4 * geo.Lc + z * (L::edge_ext ? 8 : L::sb_ext);
+        __syncthreads();
+        uint4 a = make_uint4(0u, 0u, 0u, 0u), b = a, c = a;
+        for (int t = 0; t < p.iters; ++t) {
+            sched_run1<S::dc0, 1, 0, BG, PREC, ZC>(p, s_at, app, z, t, 0, 0, 0, geo.Lc, geo, done, a, b, c);
+            sched_run1<S::dc1, 1, 1, BG, PREC, ZC>(p, s_at, app, z, t, 1, S::dc0, geo.Lc, geo.Lc, geo, done, a, b,
+                                                   c);
+            sched_run1<S::dc2, 1, 2, BG, PREC, ZC>(p, s_at, app, z, t, 2, S::dc0 + S::dc1, 2 * geo.Lc, geo.Lc, geo,
+                                                   done, a, b, c);
+            sched_run1<S::dc3, 1, 3, BG, PREC, ZC>(p, s_at, app, z, t, 3, S::dc0 + S::dc1 + S::dc2, 3 * geo.Lc,
+                                                   geo.Lc, geo, done, a, b, c);
+            sched_run1<S::d_hi, S::n_hi, 4, BG, PREC, ZC>(p, s_at, app, z, t, 4, L::b_hi, 4 * geo.Lc, geo.Le, geo,
+                                                          done, a, b, c);
+            sched_run1<S::d_lo, S::rows - 4 - S::n_hi, 4 + S::n_hi, BG, PREC, ZC, false, true>(
+                p, s_at, app, z, t, 4 + S::n_hi, L::b_lo, 4 * geo.Lc + S::n_hi * geo.Le, geo.Le, geo, done, a, b,
+                c);
+            if constexpr (S::rows % 3 == 1) {  // the next iteration's first step finds its state at phase 0
+                const uint4 x = a;
+                a = b;
+                b = c;
+                c = x;
+            } else if constexpr (S::rows % 3 == 2) {
+                const uint4 x = c;
+                c = b;
+                b = a;
+                a = x;
+            }
+            if (!done) iters_run = t + 1;
+            if (p.early_stop) {
+                if (threadIdx.x < p.G) s_flag[threadIdx.x] = 0;
+                __syncthreads();
+                const bool bad = !done && syndrome_bad_vec<1, ZC>(p, s_vb, s_rp, app, z);
+                if (bad) s_flag[g] = 1;
+                __syncthreads();
+                if (!done && s_flag[g] == 0) done = true;
+                if (__syncthreads_and(done)) break;
+            }
+        }
+        __syncthreads();
+        write_outputs(p, s_app_all, cw_base, iters_run, g, active, z);
+    } else if constexpr (K == 1) {
+        cns_sched_tile1<BG, PREC, ZC, TRUNC>(p, (int64_t)blockIdx.x * p.G, 0, smem, tab.at);
+    } else {
+        cns_sched_tile<BG, PREC, ZC, K, TRUNC>(p, (int64_t)blockIdx.x * p.G, 0, smem, tab.at);
+    }
 }
 
 // Host: the shape (1, 2) whose base graph's first `rows` row degrees the row
