@@ -3,6 +3,8 @@
 // (compute_ber), all on the device.
 #include <math.h>
 
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace ldpcx {
@@ -31,230 +33,255 @@ struct TxParams {
     int G;               // codewords per CTA
 };
 
-// Gray PAM level of h bits taken from c at stride 2 (I: offset 0, Q: offset 1):
+constexpr int kTxThreads = 256;
+
+// Gray PAM level of h label bits at stride 2 of `bits` from bit `off` (I: 0,
+// Q: 1), label bit i at bit i of the word:
 // A = (1-2a0)(2^(h-1) - (1-2a1)(2^(h-2) - ... (1-2a_{h-1}))).
-__device__ __forceinline__ int pam_level(const uint8_t *c, int h) {
-    int inner = 1 - 2 * (int)c[2 * (h - 1)];
-    for (int i = h - 2; i >= 0; --i) inner = (1 - 2 * (int)c[2 * i]) * ((1 << (h - 1 - i)) - inner);
+__device__ __forceinline__ int pam_level(uint32_t bits, int h, int off) {
+    int inner = 1 - 2 * (int)((bits >> (2 * (h - 1) + off)) & 1u);
+    for (int i = h - 2; i >= 0; --i) inner = (1 - 2 * (int)((bits >> (2 * i + off)) & 1u)) * ((1 << (h - 1 - i)) - inner);
     return inner;
 }
 
-
-// Shared-memory layout of k_tx, per CTA: [G][ns] codeword bytes (ns = n rounded
-// up to 4), [G][4 nq] packed source words, then (8-byte aligned) the block
-// table as {col Z + shift, Z - shift} pairs, the row pointers and the packed
-// lambda words of the general core.
-__host__ __device__ inline int tx_ns(int n) { return (n + 3) & ~3; }
-__host__ __device__ inline size_t tx_enc_off(int G, int n, int k) {
-    const int nq = (((k + 31) >> 5) + 3) >> 2;
-    return ((size_t)G * tx_ns(n) + (size_t)G * 16 * nq + 7) & ~(size_t)7;
+// k_tx keeps each codeword's bits packed, position v at bit v & 31 of word
+// v >> 5, so one circulant block of a parity check is a word-wide rotation (a
+// funnel shift of two words) instead of Z one-byte loads.
+// Shared memory, per CTA: the block table as {column, shift} pairs and the row
+// pointers, then per codeword its nLw packed words (n positions plus a padding
+// word that windows read past the end), the four core-row sums lambda (4 Wz
+// words; Wz = words of one block column) and, for a general core, lambda as one
+// 4Z-bit vector (inv_words words).
+struct TxLayout {
+    int nLw, Wz, per_cw;  // words
+    size_t cw_off;        // bytes before the first codeword
+    size_t bytes;
+};
+__host__ __device__ inline TxLayout tx_layout(int G, int n, int Z, int nnz, int rows, int inv_words) {
+    TxLayout t;
+    t.nLw = ((n + 31) >> 5) + 1;
+    t.Wz = (Z + 31) >> 5;
+    t.per_cw = t.nLw + 4 * t.Wz + inv_words;
+    t.cw_off = (8 * (size_t)nnz + 4 * (size_t)(rows + 1) + 15) & ~(size_t)15;
+    t.bytes = t.cw_off + 4 * (size_t)G * t.per_cw;
+    return t;
 }
-__host__ __device__ inline size_t tx_smem(int G, int n, int k, int nnz, int rows, int inv_words) {
-    return tx_enc_off(G, n, k) + 8 * (size_t)nnz + 4 * (size_t)(rows + 1) + 4 * (size_t)G * inv_words;
+
+// 32 positions of a packed codeword from position pos (pos + 32 may pass the
+// last position by less than one word).
+__device__ __forceinline__ uint32_t tx_window(const uint32_t *L, int pos) {
+    return __funnelshift_r(L[pos >> 5], L[(pos >> 5) + 1], pos & 31);
 }
 
-__global__ void __launch_bounds__(kMaxThreads) k_tx(const TxParams p) {
+// Word j of block column `col` rotated by s: bit i = position col Z + (32 j + i
+// + s) mod Z, for i < min(32, Z - 32 j) (the bits above are unspecified). The
+// range of i wraps past the column's end at most once.
+__device__ __forceinline__ uint32_t tx_rot(const uint32_t *L, int col, int s, int j, int Z) {
+    int a = 32 * j + s;
+    if (a >= Z) a -= Z;
+    const int base = col * Z, n1 = Z - a;  // n1 positions before the wrap
+    uint32_t w = tx_window(L, base + a);
+    if (n1 < 32) w = (w & ((1u << n1) - 1u)) | (tx_window(L, base) << n1);
+    return w;
+}
+
+// Writes bits 0 .. min(32, Z - 32 j) - 1 of v to positions col Z + 32 j ... of
+// L, whose bits there are zero: a word shared with another column takes an
+// atomic OR, a word of its own a plain store.
+__device__ __forceinline__ void tx_put(uint32_t *L, int col, int j, uint32_t v, int Z) {
+    const int nv = min(32, Z - 32 * j);
+    if (nv < 32) v &= (1u << nv) - 1u;
+    const int pos = col * Z + 32 * j, w = pos >> 5, o = pos & 31;
+    if (o == 0 && nv == 32) {
+        L[w] = v;
+        return;
+    }
+    atomicOr(&L[w], v << o);
+    if (o + nv > 32) atomicOr(&L[w + 1], v >> (32 - o));
+}
+
+// The m label bits of symbol s (label bit j at bit j): transmitted positions
+// m s .. m s + m - 1 in the transmit layout (from p0, the fillers skipped).
+__device__ __forceinline__ uint32_t tx_symbol_bits(const uint32_t *L, int s, int m, int p0, int k, int nf) {
+    const int v = p0 + s * m, before = k - v;  // positions ahead of the fillers
+    uint32_t w;
+    if (nf == 0 || before >= m) w = tx_window(L, v);
+    else if (before <= 0) w = tx_window(L, v + nf);
+    else w = (tx_window(L, v) & ((1u << before) - 1u)) | (tx_window(L, v + nf) & ~((1u << before) - 1u));
+    return w & ((1u << m) - 1u);
+}
+
+__global__ void __launch_bounds__(kTxThreads) k_tx(const TxParams p) {
     extern __shared__ __align__(16) unsigned char smem[];
-    const int ns = tx_ns(p.n);
+    const int Z = p.Z;
+    const TxLayout lay = tx_layout(p.G, p.n, Z, p.nnz, p.rows, p.inv_words);
+    const int nLw = lay.nLw, Wz = lay.Wz;
     const int kw = (p.k + 31) >> 5;
     const int nq = (kw + 3) >> 2;  // Philox blocks of source bits per codeword
-    uint8_t *s_c = smem;           // [G][ns] codeword bits, one byte each
-    uint32_t *s_w = reinterpret_cast<uint32_t *>(smem + (size_t)p.G * ns);  // [G][4 nq] source words
-    int2 *s_enc = reinterpret_cast<int2 *>(smem + tx_enc_off(p.G, p.n, p.k));  // [nnz] {col Z + s, Z - s}
-    int32_t *s_rp = reinterpret_cast<int32_t *>(s_enc + p.nnz);
-    uint32_t *s_lam = reinterpret_cast<uint32_t *>(s_rp + p.rows + 1);  // [G][inv_words] packed lambda
+    int2 *s_tab = reinterpret_cast<int2 *>(smem);  // [nnz] {column, shift}
+    int32_t *s_rp = reinterpret_cast<int32_t *>(s_tab + p.nnz);
+    uint32_t *s_cw = reinterpret_cast<uint32_t *>(smem + lay.cw_off);  // [G][per_cw]
     const int64_t cw_base = (int64_t)blockIdx.x * p.G;
+    const int G = p.B - cw_base < p.G ? (int)(p.B - cw_base) : p.G;  // codewords of this CTA
     const uint64_t cw0 = p.cw0 + (p.cw0_dev ? *p.cw0_dev : 0ull);
+    const int T = blockDim.x, tid = threadIdx.x;
+    auto Lp = [&](int gg) { return s_cw + (size_t)gg * lay.per_cw; };
+    auto lam = [&](int gg) { return Lp(gg) + nLw; };       // [4][Wz]
+    auto lin = [&](int gg) { return Lp(gg) + nLw + 4 * Wz; };  // [inv_words]
 
-    for (int i = threadIdx.x; i < p.nnz; i += blockDim.x) {
+    for (int i = tid; i < p.nnz; i += T) {
         const uint32_t bb = p.blk[i];
-        const int sh = (int)(bb & 0xFFFFu);
-        s_enc[i] = make_int2((int)(bb >> 16) * p.Z + sh, p.Z - sh);
+        s_tab[i] = make_int2((int)(bb >> 16), (int)(bb & 0xFFFFu));
     }
-    for (int i = threadIdx.x; i <= p.rows; i += blockDim.x) s_rp[i] = p.row_ptr[i];
-    for (int i = threadIdx.x; i < p.G * p.inv_words; i += blockDim.x) s_lam[i] = 0u;
-    // source bits (Philox stream 0), written packed to the output and to shared memory
-    for (int i = threadIdx.x; i < p.G * nq; i += blockDim.x) {
-        const int gg = i / nq, q = i - gg * nq;
+    for (int i = tid; i <= p.rows; i += T) s_rp[i] = p.row_ptr[i];
+    // source bits (Philox stream 0) to the output and to words 0 .. kw - 1; every later word
+    // (fillers, parity, padding) and the lambda vector start at zero
+    for (int gg = 0; gg < G; ++gg) {
         const int64_t cw = cw_base + gg;
-        if (cw >= p.B) continue;
-        const uint4 x = draw(p.seed, cw0 + (uint64_t)cw, 0u, (uint32_t)q);
-        const uint32_t w4[4] = {x.x, x.y, x.z, x.w};
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const int w = 4 * q + e;
-            if (w >= kw) break;
-            uint32_t word = w4[e];
-            const int valid = min(32, p.k - 32 * w);
-            if (valid < 32) word &= (1u << valid) - 1u;
-            if (p.info) p.info[cw * kw + w] = word;
-            s_w[(size_t)gg * 4 * nq + w] = word;
-        }
-    }
-    __syncthreads();
-    // one byte per bit, four bits per 32-bit store: nibble * 0x00204081 moves bit j to bit 8j (the four
-    // shifted copies of the nibble do not overlap). Bytes past k belong to parity column kb and are
-    // overwritten below.
-    const int k4 = (p.k + 3) >> 2;
-    for (int i = threadIdx.x; i < p.G * k4; i += blockDim.x) {
-        const int gg = i / k4, j = i - gg * k4;
-        if (cw_base + gg >= p.B) continue;
-        const uint32_t nib = (s_w[(size_t)gg * 4 * nq + (j >> 3)] >> (4 * (j & 7))) & 0xFu;
-        *reinterpret_cast<uint32_t *>(s_c + (size_t)gg * ns + 4 * j) = (nib * 0x00204081u) & 0x01010101u;
-    }
-    if (p.nf > 0) {
-        // filler bits are 0; bytes k .. 4 k4 - 1 already are (the last source word is masked)
-        const int f0 = 4 * k4, f1 = p.k + p.nf, nfz = f1 > f0 ? f1 - f0 : 0;
-        for (int i = threadIdx.x; i < p.G * nfz; i += blockDim.x) {
-            const int gg = i / nfz, v = f0 + (i - gg * nfz);
-            if (cw_base + gg < p.B) s_c[(size_t)gg * ns + v] = 0;
-        }
-    }
-    __syncthreads();
-
-    // systematic encoding, one thread per (codeword, z)
-    const int g = threadIdx.x / p.Z, z = threadIdx.x - g * p.Z;
-    const bool active = g < p.G && cw_base + g < p.B;
-    uint8_t *c = s_c + (size_t)(active ? g : 0) * ns;
-    const int Z = p.Z;
-    // bit of check z in block e: codeword position col Z + (z + s) mod Z; blocks of columns below
-    // `lim` Z are those with e.x < lim Z (s < Z)
-    auto at = [&](const int2 e) -> uint8_t {
-        int v = e.x + z;
-        if (z >= e.y) v -= Z;
-        return c[v];
-    };
-    uint8_t lam[4] = {0, 0, 0, 0};
-    if (active) {
-        // lambda_r = sum over the systematic blocks of core row r
-        const int kbZ = p.kb * Z;
-        for (int r = 0; r < 4; ++r) {
-            uint8_t acc = 0;
-#pragma unroll 4
-            for (int b = s_rp[r]; b < s_rp[r + 1]; ++b) {
-                const int2 e = s_enc[b];
-                if (e.x < kbZ) acc ^= at(e);
-            }
-            lam[r] = acc;
-        }
-        if (p.core_inv) {
-            // lambda as a 4Z-bit vector, bit r Z + z = lambda_r[z]
-            uint32_t *lw = s_lam + (size_t)g * p.inv_words;
-#pragma unroll
-            for (int r = 0; r < 4; ++r)
-                if (lam[r]) atomicOr(&lw[(r * Z + z) >> 5], 1u << ((r * Z + z) & 31));
-        } else {
-            c[p.kb * Z + z] = lam[0] ^ lam[1] ^ lam[2] ^ lam[3];  // p_a: the core rows sum to [I 0 0 0]
-        }
-    }
-    __syncthreads();
-    if (active && p.core_inv) {
-        // core parity p = H_core^-1 lambda: bit r Z + z is the parity of (row r Z + z of the inverse) & lambda
-        const uint32_t *lw = s_lam + (size_t)g * p.inv_words;
-#pragma unroll 1
-        for (int r = 0; r < 4; ++r) {
-            const uint32_t *row = p.core_inv + (size_t)(r * Z + z) * p.inv_words;
-            uint32_t x = 0u;
-            for (int w = 0; w < p.inv_words; ++w) x ^= __ldg(row + w) & lw[w];
-            c[(p.kb + r) * Z + z] = (uint8_t)(__popc(x) & 1);
-        }
-    } else if (active) {
-        const uint8_t pa = c[p.kb * Z + z];
-        const uint8_t pb = lam[0] ^ c[p.kb * Z + (z + 1 == Z ? 0 : z + 1)];  // row 0: P^1 p_a + p_b
-        const uint8_t pc = lam[1] ^ pa ^ pb;                                  // row 1: p_a + p_b + p_c
-        const uint8_t pd = lam[2] ^ pc;                                       // row 2: p_c + p_d
-        c[(p.kb + 1) * Z + z] = pb;
-        c[(p.kb + 2) * Z + z] = pc;
-        c[(p.kb + 3) * Z + z] = pd;
-    }
-    __syncthreads();
-    if (active) {
-        // extension rows only read columns < kb + 4, so they are independent
-        for (int r = 4; r < p.rows; ++r) {
-            uint8_t acc = 0;
-            const int ownZ = (p.kb + r) * Z;  // the row's own parity column; every other block lies below it
-            int2 eo = make_int2(ownZ, Z);
-#pragma unroll 4
-            for (int b = s_rp[r]; b < s_rp[r + 1]; ++b) {
-                const int2 e = s_enc[b];
-                if (e.x < ownZ) acc ^= at(e);
-                else eo = e;
-            }
-            // check z holds own-column bit (z + s_own) mod Z
-            int v = eo.x + z;
-            if (z >= eo.y) v -= Z;
-            c[v] = acc;
-        }
-    }
-    __syncthreads();
-
-    // the codewords themselves, packed 32 positions per word by warp ballots
-    if (p.cw_out) {
-        const int nw = (p.n + 31) >> 5;
-        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-        for (int w = warp; w < p.G * nw; w += nwarps) {
-            const int gg = w / nw, ww = w - gg * nw;
-            const int64_t cw = cw_base + gg;
-            const int pos = ww * 32 + lane;
-            const bool bit = cw < p.B && pos < p.n && s_c[(size_t)gg * ns + pos] != 0;
-            const unsigned word = __ballot_sync(0xFFFFFFFFu, bit);
-            if (lane == 0 && cw < p.B) p.cw_out[cw * nw + ww] = word;
-        }
-    }
-    if (!p.y) return;  // codewords only: no barrier follows
-
-    // Gray mapping and AWGN (Philox stream 1)
-    const int m = p.m, S = p.n_tx / m;
-    if (m == 1) {
-        const int nqs = (S + 3) >> 2;
-        for (int i = threadIdx.x; i < p.G * nqs; i += blockDim.x) {
-            const int gg = i / nqs, q = i - gg * nqs;
-            const int64_t cw = cw_base + gg;
-            if (cw >= p.B) continue;
-            const float sd = sqrtf(p.no[cw * p.no_stride] * 0.5f);
-            const uint4 x = draw(p.seed, cw0 + (uint64_t)cw, 1u, (uint32_t)q);
-            const float2 g01 = box_muller(x.x, x.y), g23 = box_muller(x.z, x.w);
-            const float gs[4] = {g01.x, g01.y, g23.x, g23.y};
-            const uint8_t *cg = s_c + (size_t)gg * ns;
+        uint32_t *L = Lp(gg);
+        for (int q = tid; q < nq; q += T) {
+            const uint4 x = draw(p.seed, cw0 + (uint64_t)cw, 0u, (uint32_t)q);
+            const uint32_t w4[4] = {x.x, x.y, x.z, x.w};
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
-                const int s = 4 * q + e;
-                if (s < S) p.y[cw * S + s] = (1.0f - 2.0f * (float)cg[tx_position(s, p.p0, p.k, p.nf)]) + sd * gs[e];
+                const int w = 4 * q + e;
+                if (w >= kw) break;
+                uint32_t word = w4[e];
+                const int valid = min(32, p.k - 32 * w);
+                if (valid < 32) word &= (1u << valid) - 1u;
+                if (p.info) p.info[cw * kw + w] = word;
+                L[w] = word;
+            }
+        }
+        for (int w = kw + tid; w < nLw; w += T) L[w] = 0u;
+        for (int w = tid; w < p.inv_words; w += T) lin(gg)[w] = 0u;
+    }
+    __syncthreads();
+
+    // lambda_r = sum over the systematic blocks of core row r, word by word
+    for (int i = tid; i < G * 4 * Wz; i += T) {
+        const int gg = i / (4 * Wz), rj = i - gg * 4 * Wz, r = rj / Wz, j = rj - r * Wz;
+        const uint32_t *L = Lp(gg);
+        uint32_t acc = 0u;
+        for (int b = s_rp[r]; b < s_rp[r + 1]; ++b) {
+            const int2 e = s_tab[b];
+            if (e.x < p.kb) acc ^= tx_rot(L, e.x, e.y, j, Z);
+        }
+        lam(gg)[rj] = acc;
+        if (p.core_inv) tx_put(lin(gg), r, j, acc, Z);  // bit r Z + z of the 4Z-bit vector
+    }
+    __syncthreads();
+    if (p.core_inv) {
+        // core parity p = H_core^-1 lambda: bit i of p (position kb Z + i) is the parity of row i of the
+        // inverse AND lambda
+        const int N = 4 * Z;
+        for (int i = tid; i < G * N; i += T) {
+            const int gg = i / N, b = i - gg * N;
+            const uint32_t *row = p.core_inv + (size_t)b * p.inv_words, *lw = lin(gg);
+            uint32_t x = 0u;
+            for (int w = 0; w < p.inv_words; ++w) x ^= __ldg(row + w) & lw[w];
+            if (__popc(x) & 1) {
+                const int v = p.kb * Z + b;
+                atomicOr(&Lp(gg)[v >> 5], 1u << (v & 31));
             }
         }
     } else {
-        const int h = m >> 1, nqs = (S + 1) >> 1;
-        for (int i = threadIdx.x; i < p.G * nqs; i += blockDim.x) {
-            const int gg = i / nqs, q = i - gg * nqs;
-            const int64_t cw = cw_base + gg;
-            if (cw >= p.B) continue;
-            const float sd = sqrtf(p.no[cw * p.no_stride] * 0.5f);
+        // the 5G dual-diagonal core: the core rows sum to [I 0 0 0], so p_a = sum of the lambdas
+        for (int i = tid; i < G * Wz; i += T) {
+            const int gg = i / Wz, j = i - gg * Wz;
+            const uint32_t *l = lam(gg);
+            tx_put(Lp(gg), p.kb, j, l[j] ^ l[Wz + j] ^ l[2 * Wz + j] ^ l[3 * Wz + j], Z);
+        }
+        __syncthreads();
+        for (int i = tid; i < G * Wz; i += T) {
+            const int gg = i / Wz, j = i - gg * Wz;
+            const uint32_t *l = lam(gg);
+            uint32_t *L = Lp(gg);
+            const uint32_t pa = l[j] ^ l[Wz + j] ^ l[2 * Wz + j] ^ l[3 * Wz + j];
+            const uint32_t pb = l[j] ^ tx_rot(L, p.kb, 1, j, Z);  // row 0: P^1 p_a + p_b
+            const uint32_t pc = l[Wz + j] ^ pa ^ pb;                // row 1: p_a + p_b + p_c
+            const uint32_t pd = l[2 * Wz + j] ^ pc;                 // row 2: p_c + p_d
+            tx_put(L, p.kb + 1, j, pb, Z);
+            tx_put(L, p.kb + 2, j, pc, Z);
+            tx_put(L, p.kb + 3, j, pd, Z);
+        }
+    }
+    __syncthreads();
+    // extension rows read only columns below kb + 4, so they are independent: check z of row r holds
+    // its own column's position (z + s_own) mod Z, so own-column bit v sums the other blocks rotated
+    // by s - s_own
+    {
+        const int items = (p.rows - 4) * Wz;
+        for (int i = tid; i < G * items; i += T) {
+            const int gg = i / items, rj = i - gg * items, r = 4 + rj / Wz, j = rj - (r - 4) * Wz;
+            const int own = p.kb + r;
+            int s_own = 0;
+            for (int b = s_rp[r]; b < s_rp[r + 1]; ++b)
+                if (s_tab[b].x == own) s_own = s_tab[b].y;
+            uint32_t *L = Lp(gg);
+            uint32_t acc = 0u;
+            for (int b = s_rp[r]; b < s_rp[r + 1]; ++b) {
+                const int2 e = s_tab[b];
+                if (e.x == own) continue;
+                int s = e.y - s_own;
+                if (s < 0) s += Z;
+                acc ^= tx_rot(L, e.x, s, j, Z);
+            }
+            tx_put(L, own, j, acc, Z);
+        }
+    }
+    __syncthreads();
+
+    // the codewords themselves, packed 32 positions per word (positions past n are zero)
+    if (p.cw_out) {
+        const int nw = (p.n + 31) >> 5;
+        for (int i = tid; i < G * nw; i += T) {
+            const int gg = i / nw, w = i - gg * nw;
+            p.cw_out[(cw_base + gg) * nw + w] = Lp(gg)[w];
+        }
+    }
+    if (!p.y) return;
+
+    // Gray mapping and AWGN (Philox stream 1): four real or two complex symbols per draw; y = fma(sd, n, x)
+    // in every mapper kernel, so k_tx and k_map_awgn agree bit for bit
+    const int m = p.m, S = p.n_tx / m;
+    const int per = m == 1 ? 4 : 2, nqs = (S + per - 1) / per;
+    for (int gg = 0; gg < G; ++gg) {
+        const int64_t cw = cw_base + gg;
+        const uint32_t *L = Lp(gg);
+        const float sd = sqrtf(p.no[cw * p.no_stride] * 0.5f);
+        for (int q = tid; q < nqs; q += T) {
             const uint4 x = draw(p.seed, cw0 + (uint64_t)cw, 1u, (uint32_t)q);
-            const float2 gn[2] = {box_muller(x.x, x.y), box_muller(x.z, x.w)};
-            const uint8_t *cb = s_c + (size_t)gg * ns + p.p0;
+            if (m == 1) {
+                const float2 g01 = box_muller(x.x, x.y), g23 = box_muller(x.z, x.w);
+                const float gs[4] = {g01.x, g01.y, g23.x, g23.y};
 #pragma unroll
-            for (int e = 0; e < 2; ++e) {
-                const int s = 2 * q + e;
-                if (s >= S) break;
-                const uint8_t *bits = cb + (size_t)s * m;
-                uint8_t gathered[8];
-                if (p.nf > 0) {  // a shortened code: the symbol's bits skip the fillers
-                    const uint8_t *cg = s_c + (size_t)gg * ns;
-                    for (int j = 0; j < m; ++j) gathered[j] = cg[tx_position(s * m + j, p.p0, p.k, p.nf)];
-                    bits = gathered;
+                for (int e = 0; e < 4; ++e) {
+                    const int s = 4 * q + e;
+                    if (s >= S) break;
+                    const int v = tx_position(s, p.p0, p.k, p.nf);
+                    p.y[cw * S + s] = __fmaf_rn(sd, gs[e], 1.0f - 2.0f * (float)((L[v >> 5] >> (v & 31)) & 1u));
                 }
-                float xi, xq;
-                if (p.points) {
-                    int l = 0;
-                    for (int j = 0; j < m; ++j) l = (l << 1) | bits[j];
-                    const float2 pt = p.points[l];
-                    xi = pt.x;
-                    xq = pt.y;
-                } else {
-                    xi = (float)pam_level(bits, h) * p.scale;
-                    xq = (float)pam_level(bits + 1, h) * p.scale;
+            } else {
+                const int h = m >> 1;
+                const float2 gn[2] = {box_muller(x.x, x.y), box_muller(x.z, x.w)};
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    const int s = 2 * q + e;
+                    if (s >= S) break;
+                    const uint32_t bits = tx_symbol_bits(L, s, m, p.p0, p.k, p.nf);
+                    float xi, xq;
+                    if (p.points) {
+                        const float2 pt = p.points[__brev(bits) >> (32 - m)];  // label MSB first
+                        xi = pt.x;
+                        xq = pt.y;
+                    } else {
+                        xi = __fmul_rn((float)pam_level(bits, h, 0), p.scale);
+                        xq = __fmul_rn((float)pam_level(bits, h, 1), p.scale);
+                    }
+                    reinterpret_cast<float2 *>(p.y)[cw * S + s] =
+                        make_float2(__fmaf_rn(sd, gn[e].x, xi), __fmaf_rn(sd, gn[e].y, xq));
                 }
-                reinterpret_cast<float2 *>(p.y)[cw * S + s] = make_float2(xi + sd * gn[e].x, xq + sd * gn[e].y);
             }
         }
     }
@@ -285,7 +312,7 @@ __global__ void __launch_bounds__(256) k_map_awgn(const uint32_t *__restrict__ b
                 const int s = 4 * q + e;
                 if (s >= S) break;
                 const uint8_t bit = (uint8_t)((row[s >> 5] >> (s & 31)) & 1u);
-                y[b * S + s] = (1.0f - 2.0f * (float)bit) + sd * gs[e];
+                y[b * S + s] = __fmaf_rn(sd, gs[e], 1.0f - 2.0f * (float)bit);
             }
         } else {
             const int h = m >> 1;
@@ -294,14 +321,14 @@ __global__ void __launch_bounds__(256) k_map_awgn(const uint32_t *__restrict__ b
             for (int e = 0; e < 2; ++e) {
                 const int s = 2 * q + e;
                 if (s >= S) break;
-                uint8_t lb[8];
+                uint32_t lb = 0u;
                 for (int j = 0; j < m; ++j) {
                     const int t = s * m + j;
-                    lb[j] = (uint8_t)((row[t >> 5] >> (t & 31)) & 1u);
+                    lb |= ((row[t >> 5] >> (t & 31)) & 1u) << j;
                 }
-                const float xi = (float)pam_level(lb, h) * scale;
-                const float xq = (float)pam_level(lb + 1, h) * scale;
-                reinterpret_cast<float2 *>(y)[b * S + s] = make_float2(xi + sd * gn[e].x, xq + sd * gn[e].y);
+                const float xi = __fmul_rn((float)pam_level(lb, h, 0), scale);
+                const float xq = __fmul_rn((float)pam_level(lb, h, 1), scale);
+                reinterpret_cast<float2 *>(y)[b * S + s] = make_float2(__fmaf_rn(sd, gn[e].x, xi), __fmaf_rn(sd, gn[e].y, xq));
             }
         }
     }
@@ -829,17 +856,18 @@ int launch_tx(ldpcx_code_t c, uint64_t seed, uint64_t cw0, const uint64_t *cw0_d
     p.nnz = c->nnz;
     p.core_inv = c->enc == kEncCoreInv ? d.core_inv : nullptr;
     p.inv_words = c->enc == kEncCoreInv ? c->inv_words : 0;
-    int G = kMaxThreads / c->Z;
-    if (G < 1) G = 1;
-    while (G > 1 && tx_smem(G, c->n, c->k, c->nnz, c->rows, p.inv_words) > 96 * 1024) --G;
+    // codewords per CTA: about 2048 transmitted positions of mapping work, within 48 KB of shared memory
+    int G = (int)std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(16, 2048 / std::max(1, c->n_tx)), B));
+    while (G > 1 && tx_layout(G, c->n, c->Z, c->nnz, c->rows, p.inv_words).bytes > 48 * 1024) --G;
     p.G = G;
-    const size_t smem = tx_smem(G, c->n, c->k, c->nnz, c->rows, p.inv_words);
+    const size_t smem = tx_layout(G, c->n, c->Z, c->nnz, c->rows, p.inv_words).bytes;
+    if (smem > 227 * 1024) return LDPCX_E_UNSUPPORTED;
     if (smem > 48 * 1024 &&
         cudaFuncSetAttribute(k_tx, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return LDPCX_E_CUDA;
-    const int threads = (G * c->Z + 31) / 32 * 32;
     const int64_t grid = (B + G - 1) / G;
-    k_tx<<<(unsigned)grid, threads, smem, stream>>>(p);
+    if (grid > 0x7FFFFFFF) return LDPCX_E_INVAL;
+    k_tx<<<(unsigned)grid, kTxThreads, smem, stream>>>(p);
     return cuda_status(cudaGetLastError());
 }
 
