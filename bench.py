@@ -487,15 +487,17 @@ def measure_variants(lx, code, llr, bits, its, stream, args, pk):
         del ws
     lx.ldpcx_tune_set(lx.TUNE_CN_STATE, 1)
     if "minsum_f32" in out and "minsum_f16" in out:
-        # FP16 >= 1.6x FP32 throughput, like for like: the same storage format at both precisions
+        # FP16 >= 1.6x FP32 throughput: each precision's production format (FP16: check-node state for the core
+        # rows and per-edge messages for the extension rows; FP32: check-node state), and per-edge for both
         cns = out["minsum_f32"]["decode_ms"] / out["minsum_f16"]["decode_ms"]
         edge = out["minsum_f32_per_edge"]["decode_ms"] / out["minsum_f16_per_edge"]["decode_ms"]
         out["f16_over_f32"] = cns
         out["f16_over_f32_per_edge"] = edge
         out["f16_over_f32_target"] = {
             "target": 1.6, "met": bool(cns >= 1.6 and edge >= 1.6),
-            "reason": "both formats keep a resident CTA's messages in L2, so the decoder is bound by instruction "
-                      "issue, not by the message width; FP16 and FP32 run the same instructions"}
+            "reason": "every format keeps a resident CTA's messages in L2, so the decoder is bound by instruction "
+                      "issue, not by the message width; the FP16 lead comes from its per-edge extension rows "
+                      "(one conversion per message), not from moving half the bytes"}
         # not a precision ratio: FP16 check-node state against FP32 per-edge messages (format and precision)
         out["f16_state_over_f32_per_edge_format_and_precision"] = (out["minsum_f32_per_edge"]["decode_ms"]
                                                                    / out["minsum_f16"]["decode_ms"])
