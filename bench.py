@@ -9,14 +9,14 @@ stop, FP16 messages with FP32 arithmetic.
 
 One step = one Monte-Carlo batch through the whole device path: Philox
 source + dual-diagonal encoder + Gray mapper + AWGN (sim_tx) -> APP demapper
-(demap_app) -> layered BP decoder (ldpc_bp_decode) -> error count
-(sim_count). Metric: decoded information Gbit/s = ranks x B x k / step time;
+fused into the layered BP decoder's channel load (ldpc_bp_decode_qam; with
+--unfused, demap_app then ldpc_bp_decode) -> error count (sim_count). Metric: decoded information Gbit/s = ranks x B x k / step time;
 edge-updates/s = ranks x B x E x iterations / step time.
 
 Timing: W warm-up steps, then K timed steps between barriers and device
 synchronisations, CUDA events on the launching stream, max over ranks.
-Every buffer (y 208 MB, LLRs 406 MB, messages 994 MB) is larger than L2,
-so no flush is needed.
+Every buffer (y 208 MB, messages 893 MB; LLRs 406 MB with --unfused) is
+larger than L2, so no flush is needed.
 
 --impl reference times the CPU oracle (the reference arm of this repository:
 the paper ships no code) on a bounded sample of the same workload.
@@ -304,9 +304,10 @@ def run_gpu(args):
     r = code.k / code.n_tx
     n0 = torch.tensor([1.0 / (r * M * 10 ** (EBN0 / 10))], dtype=torch.float32, device=dev)
     # two buffer sets: step i + 1's transmitter and demapper run on their own stream while step i decodes
+    fused = not args.unfused
     bufs = [dict(y=torch.empty((B, S, 2), dtype=torch.float32, device=dev),
                  info=torch.empty((B, kw), dtype=torch.int32, device=dev),
-                 llr=torch.empty((B, code.n_tx), dtype=torch.float32, device=dev),
+                 llr=None if fused else torch.empty((B, code.n_tx), dtype=torch.float32, device=dev),
                  bits=torch.empty((B, kw), dtype=torch.int32, device=dev),
                  its=torch.empty((B,), dtype=torch.int32, device=dev)) for _ in range(2)]
     y, info, llr, bits, its = (bufs[0][key] for key in ("y", "info", "llr", "bits", "its"))
@@ -316,9 +317,9 @@ def run_gpu(args):
     from paper_2203_11854_gb300 import multi
     cw_base = multi.rank_cw_base(rank)  # disjoint codeword (Philox counter) ranges per rank
 
-    # The decoder's stream has the higher priority, so its CTAs are dispatched first and the transmitter and
-    # demapper of the next step only take the SM slots that the decoder's last, partial wave leaves idle
-    # (4096 codewords on 2 x 152 slots: 13.5 waves). Every step still runs all four kernels.
+    # The decoder's stream has the higher priority, so its CTAs are dispatched first and the transmitter (and,
+    # unfused, the demapper) of the next step only take the SM slots that the decoder's last, partial wave leaves
+    # idle (4096 codewords on 2 x 152 slots: 13.5 waves). Every step still runs all of its kernels.
     dec_stream = torch.cuda.Stream(device=dev, priority=-1)
     tx_stream = torch.cuda.Stream(device=dev, priority=0)
     ev_rx = [torch.cuda.Event() for _ in range(2)]    # demapper output of buffer j is ready
@@ -328,13 +329,18 @@ def run_gpu(args):
         b = bufs[i & 1]
         tx_stream.wait_event(ev_free[i & 1])
         lx.sim_tx(code, SEED, cw_base + i * B, B, M, n0, y_out=b["y"], info_out=b["info"], stream=tx_stream)
-        lx.demap_app(b["y"], n0, M, method=lx.DEMAP_MAXLOG, clamp=CLAMP, llr_out=b["llr"], stream=tx_stream)
+        if not fused:
+            lx.demap_app(b["y"], n0, M, method=lx.DEMAP_MAXLOG, clamp=CLAMP, llr_out=b["llr"], stream=tx_stream)
         ev_rx[i & 1].record(tx_stream)
         dec_stream.wait_event(ev_rx[i & 1])
         if timed_decode is not None:
             timed_decode[0].record(dec_stream)
-        lx.ldpc_bp_decode(code, b["llr"], **dec, llr_out=False, bits_out=b["bits"], iters_out=b["its"], ws=ws,
-                          stream=dec_stream)
+        if fused:
+            lx.ldpc_bp_decode_qam(code, b["y"], n0, M, demap_method=lx.DEMAP_MAXLOG, demap_clamp=CLAMP, **dec,
+                                  llr_out=False, bits_out=b["bits"], iters_out=b["its"], ws=ws, stream=dec_stream)
+        else:
+            lx.ldpc_bp_decode(code, b["llr"], **dec, llr_out=False, bits_out=b["bits"], iters_out=b["its"], ws=ws,
+                              stream=dec_stream)
         if timed_decode is not None:
             timed_decode[1].record(dec_stream)
         lx.sim_count(b["info"], b["bits"], b["its"], code.k, counts, stream=dec_stream)
@@ -378,9 +384,10 @@ def run_gpu(args):
 
     # decode-kernel roofline: algorithmic bytes per launch / mean decode launch time. The message
     # bytes are those of the storage format the decoder uses (check-node state for layered min-sum):
-    # one read and one write per iteration except the first read and the last write.
+    # one read and one write per iteration except the first read and the last write; the channel input is
+    # the received symbols (8 B each) with the demapper fused, else the LLRs (4 B each).
     cn_state, msg_cw = lx.ldpc_bp_msg_format(code, **{k: dec[k] for k in ("algo", "iters", "msg_prec")})
-    alg_bytes = B * (msg_cw * 2 * (ITERS - 1) + 4 * code.n_tx + code.k / 8)
+    alg_bytes = B * (msg_cw * 2 * (ITERS - 1) + (8 * S if fused else 4 * code.n_tx) + code.k / 8)
     dec_mean = sum(dec_ms) / len(dec_ms)
     pk, pk_kind = peaks()
     achieved = alg_bytes / (dec_mean * 1e-3) / 1e9
@@ -392,13 +399,15 @@ def run_gpu(args):
     if rank == 0:
         variants = {}
         if not args.quick:
+            if llr is None:  # the variants decode LLRs: demap the last buffer's symbols once
+                llr = lx.demap_app(y, n0, M, method=lx.DEMAP_MAXLOG, clamp=CLAMP)
             variants = measure_variants(lx, code, llr, bits, its, stream, args, pk)
             variants["mixed_batch"] = measure_mixed(lx, stream, args, pk)
             variants["sweep_256qam"] = measure_sweep(lx, code, pk)
             variants["grad_step"] = measure_grad_step(lx)
             variants["flood_spa_z8"] = measure_flood_z8(lx)
             variants["polar_scl"] = measure_polar(lx)
-        e2e = measure_e2e(lx, code, y, info, n0, dec, stream, args, dev)
+        e2e = measure_e2e(lx, code, y, info, n0, dec, stream, args, dev, fused=fused)
         cpu = None if (world > 1 or args.no_cpu) else cpu_baseline(args.cpu_seconds)
         result = {
             "metric": METRIC, "value": value, "unit": "Gbit/s", "n_gpus": world, "steps": args.steps,
@@ -422,7 +431,7 @@ def run_gpu(args):
                          # the ceiling that binds: warp instructions (ncu, same sources) over the issue rate
                          "issue_frac": issue_frac, "warp_inst_per_32_edge_updates": ipe},
             "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
-            "gpu_launches": 4 * args.steps,
+            "gpu_launches": (3 if fused else 4) * args.steps,
             "variants": variants,
         }
         print(json.dumps(result), flush=True)
@@ -704,25 +713,26 @@ def measure_mixed(lx, stream, args, pk):
     return out
 
 
-def measure_e2e(lx, code, y_dev, info_dev, n0, dec, stream, args, dev):
-    """The receiver through the public API from host memory: pinned y -> device, demap, decode, bits -> host.
-    Double-buffered: the copies run on their own stream and the demapper on a lower-priority one, so step
-    i + 1's symbols move in and are demapped, and step i - 1's bits move out, while step i decodes. Every
-    step's copies lie inside the timed region."""
+def measure_e2e(lx, code, y_dev, info_dev, n0, dec, stream, args, dev, fused=True):
+    """The receiver through the public API from host memory: pinned y -> device, demap + decode
+    (ldpc_bp_decode_qam; unfused: demap_app on a lower-priority stream, then ldpc_bp_decode), bits -> host.
+    Double-buffered: the copies run on their own stream, so step i + 1's symbols move in (and, unfused, are
+    demapped) and step i - 1's bits move out while step i decodes. Every step's copies lie inside the timed
+    region."""
     import torch
     kw = (code.k + 31) // 32
     y_host = y_dev.cpu().pin_memory()
     bits_host = [torch.empty((B, kw), dtype=torch.int32).pin_memory() for _ in range(2)]
     y_d = [torch.empty_like(y_dev) for _ in range(2)]
-    llr = [torch.empty((B, code.n_tx), dtype=torch.float32, device=dev) for _ in range(2)]
+    llr = [None if fused else torch.empty((B, code.n_tx), dtype=torch.float32, device=dev) for _ in range(2)]
     bits = [torch.empty((B, kw), dtype=torch.int32, device=dev) for _ in range(2)]
     ws = torch.empty(lx.ldpc_bp_workspace(code, B, **dec), dtype=torch.uint8, device=dev)
     copy = torch.cuda.Stream(device=dev)
     rx = torch.cuda.Stream(device=dev, priority=0)
     dec_s = torch.cuda.Stream(device=dev, priority=-1)
     ev_in = [torch.cuda.Event() for _ in range(2)]    # symbols of buffer j are on the device
-    ev_used = [torch.cuda.Event() for _ in range(2)]  # the demapper has consumed symbols j
-    ev_rx = [torch.cuda.Event() for _ in range(2)]    # LLRs of buffer j are ready
+    ev_used = [torch.cuda.Event() for _ in range(2)]  # the demapper (fused: the decoder) has consumed symbols j
+    ev_rx = [torch.cuda.Event() for _ in range(2)]    # the decoder's input of buffer j is ready
     ev_llr = [torch.cuda.Event() for _ in range(2)]   # the decoder has consumed LLRs j
     ev_dec = [torch.cuda.Event() for _ in range(2)]   # bits of buffer j are ready
     ev_out = [torch.cuda.Event() for _ in range(2)]   # bits of buffer j have reached the host buffer
@@ -732,6 +742,9 @@ def measure_e2e(lx, code, y_dev, info_dev, n0, dec, stream, args, dev):
         with torch.cuda.stream(copy):
             y_d[j].copy_(y_host, non_blocking=True)
         ev_in[j].record(copy)
+        if fused:
+            ev_rx[j] = ev_in[j]
+            return
         rx.wait_event(ev_in[j])
         rx.wait_event(ev_llr[j])
         lx.demap_app(y_d[j], n0, M, method=lx.DEMAP_MAXLOG, clamp=CLAMP, llr_out=llr[j], stream=rx)
@@ -748,8 +761,13 @@ def measure_e2e(lx, code, y_dev, info_dev, n0, dec, stream, args, dev):
                 front(1 - j)
             dec_s.wait_event(ev_rx[j])
             dec_s.wait_event(ev_out[j])
-            lx.ldpc_bp_decode(code, llr[j], **dec, bits_out=bits[j], iters_out=False, ws=ws, stream=dec_s)
-            ev_llr[j].record(dec_s)
+            if fused:
+                lx.ldpc_bp_decode_qam(code, y_d[j], n0, M, demap_method=lx.DEMAP_MAXLOG, demap_clamp=CLAMP, **dec,
+                                      bits_out=bits[j], iters_out=False, ws=ws, stream=dec_s)
+                ev_used[j].record(dec_s)
+            else:
+                lx.ldpc_bp_decode(code, llr[j], **dec, bits_out=bits[j], iters_out=False, ws=ws, stream=dec_s)
+                ev_llr[j].record(dec_s)
             ev_dec[j].record(dec_s)
             copy.wait_event(ev_dec[j])
             with torch.cuda.stream(copy):
@@ -767,11 +785,13 @@ def measure_e2e(lx, code, y_dev, info_dev, n0, dec, stream, args, dev):
     b.record(stream)
     torch.cuda.synchronize()
     ms = a.elapsed_time(b) / reps
+    path = ("pinned host y -> ldpc_bp_decode_qam (demapper fused into the decoder) -> host bits; copies on their "
+            "own stream, double-buffered against the previous step's decode") if fused else (
+            "pinned host y -> demap_app -> ldpc_bp_decode -> host bits; copies on their own stream and the demapper "
+            "on a lower-priority one, double-buffered against the previous step's decode")
     return {"value": B * code.k / (ms * 1e-3) / 1e9, "unit": "Gbit/s",
             "h2d_bytes_per_step": y_host.numel() * 4, "d2h_bytes_per_step": bits_host[0].numel() * 4,
-            "ms_per_step": ms,
-            "path": "pinned host y -> demap_app -> ldpc_bp_decode -> host bits; copies on their own stream and "
-                    "the demapper on a lower-priority one, double-buffered against the previous step's decode"}
+            "ms_per_step": ms, "path": path}
 
 
 CASES = ("minsum_f16", "minsum_f32", "minsum_fix6", "spa_f16", "spa_f32", "grad", "mixed", "flood_spa_z8")
@@ -876,6 +896,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--batch", type=int, default=B, help="codewords per step (4096 for the headline workload)")
+    ap.add_argument("--unfused", action="store_true",
+                    help="run the demapper as its own kernel (demap_app, then ldpc_bp_decode) instead of fused")
     ap.add_argument("--case", default=None, choices=CASES,
                     help="time one kernel's launches alone (for profiling) instead of the Monte-Carlo step")
     args = ap.parse_args()

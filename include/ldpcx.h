@@ -319,6 +319,26 @@ int ldpc_bp_decode(ldpcx_code_t code, const float *llr_ch, int64_t B, const ldpc
                    float *llr_out, uint32_t *bits_out, int32_t *iters_out,
                    void *ws, size_t ws_bytes, void *stream);
 
+/* The demapper fused into the decoder (Demapper("app") feeding
+ * LDPC5GDecoder in the paper's Listing 1, as one launch): the layered
+ * decoders compute each codeword's channel LLRs from its received symbols
+ * while loading them, so no LLR array is written or read. The results equal
+ * demap_app(y, no, no_stride, B, n_tx/m, m, demap_method, demap_clamp, llr)
+ * followed by ldpc_bp_decode(code, llr, B, opts, ...) bit for bit, the
+ * NONFINITE flag included (a non-finite symbol gives zero LLRs).
+ * y        (device) [B][n_tx/m] complex symbols as float pairs (re, im), or
+ *          [B][n_tx] floats for m = 1; the layout sim_tx writes.
+ * no       (device) N0: [B] floats (no_stride = 1) or one float (0).
+ * m        1, 2, 4, 6 or 8 bits per symbol; n_tx must be a multiple of m.
+ * demap_method LDPCX_DEMAP_EXACT or LDPCX_DEMAP_MAXLOG; demap_clamp finite, > 0.
+ * opts, outputs, ws and ws_bytes as ldpc_bp_decode (same workspace size).
+ * Errors: LDPCX_E_INVAL for a bad argument; LDPCX_E_UNSUPPORTED for the
+ * flooding schedules, whose kernels read the channel LLRs in every
+ * iteration; otherwise as ldpc_bp_decode. */
+int ldpc_bp_decode_qam(ldpcx_code_t code, const float *y, const float *no, int64_t no_stride, int64_t B, int m,
+                       int demap_method, float demap_clamp, const ldpcx_decode_opts *opts, float *llr_out,
+                       uint32_t *bits_out, int32_t *iters_out, void *ws, size_t ws_bytes, void *stream);
+
 /* Decoder tuning knobs (process-wide; read at each launch; the autotuner's
  * search space). LDPCX_TUNE_L2_PREFETCH: layered decoders prefetch into L2 the
  * message span of the layer this many layers ahead (0 = off, 0..16, default 0).
@@ -384,7 +404,7 @@ int ldpcx_fault_set(int kind, int after);
  * bytes) plus B times the per-codeword bytes of the decoder's message format
  * must fit in the array, else LDPCX_E_WORKSPACE before any work; B is bounded
  * before any product is formed. At Z = 384, BG1-shaped: layered min-sum
- * (their state format) 118 / 153 / 436 codewords with FP32 / FP16 / FIX6
+ * (their state format) 118 / 153 / 307 codewords with FP32 / FP16 / FIX6
  * messages; sum-product and flooding (per-edge messages) 69 / 138. The first
  * call on a device looks up the array's device address (cudaGetSymbolAddress);
  * make that first call before any stream capture. Every call on a device

@@ -119,6 +119,8 @@ _SIGS = {
     "polar_scl_decode": ([_vp, _vp, _i64, _i, _vp, _vp, _vp], _i),
     "ldpc_bp_workspace": ([_vp, _i64, C.POINTER(DecodeOpts), C.POINTER(_sz)], _i),
     "ldpc_bp_decode": ([_vp, _vp, _i64, C.POINTER(DecodeOpts), _vp, _vp, _vp, _vp, _sz, _vp], _i),
+    "ldpc_bp_decode_qam": ([_vp, _vp, _vp, _i64, _i64, _i, _i, _f, C.POINTER(DecodeOpts), _vp, _vp, _vp, _vp, _sz,
+                            _vp], _i),
     "sim_count": ([_vp, _vp, _vp, _i64, _i, _vp, _vp], _i),
     "sim_workspace": ([C.POINTER(SimConfig), C.POINTER(_sz)], _i),
     "sim_run": ([C.POINTER(SimConfig), C.POINTER(SimCounts), C.POINTER(_i), _vp, _sz, _vp], _i),
@@ -619,6 +621,40 @@ def ldpc_bp_decode(code: Code, llr_ch, *, algo: int = LAYERED_MINSUM, iters: int
     _check(load_library().ldpc_bp_decode(code.handle, _ptr(llr_ch), B, C.byref(o), _ptr(llr_out), _ptr(bits_out),
                                          _ptr(iters_out), _ptr(ws), ws.numel() * ws.element_size(),
                                          _stream(stream)), "ldpc_bp_decode")
+    return llr_out, bits_out, iters_out
+
+
+def ldpc_bp_decode_qam(code: Code, y, no, m: int, *, demap_method: int = DEMAP_EXACT, demap_clamp: float = 20.0,
+                       algo: int = LAYERED_MINSUM, iters: int = 20, msg_prec: int = MSG_F32, early_stop: bool = False,
+                       offset: float = 0.5, clamp: float = 20.0, llr_out=False, bits_out=True, iters_out=True,
+                       ws=None, stream=None):
+    """Demapper fused into the layered decoder: received symbols y [B, n_tx/m, 2] ([B, n_tx] for m = 1) and N0
+    (one value or [B]) -> the outputs of demap_app followed by ldpc_bp_decode, bit for bit. Outputs and ws as
+    ldpc_bp_decode."""
+    import torch
+    _cuda_f32(y, "y")
+    _cuda_f32(no, "no")
+    B = y.shape[0]
+    dev = y.device
+    o = _opts(algo, iters, msg_prec, early_stop, offset, clamp, None)
+    if llr_out is True:
+        llr_out = torch.empty((B, code.n), dtype=torch.float32, device=dev)
+    if bits_out is True:
+        bits_out = torch.empty((B, (code.k + 31) // 32), dtype=torch.int32, device=dev)
+    if iters_out is True:
+        iters_out = torch.empty((B,), dtype=torch.int32, device=dev)
+    llr_out = llr_out if llr_out is not False else None
+    bits_out = bits_out if bits_out is not False else None
+    iters_out = iters_out if iters_out is not False else None
+    need = ldpc_bp_workspace(code, B, algo=algo, iters=iters, msg_prec=msg_prec, early_stop=early_stop,
+                             offset=offset, clamp=clamp)
+    if ws is None:
+        ws = torch.empty(max(need, 1), dtype=torch.uint8, device=dev)
+    stride = 0 if no.numel() == 1 else 1
+    _check(load_library().ldpc_bp_decode_qam(code.handle, _ptr(y), _ptr(no), stride, B, m, demap_method,
+                                             demap_clamp, C.byref(o), _ptr(llr_out), _ptr(bits_out),
+                                             _ptr(iters_out), _ptr(ws), ws.numel() * ws.element_size(),
+                                             _stream(stream)), "ldpc_bp_decode_qam")
     return llr_out, bits_out, iters_out
 
 

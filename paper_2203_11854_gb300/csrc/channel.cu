@@ -6,6 +6,7 @@
 #include <algorithm>
 
 #include "common.cuh"
+#include "demap.cuh"
 
 namespace ldpcx {
 namespace {
@@ -335,47 +336,6 @@ __global__ void __launch_bounds__(256) k_map_awgn(const uint32_t *__restrict__ b
 }
 
 // ---------------------------------------------------------------- demapper
-// Per I/Q dimension: metrics d_l = -(y - A_l s)^2 / N0 over the 2^h PAM levels;
-// bit i of the dimension gets LSE/max over levels whose label has bit i = 0,
-// minus the same over bit i = 1.
-template <int H>
-__device__ __forceinline__ void demap_dim(float y, float inv_n0, float scale, int method, float clamp, float *out) {
-    constexpr int P = 1 << H;
-    float d[P];
-#pragma unroll
-    for (int l = 0; l < P; ++l) {
-        // label bits a_i = bit (H-1-i) of l; level by the Gray recursion
-        int inner = 1 - 2 * ((l >> 0) & 1);
-#pragma unroll
-        for (int i = H - 2; i >= 0; --i) inner = (1 - 2 * ((l >> (H - 1 - i)) & 1)) * ((1 << (H - 1 - i)) - inner);
-        const float e = y - (float)inner * scale;
-        d[l] = -(e * e) * inv_n0;
-    }
-#pragma unroll
-    for (int i = 0; i < H; ++i) {
-        const int bit = H - 1 - i;
-        float mx0 = -INFINITY, mx1 = -INFINITY;
-#pragma unroll
-        for (int l = 0; l < P; ++l) {
-            if ((l >> bit) & 1) mx1 = fmaxf(mx1, d[l]);
-            else mx0 = fmaxf(mx0, d[l]);
-        }
-        float L;
-        if (method == LDPCX_DEMAP_MAXLOG) {
-            L = mx0 - mx1;
-        } else {
-            float s0 = 0.0f, s1 = 0.0f;
-#pragma unroll
-            for (int l = 0; l < P; ++l) {
-                if ((l >> bit) & 1) s1 += expf(d[l] - mx1);
-                else s0 += expf(d[l] - mx0);
-            }
-            L = (mx0 - mx1) + (logf(s0) - logf(s1));
-        }
-        out[i] = fminf(fmaxf(L, -clamp), clamp);
-    }
-}
-
 template <int M>
 __global__ void __launch_bounds__(256) k_demap(const float *__restrict__ y, const float *__restrict__ no,
                                                int64_t no_stride, int64_t B, int64_t S, int method, float clamp,
@@ -385,90 +345,29 @@ __global__ void __launch_bounds__(256) k_demap(const float *__restrict__ y, cons
     const float inv_shared = no_stride ? 0.0f : 1.0f / no[0];  // one N0 for all: no per-symbol division
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
         const float inv_n0 = no_stride ? 1.0f / no[i / S] : inv_shared;
+        float L[M];
         if constexpr (M == 1) {
-            float v = y[i];
-            float L = 4.0f * v * inv_n0;
-            if (!isfinite(v)) {
-                bad = true;
-                L = 0.0f;
-            }
-            llr[i] = fminf(fmaxf(L, -clamp), clamp);
+            demap_symbol<1>(y[i], 0.0f, inv_n0, scale, method, clamp, L, bad);
         } else {
-            constexpr int H = M / 2;
             const float2 v = reinterpret_cast<const float2 *>(y)[i];
-            float oi[H], oq[H];
-            if (isfinite(v.x) && isfinite(v.y)) {
-                demap_dim<H>(v.x, inv_n0, scale, method, clamp, oi);
-                demap_dim<H>(v.y, inv_n0, scale, method, clamp, oq);
-            } else {
-                bad = true;
+            demap_symbol<M>(v.x, v.y, inv_n0, scale, method, clamp, L, bad);
+        }
+        float *o = llr + i * M;
+        if constexpr (M == 1) {
+            o[0] = L[0];
+        } else if constexpr (M == 2) {
+            reinterpret_cast<float2 *>(o)[0] = make_float2(L[0], L[1]);
+        } else if constexpr (M == 4) {
+            reinterpret_cast<float4 *>(o)[0] = make_float4(L[0], L[1], L[2], L[3]);
+        } else {
 #pragma unroll
-                for (int j = 0; j < H; ++j) oi[j] = oq[j] = 0.0f;
-            }
-            float *o = llr + i * M;
-            if constexpr (M == 2) {
-                reinterpret_cast<float2 *>(o)[0] = make_float2(oi[0], oq[0]);
-            } else if constexpr (M == 4) {
-                reinterpret_cast<float4 *>(o)[0] = make_float4(oi[0], oq[0], oi[1], oq[1]);
-            } else {
-#pragma unroll
-                for (int j = 0; j < H; ++j) {
-                    o[2 * j] = oi[j];
-                    o[2 * j + 1] = oq[j];
-                }
-            }
+            for (int j = 0; j < M; ++j) o[j] = L[j];
         }
     }
     if (bad) latch(&g_status, LDPCX_FLAG_NONFINITE);
 }
 
 // ------------------------------------------------------ demapper with prior
-// demap_dim with a-priori LLRs la[0..H) of the dimension's bits: the metric of
-// level l gains sum_i (1 - 2 a_i(l)) la_i / 2. Extrinsic output leaves bit i's
-// own term out, which shifts the two sets of bit i by -la_i/2 and +la_i/2, so
-// it is the a-posteriori value minus la_i.
-template <int H>
-__device__ __forceinline__ void demap_dim_prior(float y, float inv_n0, float scale, int method, float clamp,
-                                                const float *la, int out_mode, float *out) {
-    constexpr int P = 1 << H;
-    float d[P];
-#pragma unroll
-    for (int l = 0; l < P; ++l) {
-        int inner = 1 - 2 * ((l >> 0) & 1);
-#pragma unroll
-        for (int i = H - 2; i >= 0; --i) inner = (1 - 2 * ((l >> (H - 1 - i)) & 1)) * ((1 << (H - 1 - i)) - inner);
-        const float e = y - (float)inner * scale;
-        float pr = 0.0f;
-#pragma unroll
-        for (int i = 0; i < H; ++i) pr += ((l >> (H - 1 - i)) & 1) ? -la[i] : la[i];
-        d[l] = fmaf(0.5f, pr, -(e * e) * inv_n0);
-    }
-#pragma unroll
-    for (int i = 0; i < H; ++i) {
-        const int bit = H - 1 - i;
-        float mx0 = -INFINITY, mx1 = -INFINITY;
-#pragma unroll
-        for (int l = 0; l < P; ++l) {
-            if ((l >> bit) & 1) mx1 = fmaxf(mx1, d[l]);
-            else mx0 = fmaxf(mx0, d[l]);
-        }
-        float L;
-        if (method == LDPCX_DEMAP_MAXLOG) {
-            L = mx0 - mx1;
-        } else {
-            float s0 = 0.0f, s1 = 0.0f;
-#pragma unroll
-            for (int l = 0; l < P; ++l) {
-                if ((l >> bit) & 1) s1 += expf(d[l] - mx1);
-                else s0 += expf(d[l] - mx0);
-            }
-            L = (mx0 - mx1) + (logf(s0) - logf(s1));
-        }
-        if (out_mode == LDPCX_DEMAP_OUT_EXTRINSIC) L -= la[i];
-        out[i] = fminf(fmaxf(L, -clamp), clamp);
-    }
-}
-
 template <int M>
 __global__ void __launch_bounds__(256) k_demap_prior(const float *__restrict__ y, const float *__restrict__ no,
                                                      int64_t no_stride, int64_t B, int64_t S, int method, float clamp,
@@ -798,14 +697,6 @@ __global__ void __launch_bounds__(256) k_count(const uint32_t *__restrict__ ref,
     }
 }
 
-
-bool valid_m(int m) { return m == 1 || m == 2 || m == 4 || m == 6 || m == 8; }
-
-float qam_scale(int m) {
-    if (m == 1) return 1.0f;
-    const int h = m / 2;
-    return (float)(1.0 / sqrt(2.0 * (double)((1 << (2 * h)) - 1) / 3.0));
-}
 
 }  // namespace
 

@@ -306,6 +306,43 @@ extern "C" int ldpc_bp_decode(ldpcx_code_t c, const float *llr_ch, int64_t B, co
     return ldpcx::decode_impl(c, llr_ch, B, o, llr_out, bits_out, iters_out, ws, ws_bytes, nullptr, stream);
 }
 
+extern "C" int ldpc_bp_decode_qam(ldpcx_code_t c, const float *y, const float *no, int64_t no_stride, int64_t B,
+                                  int m, int demap_method, float demap_clamp, const ldpcx_decode_opts *o,
+                                  float *llr_out, uint32_t *bits_out, int32_t *iters_out, void *ws, size_t ws_bytes,
+                                  void *stream) {
+    using namespace ldpcx;
+    using namespace ldpcx::dec;
+    if (!c || B < 0 || !valid_m(m) || (no_stride != 0 && no_stride != 1)) return LDPCX_E_INVAL;
+    if (demap_method != LDPCX_DEMAP_EXACT && demap_method != LDPCX_DEMAP_MAXLOG) return LDPCX_E_INVAL;
+    if (!(demap_clamp > 0.0f) || isinf(demap_clamp) || c->n_tx % m != 0) return LDPCX_E_INVAL;
+    int st = check_opts(c, o);
+    if (st) return st;
+    // the flooding kernels read the channel LLRs again in every iteration
+    if (o->algo != LDPCX_LAYERED_MINSUM && o->algo != LDPCX_LAYERED_SPA) return LDPCX_E_UNSUPPORTED;
+    if (B == 0) return LDPCX_OK;
+    if (!y || !no) return LDPCX_E_INVAL;
+    size_t need = 0;
+    ldpc_bp_workspace(c, B, o, &need);
+    if (!ws || ws_bytes < need || ((uintptr_t)ws & 255u)) return LDPCX_E_WORKSPACE;
+    DevCode d;
+    st = code_device(c, &d);
+    if (st) return st;
+    DecodePlan pl;
+    st = decode_plan(c, o, &pl);
+    if (st) return st;
+    Params p = decode_params(c, d.blk, d.row_ptr, nullptr, B, o, llr_out, bits_out, iters_out, ws, msg_stride(c),
+                             nullptr, pl.layered);
+    if (!p.status) return LDPCX_E_CUDA;
+    p.sym = y;
+    p.sym_no = no;
+    p.sym_no_stride = no_stride;
+    p.qam_m = m;
+    p.demap_method = demap_method;
+    p.demap_clamp = demap_clamp;
+    p.qam_scale = qam_scale(m);
+    return decode_launch(pl, c, p, B, stream);
+}
+
 namespace ldpcx {
 namespace {
 __global__ void k_phi(const float *x, float *out, int64_t n, int fast) {

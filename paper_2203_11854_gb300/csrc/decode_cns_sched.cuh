@@ -35,12 +35,15 @@ template <int BG, int PREC> struct SchedLayout {
     using S = Sched<BG>;
     static constexpr int sb_core = cns_slot_bytes<PREC>(S::dc1);  // slot bytes of the core rows
     static constexpr int sb_ext = cns_slot_bytes<PREC>(S::d_hi);  // and of the extension rows
-    // BG1-shaped codes with FP16 messages (one check node per thread) keep per-edge messages for the
-    // extension rows (degree 6 and 5): a node's binary16 messages in two planes of the row's region,
-    // halves 0..3 in plane A (8 B per node), halves 4 and 5 in plane B (4 B per node). Rebuilding a
-    // message is then one conversion instead of a select on two masks; the core rows (degree 18 and
-    // 19) keep the check-node state.
-    static constexpr bool edge_ext = BG == 1 && PREC == kF16;
+    // BG1-shaped codes with FP16 or 6-bit messages (one check node per thread) keep per-edge messages
+    // for the extension rows (degree 6 and 5): a node's messages in two planes of the row's region,
+    // messages 0..3 in plane A, 4 and 5 in plane B; binary16 takes 8 + 4 B per node, 6-bit one byte
+    // per message, 4 + 2 B. Rebuilding a message is then a conversion (FP16) or a byte permute and a
+    // subtraction (6-bit) instead of a select on two masks; the core rows (degree 18 and 19) keep the
+    // check-node state.
+    static constexpr bool edge_ext = BG == 1 && (PREC == kF16 || PREC == kFix6);
+    static constexpr int edge_a = PREC == kFix6 ? 4 : 8;     // plane A bytes per node
+    static constexpr int edge_row = PREC == kFix6 ? 6 : 12;  // bytes per node of an extension row
     static constexpr int b_hi = S::dc0 + S::dc1 + S::dc2 + S::dc3;  // first block of the extension rows
     static constexpr int b_lo = b_hi + S::n_hi * S::d_hi;
     static_assert(cns_slot_bytes<PREC>(S::dc0) == sb_core && cns_slot_bytes<PREC>(S::dc2) == sb_core &&
@@ -76,14 +79,17 @@ struct SchedGeo {
 
 // Bytes of one codeword's state under the compiled schedule (each row region
 // rounded to 16 B): check-node state for every row, or, for BG1-shaped codes
-// with FP16 messages and one check node per thread, the state of the four core
-// rows followed by 12 B of per-edge messages per node of each extension row.
+// with FP16 or 6-bit messages and one check node per thread, the state of the
+// four core rows followed by 12 B (FP16) or 6 B (6-bit) of per-edge messages
+// per node of each extension row.
 __host__ inline int64_t sched_state_bytes(int bg, int prec, int kpt, const int32_t *row_ptr, int rows, int Z) {
-    if (bg == 1 && prec == kF16 && kpt == 1) {
+    if (bg == 1 && (prec == kF16 || prec == kFix6) && kpt == 1) {
+        const int64_t ext = prec == kFix6 ? 6 : 12;
         int64_t b = 0;
         for (int r = 0; r < rows; ++r) {
             const int d = row_ptr[r + 1] - row_ptr[r];
-            b += r < 4 ? (cns_slot_bytes<kF16>(d) * (int64_t)Z + 15) / 16 * 16 : (12 * (int64_t)Z + 15) / 16 * 16;
+            const int core = prec == kFix6 ? cns_slot_bytes<kFix6>(d) : cns_slot_bytes<kF16>(d);
+            b += r < 4 ? (core * (int64_t)Z + 15) / 16 * 16 : (ext * Z + 15) / 16 * 16;
         }
         return b;
     }
@@ -92,11 +98,30 @@ __host__ inline int64_t sched_state_bytes(int bg, int prec, int kpt, const int32
     return cns_bytes_per_cw<kFix6>(row_ptr, rows, Z);
 }
 
-// Per-edge extension rows: a node's messages (plane A: halves 0..3, plane B: halves 4, 5).
+// Per-edge extension rows: a node's messages (plane A: messages 0..3, plane B: 4, 5).
+template <int PREC>
 __device__ __forceinline__ uint4 edge_ext_load(const unsigned char *a, const unsigned char *b) {
-    const uint2 va = __ldcg(reinterpret_cast<const uint2 *>(a));
-    return make_uint4(va.x, va.y, __ldcg(reinterpret_cast<const unsigned *>(b)), 0u);
+    if constexpr (PREC == kFix6) {
+        return make_uint4(__ldcg(reinterpret_cast<const unsigned *>(a)),
+                          (unsigned)__ldcg(reinterpret_cast<const unsigned short *>(b)), 0u, 0u);
+    } else {
+        const uint2 va = __ldcg(reinterpret_cast<const uint2 *>(a));
+        return make_uint4(va.x, va.y, __ldcg(reinterpret_cast<const unsigned *>(b)), 0u);
+    }
 }
+
+// A 6-bit message R (a multiple of 0.5 in [-15.5, 15.5]) is stored as the byte
+// 32 + 2R: that byte under the upper bytes of 1.5 * 2^22 (0x4AC00000, whose
+// mantissa step is 0.5) reads as 1.5 * 2^22 + 16 + R exactly, so one byte
+// permute and one subtraction rebuild R, and one addition gives the byte back.
+// A zero message is the byte 32, so the first iteration starts from bytes of
+// 32, not from zero bytes; it is stored as +0 (the 6-bit store has no -0, as in
+// the check-node state; the sums are the same).
+constexpr float kFix6Bias = 6291472.0f;  // 1.5 * 2^22 + 16
+__device__ __forceinline__ float fix6_byte_value(unsigned w, unsigned j) {
+    return __fsub_rn(__uint_as_float(__byte_perm(w, 0x4AC00000u, 0x7650u | j)), kFix6Bias);
+}
+__device__ __forceinline__ unsigned fix6_byte_of(float r) { return __float_as_uint(__fadd_rn(r, kFix6Bias)); }
 __device__ __forceinline__ float half_lo(unsigned w) { return __low2float(*reinterpret_cast<const __half2 *>(&w)); }
 __device__ __forceinline__ float half_hi(unsigned w) { return __high2float(*reinterpret_cast<const __half2 *>(&w)); }
 __device__ __forceinline__ unsigned half_pack(float a, float b) {
@@ -105,10 +130,10 @@ __device__ __forceinline__ unsigned half_pack(float a, float b) {
 }
 
 // Layered min-sum update of check node z of an extension row of degree D with
-// per-edge FP16 messages: the rule of cns_update_k, the old messages read
-// from the packed halves and the new (rounded) ones packed back, so the
-// stored values, and every APP, are the same bit for bit.
-template <int D>
+// per-edge FP16 or 6-bit messages: the rule of cns_update_k, the old messages
+// read from the packed halves (bytes) and the new rounded ones packed back, so
+// the stored values, and every APP, are the same bit for bit.
+template <int D, int PREC>
 __device__ __forceinline__ void edge_ext_update(const Params &p, float *app, const int2 *at, int z,
                                                 const uint4 &s_old, unsigned char *slot_a, unsigned char *slot_b,
                                                 bool store) {
@@ -119,12 +144,14 @@ __device__ __forceinline__ void edge_ext_update(const Params &p, float *app, con
 #pragma unroll
     for (int j = D - 1; j >= 0; --j) {
         vi[j] = vn_off_mixed(p, at[j], z);
-        const float old = (j & 1) ? half_hi(w[j >> 1]) : half_lo(w[j >> 1]);
+        const float old = PREC == kFix6 ? fix6_byte_value(w[j >> 2], (unsigned)(j & 3))
+                          : (j & 1)     ? half_hi(w[j >> 1])
+                                        : half_lo(w[j >> 1]);
         T[j] = __fsub_rn(app_at(app, vi[j]), old);
     }
     FastMinSum<D> cn;
     cn.prepare(T, D, p.offset, p.clamp);
-    CnsMag<kF16> mn;
+    CnsMag<PREC> mn;
     mn.set(cn.v1, cn.v2);
     const unsigned sxs = cn.sx & 0x80000000u;
     const unsigned b1 = __float_as_uint(mn.r1), b2 = __float_as_uint(mn.r2);
@@ -138,8 +165,19 @@ __device__ __forceinline__ void edge_ext_update(const Params &p, float *app, con
         app_at(app, vi[j]) = __fadd_rn(T[j], R[j]);
     }
     if (store) {
-        __stcg(reinterpret_cast<uint2 *>(slot_a), make_uint2(half_pack(R[0], R[1]), half_pack(R[2], R[3])));
-        __stcg(reinterpret_cast<unsigned *>(slot_b), half_pack(R[4], D > 5 ? R[D - 1] : 0.0f));
+        if constexpr (PREC == kFix6) {
+            unsigned f[6];
+#pragma unroll
+            for (int j = 0; j < D; ++j) f[j] = fix6_byte_of(R[j]);
+            if constexpr (D == 5) f[5] = 32u;  // a zero message in the unused slot
+            const unsigned a = __byte_perm(__byte_perm(f[0], f[1], 0x0040u), __byte_perm(f[2], f[3], 0x0040u),
+                                           0x5410u);
+            __stcg(reinterpret_cast<unsigned *>(slot_a), a);
+            __stcg(reinterpret_cast<unsigned short *>(slot_b), (unsigned short)__byte_perm(f[4], f[5], 0x0040u));
+        } else {
+            __stcg(reinterpret_cast<uint2 *>(slot_a), make_uint2(half_pack(R[0], R[1]), half_pack(R[2], R[3])));
+            __stcg(reinterpret_cast<unsigned *>(slot_b), half_pack(R[4], D > 5 ? R[D - 1] : 0.0f));
+        }
     }
 }
 
@@ -452,10 +490,11 @@ __device__ __forceinline__ void cns_sched_tile(const Params &p, int64_t cw_base,
 // One check node per thread (K = 1): the same schedule, update and prefetch
 // with scalar registers throughout and the slot addresses formed from two
 // per-thread bases (core and extension rows), so a step adds one row offset.
-// BG1-shaped codes with FP16 messages keep the extension rows per edge
-// (SchedLayout::edge_ext); plane B of a node lies 8 Z - 4 z bytes past its
-// plane A, an offset formed where it is used (a register held across the whole
-// kernel costs more than the multiply-add).
+// BG1-shaped codes with FP16 or 6-bit messages keep the extension rows per
+// edge (SchedLayout::edge_ext); plane B of a node lies a Z - (2a - e) z bytes
+// past its plane A (a = plane A bytes per node, e = bytes per node; 8 Z - 4 z
+// for FP16), an offset formed where it is used (a register held across the
+// whole kernel costs more than the multiply-add).
 
 // Layered min-sum update of check node z of a row of exact degree D from its
 // check-node state (the rule of cns_update_k for one node).
@@ -500,7 +539,8 @@ __device__ __forceinline__ void sched_step1(const Params &p, const int2 *s_at, f
                                             int b0, int off, const SchedGeo &geo, bool done, const uint4 &s_cur,
                                             uint4 &s_far) {
     using L = SchedLayout<BG, PREC>;
-    const int pb = 8 * (ZC ? ZC : p.Z) - 4 * z;  // plane B past plane A (per-edge extension rows)
+    // plane B past plane A (per-edge extension rows): the rest of plane A, then this node's plane B slot
+    const int pb = L::edge_a * (ZC ? ZC : p.Z) - (2 * L::edge_a - L::edge_row) * z;
     // an extension row: the core rows of both shapes have degree 10 or more, the extension rows 6 or less
     constexpr bool ext_row = D <= 8;
     int r2, t2;
@@ -509,20 +549,24 @@ __device__ __forceinline__ void sched_step1(const Params &p, const int2 *s_at, f
     const bool zero = MODE == kStepExtWrap ? false : t2 == 0;
     const bool fetch = MODE == kStepAny ? t2 < p.iters : MODE == kStepExtWrap ? t + 1 < p.iters : true;
     if (zero) {
-        s_far = make_uint4(0u, 0u, 0u, 0u);  // iteration 0: zero messages
+        // iteration 0: zero messages (all-zero words, except per-edge 6-bit rows: bytes of 32)
+        if constexpr (L::edge_ext && PREC == kFix6)
+            s_far = core2 ? make_uint4(0u, 0u, 0u, 0u) : make_uint4(0x20202020u, 0x2020u, 0u, 0u);
+        else
+            s_far = make_uint4(0u, 0u, 0u, 0u);
     } else if (!done && fetch) {
         if (core2) {
             s_far = cns_load(geo.core_z + r2 * geo.Lc, L::sb_core);
         } else {
             const unsigned char *a = geo.ext_z + (r2 - 4) * geo.Le;
-            if constexpr (L::edge_ext) s_far = edge_ext_load(a, a + pb);
+            if constexpr (L::edge_ext) s_far = edge_ext_load<PREC>(a, a + pb);
             else s_far = cns_load(a, L::sb_ext);
         }
     }
     if (!done) {
         if constexpr (L::edge_ext && ext_row) {
             unsigned char *slot = geo.ext_z - 4 * geo.Lc + off;
-            edge_ext_update<D>(p, app, s_at + b0, z, s_cur, slot, slot + pb, t + 1 < p.iters);
+            edge_ext_update<D, PREC>(p, app, s_at + b0, z, s_cur, slot, slot + pb, t + 1 < p.iters);
         } else {
             unsigned char *slot = (ext_row ? geo.ext_z - 4 * geo.Lc : geo.core_z) + off;
             cns_update1<D, PREC>(p, app, s_at + b0, z, s_cur, slot, t + 1 < p.iters);
@@ -634,9 +678,9 @@ __device__ __forceinline__ void cns_sched_tile1(const Params &p, int64_t cw_base
     int iters_run = 0;
     SchedGeo geo;
     geo.Lc = (L::sb_core * ZV + 15) / 16 * 16;
-    geo.Le = L::edge_ext ? (12 * ZV + 15) / 16 * 16 : (L::sb_ext * ZV + 15) / 16 * 16;
+    geo.Le = L::edge_ext ? (L::edge_row * ZV + 15) / 16 * 16 : (L::sb_ext * ZV + 15) / 16 * 16;
     geo.core_z = st + z * L::sb_core;
-    geo.ext_z = st + 4 * geo.Lc + z * (L::edge_ext ? 8 : L::sb_ext);
+    geo.ext_z = st + 4 * geo.Lc + z * (L::edge_ext ? L::edge_a : L::sb_ext);
     __syncthreads();
 
     const int n_hi = min(S::n_hi, p.rows - 4), n_lo = p.rows - 4 - n_hi;
@@ -719,9 +763,9 @@ __global__ void __launch_bounds__(kMaxThreads / K, 2)
         int iters_run = 0;
         SchedGeo geo;
         geo.Lc = (L::sb_core * ZV + 15) / 16 * 16;
-        geo.Le = L::edge_ext ? (12 * ZV + 15) / 16 * 16 : (L::sb_ext * ZV + 15) / 16 * 16;
+        geo.Le = L::edge_ext ? (L::edge_row * ZV + 15) / 16 * 16 : (L::sb_ext * ZV + 15) / 16 * 16;
         geo.core_z = st + z * L::sb_core;
-        geo.ext_z = st + 4 * geo.Lc + z * (L::edge_ext ? 8 : L::sb_ext);
+        geo.ext_z = st + 4 * geo.Lc + z * (L::edge_ext ? L::edge_a : L::sb_ext);
         __syncthreads();
         uint4 a = make_uint4(0u, 0u, 0u, 0u), b = a, c = a;
         for (int t = 0; t < p.iters; ++t) {

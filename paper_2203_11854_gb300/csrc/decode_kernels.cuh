@@ -24,6 +24,7 @@
 #include <type_traits>
 
 #include "common.cuh"
+#include "demap.cuh"
 
 namespace ldpcx {
 namespace dec {
@@ -123,6 +124,13 @@ struct Params {
     int iters, early_stop;
     float offset, clamp, phi_lo;  // phi_lo = phi(clamp)
     const float *llr;             // [B][n_tx]
+    // fused demapper (llr unused when sym is set): received symbols [B][n_tx/m] (float2, or float for
+    // m = 1), N0 [B] (sym_no_stride 1) or [1] (0), and demap_app's other arguments
+    const float *sym;
+    const float *sym_no;
+    int64_t sym_no_stride;
+    int qam_m, demap_method;
+    float demap_clamp, qam_scale;
     void *msg;                    // [B][msg_stride]
     int64_t msg_stride;
     const float *weights;         // flooding: [iters][nnz] or null
@@ -183,10 +191,117 @@ __device__ __forceinline__ float channel_llr(const Params &p, int64_t cw, int v,
     return 0.0f;
 }
 
+// The fused demapper: the channel LLRs of the CTA's codewords computed from
+// the received symbols, the values demap_app writes (same arithmetic, then the
+// decoder's clamp), placed as load_channel places them, so decoding is the same
+// bit for bit as demap_app followed by the decoder. Out of line: one copy per
+// translation unit instead of one per kernel. The parameters are read once
+// into registers (through the reference every shared-memory store would force
+// them to be read again).
+struct QamLoad {
+    const float *y;  // this codeword's symbols
+    float inv_n0, scale, dclamp, clamp;
+    int S, p0, k, nf, method;
+    bool vec;        // contiguous transmit layout from a 16-byte-aligned p0: vector stores
+};
+// The demapper's values are finite and within +-dclamp (fminf / fmaxf drop a NaN), so the decoder's clamp
+// of its input reduces to min / max, or to nothing when dclamp <= clamp; + 0 maps -0 to +0 as it does.
+__device__ __forceinline__ float qam_llr(float L, float clamp, bool clip) {
+    return (clip ? fminf(fmaxf(L, -clamp), clamp) : L) + 0.0f;
+}
+template <int M>
+__device__ __forceinline__ void qam_channel(const QamLoad q, float *a, bool &bad) {
+    constexpr int W = M == 1 ? 1 : 2;  // floats per symbol
+    constexpr int U = 8;               // symbols per thread in flight
+    const int bd = blockDim.x;
+    const bool clip = q.dclamp > q.clamp;
+    for (int s0 = threadIdx.x; s0 < q.S; s0 += U * bd) {
+        float v[U][W];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int s = s0 + u * bd;
+#pragma unroll
+            for (int w = 0; w < W; ++w) v[u][w] = 0.0f;
+            if (s < q.S) {
+                if constexpr (W == 1) {
+                    v[u][0] = __ldcs(q.y + s);
+                } else {
+                    const float2 t = __ldcs(reinterpret_cast<const float2 *>(q.y) + s);
+                    v[u][0] = t.x;
+                    v[u][1] = t.y;
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int s = s0 + u * bd;
+            if (s >= q.S) break;
+            float L[M];
+            demap_symbol<M>(v[u][0], v[u][W - 1], q.inv_n0, q.scale, q.method, q.dclamp, L, bad);
+#pragma unroll
+            for (int j = 0; j < M; ++j) L[j] = qam_llr(L[j], q.clamp, clip);
+            if (q.vec) {
+                float *o = a + q.p0 + s * M;
+                if constexpr (M == 4 || M == 8) {
+#pragma unroll
+                    for (int j = 0; j < M; j += 4)
+                        *reinterpret_cast<float4 *>(o + j) = make_float4(L[j], L[j + 1], L[j + 2], L[j + 3]);
+                } else if constexpr (M == 2 || M == 6) {
+#pragma unroll
+                    for (int j = 0; j < M; j += 2) *reinterpret_cast<float2 *>(o + j) = make_float2(L[j], L[j + 1]);
+                } else {
+                    o[0] = L[0];
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < M; ++j) a[tx_position(s * M + j, q.p0, q.k, q.nf)] = L[j];
+            }
+        }
+    }
+}
+static __device__ __noinline__ void load_channel_qam(const Params &p, float *app, int64_t cw_base) {
+    const int G = p.G, n = p.n, k = p.k, nf = p.nf, p0 = p.p0, n_tx = p.n_tx, m = p.qam_m;
+    const int64_t B = p.B;
+    const float clamp = p.clamp;
+    const float *sym = p.sym, *sym_no = p.sym_no;
+    const bool per_cw = p.sym_no_stride != 0;
+    // vector stores: no fillers to skip, p0 and the row length multiples of 4 floats (16-byte aligned rows)
+    const bool vec = nf == 0 && ((p0 | n) & 3) == 0;
+    QamLoad q{nullptr, 0.0f, p.qam_scale, p.demap_clamp, clamp, n_tx / m, p0, k, nf, p.demap_method, vec};
+    unsigned int *status = p.status;
+    bool bad = false;
+    for (int g = 0; g < G; ++g) {
+        const int64_t cw = cw_base + g;
+        float *a = app + (size_t)g * n;
+        // positions without a received bit: punctured and untransmitted (0), fillers (+clamp)
+        for (int v = threadIdx.x; v < n; v += blockDim.x) {
+            const bool fill = v >= k && v < k + nf;
+            const int t = v - p0 - (v >= k ? nf : 0);
+            if (fill) a[v] = clamp;
+            else if (v < p0 || t >= n_tx || cw >= B) a[v] = 0.0f;
+        }
+        if (cw >= B) continue;
+        q.inv_n0 = 1.0f / sym_no[per_cw ? cw : 0];
+        q.y = sym + cw * q.S * (m == 1 ? 1 : 2);
+        switch (m) {
+            case 1: qam_channel<1>(q, a, bad); break;
+            case 2: qam_channel<2>(q, a, bad); break;
+            case 4: qam_channel<4>(q, a, bad); break;
+            case 6: qam_channel<6>(q, a, bad); break;
+            default: qam_channel<8>(q, a, bad); break;
+        }
+    }
+    if (bad) latch(status, LDPCX_FLAG_NONFINITE);
+}
+
 // Load the channel LLRs of the CTA's codewords into app (placed: punctured and
 // untransmitted positions are 0). When the row layout allows, 16-byte loads,
 // four per thread in flight (streaming: the LLRs are read once).
 __device__ inline void load_channel(const Params &p, float *app, int64_t cw_base) {
+    if (p.sym) {
+        load_channel_qam(p, app, cw_base);
+        return;
+    }
     bool bad = false;
     if (p.nf == 0 && ((p.p0 | p.n_tx | p.n) & 3) == 0 && (reinterpret_cast<uintptr_t>(p.llr) & 15u) == 0) {
         const int bd = blockDim.x, n4 = p.n_tx >> 2;

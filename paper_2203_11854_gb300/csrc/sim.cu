@@ -3,11 +3,13 @@
 // error count on the device.
 //
 // Each batch's N0 and first codeword index are written by the host into the
-// device copy its transmitter reads. Eager mode runs the four launches of a
-// batch one after another on one stream. Graph mode splits a batch into a front (transmitter + demapper into one of
-// two buffer sets, with that set's N0 and first codeword index written by the
-// host) and a back (decoder + error count from that set), captured once per
-// set as four CUDA graphs. The front of the next batch runs on a second,
+// device copy its transmitter reads. The layered decoders demap while loading
+// the channel (ldpc_bp_decode_qam); the flooding ones read the LLRs of a
+// separate demapper launch. Eager mode runs a batch's launches one after
+// another on one stream. Graph mode splits a batch into a front (transmitter,
+// and the demapper when it is separate, into one of two buffer sets, with that
+// set's N0 and first codeword index written by the host) and a back (decoder +
+// error count from that set), captured once per set as four CUDA graphs. The front of the next batch runs on a second,
 // lower-priority stream while the current batch decodes, so it fills the SM
 // slots the decoder's last wave leaves idle. The next batch is guessed before
 // the host has read the current counts (the same point, or the next point after
@@ -154,6 +156,13 @@ struct SimLayout {
 
 size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
+// The layered decoders take the received symbols and demap them while loading
+// the channel (ldpc_bp_decode_qam, the same results as demap_app then
+// ldpc_bp_decode); the flooding decoders read LLRs, which the front writes.
+bool fused_demap(const ldpcx_sim_config *c) {
+    return c->dec.algo == LDPCX_LAYERED_MINSUM || c->dec.algo == LDPCX_LAYERED_SPA;
+}
+
 int layout(const ldpcx_sim_config *c, SimLayout *L) {
     if (!c || !c->code) return LDPCX_E_INVAL;
     const ldpcx_code *code = c->code;
@@ -180,7 +189,7 @@ int layout(const ldpcx_sim_config *c, SimLayout *L) {
     L->dec = take(dec);
     for (int s = 0; s < 2; ++s) {
         L->y[s] = take(sizeof(float) * (size_t)B * L->S * (c->m == 1 ? 1 : 2));
-        L->llr[s] = take(sizeof(float) * (size_t)B * code->n_tx);
+        L->llr[s] = fused_demap(c) ? 0 : take(sizeof(float) * (size_t)B * code->n_tx);
         L->ref[s] = take(sizeof(uint32_t) * (size_t)B * L->kw);
         L->no[s] = take(sizeof(float));
         L->cw0[s] = take(sizeof(uint64_t));
@@ -194,22 +203,29 @@ int layout(const ldpcx_sim_config *c, SimLayout *L) {
 }
 
 // Front of a batch into buffer set s: transmitter (codewords from the set's
-// device index) and demapper.
+// device index) and, for the flooding decoders, the demapper.
 int run_front(const ldpcx_sim_config *c, const SimLayout &L, char *ws, int s, cudaStream_t st) {
     float *y = (float *)(ws + L.y[s]), *llr = (float *)(ws + L.llr[s]), *no = (float *)(ws + L.no[s]);
     uint32_t *ref = (uint32_t *)(ws + L.ref[s]);
     const uint64_t *cw0 = (const uint64_t *)(ws + L.cw0[s]);
     int r = ldpcx::launch_tx(c->code, c->seed, 0, cw0, c->batch, c->m, no, 0, y, ref, st);
-    if (!r) r = demap_app(y, no, 0, c->batch, L.S, c->m, c->demap_method, c->demap_clamp, llr, st);
+    if (!r && !fused_demap(c)) r = demap_app(y, no, 0, c->batch, L.S, c->m, c->demap_method, c->demap_clamp, llr, st);
     return r;
 }
 
-// Back of a batch from buffer set s: decoder and error count into the point's counters.
+// Back of a batch from buffer set s: decoder (with the demapper fused into it
+// for the layered schedules) and error count into the point's counters.
 int run_back(const ldpcx_sim_config *c, const SimLayout &L, char *ws, int s, cudaStream_t st) {
-    float *llr = (float *)(ws + L.llr[s]);
     uint32_t *ref = (uint32_t *)(ws + L.ref[s]), *hat = (uint32_t *)(ws + L.hat);
     int32_t *iters = (int32_t *)(ws + L.iters);
-    int r = ldpc_bp_decode(c->code, llr, c->batch, &c->dec, nullptr, hat, iters, ws + L.dec, L.dec_bytes, st);
+    int r;
+    if (fused_demap(c))
+        r = ldpc_bp_decode_qam(c->code, (const float *)(ws + L.y[s]), (const float *)(ws + L.no[s]), 0, c->batch,
+                               c->m, c->demap_method, c->demap_clamp, &c->dec, nullptr, hat, iters, ws + L.dec,
+                               L.dec_bytes, st);
+    else
+        r = ldpc_bp_decode(c->code, (const float *)(ws + L.llr[s]), c->batch, &c->dec, nullptr, hat, iters,
+                           ws + L.dec, L.dec_bytes, st);
     if (!r) r = sim_count(ref, hat, iters, c->batch, c->code->k, (int64_t *)(ws + L.acc), st);
     return r;
 }

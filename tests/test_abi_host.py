@@ -163,3 +163,28 @@ def test_qam_map_awgn_argument_checks(lx):
     assert L.qam_map_awgn(one, 2, 8, 3, 1, 0, one, 0, one, None) == -1    # m not a constellation size
     assert L.qam_map_awgn(one, 2, 8, 4, 1, 0, one, 2, one, None) == -1    # N0 stride 0 or 1
     assert L.qam_map_awgn(None, 2, 8, 4, 1, 0, one, 0, one, None) == -1   # null bits
+
+
+def test_decode_qam_argument_checks(lx):
+    """ldpc_bp_decode_qam refuses bad arguments and the flooding schedules before any device work."""
+    L = lx.load_library()
+    code = lx.qc_ldpc_build(2, 8)  # n_tx = 416: m = 1, 2, 4, 8 divide it, m = 6 does not
+    one = C.c_void_p(16)  # never dereferenced: every call below returns before device work
+
+    def call(B=2, m=4, stride=0, method=lx.DEMAP_MAXLOG, dclamp=20.0, algo=lx.LAYERED_MINSUM, y=one, ws=None, nws=0):
+        o = lx.DecodeOpts(algo, 20, lx.MSG_F16, 0, 0.5, 20.0, None)
+        return L.ldpc_bp_decode_qam(code.handle, y, one, stride, B, m, method, dclamp, C.byref(o), None, one, None,
+                                    ws, nws, None)
+
+    assert call(B=0) == 0                               # nothing to do
+    assert call(m=3) == -1                              # not a constellation size
+    assert call(m=6) == -1                              # m does not divide n_tx
+    assert call(stride=2) == -1                         # N0 stride 0 or 1
+    assert call(method=2) == -1                         # demapper method
+    assert call(dclamp=0.0) == -1                       # demapper clamp > 0
+    assert call(dclamp=float("inf")) == -1              # and finite
+    assert call(algo=lx.FLOOD_SPA) == -2                # flooding reads the channel LLRs every iteration
+    assert call(algo=lx.FLOOD_MINSUM) == -2
+    assert call(y=None) == -1                           # null symbols
+    assert call() == -4                                 # missing workspace
+    assert L.ldpc_bp_decode_qam(None, one, one, 0, 2, 4, 0, 20.0, None, None, one, None, None, 0, None) == -1

@@ -97,7 +97,7 @@ def test_noalloc_minsum_equals_oracle_replay(lx, orc, prec):
 @pytest.mark.parametrize("algo,prec,limit", [
     (0, 1, 153),  # layered min-sum, FP16: core-row state + per-edge extension rows, 218112 bytes per codeword
     (0, 0, 118),  # FP32 state: 282624 bytes
-    (0, 2, 436),  # 6-bit state: 76800 bytes
+    (0, 2, 307),  # 6-bit: core-row state + per-edge extension rows, 109056 bytes
     (1, 1, 138),  # layered sum-product, FP16 per-edge messages: 242688 bytes
 ])
 def test_noalloc_refuses_batches_beyond_the_array(lx, algo, prec, limit):
