@@ -122,7 +122,8 @@ class Clocks:
                 "reasons": reasons, "samples": len(inside), "interval_ms": 20}
 
 
-KERNEL_SOURCES = ("decode_kernels.cuh", "decode_cns.cuh", "decode_cns_sched.cuh", "decode_cns_sched_f16.cu")  # profiled kernel
+KERNEL_SOURCES = ("decode_kernels.cuh", "demap.cuh", "decode_cns.cuh", "decode_cns_sched.cuh",
+                  "decode_cns_sched_f16.cu")  # profiled kernel
 
 
 def decoder_digest():
@@ -188,13 +189,13 @@ def issue_peak():
     return torch.cuda.get_device_properties(0).multi_processor_count * 4 * pk.get("sm_max_mhz", 2070.0) * 1e6
 
 
-def inst_per_32_edges(profile, kernel_sub=None):
-    """Warp instructions per 32 edge updates from a current ncu summary, or None."""
+def inst_per_32_edges(profile, kernel_sub=None, key="warp instructions per 32 edge updates"):
+    """Warp instructions per 32 edge updates (the figure named key) from a current ncu summary, or None."""
     for sec in profile_sections(profile):
         if kernel_sub and kernel_sub not in sec.get("kernel", ""):
             continue
-        if sec.get("current") and "warp instructions per 32 edge updates" in sec:
-            return float(sec["warp instructions per 32 edge updates"])
+        if sec.get("current") and key in sec:
+            return float(sec[key])
     return None
 
 
@@ -485,7 +486,9 @@ def measure_variants(lx, code, llr, bits, its, stream, args, pk):
             out[name]["mufu_frac"] = 6 * B * code.edges * ITERS / (ms * 1e-3) / mufu_peak
         # instruction-issue fraction: warp instructions per 32 edge updates (ncu, same kernel sources) times
         # the edge updates per second, over SMs x 4 schedulers x the maximum SM clock
-        prof = {"minsum_f16": ("decode_layered_minsum_f16_bg1_z384.md", None),
+        prof = {"minsum_f16": ("decode_layered_minsum_f16_bg1_z384.md", None,
+                               "warp instructions per 32 edge updates, LLR input"),
+                "minsum_fix6": ("decode_layered_minsum_fix6_bg1_z384.md", None),
                 "spa_f16": ("decode_layered_spa_f16_bg1_z384.md", None)}.get(name)
         ipe = inst_per_32_edges(*prof) if prof else None
         if ipe is not None:
@@ -794,14 +797,16 @@ def measure_e2e(lx, code, y_dev, info_dev, n0, dec, stream, args, dev, fused=Tru
             "ms_per_step": ms, "path": path}
 
 
-CASES = ("minsum_f16", "minsum_f32", "minsum_fix6", "spa_f16", "spa_f32", "grad", "mixed", "flood_spa_z8")
+CASES = ("minsum_f16", "minsum_f32", "minsum_fix6", "spa_f16", "spa_f32", "qam_minsum_f16", "grad", "mixed",
+         "flood_spa_z8")
 
 
 def run_case(args):
     """One kernel's launches alone, for timing and for small-case ncu captures: W untimed launches, then K
     launches between CUDA events on the launching stream. Prints one JSON line with the mean launch time.
     minsum_* / spa_*: ldpc_bp_decode of the BG1-shaped Z=384 code (20 iterations, no early stop) on --batch
-    codewords of the 16-QAM workload; grad: the weighted flooding sum-product forward with checkpoints and
+    codewords of the 16-QAM workload; qam_minsum_f16: the same decode from the received symbols with the
+    demapper fused (ldpc_bp_decode_qam, the bench step's decode launch); grad: the weighted flooding sum-product forward with checkpoints and
     its adjoint (BG2-shaped Z=64, 10 iterations, --batch codewords); mixed: the persistent mixed-code launch
     (8192 codewords); flood_spa_z8: flooding sum-product FP32, BG2-shaped Z=8, 20 iterations."""
     import torch
@@ -812,9 +817,11 @@ def run_case(args):
     Bc = args.batch
     name = args.case
     info = {}
-    if name.startswith(("minsum_", "spa_")):
-        algo = lx.LAYERED_MINSUM if name.startswith("minsum_") else lx.LAYERED_SPA
-        prec = {"f16": lx.MSG_F16, "f32": lx.MSG_F32, "fix6": lx.MSG_FIX6}[name.split("_")[1]]
+    if name.startswith(("minsum_", "spa_", "qam_")):
+        fused = name.startswith("qam_")
+        base = name[4:] if fused else name
+        algo = lx.LAYERED_MINSUM if base.startswith("minsum_") else lx.LAYERED_SPA
+        prec = {"f16": lx.MSG_F16, "f32": lx.MSG_F32, "fix6": lx.MSG_FIX6}[base.split("_")[1]]
         code = lx.qc_ldpc_build(BG, Z, punct_cols=PUNCT)
         r = code.k / code.n_tx
         n0 = torch.tensor([1.0 / (r * M * 10 ** (EBN0 / 10))], dtype=torch.float32, device=dev)
@@ -828,10 +835,15 @@ def run_case(args):
         cn_state, msg_cw = lx.ldpc_bp_msg_format(code, algo=algo, iters=ITERS, msg_prec=prec)
         info = {"codewords": Bc, "edges": code.edges, "iters": ITERS, "message_bytes_per_codeword_iteration": msg_cw,
                 "message_format": "check-node state" if cn_state else "per-edge messages",
-                "algorithmic_bytes_per_launch": Bc * (msg_cw * 2 * (ITERS - 1) + 4 * code.n_tx + code.k / 8)}
+                "algorithmic_bytes_per_launch": Bc * (msg_cw * 2 * (ITERS - 1) + (8 * code.n_tx // M if fused else
+                                                                               4 * code.n_tx) + code.k / 8)}
 
         def fn():
-            lx.ldpc_bp_decode(code, llr, **dec, bits_out=bits, iters_out=its, ws=ws, stream=stream)
+            if fused:
+                lx.ldpc_bp_decode_qam(code, y, n0, M, demap_method=lx.DEMAP_MAXLOG, demap_clamp=CLAMP, **dec,
+                                      bits_out=bits, iters_out=its, ws=ws, stream=stream)
+            else:
+                lx.ldpc_bp_decode(code, llr, **dec, bits_out=bits, iters_out=its, ws=ws, stream=stream)
     elif name == "flood_spa_z8":
         code = lx.qc_ldpc_build(2, 8)
         n0 = torch.tensor([1.0 / (code.k / code.n_tx * 2 * 10 ** (2.0 / 10))], dtype=torch.float32, device=dev)
