@@ -450,14 +450,17 @@ int ldpc_bp_decode_mixed(const ldpcx_batch_group *groups, int n_groups, const ld
  * Sec. III-C, Listing 2). Supported for weighted flooding sum-product
  * (LDPCX_FLOOD_SPA, FP32 messages, no early stop): the forward pass
  * ldpc_bp_decode_ckpt stores each iteration's check-to-variable messages C^t
- * (t = 0 .. iters-2) as FP32 checkpoints; ldpc_bp_backward walks the
- * iterations in reverse, recomputes APP^t = L + sum C^(t-1) and the check-node
- * quantities of iteration t from the checkpoint, and propagates the adjoints
+ * and the APP after it, APP^(t+1) = L + sum C^t (t = 0 .. iters-2), as FP32
+ * checkpoints; ldpc_bp_backward walks the iterations in reverse, takes APP^t
+ * (L for t = 0) and recomputes the check-node quantities of iteration t from
+ * the checkpoints, and propagates the adjoints
  *   dC_e/dV_e' = s_e phi'(x_e) [lo < S_e < hi] phi'(a_e') sgn(V_e') [lo <= |V_e'| <= hi]
  * (e' != e in the same check; x_e = clamp(S_e), a = clamp(|V|), phi'(x) =
  * -1/sinh(x)), V_e = w (APP_v - C_e(old)), APP = L + sum C, L = clamp(llr_ch).
  *
- * ckpt bytes = 4 * max(iters-1, 1) * B * round_up(edges, 128). */
+ * ckpt bytes = 4 * max(iters-1, 1) * B * (round_up(edges, 128) + round_up(n, 32)):
+ * the messages [iters-1][B][round_up(edges, 128)], then the APP values
+ * [iters-1][B][round_up(n, 32)]. */
 int ldpc_bp_ckpt_bytes(ldpcx_code_t code, int64_t B, const ldpcx_decode_opts *opts, size_t *ckpt_bytes);
 /* ldpc_bp_decode plus checkpoints (device, >= ldpc_bp_ckpt_bytes, 16-byte aligned). */
 int ldpc_bp_decode_ckpt(ldpcx_code_t code, const float *llr_ch, int64_t B, const ldpcx_decode_opts *opts,

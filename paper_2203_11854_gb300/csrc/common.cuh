@@ -62,6 +62,8 @@ unsigned int take_status_decode(cudaStream_t s);
 unsigned int *status_word_decode();
 // Bytes of the adjoint checkpoints for B codewords and `iters` iterations.
 size_t ckpt_bytes(const ldpcx_code *c, int64_t B, int iters);
+// Floats per codeword of the APP checkpoints that follow the message checkpoints.
+inline int64_t ckpt_app_stride(int n) { return ((int64_t)n + 31) / 32 * 32; }
 unsigned int take_status_channel(cudaStream_t s);
 
 // Transmitter launch (source, encoder, mapper, AWGN); cw0_dev optional;

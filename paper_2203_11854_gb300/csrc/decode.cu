@@ -268,6 +268,7 @@ dec::Params dec::decode_params(const ldpcx_code *c, const uint32_t *blk, const i
     p.weights = o->weights;
     p.ckpt = ckpt;
     p.ckpt_tstride = B * stride;
+    p.ckpt_app_stride = ckpt_app_stride(c->n);
     p.llr_out = llr_out;
     p.bits_out = bits_out;
     p.iters_out = iters_out;
@@ -295,7 +296,8 @@ int dec::decode_launch(const DecodePlan &pl, const ldpcx_code *c, const Params &
 }
 
 size_t ckpt_bytes(const ldpcx_code *c, int64_t B, int iters) {
-    return sizeof(float) * (size_t)(iters > 1 ? iters - 1 : 1) * (size_t)B * (size_t)msg_stride(c);
+    return sizeof(float) * (size_t)(iters > 1 ? iters - 1 : 1) * (size_t)B *
+           (size_t)(msg_stride(c) + ckpt_app_stride(c->n));
 }
 
 }  // namespace ldpcx

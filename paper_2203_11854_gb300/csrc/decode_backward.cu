@@ -13,8 +13,7 @@
 //   gV_e  = phi'(a_e) sgn(V_e) [lo <= |V_e| <= hi] sum_{e' != e} u_e'
 //   gw   += gV_e (APP^t_v - C^(t-1)_e),  gA^t_v += w gV_e,  carry_e = -w gV_e
 //   dLoss/dL = sum_t gA^t (through the channel clamp).
-// APP^t is recomputed from the checkpointed C^(t-1) in the forward's row order,
-// so it equals the forward's value bit for bit. phi and phi' are evaluated with
+// APP^t is the forward's own value, checkpointed after each iteration. phi and phi' are evaluated with
 // the hardware exponential, reciprocal and logarithm (phi_fast, dphi_fast:
 // within about 2e-5 and 1e-6 relative), the exclusive sums S_e as in the
 // forward's check node (the largest term left out of the running sum) and the
@@ -35,7 +34,8 @@ struct BwdParams {
     const float *llr;       // [B][n_tx]
     const float *weights;   // [iters][nnz] or null (all ones)
     const float *ckpt;      // [iters-1][B][stride]
-    int64_t stride, tstride;
+    const float *ckpt_app;  // [iters-1][B][app_stride]: APP^(t+1) after forward iteration t
+    int64_t stride, tstride, app_stride;
     const float *grad_out;  // [B][n]
     float *grad_llr;        // [B][n_tx]
     float *grad_w;          // [iters][nnz] (accumulated) or null
@@ -135,31 +135,14 @@ __global__ void __launch_bounds__(512, TPC == 4 ? 2 : 1) k_backward(const BwdPar
     __syncthreads();
 
     for (int t = p.iters - 1; t >= 0; --t) {
-        // APP^t = L + sum of C^(t-1), added row by row as in the forward pass
-        for (int gg = 0; gg < p.G; ++gg)
-            for (int v = threadIdx.x; v < p.n; v += blockDim.x) s_app[(size_t)gg * p.n + v] = placed_llr(p, cw_base + gg, v);
-        __syncthreads();
-        const float *ck = t >= 1 ? p.ckpt + (size_t)(t - 1) * p.tstride + (active ? cw : 0) * p.stride + z : nullptr;
-        if (ck) {
-            float cn[DPT];
-            row_values<DPT, TPC>(ck, active, s_rp[0], s_rp[1] - s_rp[0], q, p.Z, cn);
-            for (int r = 0; r < p.rows; ++r) {
-                const int b0 = s_rp[r], deg = s_rp[r + 1] - b0;
-                float cc[DPT];
-#pragma unroll
-                for (int i = 0; i < DPT; ++i) cc[i] = cn[i];
-                if (r + 1 < p.rows) row_values<DPT, TPC>(ck, active, s_rp[r + 1], s_rp[r + 2] - s_rp[r + 1], q, p.Z, cn);
-#pragma unroll
-                for (int i = 0; i < DPT; ++i) {
-                    const int j = q + TPC * i;
-                    if (TPC * i < deg && active && j < deg) {
-                        const int v = vn_of(s_vb[b0 + j], z, p.Z);
-                        s_app[off + v] = __fadd_rn(s_app[off + v], cc[i]);
-                    }
-                }
-                __syncthreads();
-            }
+        // APP^t: the clamped channel LLRs (t = 0) or the forward's own APP^t from its checkpoint
+        const float *ca = t >= 1 ? p.ckpt_app + (size_t)(t - 1) * p.B * p.app_stride : nullptr;
+        for (int gg = 0; gg < p.G; ++gg) {
+            const int64_t c2 = cw_base + gg;
+            for (int v = threadIdx.x; v < p.n; v += blockDim.x)
+                s_app[(size_t)gg * p.n + v] = !ca ? placed_llr(p, c2, v) : c2 < p.B ? ca[c2 * p.app_stride + v] : 0.0f;
         }
+        const float *ck = t >= 1 ? p.ckpt + (size_t)(t - 1) * p.tstride + (active ? cw : 0) * p.stride + z : nullptr;
         // dLoss/dL collects every gA^(t+1) (transmitted positions only); gA^t starts from zero
         for (int gg = 0; gg < p.G; ++gg) {
             const int64_t c2 = cw_base + gg;
@@ -363,6 +346,8 @@ extern "C" int ldpc_bp_backward(ldpcx_code_t c, const float *llr_ch, int64_t B, 
     p.ckpt = (const float *)ckpt;
     p.stride = stride_of(c);
     p.tstride = B * p.stride;
+    p.app_stride = ckpt_app_stride(c->n);
+    p.ckpt_app = p.ckpt + (size_t)(o->iters > 1 ? o->iters - 1 : 1) * p.tstride;
     p.grad_out = grad_llr_out;
     p.grad_llr = grad_llr_ch;
     p.grad_w = grad_weights;

@@ -177,6 +177,16 @@ __global__ void __launch_bounds__(512, TPC > 1 ? 2 : 1) k_flooding(const Params 
         float *tmp = cur;
         cur = nxt;
         nxt = tmp;
+        if (p.ckpt && store) {
+            // APP^(t+1) for the adjoint, after the message checkpoints (no early stop here)
+            float *ca = p.ckpt + (size_t)(p.iters - 1) * p.ckpt_tstride + (size_t)t * p.B * p.ckpt_app_stride;
+            for (int gg = 0; gg < p.G; ++gg) {
+                const int64_t c2 = cw_base + gg;
+                if (c2 >= p.B) break;
+                for (int v = threadIdx.x; v < p.n; v += blockDim.x)
+                    ca[c2 * p.ckpt_app_stride + v] = cur[(size_t)gg * p.n + v];
+            }
+        }
         if (!done) iters_run = t + 1;
         if (p.early_stop) {
             if (threadIdx.x < p.G) s_flag[threadIdx.x] = 0;

@@ -136,6 +136,7 @@ struct Params {
     const float *weights;         // flooding: [iters][nnz] or null
     float *ckpt;                  // flooding: C^t checkpoints [iters-1][B][msg_stride] (FP32) or null
     int64_t ckpt_tstride;         // B * msg_stride
+    int64_t ckpt_app_stride;      // floats per codeword of the APP checkpoints after the messages
     float *llr_out;               // [B][n] or null
     uint32_t *bits_out;           // [B][kw] or null
     int32_t *iters_out;           // [B] or null

@@ -188,3 +188,12 @@ def test_decode_qam_argument_checks(lx):
     assert call(y=None) == -1                           # null symbols
     assert call() == -4                                 # missing workspace
     assert L.ldpc_bp_decode_qam(None, one, one, 0, 2, 4, 0, 20.0, None, None, one, None, None, 0, None) == -1
+
+
+def test_ckpt_bytes_hold_messages_and_app(lx):
+    """The differentiable decode's checkpoints: per iteration but the last, every codeword's messages (edges
+    rounded up to 128 floats) and its APP values (n rounded up to 32 floats)."""
+    code = lx.qc_ldpc_build(2, 8)  # 197 blocks x 8 = 1576 edges, n = 416
+    per_cw = (1576 + 127) // 128 * 128 + (416 + 31) // 32 * 32
+    assert lx.ldpc_bp_ckpt_bytes(code, 10, iters=8) == 4 * 7 * 10 * per_cw
+    assert lx.ldpc_bp_ckpt_bytes(code, 3, iters=1) == 4 * 1 * 3 * per_cw  # one slot even without a stored iteration
