@@ -347,7 +347,8 @@ int ldpc_bp_decode_qam(ldpcx_code_t code, const float *y, const float *no, int64
  * z and z + Z/2, honoured when Z is even. Other kernels use one.
  * LDPCX_TUNE_CW_PER_CTA: codewords decoded together by one CTA of
  * ldpc_bp_decode (0 = automatic: about 384 check nodes per CTA within the
- * shared-memory budget; a smaller value gives smaller CTAs, more per SM), and
+ * shared-memory budget, fewer when the batch would give the SMs fewer than
+ * about four CTAs each; a smaller value gives smaller CTAs, more per SM), and
  * the cap on the codewords of one work item of ldpc_bp_decode_mixed (smaller
  * items: a finer queue, less waiting on a tile's slowest codeword).
  * LDPCX_TUNE_SPECIALISED: 1 (default) = use the layered min-sum kernels built

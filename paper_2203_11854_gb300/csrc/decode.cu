@@ -29,17 +29,17 @@ int64_t cns_bytes(const ldpcx_code *c, int prec) {
     return cns_bytes_per_cw<kFix6>(rp, c->rows, c->Z);
 }
 
-KernelFn pick_kernel(int max_deg, bool layered, int algo, int prec, int zpt, int Z) {
+KernelFn pick_kernel(int max_deg, bool layered, int algo, int prec, int zpt, int Z, bool qam) {
     if (!layered) return flooding_kernel(max_deg, algo, prec, flood_tpc(Z));
     if (zpt == 1 && g_specialised.load()) {
-        KernelFn f = prec == kF32 ? layered_kernel_zc_f32(max_deg, algo, Z)
-                   : prec == kF16 ? layered_kernel_zc_f16(max_deg, algo, Z)
-                                  : layered_kernel_zc_fix6(max_deg, algo, Z);
+        KernelFn f = prec == kF32 ? layered_kernel_zc_f32(max_deg, algo, Z, qam)
+                   : prec == kF16 ? layered_kernel_zc_f16(max_deg, algo, Z, qam)
+                                  : layered_kernel_zc_fix6(max_deg, algo, Z, qam);
         if (f) return f;
     }
-    if (prec == kF32) return layered_kernel_f32(max_deg, algo, zpt);
-    if (prec == kF16) return layered_kernel_f16(max_deg, algo, zpt);
-    return layered_kernel_fix6(max_deg, algo, zpt);
+    if (prec == kF32) return layered_kernel_f32(max_deg, algo, zpt, qam);
+    if (prec == kF16) return layered_kernel_f16(max_deg, algo, zpt, qam);
+    return layered_kernel_fix6(max_deg, algo, zpt, qam);
 }
 
 size_t msg_bytes(int prec) { return prec == kF32 ? 4 : prec == kF16 ? 2 : 1; }
@@ -71,7 +71,7 @@ std::atomic<int> g_cw_per_cta{0};  // 0 = automatic
 // Codewords per CTA: enough check-node threads to fill ~384 threads (layered)
 // or up to 512 threads of TPC per check node (flooding), bounded by the shared
 // memory that keeps two CTAs per SM (layered; flooding with TPC > 1) or one.
-int pick_G(const ldpcx_code *c, bool layered) {
+int pick_G(const ldpcx_code *c, bool layered, int64_t B) {
     const size_t per_cw = sizeof(float) * (size_t)c->n * (layered ? 1 : 2);
     const int tpc = layered ? 1 : flood_tpc(c->Z);
     const size_t budget = layered || tpc > 1 ? 105 * 1024 : 210 * 1024;
@@ -79,7 +79,14 @@ int pick_G(const ldpcx_code *c, bool layered) {
     if (G < 1) G = 1;
     while (G > 1 && per_cw * G > budget) --G;
     const int want = g_cw_per_cta.load();
-    if (want > 0 && want < G) G = want;  // autotuner: smaller tiles, more CTAs per SM
+    if (want > 0) {
+        if (want < G) G = want;  // autotuner: smaller tiles, more CTAs per SM
+    } else {
+        // a small batch: fewer codewords per CTA, so that its CTAs (each a serial chain of row steps) spread
+        // over about four per SM instead of crowding a few
+        const int64_t spread = B / (4 * (int64_t)sm_count());
+        if (spread < G) G = spread < 1 ? 1 : (int)spread;
+    }
     return G;
 }
 
@@ -178,7 +185,7 @@ int check_differentiable(const ldpcx_code *c, const ldpcx_decode_opts *o) {
 
 }  // namespace
 
-int dec::decode_plan(const ldpcx_code *c, const ldpcx_decode_opts *o, DecodePlan *pl) {
+int dec::decode_plan(const ldpcx_code *c, const ldpcx_decode_opts *o, DecodePlan *pl, bool qam) {
     *pl = DecodePlan{};
     const bool layered = o->algo == LDPCX_LAYERED_MINSUM || o->algo == LDPCX_LAYERED_SPA;
     const int algo = (o->algo == LDPCX_LAYERED_MINSUM || o->algo == LDPCX_FLOOD_MINSUM) ? kMinSum : kSpa;
@@ -188,10 +195,10 @@ int dec::decode_plan(const ldpcx_code *c, const ldpcx_decode_opts *o, DecodePlan
         const int want = g_zpt.load();
         zpt = (want == 2 && c->Z % 2 == 0) ? 2 : 1;
     }
-    KernelFn fn = pick_kernel(c->max_deg, layered, algo, o->msg_prec, zpt, c->Z);
+    KernelFn fn = pick_kernel(c->max_deg, layered, algo, o->msg_prec, zpt, c->Z, qam);
     if (!fn && zpt == 2) {  // two check nodes per thread not built: fall back to one
         zpt = 1;
-        fn = pick_kernel(c->max_deg, layered, algo, o->msg_prec, zpt, c->Z);
+        fn = pick_kernel(c->max_deg, layered, algo, o->msg_prec, zpt, c->Z, qam);
     }
     if (!fn) return LDPCX_E_UNSUPPORTED;
     pl->fn = fn;
@@ -273,7 +280,7 @@ dec::Params dec::decode_params(const ldpcx_code *c, const uint32_t *blk, const i
     p.bits_out = bits_out;
     p.iters_out = iters_out;
     p.B = B;
-    p.G = pick_G(c, layered);
+    p.G = pick_G(c, layered, B);
     p.pf_dist = layered ? g_pf_dist.load() : 0;
     p.msg_size = (int)msg_bytes(o->msg_prec);
     p.status = status_word_decode();
@@ -330,7 +337,7 @@ extern "C" int ldpc_bp_decode_qam(ldpcx_code_t c, const float *y, const float *n
     st = code_device(c, &d);
     if (st) return st;
     DecodePlan pl;
-    st = decode_plan(c, o, &pl);
+    st = decode_plan(c, o, &pl, true);
     if (st) return st;
     Params p = decode_params(c, d.blk, d.row_ptr, nullptr, B, o, llr_out, bits_out, iters_out, ws, msg_stride(c),
                              nullptr, pl.layered);

@@ -420,7 +420,7 @@ __device__ __forceinline__ void cns_tile(const Params &p, int64_t cw_base, int64
 }
 
 template <int DMAX, int PREC, int ZC = 0>
-__global__ void __launch_bounds__(kMaxThreads, 2) k_layered_cns(const Params p) {
+__global__ void __launch_bounds__(kMaxThreads, 2) k_layered_cns(const __grid_constant__ Params p) {
     extern __shared__ __align__(16) unsigned char smem[];
     cns_tile<DMAX, PREC, ZC>(p, (int64_t)blockIdx.x * p.G, 0, smem);
 }

@@ -739,7 +739,7 @@ __device__ __forceinline__ void cns_sched_tile1(const Params &p, int64_t cw_base
 // (called as a function) compiles to about 8 % more instructions on sm_103a.
 template <int BG, int PREC, int ZC = 0, int K = 1, bool TRUNC = false>
 __global__ void __launch_bounds__(kMaxThreads / K, 2)
-    k_layered_cns_sched(const Params p, const __grid_constant__ SchedTab tab) {
+    k_layered_cns_sched(const __grid_constant__ Params p, const __grid_constant__ SchedTab tab) {
     extern __shared__ __align__(16) unsigned char smem[];
     if constexpr (K == 1 && !TRUNC) {
         using S = Sched<BG>;

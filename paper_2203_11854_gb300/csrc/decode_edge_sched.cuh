@@ -118,7 +118,7 @@ __device__ __forceinline__ void edge_run(const Params &p, const int2 *s_at, floa
 
 template <int BG, int ALGO, int PREC, int ZC = 0>
 __global__ void __launch_bounds__(kMaxThreads, 2)
-    k_layered_edge_sched(const Params p, const __grid_constant__ SchedTab tab) {
+    k_layered_edge_sched(const __grid_constant__ Params p, const __grid_constant__ SchedTab tab) {
     using S = Sched<BG>;
     using L = SchedLayout<BG, PREC>;
     using MT = typename MsgT<PREC>::T;

@@ -121,7 +121,7 @@ __device__ __forceinline__ void flood_update_tpc(const Params &p, bool act, int 
 // node of the current row). Rows add into the accumulator one after another,
 // so the APP sums run in ascending row order.
 template <int DMAX, int ALGO, int PREC, int TPC>
-__global__ void __launch_bounds__(512, TPC > 1 ? 2 : 1) k_flooding(const Params p) {
+__global__ void __launch_bounds__(512, TPC > 1 ? 2 : 1) k_flooding(const __grid_constant__ Params p) {
     using MT = typename MsgT<PREC>::T;
     extern __shared__ __align__(16) unsigned char smem[];
     float *s_a = reinterpret_cast<float *>(smem);
@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(512, TPC > 1 ? 2 : 1) k_flooding(const Params 
     load_tables(p, s_vb, s_rp);
     const int64_t cw_base = (int64_t)blockIdx.x * p.G;
     for (int i = threadIdx.x; i < p.G; i += blockDim.x) s_done[i] = (cw_base + i >= p.B) ? 1 : 0;
-    load_channel(p, s_a, cw_base);
+    load_channel_llr(p, s_a, cw_base);  // the flooding decoders take LLRs only
 
     const int node = threadIdx.x / TPC, q = threadIdx.x - node * TPC;
     const int g = node / p.Z, z = node - g * p.Z;
@@ -180,11 +180,18 @@ __global__ void __launch_bounds__(512, TPC > 1 ? 2 : 1) k_flooding(const Params 
         if (p.ckpt && store) {
             // APP^(t+1) for the adjoint, after the message checkpoints (no early stop here)
             float *ca = p.ckpt + (size_t)(p.iters - 1) * p.ckpt_tstride + (size_t)t * p.B * p.ckpt_app_stride;
+            const bool vec = (p.n & 3) == 0;  // 16-byte rows on both sides (the stride is a multiple of 32)
             for (int gg = 0; gg < p.G; ++gg) {
                 const int64_t c2 = cw_base + gg;
                 if (c2 >= p.B) break;
-                for (int v = threadIdx.x; v < p.n; v += blockDim.x)
-                    ca[c2 * p.ckpt_app_stride + v] = cur[(size_t)gg * p.n + v];
+                float *dst = ca + c2 * p.ckpt_app_stride;
+                const float *a = cur + (size_t)gg * p.n;
+                if (vec) {
+                    for (int v = threadIdx.x; v < (p.n >> 2); v += blockDim.x)
+                        reinterpret_cast<float4 *>(dst)[v] = reinterpret_cast<const float4 *>(a)[v];
+                } else {
+                    for (int v = threadIdx.x; v < p.n; v += blockDim.x) dst[v] = a[v];
+                }
             }
         }
         if (!done) iters_run = t + 1;

@@ -196,9 +196,10 @@ __device__ __forceinline__ float channel_llr(const Params &p, int64_t cw, int v,
 // the received symbols, the values demap_app writes (same arithmetic, then the
 // decoder's clamp), placed as load_channel places them, so decoding is the same
 // bit for bit as demap_app followed by the decoder. Out of line: one copy per
-// translation unit instead of one per kernel. The parameters are read once
-// into registers (through the reference every shared-memory store would force
-// them to be read again).
+// translation unit instead of one per kernel (the kernels declare their Params
+// __grid_constant__, so the function may take its address). The parameters are
+// read once into registers (through the reference every shared-memory store
+// would force them to be read again).
 struct QamLoad {
     const float *y;  // this codeword's symbols
     float inv_n0, scale, dclamp, clamp;
@@ -260,7 +261,7 @@ __device__ __forceinline__ void qam_channel(const QamLoad q, float *a, bool &bad
         }
     }
 }
-static __device__ __noinline__ void load_channel_qam(const Params &p, float *app, int64_t cw_base) {
+__device__ __forceinline__ void load_channel_qam_body(const Params &p, float *app, int64_t cw_base) {
     const int G = p.G, n = p.n, k = p.k, nf = p.nf, p0 = p.p0, n_tx = p.n_tx, m = p.qam_m;
     const int64_t B = p.B;
     const float clamp = p.clamp;
@@ -295,14 +296,14 @@ static __device__ __noinline__ void load_channel_qam(const Params &p, float *app
     if (bad) latch(status, LDPCX_FLAG_NONFINITE);
 }
 
+static __device__ __noinline__ void load_channel_qam(const Params &p, float *app, int64_t cw_base) {
+    load_channel_qam_body(p, app, cw_base);
+}
+
 // Load the channel LLRs of the CTA's codewords into app (placed: punctured and
 // untransmitted positions are 0). When the row layout allows, 16-byte loads,
 // four per thread in flight (streaming: the LLRs are read once).
-__device__ inline void load_channel(const Params &p, float *app, int64_t cw_base) {
-    if (p.sym) {
-        load_channel_qam(p, app, cw_base);
-        return;
-    }
+__device__ __forceinline__ void load_channel_llr(const Params &p, float *app, int64_t cw_base) {
     bool bad = false;
     if (p.nf == 0 && ((p.p0 | p.n_tx | p.n) & 3) == 0 && (reinterpret_cast<uintptr_t>(p.llr) & 15u) == 0) {
         const int bd = blockDim.x, n4 = p.n_tx >> 2;
@@ -336,6 +337,27 @@ __device__ inline void load_channel(const Params &p, float *app, int64_t cw_base
         for (int v = threadIdx.x; v < p.n; v += blockDim.x) app[(size_t)g * p.n + v] = channel_llr(p, cw, v, bad);
     }
     if (bad) latch(p.status, LDPCX_FLAG_NONFINITE);
+}
+
+// The channel load of every decoder: from the received symbols (the fused
+// demapper, out of line) or from the LLRs.
+__device__ inline void load_channel(const Params &p, float *app, int64_t cw_base) {
+    if (p.sym) {
+        load_channel_qam(p, app, cw_base);
+        return;
+    }
+    load_channel_llr(p, app, cw_base);
+}
+
+// The channel load chosen at compile time (kCh*): the per-edge kernels are
+// built once per input kind, since holding the fused path at all costs their
+// main loop about 9 %.
+constexpr int kChAny = 0, kChLlr = 1, kChQam = 2;
+template <int CH>
+__device__ __forceinline__ void load_channel_as(const Params &p, float *app, int64_t cw_base) {
+    if constexpr (CH == kChLlr) load_channel_llr(p, app, cw_base);
+    else if constexpr (CH == kChQam) load_channel_qam_body(p, app, cw_base);
+    else load_channel(p, app, cw_base);
 }
 
 // Shared-memory block table entry: (col * Z) << 16 | shift. Variable node of
@@ -772,8 +794,9 @@ template <int ZPT> constexpr int layered_threads() { return kMaxThreads / ZPT; }
 // One tile of the layered schedule: the G codewords cw_base .. cw_base+G-1 of
 // p, decoded by the whole CTA. Messages of codeword cw live at
 // msg + (cw - msg_cw0) * msg_stride (msg_cw0 = 0: one slot per codeword of the
-// batch; msg_cw0 = cw_base: one slot per codeword of the tile).
-template <int DMAX, int ALGO, int PREC, int ZPT, int ZC = 0>
+// batch; msg_cw0 = cw_base: one slot per codeword of the tile). CH: the
+// channel load (kCh*).
+template <int DMAX, int ALGO, int PREC, int ZPT, int ZC = 0, int CH = kChAny>
 __device__ __forceinline__ void layered_tile(const Params &p, int64_t cw_base, int64_t msg_cw0,
                                              unsigned char *smem) {
     const int ZV = ZC ? ZC : p.Z;  // lifting size (compile-time when ZC != 0)
@@ -784,7 +807,7 @@ __device__ __forceinline__ void layered_tile(const Params &p, int64_t cw_base, i
     int *s_flag = reinterpret_cast<int *>(s_rp + p.rows + 1);
 
     load_tables(p, s_vb, s_rp);
-    load_channel(p, s_app_all, cw_base);
+    load_channel_as<CH>(p, s_app_all, cw_base);
 
     const int zq = ZV / ZPT;  // threads per codeword
     const int g = threadIdx.x / zq, z0 = (threadIdx.x - g * zq) * ZPT;
@@ -830,29 +853,36 @@ __device__ __forceinline__ void layered_tile(const Params &p, int64_t cw_base, i
     write_outputs(p, s_app_all, cw_base, iters_run, g, active, z0);
 }
 
-// ZC: compile-time lifting size (0 = the runtime p.Z).
-template <int DMAX, int ALGO, int PREC, int ZPT, int ZC = 0>
-__global__ void __launch_bounds__(layered_threads<ZPT>(), 2) k_layered(const Params p) {
+// ZC: compile-time lifting size (0 = the runtime p.Z); CH: channel input,
+// LLRs (kChLlr) or received symbols (kChQam).
+template <int DMAX, int ALGO, int PREC, int ZPT, int ZC = 0, int CH = kChLlr>
+__global__ void __launch_bounds__(layered_threads<ZPT>(), 2) k_layered(const __grid_constant__ Params p) {
     extern __shared__ __align__(16) unsigned char smem[];
-    layered_tile<DMAX, ALGO, PREC, ZPT, ZC>(p, (int64_t)blockIdx.x * p.G, 0, smem);
+    layered_tile<DMAX, ALGO, PREC, ZPT, ZC, CH>(p, (int64_t)blockIdx.x * p.G, 0, smem);
 }
 
 using KernelFn = void (*)(Params);
 
+// The per-edge kernel for an input kind (one check node per thread).
+template <int DMAX, int ALGO, int PREC, int ZC = 0>
+KernelFn layered_ch(bool qam) {
+    return qam ? k_layered<DMAX, ALGO, PREC, 1, ZC, kChQam> : k_layered<DMAX, ALGO, PREC, 1, ZC, kChLlr>;
+}
+
 // Kernel lookup per translation unit (nullptr when the combination is not built).
 // zpt: check nodes per thread (2 needs an even Z).
-KernelFn layered_kernel_f32(int dmax, int algo, int zpt);
-KernelFn layered_kernel_f16(int dmax, int algo, int zpt);
-KernelFn layered_kernel_fix6(int dmax, int algo, int zpt);
+KernelFn layered_kernel_f32(int dmax, int algo, int zpt, bool qam = false);
+KernelFn layered_kernel_f16(int dmax, int algo, int zpt, bool qam = false);
+KernelFn layered_kernel_fix6(int dmax, int algo, int zpt, bool qam = false);
 KernelFn flooding_kernel(int dmax, int algo, int prec, int tpc);
 // Threads per check node of the flooding kernels: as many as keep a CTA of one
 // codeword within 512 threads.
 inline int flood_tpc(int Z) { return Z <= 128 ? 4 : Z <= 256 ? 2 : 1; }
 // Layered min-sum kernels specialised for a compile-time lifting size (nullptr
 // when none is built for Z): the hot loop's addresses become immediates.
-KernelFn layered_kernel_zc_f32(int dmax, int algo, int Z);
-KernelFn layered_kernel_zc_f16(int dmax, int algo, int Z);
-KernelFn layered_kernel_zc_fix6(int dmax, int algo, int Z);
+KernelFn layered_kernel_zc_f32(int dmax, int algo, int Z, bool qam = false);
+KernelFn layered_kernel_zc_f16(int dmax, int algo, int Z, bool qam = false);
+KernelFn layered_kernel_zc_fix6(int dmax, int algo, int Z, bool qam = false);
 
 }  // namespace dec
 }  // namespace ldpcx

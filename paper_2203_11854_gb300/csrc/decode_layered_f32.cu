@@ -4,18 +4,18 @@
 namespace ldpcx {
 namespace dec {
 
-KernelFn layered_kernel_f32(int dmax, int algo, int zpt) {
+KernelFn layered_kernel_f32(int dmax, int algo, int zpt, bool qam) {
     constexpr int PREC = kF32;
     if (dmax > 20) return nullptr;
     if (zpt != 1) return nullptr;  // one check node per thread (two measured slower here: bank conflicts)
-    if (algo == kMinSum) return dmax <= 12 ? k_layered<12, kMinSum, PREC, 1> : k_layered<20, kMinSum, PREC, 1>;
-    return dmax <= 12 ? k_layered<12, kSpa, PREC, 1> : k_layered<20, kSpa, PREC, 1>;
+    if (algo == kMinSum) return dmax <= 12 ? layered_ch<12, kMinSum, PREC>(qam) : layered_ch<20, kMinSum, PREC>(qam);
+    return dmax <= 12 ? layered_ch<12, kSpa, PREC>(qam) : layered_ch<20, kSpa, PREC>(qam);
 }
 
-KernelFn layered_kernel_zc_f32(int dmax, int algo, int Z) {
+KernelFn layered_kernel_zc_f32(int dmax, int algo, int Z, bool qam) {
     constexpr int PREC = kF32;
     if (algo != kMinSum || dmax > 20) return nullptr;
-    if (Z == 384) return dmax <= 12 ? k_layered<12, kMinSum, PREC, 1, 384> : k_layered<20, kMinSum, PREC, 1, 384>;
+    if (Z == 384) return dmax <= 12 ? layered_ch<12, kMinSum, PREC, 384>(qam) : layered_ch<20, kMinSum, PREC, 384>(qam);
     return nullptr;
 }
 

@@ -109,10 +109,10 @@ __global__ void __launch_bounds__(kMaxThreads, 2) k_mixed(const MixedParams m) {
             } else if (gd.cns) {
                 cns_tile<DMAX, PREC, 0>(p, item.cw_base, item.cw_base, smem);
             } else {
-                layered_tile<DMAX, ALGO, PREC, 1>(p, item.cw_base, item.cw_base, smem);
+                layered_tile<DMAX, ALGO, PREC, 1, 0, kChLlr>(p, item.cw_base, item.cw_base, smem);
             }
         } else {
-            layered_tile<DMAX, ALGO, PREC, 1>(p, item.cw_base, item.cw_base, smem);
+            layered_tile<DMAX, ALGO, PREC, 1, 0, kChLlr>(p, item.cw_base, item.cw_base, smem);
         }
         __syncthreads();  // every thread has read s_item before it is overwritten
     }

@@ -20,8 +20,10 @@ struct DecodePlan {
     int64_t state_bytes = 0;  // with cns: bytes of one codeword's state in the kernel's format
 };
 
-// Picks the kernel; LDPCX_E_UNSUPPORTED when none is built for the code.
-int decode_plan(const ldpcx_code *c, const ldpcx_decode_opts *o, DecodePlan *pl);
+// Picks the kernel; LDPCX_E_UNSUPPORTED when none is built for the code. qam:
+// the channel input is received symbols (ldpc_bp_decode_qam), which the
+// per-edge kernels take in a build of their own.
+int decode_plan(const ldpcx_code *c, const ldpcx_decode_opts *o, DecodePlan *pl, bool qam = false);
 
 // Message (or check-node state) bytes one codeword needs under the plan.
 int64_t decode_plan_bytes_per_cw(const ldpcx_code *c, const ldpcx_decode_opts *o, const DecodePlan &pl);

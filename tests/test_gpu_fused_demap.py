@@ -119,3 +119,20 @@ def test_fused_nonfinite_symbols(lx):
     b = two_step(lx, code, y, no, 4, lx.DEMAP_EXACT, 20.0, dec)
     lx.ldpcx_sync_status()
     assert_same(a, b)
+
+
+@pytest.mark.parametrize("name,B", [("bg1_z384", 12), ("bg2_z8", 37), ("bg1_z16_short300", 33)])
+@pytest.mark.parametrize("prec", [0, 1, 2])
+def test_fused_per_edge_minsum(lx, name, B, prec):
+    """With the check-node state switched off, min-sum runs the per-edge kernels, which are built once per
+    input kind: the symbol-input build equals the LLR-input build after demap_app."""
+    code = build(lx, name)
+    dec = dict(algo=0, msg_prec=prec, iters=10, early_stop=True, offset=0.5, clamp=20.0)
+    m = 4 if code.n_tx % 4 == 0 else 2
+    y, no = channel(lx, code, B, m, 2.5, per_cw=True)
+    lx.ldpcx_tune_set(lx.TUNE_CN_STATE, 0)
+    try:
+        assert_same(fused(lx, code, y, no, m, lx.DEMAP_MAXLOG, 20.0, dec),
+                    two_step(lx, code, y, no, m, lx.DEMAP_MAXLOG, 20.0, dec))
+    finally:
+        lx.ldpcx_tune_set(lx.TUNE_CN_STATE, 1)
