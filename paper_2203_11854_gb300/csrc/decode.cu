@@ -209,7 +209,7 @@ int dec::decode_plan(const ldpcx_code *c, const ldpcx_decode_opts *o, DecodePlan
         int bg = sched_shape(c);
         if (bg && c->rows != (bg == 1 ? Sched<1>::rows : Sched<2>::rows)) bg = 0;
         SchedFn sf = bg && c->nnz <= kSchedMaxBlocks
-                         ? layered_edge_sched_kernel(bg, algo, o->msg_prec, g_specialised.load() ? c->Z : 0)
+                         ? layered_edge_sched_kernel(bg, algo, o->msg_prec, g_specialised.load() ? c->Z : 0, qam)
                          : nullptr;
         if (sf) {
             pl->sf = sf;
@@ -225,7 +225,7 @@ int dec::decode_plan(const ldpcx_code *c, const ldpcx_decode_opts *o, DecodePlan
         const int bg = g_sched.load() ? sched_shape(c) : 0;
         const bool trunc = bg && c->rows != (bg == 1 ? Sched<1>::rows : Sched<2>::rows);
         const int kpt = !trunc && g_zpt.load() == 2 && c->Z % 2 == 0 ? 2 : 1;  // check nodes per thread
-        SchedFn sf = bg && c->nnz <= kSchedMaxBlocks ? layered_cns_sched_kernel(bg, o->msg_prec, zs, kpt, trunc)
+        SchedFn sf = bg && c->nnz <= kSchedMaxBlocks ? layered_cns_sched_kernel(bg, o->msg_prec, zs, kpt, trunc, qam)
                                                      : nullptr;
         const int64_t sb = bg ? sched_state_bytes(bg, o->msg_prec, kpt, c->row_ptr.data(), c->rows, c->Z) : 0;
         if (sf && sb <= ws_cw) {

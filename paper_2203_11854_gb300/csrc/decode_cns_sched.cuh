@@ -737,7 +737,11 @@ __device__ __forceinline__ void cns_sched_tile1(const Params &p, int64_t cw_base
 // The kernel. For a full base graph with one check node per thread the tile
 // is written out in the kernel body: the same steps as cns_sched_tile1, which
 // (called as a function) compiles to about 8 % more instructions on sm_103a.
-template <int BG, int PREC, int ZC = 0, int K = 1, bool TRUNC = false>
+// That form is built for LLR input alone (CH = kChLlr: 0.4 % faster than with
+// the fused path beside it) and for either input (kChAny, calling the fused
+// demapper's load out of line: inlined, it costs the main loop 1.3 %); the
+// other forms take either input.
+template <int BG, int PREC, int ZC = 0, int K = 1, bool TRUNC = false, int CH = kChAny>
 __global__ void __launch_bounds__(kMaxThreads / K, 2)
     k_layered_cns_sched(const __grid_constant__ Params p, const __grid_constant__ SchedTab tab) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -752,7 +756,7 @@ __global__ void __launch_bounds__(kMaxThreads / K, 2)
         int32_t *s_rp = reinterpret_cast<int32_t *>(s_vb + p.nnz);
         int *s_flag = reinterpret_cast<int *>(s_rp + p.rows + 1);
         load_tables(p, s_vb, s_rp);  // for the syndrome check
-        load_channel(p, s_app_all, cw_base);
+        load_channel_as<CH>(p, s_app_all, cw_base);
         const int g = threadIdx.x / ZV, z = threadIdx.x - g * ZV;
         const int64_t cw = cw_base + g;
         const bool active = g < p.G && cw < p.B;
@@ -836,7 +840,8 @@ using SchedFn = void (*)(Params, SchedTab);
 // Kernel for a code whose row degrees follow the base graph of shape bg (1 or
 // 2), full (k check nodes per thread: 1, or 2 when Z is even) or truncated
 // (trunc, one check node per thread), or nullptr.
-SchedFn layered_cns_sched_kernel(int bg, int prec, int Z, int k, bool trunc);
+// qam: the channel input is received symbols (ldpc_bp_decode_qam).
+SchedFn layered_cns_sched_kernel(int bg, int prec, int Z, int k, bool trunc, bool qam = false);
 
 }  // namespace dec
 }  // namespace ldpcx

@@ -8,15 +8,18 @@ namespace ldpcx {
 namespace dec {
 
 template <int BG>
-SchedFn cns_sched_f32_bg(int Z, int k, bool trunc) {
+SchedFn cns_sched_f32_bg(int Z, int k, bool trunc, bool qam) {
     if (trunc) return k_layered_cns_sched<BG, kF32, 0, 1, true>;
     if (k == 2) return Z == 384 ? k_layered_cns_sched<BG, kF32, 384, 2> : k_layered_cns_sched<BG, kF32, 0, 2>;
-    return Z == 384 ? k_layered_cns_sched<BG, kF32, 384, 1> : k_layered_cns_sched<BG, kF32, 0, 1>;
+    if (qam) return Z == 384 ? k_layered_cns_sched<BG, kF32, 384, 1, false, kChAny>
+                             : k_layered_cns_sched<BG, kF32, 0, 1, false, kChAny>;
+    return Z == 384 ? k_layered_cns_sched<BG, kF32, 384, 1, false, kChLlr>
+                    : k_layered_cns_sched<BG, kF32, 0, 1, false, kChLlr>;
 }
 
-SchedFn cns_sched_f32(int bg, int Z, int k, bool trunc) {
-    if (bg == 1) return cns_sched_f32_bg<1>(Z, k, trunc);
-    if (bg == 2) return cns_sched_f32_bg<2>(Z, k, trunc);
+SchedFn cns_sched_f32(int bg, int Z, int k, bool trunc, bool qam) {
+    if (bg == 1) return cns_sched_f32_bg<1>(Z, k, trunc, qam);
+    if (bg == 2) return cns_sched_f32_bg<2>(Z, k, trunc, qam);
     return nullptr;
 }
 

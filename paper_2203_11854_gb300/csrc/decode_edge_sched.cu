@@ -7,14 +7,16 @@ namespace ldpcx {
 namespace dec {
 
 template <int BG, int PREC>
-SchedFn edge_sched_for(int Z) {
-    return Z == 384 ? k_layered_edge_sched<BG, kSpa, PREC, 384> : k_layered_edge_sched<BG, kSpa, PREC, 0>;
+SchedFn edge_sched_for(int Z, bool qam) {
+    if (qam)
+        return Z == 384 ? k_layered_edge_sched<BG, kSpa, PREC, 384, kChAny> : k_layered_edge_sched<BG, kSpa, PREC, 0, kChAny>;
+    return Z == 384 ? k_layered_edge_sched<BG, kSpa, PREC, 384, kChLlr> : k_layered_edge_sched<BG, kSpa, PREC, 0, kChLlr>;
 }
 
-SchedFn layered_edge_sched_kernel(int bg, int algo, int prec, int Z) {
+SchedFn layered_edge_sched_kernel(int bg, int algo, int prec, int Z, bool qam) {
     if (algo != kSpa || (bg != 1 && bg != 2)) return nullptr;
-    if (prec == kF32) return bg == 1 ? edge_sched_for<1, kF32>(Z) : edge_sched_for<2, kF32>(Z);
-    if (prec == kF16) return bg == 1 ? edge_sched_for<1, kF16>(Z) : edge_sched_for<2, kF16>(Z);
+    if (prec == kF32) return bg == 1 ? edge_sched_for<1, kF32>(Z, qam) : edge_sched_for<2, kF32>(Z, qam);
+    if (prec == kF16) return bg == 1 ? edge_sched_for<1, kF16>(Z, qam) : edge_sched_for<2, kF16>(Z, qam);
     return nullptr;
 }
 

@@ -116,7 +116,9 @@ __device__ __forceinline__ void edge_run(const Params &p, const int2 *s_at, floa
     if constexpr (COUNT % 2 == 1) edge_step<D, BG, ALGO, PREC>(p, s_at, app, mp, z, t, r, bb, done, R0, R1);
 }
 
-template <int BG, int ALGO, int PREC, int ZC = 0>
+// CH: channel input, LLRs alone (kChLlr) or either (kChAny: the fused
+// demapper's load out of line, for ldpc_bp_decode_qam).
+template <int BG, int ALGO, int PREC, int ZC = 0, int CH = kChAny>
 __global__ void __launch_bounds__(kMaxThreads, 2)
     k_layered_edge_sched(const __grid_constant__ Params p, const __grid_constant__ SchedTab tab) {
     using S = Sched<BG>;
@@ -132,7 +134,7 @@ __global__ void __launch_bounds__(kMaxThreads, 2)
 
     load_tables(p, s_vb, s_rp);  // for the syndrome check
     const int64_t cw_base = (int64_t)blockIdx.x * p.G;
-    load_channel(p, s_app_all, cw_base);
+    load_channel_as<CH>(p, s_app_all, cw_base);
     const int g = threadIdx.x / ZV, z = threadIdx.x - g * ZV;
     const int64_t cw = cw_base + g;
     const bool active = g < p.G && cw < p.B;
@@ -177,7 +179,7 @@ __global__ void __launch_bounds__(kMaxThreads, 2)
 
 // Kernel for a code whose row degrees follow the full base graph of shape bg,
 // sum-product with FP32 or FP16 messages, or nullptr.
-SchedFn layered_edge_sched_kernel(int bg, int algo, int prec, int Z);
+SchedFn layered_edge_sched_kernel(int bg, int algo, int prec, int Z, bool qam = false);
 
 }  // namespace dec
 }  // namespace ldpcx

@@ -12,14 +12,14 @@ KernelFn cns_for(int dmax, int Z) {
     return dmax <= 12 ? k_layered_cns<12, PREC, 0> : k_layered_cns<20, PREC, 0>;
 }
 
-SchedFn cns_sched_f32(int bg, int Z, int k, bool trunc);
-SchedFn cns_sched_f16(int bg, int Z, int k, bool trunc);
-SchedFn cns_sched_fix6(int bg, int Z, int k, bool trunc);
+SchedFn cns_sched_f32(int bg, int Z, int k, bool trunc, bool qam);
+SchedFn cns_sched_f16(int bg, int Z, int k, bool trunc, bool qam);
+SchedFn cns_sched_fix6(int bg, int Z, int k, bool trunc, bool qam);
 
-SchedFn layered_cns_sched_kernel(int bg, int prec, int Z, int k, bool trunc) {
-    if (prec == kF32) return cns_sched_f32(bg, Z, k, trunc);
-    if (prec == kF16) return cns_sched_f16(bg, Z, k, trunc);
-    return cns_sched_fix6(bg, Z, k, trunc);
+SchedFn layered_cns_sched_kernel(int bg, int prec, int Z, int k, bool trunc, bool qam) {
+    if (prec == kF32) return cns_sched_f32(bg, Z, k, trunc, qam);
+    if (prec == kF16) return cns_sched_f16(bg, Z, k, trunc, qam);
+    return cns_sched_fix6(bg, Z, k, trunc, qam);
 }
 
 KernelFn layered_cns_kernel(int dmax, int prec, int Z) {
