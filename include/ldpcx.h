@@ -299,11 +299,13 @@ int ldpc_bp_msg_format(ldpcx_code_t code, const ldpcx_decode_opts *opts, int *cn
 /* The sum-product check-node function phi(x) = -ln tanh(x/2) = ln(1 + 2/(e^x
  * - 1)) as the decoders evaluate it, on n device floats x (each in
  * [phi(clamp), clamp] as the decoders use it; x > 0 required). fast = 0: from
- * the CUDA library functions expm1f, IEEE division and log1pf (flooding
- * decoders and the adjoint); fast = 1: from the hardware 2^x, 1/x and log2
- * approximations with Taylor series where a difference would cancel (layered
- * sum-product). Exposed so that tests can bound both against FP64.
- * Asynchronous on stream; LDPCX_E_INVAL for n < 0 or null pointers with n > 0. */
+ * the CUDA library functions expm1f, IEEE division and log1pf; fast = 1: from
+ * the hardware 2^x, 1/x and log2 approximations with Taylor series where a
+ * difference would cancel (flooding sum-product and its adjoint); fast = 2:
+ * the same approximations in bits, phi(x) / ln 2 of x log2 e, times ln 2 here
+ * (layered sum-product, which sums the terms in bits). Exposed so that tests
+ * can bound each against FP64. Asynchronous on stream; LDPCX_E_INVAL for
+ * n < 0, null pointers with n > 0 or fast outside 0..2. */
 int ldpcx_phi(const float *x, float *out, int64_t n, int fast, void *stream);
 
 /* Decode B codewords.

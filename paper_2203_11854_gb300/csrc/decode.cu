@@ -356,13 +356,13 @@ namespace ldpcx {
 namespace {
 __global__ void k_phi(const float *x, float *out, int64_t n, int fast) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        out[i] = fast ? dec::phi_fast(x[i]) : dec::phi(x[i]);
+        out[i] = fast == 2 ? dec::phi_bits(x[i] * dec::kLog2e) * dec::kLn2 : fast ? dec::phi_fast(x[i]) : dec::phi(x[i]);
 }
 }  // namespace
 }  // namespace ldpcx
 
 extern "C" int ldpcx_phi(const float *x, float *out, int64_t n, int fast, void *stream) {
-    if (n < 0 || (n > 0 && (!x || !out))) return LDPCX_E_INVAL;
+    if (n < 0 || (n > 0 && (!x || !out)) || fast < 0 || fast > 2) return LDPCX_E_INVAL;
     if (n == 0) return LDPCX_OK;
     const int64_t blocks = std::min<int64_t>((n + 255) / 256, 4096);
     ldpcx::k_phi<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(x, out, n, fast);

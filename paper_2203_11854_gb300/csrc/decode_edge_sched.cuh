@@ -36,15 +36,15 @@ __device__ __forceinline__ void edge_update(const Params &p, float *app, const i
         if constexpr (kSparse) vi[j] = v;
         T[j] = __fsub_rn(app_at(app, v), old);
     }
-    using CN = typename std::conditional<ALGO == kMinSum, FastMinSum<D>, CheckNode<D, kSpa, true>>::type;
+    using CN = typename std::conditional<ALGO == kMinSum, FastMinSum<D>, SpaNode<D>>::type;
     CN cn;
     if constexpr (ALGO == kMinSum) cn.prepare(T, D, p.offset, p.clamp);
-    else cn.prepare(T, D, p.offset, p.clamp, p.phi_lo);
+    else cn.prepare(T, D, p.clamp, p.phi_lo);
 #pragma unroll
     for (int j = 0; j < D; ++j) {
         float r[1], rq[1];
         if constexpr (ALGO == kMinSum) r[0] = cn.value(T[j]);
-        else r[0] = cn.value(j, p.clamp, p.phi_lo);
+        else r[0] = cn.value(j, T[j], p.clamp, p.phi_lo, p.k_one);
         MsgVec<PREC, 1>::round_store(ml + (size_t)j * p.Z, r, rq, store);
         int v;
         if constexpr (kSparse) v = vi[j];

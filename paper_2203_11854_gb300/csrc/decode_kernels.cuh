@@ -368,41 +368,6 @@ __device__ __forceinline__ int vn_at(uint32_t vb, int z, int Z) {
     return (int)(vb >> 16) + zz;
 }
 
-// Check-node rule on the variable-to-check inputs T[0..deg): prepare() reduces
-// the inputs to the check's state, value(j) then gives the (clamped, not yet
-// rounded) check-to-variable message of edge j.
-template <int DMAX, int ALGO, bool FAST = false> struct CheckNode;
-
-template <int DMAX, bool FAST> struct CheckNode<DMAX, kMinSum, FAST> {
-    float v1, v2;   // offset, floored and clamped smallest / second smallest |T|
-    int idx;        // first index of the smallest |T|
-    unsigned neg;   // bit j: T_j < 0
-    unsigned par;   // parity of the negative inputs
-    __device__ __forceinline__ void prepare(const float (&T)[DMAX], int deg, float offset, float clamp, float) {
-        float m1 = INFINITY, m2 = INFINITY;
-        idx = 0;
-        neg = 0;
-#pragma unroll
-        for (int j = 0; j < DMAX; ++j) {
-            if (j < deg) {
-                const float a = fabsf(T[j]);
-                const bool lt = a < m1;
-                m2 = lt ? m1 : fminf(m2, a);
-                m1 = lt ? a : m1;
-                idx = lt ? j : idx;
-                neg |= (T[j] < 0.0f ? 1u : 0u) << j;
-            }
-        }
-        par = __popc(neg) & 1u;
-        v1 = fminf(fmaxf(__fsub_rn(m1, offset), 0.0f), clamp);
-        v2 = fminf(fmaxf(__fsub_rn(m2, offset), 0.0f), clamp);
-    }
-    __device__ __forceinline__ float value(int j, float, float) const {
-        const float mag = (j == idx) ? v2 : v1;
-        return ((par ^ (neg >> j)) & 1u) ? -mag : mag;
-    }
-};
-
 // min(|a|, |b|) with the sign bit sign(a) XOR sign(b) (inputs are never NaN).
 __device__ __forceinline__ float min_xorsign_abs(float a, float b) {
     float d;
@@ -442,42 +407,73 @@ template <int N> struct FastMinSum {
     }
 };
 
-// Sum-product check node; FAST evaluates phi with phi_fast (layered kernels),
-// otherwise with the library functions (flooding, whose adjoint recomputes it).
-template <int DMAX, bool FAST> struct CheckNode<DMAX, kSpa, FAST> {
-    float f[DMAX];       // phi(|T_j|) with the argument clamped to [phi(clamp), clamp]
-    float s_rest, s_all; // sum without the largest term / with it
-    int jm;              // index of the largest term
-    unsigned neg, par;
-    __device__ __forceinline__ void prepare(const float (&T)[DMAX], int deg, float, float clamp, float phi_lo) {
-        float fmax = -1.0f;
-        jm = 0;
-        neg = 0;
+// phi in bits, g(x) = phi(x) / ln 2 = log2(1 + 2/(e^x - 1)), of an argument also
+// given in bits (xb = x log2 e, so e^x = 2^xb): the approximations and series of
+// phi_fast with the series' coefficients scaled, so that neither an input nor an
+// output of it needs a multiplication by log2 e or ln 2.
+//   e^x - 1 = xb (c1 + xb (c2 + xb (c3 + xb c4))), c_k = (ln 2)^k / k!, x < 1/16
+//   log2(1 + y) = r (d1 + r (d2 + r (d3 + r d4))), y = 2r, r = 1/(e^x - 1) < 1/32
+//             (2r - 2r^2 + 8r^3/3 - 4r^4 over ln 2)
+// The truncation errors are those of phi_fast. Outside [phi(clamp), clamp] the
+// value still lies on the right side of the clamp: e^x - 1 = 0 gives r = inf and
+// g = inf; e^x = inf gives r = 0 and g = 0.
+__device__ __forceinline__ float phi_bits(float xb) {
+    constexpr float c1 = 0.693147180559945309f, c2 = 0.240226506959100712f, c3 = 0.0555041086648215800f,
+                    c4 = 0.00961812910762847717f;
+    constexpr float d1 = 2.88539008177792681f, d2 = -2.88539008177792681f, d3 = 3.84718677570390241f,
+                    d4 = -5.77078016355585362f;
+    const float em1 = xb < 0.0625f * kLog2e ? xb * (c1 + xb * (c2 + xb * (c3 + xb * c4))) : hw_exp2(xb) - 1.0f;
+    const float r = hw_rcp(em1);
+    return r < 0.03125f ? r * (d1 + r * (d2 + r * (d3 + r * d4))) : hw_log2(fmaf(2.0f, r, 1.0f));
+}
+
+// Layered sum-product check node on the variable-to-check inputs T[0..deg):
+// R_j = s_j phi(sum_{i != j} phi(|T_i|)), every phi argument in [phi(clamp),
+// clamp] (sum-product reading of the clamps), s_j the product of the other
+// inputs' signs.
+//  * The terms g_i = phi(|T_i|) are kept in bits; the exclusive sum of edge j is
+//    s_rest + (g_max - g_j), where s_rest sums every term but the largest one
+//    (each term is added as min(term, largest so far), the largest so far kept
+//    apart): no term is ever subtracted from a sum that holds it, so nothing
+//    cancels (g_max - g_j is exact for g_j >= g_max / 2, and at least g_max / 2
+//    otherwise).
+//  * Clamping the outer argument to [phi(clamp), clamp] equals clamping the
+//    result to the same interval (phi is decreasing and its own inverse), so the
+//    result is clamped instead; the inner arguments keep their clamp, which also
+//    keeps every term finite.
+//  * The layered T is never -0.0 (the channel load maps -0.0 to +0.0; x - x and
+//    x + (-0.0) give +0.0 for x = +0.0), so the sign of T_j is its sign bit, the
+//    sign product an XOR of sign bits, and s_j the sign bit of bits(T_j) + that
+//    XOR (an addition flips bit 31 or not), formed by a multiply-add.
+template <int N> struct SpaNode {
+    float g[N];          // phi(|T_j|) in bits
+    float s_rest, g_max; // sum of the terms without the largest one; the largest one
+    unsigned sxs;        // XOR of the sign bits of T (bit 31)
+    __device__ __forceinline__ void prepare(const float (&T)[N], int deg, float clamp, float phi_lo) {
+        unsigned sx = 0;
+        s_rest = 0.0f;
+        g_max = 0.0f;
 #pragma unroll
-        for (int j = 0; j < DMAX; ++j) {
+        for (int j = 0; j < N; ++j) {
             if (j < deg) {
-                const float a = fminf(fmaxf(fabsf(T[j]), phi_lo), clamp);
-                f[j] = phi_t<FAST>(a);
-                const bool gt = f[j] > fmax;
-                fmax = gt ? f[j] : fmax;
-                jm = gt ? j : jm;
-                neg |= (T[j] < 0.0f ? 1u : 0u) << j;
+                g[j] = phi_bits(fminf(fmaxf(fabsf(T[j]), phi_lo), clamp) * kLog2e);
+                if (j == 0) {
+                    g_max = g[0];
+                } else {
+                    s_rest = __fadd_rn(s_rest, fminf(g[j], g_max));
+                    g_max = fmaxf(g_max, g[j]);
+                }
+                sx ^= __float_as_uint(T[j]);
             }
         }
-        par = __popc(neg) & 1u;
-        // Exclusive sums without cancellation: the largest term is left out of
-        // the running sum, so s_all - f_j (f_j <= largest) loses at most a bit.
-        s_rest = 0.0f;
-#pragma unroll
-        for (int j = 0; j < DMAX; ++j)
-            if (j < deg && j != jm) s_rest = __fadd_rn(s_rest, f[j]);
-        s_all = __fadd_rn(s_rest, fmax);
+        sxs = sx & 0x80000000u;
     }
-    __device__ __forceinline__ float value(int j, float clamp, float phi_lo) const {
-        float x = (j == jm) ? s_rest : __fsub_rn(s_all, f[j]);
-        x = fminf(fmaxf(x, phi_lo), clamp);
-        const float mag = fminf(phi_t<FAST>(x), clamp);
-        return ((par ^ (neg >> j)) & 1u) ? -mag : mag;
+    // message of edge j (input T_j), clamped, not yet rounded to the message format
+    __device__ __forceinline__ float value(int j, float Tj, float clamp, float phi_lo, unsigned one) const {
+        const float x = __fadd_rn(s_rest, __fsub_rn(g_max, g[j]));
+        const float mag = fminf(fmaxf(phi_bits(x) * kLn2, phi_lo), clamp);
+        const unsigned U = __float_as_uint(Tj) * one + sxs;
+        return __uint_as_float((U & 0x80000000u) | __float_as_uint(mag));
     }
 };
 
@@ -683,12 +679,12 @@ __device__ __forceinline__ void layer_update(const Params &p, int deg, float *ap
             for (int k = 0; k < ZPT; ++k) T[k][j] = 0.0f;
         }
     }
-    using CN = typename std::conditional<ALGO == kMinSum, FastMinSum<N>, CheckNode<N, kSpa, true>>::type;
+    using CN = typename std::conditional<ALGO == kMinSum, FastMinSum<N>, SpaNode<N>>::type;
     CN cn[ZPT];
 #pragma unroll
     for (int k = 0; k < ZPT; ++k) {
         if constexpr (ALGO == kMinSum) cn[k].prepare(T[k], D ? D : deg, p.offset, p.clamp);
-        else cn[k].prepare(T[k], D ? D : deg, p.offset, p.clamp, p.phi_lo);
+        else cn[k].prepare(T[k], D ? D : deg, p.clamp, p.phi_lo);
     }
 #pragma unroll
     for (int j = 0; j < N; ++j) {
@@ -697,7 +693,7 @@ __device__ __forceinline__ void layer_update(const Params &p, int deg, float *ap
 #pragma unroll
             for (int k = 0; k < ZPT; ++k) {
                 if constexpr (ALGO == kMinSum) r[k] = cn[k].value(T[k][j]);
-                else r[k] = cn[k].value(j, p.clamp, p.phi_lo);
+                else r[k] = cn[k].value(j, T[k][j], p.clamp, p.phi_lo, p.k_one);
             }
             MsgVec<PREC, ZPT>::round_store(ml + (size_t)j * ZV, r, rq, store);
             int v[ZPT];

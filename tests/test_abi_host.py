@@ -118,6 +118,10 @@ def test_argument_validation(lx):
     assert L.sim_tx(ucode.handle, 1, 0, 4, 2, 16, 0, 16, 16, None) == -2
     assert L.sim_codewords(ucode.handle, 1, 0, 4, 16, None) == -2
     assert lx.ldpcx_status_str(-4).startswith("LDPCX_E_WORKSPACE")
+    # phi: the form is one of the three, checked before any launch
+    for fast in (-1, 3):
+        assert L.ldpcx_phi(16, 16, 4, fast, None) == -1, fast
+    assert L.ldpcx_phi(None, None, 0, 2, None) == 0
 
 
 @pytest.mark.skipif(os.environ.get("CUDA_VISIBLE_DEVICES") is None and __import__("torch").cuda.is_available(),
