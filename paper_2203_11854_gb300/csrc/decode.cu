@@ -30,7 +30,7 @@ int64_t cns_bytes(const ldpcx_code *c, int prec) {
 }
 
 KernelFn pick_kernel(int max_deg, bool layered, int algo, int prec, int zpt, int Z, bool qam) {
-    if (!layered) return flooding_kernel(max_deg, algo, prec, flood_tpc(Z));
+    if (!layered) return flooding_kernel(max_deg, algo, prec);
     if (zpt == 1 && g_specialised.load()) {
         KernelFn f = prec == kF32 ? layered_kernel_zc_f32(max_deg, algo, Z, qam)
                    : prec == kF16 ? layered_kernel_zc_f16(max_deg, algo, Z, qam)
@@ -69,13 +69,13 @@ std::atomic<int> g_zpt{0};
 std::atomic<int> g_cw_per_cta{0};  // 0 = automatic
 
 // Codewords per CTA: enough check-node threads to fill ~384 threads (layered)
-// or up to 512 threads of TPC per check node (flooding), bounded by the shared
-// memory that keeps two CTAs per SM (layered; flooding with TPC > 1) or one.
+// or up to 16 codewords (flooding, whose threads loop over the CTA's check and
+// variable nodes), bounded by the shared memory that keeps two CTAs per SM
+// (layered; flooding where two fit) or one.
 int pick_G(const ldpcx_code *c, bool layered, int64_t B) {
     const size_t per_cw = sizeof(float) * (size_t)c->n * (layered ? 1 : 2);
-    const int tpc = layered ? 1 : flood_tpc(c->Z);
-    const size_t budget = layered || tpc > 1 ? 105 * 1024 : 210 * 1024;
-    int G = layered ? kMaxThreads / c->Z : 512 / (c->Z * tpc);
+    const size_t budget = layered || per_cw <= 105 * 1024 ? 105 * 1024 : 210 * 1024;
+    int G = layered ? kMaxThreads / c->Z : 16;
     if (G < 1) G = 1;
     while (G > 1 && per_cw * G > budget) --G;
     const int want = g_cw_per_cta.load();
@@ -290,12 +290,11 @@ dec::Params dec::decode_params(const ldpcx_code *c, const uint32_t *blk, const i
 
 int dec::decode_launch(const DecodePlan &pl, const ldpcx_code *c, const Params &p, int64_t B, void *stream) {
     if (pl.sf) return launch_sched(pl.sf, c, p, B, pl.kpt, stream);
-    const size_t smem = pl.cns ? cns_smem_bytes(p) : smem_bytes(p, pl.layered ? 1 : 2);
+    const size_t smem = pl.cns ? cns_smem_bytes(p) : pl.layered ? smem_bytes(p, 1) : flood_smem_bytes(p);
     if (smem > 227 * 1024) return LDPCX_E_UNSUPPORTED;
     if (cudaFuncSetAttribute(pl.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return LDPCX_E_CUDA;
-    int threads = pl.layered ? p.G * (p.Z / pl.zpt) : p.G * p.Z * flood_tpc(p.Z);
-    threads = (threads + 31) / 32 * 32;
+    int threads = pl.layered ? (p.G * (p.Z / pl.zpt) + 31) / 32 * 32 : flood_threads(p.G, p.n);
     const int64_t grid = (B + p.G - 1) / p.G;
     if (grid > 0x7FFFFFFF) return LDPCX_E_INVAL;
     pl.fn<<<(unsigned)grid, threads, smem, (cudaStream_t)stream>>>(p);

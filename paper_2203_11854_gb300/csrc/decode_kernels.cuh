@@ -468,12 +468,16 @@ template <int N> struct SpaNode {
         }
         sxs = sx & 0x80000000u;
     }
+    // magnitude of the message of edge j, clamped
+    __device__ __forceinline__ float mag(int j, float clamp, float phi_lo) const {
+        const float x = __fadd_rn(s_rest, __fsub_rn(g_max, g[j]));
+        return fminf(fmaxf(phi_bits(x) * kLn2, phi_lo), clamp);
+    }
     // message of edge j (input T_j), clamped, not yet rounded to the message format
     __device__ __forceinline__ float value(int j, float Tj, float clamp, float phi_lo, unsigned one) const {
-        const float x = __fadd_rn(s_rest, __fsub_rn(g_max, g[j]));
-        const float mag = fminf(fmaxf(phi_bits(x) * kLn2, phi_lo), clamp);
+        const float m = mag(j, clamp, phi_lo);
         const unsigned U = __float_as_uint(Tj) * one + sxs;
-        return __uint_as_float((U & 0x80000000u) | __float_as_uint(mag));
+        return __uint_as_float((U & 0x80000000u) | __float_as_uint(m));
     }
 };
 
@@ -870,10 +874,20 @@ KernelFn layered_ch(bool qam) {
 KernelFn layered_kernel_f32(int dmax, int algo, int zpt, bool qam = false);
 KernelFn layered_kernel_f16(int dmax, int algo, int zpt, bool qam = false);
 KernelFn layered_kernel_fix6(int dmax, int algo, int zpt, bool qam = false);
-KernelFn flooding_kernel(int dmax, int algo, int prec, int tpc);
-// Threads per check node of the flooding kernels: as many as keep a CTA of one
-// codeword within 512 threads.
-inline int flood_tpc(int Z) { return Z <= 128 ? 4 : Z <= 256 ? 2 : 1; }
+KernelFn flooding_kernel(int dmax, int algo, int prec);
+// Shared memory of the flooding kernel: two APP arrays per codeword, the block
+// table by rows and by columns with their row and column pointers, and three
+// words per codeword.
+__host__ __device__ inline size_t flood_smem_bytes(const Params &p) {
+    return sizeof(float) * 2 * (size_t)p.G * p.n + sizeof(uint32_t) * 2 * (size_t)p.nnz +
+           sizeof(int32_t) * (size_t)(p.rows + 1 + p.n / p.Z + 1) + 3 * sizeof(int) * (size_t)p.G;
+}
+// Threads per CTA of the flooding kernel: about one per variable node of its
+// codewords, a multiple of 32 within 64..512.
+inline int flood_threads(int G, int n) {
+    const int64_t t = ((int64_t)G * n + 31) / 32 * 32;
+    return t < 64 ? 64 : t > 512 ? 512 : (int)t;
+}
 // Layered min-sum kernels specialised for a compile-time lifting size (nullptr
 // when none is built for Z): the hot loop's addresses become immediates.
 KernelFn layered_kernel_zc_f32(int dmax, int algo, int Z, bool qam = false);

@@ -94,7 +94,7 @@ def test_layered_minsum_bit_exact(lx, orc, name, prec, early_stop):
         assert oits.min() < 8  # some codewords stop early: the path is exercised
 
 
-# flooding runs four threads per check node up to Z = 128, two up to 256, one above
+# flooding: Z = 8 (a warp spans four rows), 64, a truncated Z = 128 code, 200 and 384
 @pytest.mark.parametrize("name", ["bg2_z8", "bg2_z64", "bg1_z128_r13", "bg2_z200", "bg1_z384"])
 @pytest.mark.parametrize("prec", [0, 1, 2])
 @pytest.mark.parametrize("weighted", [False, True])
