@@ -4,6 +4,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <climits>
 #include <atomic>
 
 #include "decode_plan.cuh"
@@ -68,19 +69,47 @@ std::atomic<int> g_pf_dist{0};
 std::atomic<int> g_zpt{0};
 std::atomic<int> g_cw_per_cta{0};  // 0 = automatic
 
+// Flooding: the codewords per CTA, up to gmax, with the fewest waves of CTAs
+// times codewords per CTA (a CTA's time grows with its codewords, its waves
+// run one after another), ties to the larger G (more independent nodes per
+// thread). CTAs per SM from the threads (64 registers each) and the shared
+// memory of one CTA.
+int pick_G_flood(const ldpcx_code *c, int64_t B, int gmax) {
+    const size_t per_cw = 2 * sizeof(float) * (size_t)c->n;
+    const size_t tables = 2 * sizeof(uint32_t) * c->nnz + sizeof(int32_t) * (c->rows + c->n / c->Z + 2) + 64;
+    int best = 1;
+    int64_t best_cost = INT64_MAX;
+    for (int g = 1; g <= gmax; ++g) {
+        const int threads = flood_threads(g, c->n);
+        int per_sm = std::min(65536 / (threads * 64), 2048 / threads);
+        per_sm = std::min<int>(per_sm, (int)((227 * 1024) / (per_cw * g + tables + 1024)));
+        if (per_sm < 1) per_sm = 1;
+        const int64_t slots = (int64_t)per_sm * sm_count();
+        const int64_t ctas = (B + g - 1) / g;
+        const int64_t cost = (ctas + slots - 1) / slots * g;
+        if (cost <= best_cost) {
+            best_cost = cost;
+            best = g;
+        }
+    }
+    return best;
+}
+
 // Codewords per CTA: enough check-node threads to fill ~384 threads (layered)
-// or up to 16 codewords (flooding, whose threads loop over the CTA's check and
+// or up to 32 codewords (flooding, whose threads loop over the CTA's check and
 // variable nodes), bounded by the shared memory that keeps two CTAs per SM
 // (layered; flooding where two fit) or one.
 int pick_G(const ldpcx_code *c, bool layered, int64_t B) {
     const size_t per_cw = sizeof(float) * (size_t)c->n * (layered ? 1 : 2);
     const size_t budget = layered || per_cw <= 105 * 1024 ? 105 * 1024 : 210 * 1024;
-    int G = layered ? kMaxThreads / c->Z : 16;
+    int G = layered ? kMaxThreads / c->Z : 32;
     if (G < 1) G = 1;
     while (G > 1 && per_cw * G > budget) --G;
     const int want = g_cw_per_cta.load();
     if (want > 0) {
         if (want < G) G = want;  // autotuner: smaller tiles, more CTAs per SM
+    } else if (!layered) {
+        G = pick_G_flood(c, B, G);
     } else {
         // a small batch: fewer codewords per CTA, so that its CTAs (each a serial chain of row steps) spread
         // over about four per SM instead of crowding a few

@@ -13,32 +13,11 @@
 // accumulation bit for bit, with two block barriers per iteration instead of
 // one per row. The messages of the last iteration are stored too (phase 2
 // reads them).
+#include "decode_cols.cuh"
 #include "decode_kernels.cuh"
 
 namespace ldpcx {
 namespace dec {
-
-// Work items of a strided loop over a grid of rows x Z (check nodes) or
-// columns x Z (variable nodes): the item's row or column and its z, advanced
-// by the CTA's thread count without a division per item.
-struct ZWalk {
-    int q, z;    // row or column, and z, of the current item
-    int dq, dz;  // the stride in rows (columns) and in z
-    __device__ __forceinline__ ZWalk(int Z) {
-        q = threadIdx.x / Z;
-        z = threadIdx.x - q * Z;
-        dq = blockDim.x / Z;
-        dz = blockDim.x - dq * Z;
-    }
-    __device__ __forceinline__ void next(int Z) {
-        z += dz;
-        q += dq;
-        if (z >= Z) {
-            z -= Z;
-            ++q;
-        }
-    }
-};
 
 // Check node z of row r (blocks b0 .. b0 + deg) of one codeword: the flooding
 // update from the previous APP `app`, messages of the codeword at ml (edge b
@@ -103,7 +82,9 @@ __device__ __forceinline__ void flood_check(const Params &p, const float *app, c
     }
 }
 
-// Flooding BP, G codewords per CTA (flood_threads threads).
+// Flooding BP, G codewords per CTA (flood_threads threads); each phase is one
+// strided loop over the items of all G codewords, so that small codes fill the
+// CTA.
 template <int DMAX, int ALGO, int PREC>
 __global__ void __launch_bounds__(512, 2) k_flooding(const __grid_constant__ Params p) {
     using MT = typename MsgT<PREC>::T;
@@ -120,24 +101,7 @@ __global__ void __launch_bounds__(512, 2) k_flooding(const __grid_constant__ Par
     int *s_iters = s_done + p.G;
 
     load_tables(p, s_vb, s_rp);
-    // the column lists: thread c collects the blocks of column c in block order (once per CTA)
-    for (int c = threadIdx.x; c < cols; c += blockDim.x) {
-        int cnt = 0;
-        for (int b = 0; b < p.nnz; ++b) cnt += (int)(p.blk[b] >> 16) == c ? 1 : 0;
-        s_cp[c + 1] = cnt;
-    }
-    if (threadIdx.x == 0) s_cp[0] = 0;
-    __syncthreads();
-    if (threadIdx.x == 0)
-        for (int c = 0; c < cols; ++c) s_cp[c + 1] += s_cp[c];
-    __syncthreads();
-    for (int c = threadIdx.x; c < cols; c += blockDim.x) {
-        int e = s_cp[c];
-        for (int b = 0; b < p.nnz; ++b) {
-            const uint32_t bk = p.blk[b];
-            if ((int)(bk >> 16) == c) s_cb[e++] = (uint32_t)b << 16 | (bk & 0xFFFFu);
-        }
-    }
+    build_col_lists(p.blk, p.nnz, cols, s_cp, s_cb);
     const int64_t cw_base = (int64_t)blockIdx.x * p.G;
     for (int i = threadIdx.x; i < p.G; i += blockDim.x) {
         s_done[i] = (cw_base + i >= p.B) ? 1 : 0;
@@ -150,44 +114,53 @@ __global__ void __launch_bounds__(512, 2) k_flooding(const __grid_constant__ Par
         __syncthreads();
         const float *w_t = p.weights ? p.weights + (size_t)t * p.nnz : nullptr;
         const bool ckpt = p.ckpt && t + 1 < p.iters;
-        // phase 1: every check node of the codewords still decoding
-        for (int gg = 0; gg < p.G; ++gg) {
-            if (s_done[gg]) continue;
-            const int64_t cw = cw_base + gg;
-            const float *app = cur + (size_t)gg * p.n;
-            MT *mp = reinterpret_cast<MT *>(p.msg) + cw * p.msg_stride;
-            float *ck = ckpt ? p.ckpt + (size_t)t * p.ckpt_tstride + (size_t)cw * p.msg_stride : nullptr;
-            ZWalk it(p.Z);
-            for (; it.q < p.rows; it.next(p.Z)) {
-                const int b0 = s_rp[it.q], deg = s_rp[it.q + 1] - b0;
-                flood_check<DMAX, ALGO, PREC>(p, app, s_vb + b0, deg, it.z, mp + (size_t)b0 * p.Z + it.z,
-                                              w_t ? w_t + b0 : nullptr, t > 0,
-                                              ck ? ck + (size_t)b0 * p.Z + it.z : nullptr);
+        // phase 1: every check node of the codewords still decoding, items (codeword, row, z) with z fastest
+        {
+            GZWalk it(p.Z, p.rows);
+            for (; it.g < p.G; it.next(p.Z, p.rows)) {
+                const int gg = it.g, r = it.q;
+                if (s_done[gg]) continue;
+                const int64_t cw = cw_base + gg;
+                const int b0 = s_rp[r], deg = s_rp[r + 1] - b0;
+                const size_t e0 = (size_t)b0 * p.Z + it.z;
+                MT *mp = reinterpret_cast<MT *>(p.msg) + cw * p.msg_stride;
+                float *ck = ckpt ? p.ckpt + (size_t)t * p.ckpt_tstride + (size_t)cw * p.msg_stride + e0 : nullptr;
+                flood_check<DMAX, ALGO, PREC>(p, cur + (size_t)gg * p.n, s_vb + b0, deg, it.z, mp + e0,
+                                              w_t ? w_t + b0 : nullptr, t > 0, ck);
             }
         }
         __syncthreads();
-        // phase 2: every variable node; a stopped codeword carries its APP forward unchanged
-        for (int gg = 0; gg < p.G; ++gg) {
-            const int64_t cw = cw_base + gg;
-            if (cw >= p.B) break;
-            const bool keep = s_done[gg] != 0;
-            const MT *mp = reinterpret_cast<const MT *>(p.msg) + cw * p.msg_stride;
-            const float *a0 = cur + (size_t)gg * p.n;
-            float *a1 = nxt + (size_t)gg * p.n;
-            ZWalk it(p.Z);
-            for (; it.q < cols; it.next(p.Z)) {
-                const int v = it.q * p.Z + it.z;
-                if (keep) {
-                    a1[v] = a0[v];
+        // phase 2: every variable node, items (codeword, column, z); a stopped codeword carries its APP forward
+        {
+            GZWalk it(p.Z, cols);
+            for (; it.g < p.G; it.next(p.Z, cols)) {
+                const int gg = it.g, c = it.q;
+                const int64_t cw = cw_base + gg;
+                if (cw >= p.B) continue;
+                const int v = c * p.Z + it.z;
+                float *a1 = nxt + (size_t)gg * p.n;
+                if (s_done[gg]) {
+                    a1[v] = cur[(size_t)gg * p.n + v];
                     continue;
                 }
+                const MT *mp = reinterpret_cast<const MT *>(p.msg) + cw * p.msg_stride;
                 bool bad = false;
                 float a = channel_llr(p, cw, v, bad);
-                for (int e = s_cp[it.q]; e < s_cp[it.q + 1]; ++e) {
-                    const uint32_t cb = s_cb[e];
-                    int zc = it.z - (int)(cb & 0xFFFFu);
-                    zc += zc < 0 ? p.Z : 0;
-                    a = __fadd_rn(a, msg_load<PREC>(mp + (size_t)(cb >> 16) * p.Z + zc));
+                // four loads in flight, then their sums in order
+                const int e1 = s_cp[c + 1];
+                for (int e = s_cp[c]; e < e1; e += 4) {
+                    float m[4];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        m[i] = 0.0f;
+                        if (e + i < e1) {
+                            const uint32_t cb = s_cb[e + i];
+                            m[i] = msg_load<PREC>(mp + (size_t)(cb >> 16) * p.Z + col_check_z(cb, it.z, p.Z));
+                        }
+                    }
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+                        if (e + i < e1) a = __fadd_rn(a, m[i]);
                 }
                 a1[v] = a;
             }
@@ -218,18 +191,16 @@ __global__ void __launch_bounds__(512, 2) k_flooding(const __grid_constant__ Par
         if (p.early_stop) {
             for (int gg = threadIdx.x; gg < p.G; gg += blockDim.x) s_flag[gg] = 0;
             __syncthreads();
-            for (int gg = 0; gg < p.G; ++gg) {
-                if (s_done[gg]) continue;
-                const float *a = cur + (size_t)gg * p.n;
-                bool bad = false;
-                ZWalk it(p.Z);
-                for (; it.q < p.rows; it.next(p.Z)) {
+            {
+                GZWalk it(p.Z, p.rows);
+                for (; it.g < p.G; it.next(p.Z, p.rows)) {
+                    const int gg = it.g, r = it.q;
+                    if (s_done[gg]) continue;
+                    const float *a = cur + (size_t)gg * p.n;
                     unsigned pr = 0;
-                    for (int b = s_rp[it.q]; b < s_rp[it.q + 1]; ++b)
-                        pr ^= a[vn_at(s_vb[b], it.z, p.Z)] < 0.0f ? 1u : 0u;
-                    bad |= pr != 0;
+                    for (int b = s_rp[r]; b < s_rp[r + 1]; ++b) pr ^= a[vn_at(s_vb[b], it.z, p.Z)] < 0.0f ? 1u : 0u;
+                    if (pr) s_flag[gg] = 1;
                 }
-                if (bad) s_flag[gg] = 1;
             }
             __syncthreads();
             bool all = true;
