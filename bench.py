@@ -689,6 +689,7 @@ def measure_mixed(lx, stream, args, pk):
     counts = torch.zeros(5, dtype=torch.int64, device="cuda")
     res = persistent()
     alg_bytes = 0.0
+    edge_updates = 0
     for (c, l), info, (_, b_, it) in zip(groups, infos, res):
         lx.sim_count(info, b_, it, c.k, counts)
         _, msg_cw = lx.ldpc_bp_msg_format(c, **{k: dec[k] for k in ("algo", "iters", "msg_prec")})
@@ -696,6 +697,7 @@ def measure_mixed(lx, stream, args, pk):
         reads = (its - 1).clamp(min=0).sum().item()
         writes = torch.where(its < dec["iters"], its, its - 1).sum().item()
         alg_bytes += msg_cw * (reads + writes) + l.shape[0] * (4 * c.n_tx + c.k / 8)
+        edge_updates += c.edges * its.sum().item()
     lx.ldpcx_tune_set(lx.TUNE_CW_PER_CTA, 0)
     try:
         os.remove(cache)
@@ -710,9 +712,18 @@ def measure_mixed(lx, stream, args, pk):
     out["autotune"] = {"knob": "codewords per work item (LDPCX_TUNE_CW_PER_CTA; 0 = automatic)",
                        "best": tuned["best"], "timings": tuned["timings"]}
     achieved = alg_bytes / (out["persistent"]["ms"] * 1e-3) / 1e9
+    out["edge_updates_per_s"] = edge_updates / (out["persistent"]["ms"] * 1e-3)
     out["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
                        "frac": achieved / pk["hbm_gbs"], "algorithmic_bytes_per_launch": alg_bytes,
                        "note": "each codeword's own message format (check-node state) for the iterations it ran"}
+    # the ceiling that binds: instruction issue, SM issue per active cycle of the launch (ncu, same sources) over
+    # the four schedulers of an SM
+    for sec in profile_sections("decode_mixed_minsum_f16_8192cw.md"):
+        if sec.get("current"):
+            try:
+                out["roofline"]["issue_frac"] = float(sec["SM issue (sm__inst_executed per active cycle)"].split()[0]) / 4
+            except (KeyError, ValueError):
+                pass
     return out
 
 

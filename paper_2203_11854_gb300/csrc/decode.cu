@@ -4,7 +4,6 @@
 #include <math.h>
 
 #include <algorithm>
-#include <climits>
 #include <atomic>
 
 #include "decode_plan.cuh"
@@ -69,25 +68,28 @@ std::atomic<int> g_pf_dist{0};
 std::atomic<int> g_zpt{0};
 std::atomic<int> g_cw_per_cta{0};  // 0 = automatic
 
-// Flooding: the codewords per CTA, up to gmax, with the fewest waves of CTAs
-// times codewords per CTA (a CTA's time grows with its codewords, its waves
-// run one after another), ties to the larger G (more independent nodes per
-// thread). CTAs per SM from the threads (64 registers each) and the shared
-// memory of one CTA.
+// Flooding: the codewords per CTA, up to gmax, by a cost that follows the
+// GB300 timings of Z = 8 and Z = 64 batches: the most codewords one SM decodes,
+// ceil(CTAs / SMs) G (and at least its resident CTAs' G each, when the batch
+// leaves an SM part empty), scaled up where a thread would have fewer than two
+// check nodes per phase (latency left exposed); ties to the larger G. CTAs per
+// SM from the threads (64 registers each) and the shared memory of one CTA.
 int pick_G_flood(const ldpcx_code *c, int64_t B, int gmax) {
     const size_t per_cw = 2 * sizeof(float) * (size_t)c->n;
     const size_t tables = 2 * sizeof(uint32_t) * c->nnz + sizeof(int32_t) * (c->rows + c->n / c->Z + 2) + 64;
+    const int64_t sms = sm_count();
     int best = 1;
-    int64_t best_cost = INT64_MAX;
+    double best_cost = 1e300;
     for (int g = 1; g <= gmax; ++g) {
         const int threads = flood_threads(g, c->n);
         int per_sm = std::min(65536 / (threads * 64), 2048 / threads);
         per_sm = std::min<int>(per_sm, (int)((227 * 1024) / (per_cw * g + tables + 1024)));
         if (per_sm < 1) per_sm = 1;
-        const int64_t slots = (int64_t)per_sm * sm_count();
         const int64_t ctas = (B + g - 1) / g;
-        const int64_t cost = (ctas + slots - 1) / slots * g;
-        if (cost <= best_cost) {
+        const int64_t on_sm = std::max<int64_t>((ctas + sms - 1) / sms, per_sm);
+        const double nodes_per_thread = (double)g * c->rows * c->Z / threads;
+        const double cost = (double)(on_sm * g) * std::max(1.0, 2.0 / nodes_per_thread);
+        if (cost <= best_cost * (1.0 + 1e-9)) {
             best_cost = cost;
             best = g;
         }
