@@ -177,6 +177,42 @@ def test_spa_weighted_flooding_within_tolerance(lx, orc, prec):
     assert spa_close(g, app).all(), spa_report(g, app)
 
 
+@pytest.mark.parametrize("name", ["bg2_z8", "bg2_z16_r4", "bg2_z64"])
+@pytest.mark.parametrize("algo", ["minsum", "spa"])
+def test_flooding_codewords_per_cta_agree(lx, orc, name, algo):
+    """Flooding with 1, 2, 3, 5 and 8 codewords per CTA (a CTA's threads walk the nodes of all its codewords,
+    across codeword boundaries within a warp at small Z) and the automatic choice: identical outputs, with
+    early stop (codewords stop in different iterations within one CTA) and weights; min-sum also equals
+    the oracle's FP32 replay."""
+    bg, Z, rows_kept, punct, _ = CODES[name]
+    ocode = orc.Code(bg, Z, rows_kept=rows_kept, punct_cols=punct)
+    B = 61  # ragged against every tile size
+    u = inputs.info_bits(41, B, ocode.k)
+    L = inputs.gaussian_llrs(ocode.encoder.encode(u), STRONG.get(name, 2.2), 42)
+    L_tx = np.ascontiguousarray(L[:, ocode.p0:ocode.p0 + ocode.n_tx])
+    code = gpu_code(lx, name)
+    w = (0.6 + 0.8 * inputs.rng(43).random((8, code.nnz))).astype(np.float32)
+    a = lx.FLOOD_MINSUM if algo == "minsum" else lx.FLOOD_SPA
+    outs = []
+    try:
+        for G in (1, 2, 3, 5, 8, 0):
+            lx.ldpcx_tune_set(lx.TUNE_CW_PER_CTA, G)
+            llr, bits, its = lx.ldpc_bp_decode(code, cuda(L_tx), algo=a, iters=8, msg_prec=1, early_stop=True,
+                                               llr_out=True, weights=cuda(w))
+            outs.append((llr.cpu().numpy(), bits.cpu().numpy(), its.cpu().numpy()))
+    finally:
+        lx.ldpcx_tune_set(lx.TUNE_CW_PER_CTA, 0)
+    for o in outs[1:]:
+        assert np.array_equal(o[0], outs[0][0]) and np.array_equal(o[1], outs[0][1])
+        assert np.array_equal(o[2], outs[0][2])
+    assert len(np.unique(outs[0][2])) > 1  # codewords of one CTA stop in different iterations
+    if algo == "minsum":
+        app, hard, oits = orc.decode(ocode.graph, orc.place_llr(L_tx, ocode.p0, ocode.n), algo=0, schedule=1, iters=8,
+                                     prec=1, store=1, early_stop=True, weights=w.astype(np.float64))
+        assert np.array_equal(outs[0][0], app.astype(np.float32))
+        assert np.array_equal(outs[0][2], oits)
+
+
 def test_tx_noiseless_symbols_and_bits(lx, orc):
     for name, m in [("bg1_z384", 4), ("bg2_z8", 2), ("bg1_z384", 8), ("bg2_z64", 1), ("bg1_z128_r13", 6)]:
         bg, Z, rows_kept, punct, B = CODES[name]
