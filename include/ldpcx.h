@@ -301,10 +301,10 @@ int ldpc_bp_msg_format(ldpcx_code_t code, const ldpcx_decode_opts *opts, int *cn
  * [phi(clamp), clamp] as the decoders use it; x > 0 required). fast = 0: from
  * the CUDA library functions expm1f, IEEE division and log1pf; fast = 1: from
  * the hardware 2^x, 1/x and log2 approximations with Taylor series where a
- * difference would cancel (flooding sum-product and its adjoint); fast = 2:
- * the same approximations in bits, phi(x) / ln 2 of x log2 e, times ln 2 here
- * (layered sum-product, which sums the terms in bits). Exposed so that tests
- * can bound each against FP64. Asynchronous on stream; LDPCX_E_INVAL for
+ * difference would cancel (the adjoint of flooding sum-product); fast = 2:
+ * the same approximations in bits, phi(x) / ln 2 of x log2 e, times ln 2
+ * here (layered and flooding sum-product, which sum the terms in bits).
+ * Exposed so that tests can bound each against FP64. Asynchronous on stream; LDPCX_E_INVAL for
  * n < 0, null pointers with n > 0 or fast outside 0..2. */
 int ldpcx_phi(const float *x, float *out, int64_t n, int fast, void *stream);
 
@@ -348,9 +348,11 @@ int ldpc_bp_decode_qam(ldpcx_code_t code, const float *y, const float *no, int64
  * a compiled-in schedule (LDPCX_TUNE_SCHEDULE): 0 = auto = 1; 2 = check nodes
  * z and z + Z/2, honoured when Z is even. Other kernels use one.
  * LDPCX_TUNE_CW_PER_CTA: codewords decoded together by one CTA of
- * ldpc_bp_decode (0 = automatic: about 384 check nodes per CTA within the
- * shared-memory budget, fewer when the batch would give the SMs fewer than
- * about four CTAs each; a smaller value gives smaller CTAs, more per SM), and
+ * ldpc_bp_decode (0 = automatic: layered, about 384 check nodes per CTA
+ * within the shared-memory budget, fewer when the batch would give the SMs
+ * fewer than about four CTAs each; flooding, up to 32 codewords by the fewest
+ * codewords per SM, raised where a thread would have fewer than two check
+ * nodes; a smaller value gives smaller CTAs, more per SM), and
  * the cap on the codewords of one work item of ldpc_bp_decode_mixed (smaller
  * items: a finer queue, less waiting on a tile's slowest codeword).
  * LDPCX_TUNE_SPECIALISED: 1 (default) = use the layered min-sum kernels built

@@ -583,7 +583,8 @@ def ldpc_bp_msg_format(code: Code, *, algo: int = LAYERED_MINSUM, iters: int = 2
 
 def ldpcx_phi(x, *, fast: int = 0, out=None, stream=None):
     """phi(x) = ln(1 + 2/(e^x - 1)) as the decoders evaluate it (x: CUDA float32); fast = 0 library
-    functions, 1 (or True) the hardware approximations, 2 the same in bits (layered sum-product)."""
+    functions, 1 (or True) the hardware approximations (the adjoint), 2 the same in bits (the layered and
+    flooding check node)."""
     import torch
     assert x.is_cuda and x.dtype == torch.float32 and x.is_contiguous()
     out = torch.empty_like(x) if out is None else out

@@ -1,8 +1,8 @@
 """The decoders' phi(x) = ln(1 + 2/(e^x - 1)) against FP64 over the range the
 sum-product decoders use, [phi(20), 20]: the library-function form within a few
 binary32 ulps, the fast forms (hardware approximations plus Taylor series where
-a difference cancels; in nats for flooding and the adjoint, in bits for the
-layered check node) within 3e-5 relative."""
+a difference cancels; in nats for the adjoint, in bits for the layered and
+flooding check node) within 3e-5 relative."""
 import numpy as np
 import pytest
 
