@@ -67,27 +67,28 @@ template <> struct CnsMag<kF16> {
         return __uint_as_float(__float_as_uint(m) | (neg << 31));
     }
 };
-// Integer <-> float for 0 <= x < 2^22 with FP32 adds instead of conversion
-// instructions: adding 1.5 * 2^23 puts the integer nearest to x (ties to even,
-// the FADD's rounding) in the low mantissa bits; subtracting it back is exact.
-constexpr float kMagic = 12582912.0f;  // 1.5 * 2^23, bits 0x4B400000
-__device__ __forceinline__ float fix6_round(float x) { return __fsub_rn(__fadd_rn(x, kMagic), kMagic); }
-__device__ __forceinline__ float fix6_value(unsigned q) { return __fsub_rn(__uint_as_float(0x4B400000u | q), kMagic); }
+// The 0.5 grid with FP32 adds instead of conversion instructions: adding
+// 1.5 * 2^22 (whose ulp is 0.5) rounds 0 <= x < 2^21 to the nearest multiple of
+// 0.5, ties to an even number of halves (= rint(2 x) / 2), and leaves that
+// number of halves as an integer in the low mantissa bits; subtracting it back
+// is exact.
+constexpr float kHalfMagic = 6291456.0f;  // 1.5 * 2^22, bits 0x4AC00000
 
 template <> struct CnsMag<kFix6> {
     int q1, q2;      // magnitude codes 0..31 (steps of 0.5)
     float r1, r2;    // their values
-    // q = min(31, rint(2 v)) for 0 <= v <= clamp (2 v < 2^22)
+    // q = min(31, rint(2 v)) and r = q / 2 for 0 <= v <= clamp
     __device__ __forceinline__ void set(float v1, float v2) {
-        const float a = fminf(fix6_round(v1 * 2.0f), 31.0f), b = fminf(fix6_round(v2 * 2.0f), 31.0f);
-        q1 = (int)(__float_as_uint(__fadd_rn(a, kMagic)) & 63u);
-        q2 = (int)(__float_as_uint(__fadd_rn(b, kMagic)) & 63u);
-        r1 = a * 0.5f;
-        r2 = b * 0.5f;
+        const float a = fminf(__fadd_rn(v1, kHalfMagic), kHalfMagic + 15.5f);
+        const float b = fminf(__fadd_rn(v2, kHalfMagic), kHalfMagic + 15.5f);
+        q1 = (int)(__float_as_uint(a) & 63u);
+        q2 = (int)(__float_as_uint(b) & 63u);
+        r1 = __fsub_rn(a, kHalfMagic);
+        r2 = __fsub_rn(b, kHalfMagic);
     }
     __device__ __forceinline__ void values() {
-        r1 = fix6_value((unsigned)q1) * 0.5f;
-        r2 = fix6_value((unsigned)q2) * 0.5f;
+        r1 = __fsub_rn(__uint_as_float(0x4AC00000u | (unsigned)q1), kHalfMagic);
+        r2 = __fsub_rn(__uint_as_float(0x4AC00000u | (unsigned)q2), kHalfMagic);
     }
     // The 6-bit store holds a signed integer, so it has no negative zero; a
     // zero message here may carry the sign bit. Both give the same sums: the

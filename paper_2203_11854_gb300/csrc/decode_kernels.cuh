@@ -114,7 +114,6 @@ __device__ __forceinline__ float phi_fast(float x) {
     return y < 0.0625f ? y * (1.0f - y * (0.5f - y * (1.0f / 3.0f - y * 0.25f))) : hw_log2(1.0f + y) * kLn2;
 }
 
-template <bool FAST> __device__ __forceinline__ float phi_t(float x) { return FAST ? phi_fast(x) : phi(x); }
 
 struct Params {
     const uint32_t *blk;
