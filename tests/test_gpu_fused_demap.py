@@ -136,3 +136,20 @@ def test_fused_per_edge_minsum(lx, name, B, prec):
                     two_step(lx, code, y, no, m, lx.DEMAP_MAXLOG, 20.0, dec))
     finally:
         lx.ldpcx_tune_set(lx.TUNE_CN_STATE, 1)
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_fused_full_size_launch_equals_two_step(lx, prec):
+    """The launch the bench step times: BG1-shaped Z = 384, 4096 codewords, 16-QAM max-log at Eb/N0 = 2 dB with
+    one N0, layered min-sum for 20 iterations without early stop (FP16; 6-bit as in the 256-QAM sweep's
+    variant), bits and iteration counts only. Equal bit for bit to demap_app followed by ldpc_bp_decode,
+    whose full-size launch is compared with the oracle's FP32 replay in test_gpu_parity.py."""
+    code = build(lx, "bg1_z384")
+    B, m = 4096, 4
+    dec = dict(algo=0, msg_prec=prec, iters=20, early_stop=False, offset=0.5, clamp=20.0)
+    y, no = channel(lx, code, B, m, 2.0, per_cw=False)
+    _, bits_f, its_f = lx.ldpc_bp_decode_qam(code, y, no, m, demap_method=lx.DEMAP_MAXLOG, demap_clamp=20.0, **dec)
+    llr = lx.demap_app(y, no, m, method=lx.DEMAP_MAXLOG, clamp=20.0)
+    _, bits_t, its_t = lx.ldpc_bp_decode(code, llr, **dec)
+    assert torch.equal(bits_f, bits_t) and torch.equal(its_f, its_t)
+    assert (its_f == 20).all()
