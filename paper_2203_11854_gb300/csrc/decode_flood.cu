@@ -82,6 +82,20 @@ __device__ __forceinline__ void flood_check(const Params &p, const float *app, c
     }
 }
 
+// The check-node update with an exact-degree body for the short rows of the
+// 5G-shaped base graphs (the extension rows: degree 4 or 5, 5 or 6), where
+// no edge slot is predicated off, and the predicated DMAX body for the rest
+// (the dense core rows lose a slot or two): the same operations in the same
+// order either way.
+template <int DMAX, int ALGO, int PREC>
+__device__ __forceinline__ void flood_check_any(const Params &p, const float *app, const uint32_t *vb, int deg, int z,
+                                                typename MsgT<PREC>::T *ml, const float *w, bool load, float *ck) {
+    constexpr int D0 = DMAX <= 12 ? 4 : 5;
+    if (deg == D0) flood_check<D0, ALGO, PREC>(p, app, vb, D0, z, ml, w, load, ck);
+    else if (deg == D0 + 1) flood_check<D0 + 1, ALGO, PREC>(p, app, vb, D0 + 1, z, ml, w, load, ck);
+    else flood_check<DMAX, ALGO, PREC>(p, app, vb, deg, z, ml, w, load, ck);
+}
+
 // Flooding BP, G codewords per CTA (flood_threads threads); each phase is one
 // strided loop over the items of all G codewords, so that small codes fill the
 // CTA.
@@ -125,7 +139,7 @@ __global__ void __launch_bounds__(512, 2) k_flooding(const __grid_constant__ Par
                 const size_t e0 = (size_t)b0 * p.Z + it.z;
                 MT *mp = reinterpret_cast<MT *>(p.msg) + cw * p.msg_stride;
                 float *ck = ckpt ? p.ckpt + (size_t)t * p.ckpt_tstride + (size_t)cw * p.msg_stride + e0 : nullptr;
-                flood_check<DMAX, ALGO, PREC>(p, cur + (size_t)gg * p.n, s_vb + b0, deg, it.z, mp + e0,
+                flood_check_any<DMAX, ALGO, PREC>(p, cur + (size_t)gg * p.n, s_vb + b0, deg, it.z, mp + e0,
                                               w_t ? w_t + b0 : nullptr, t > 0, ck);
             }
         }
