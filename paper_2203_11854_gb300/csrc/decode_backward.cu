@@ -21,6 +21,8 @@
 // accumulates in grad_llr itself, iteration by iteration.
 #include <math.h>
 
+#include <type_traits>
+
 #include "decode_kernels.cuh"
 
 namespace ldpcx {
@@ -170,91 +172,104 @@ __global__ void __launch_bounds__(512, TPC == 4 ? 2 : 1) k_backward(const BwdPar
                 row_values<DPT, TPC>(ck, active && ck, b1, d1, q, p.Z, ckn);
                 row_values<DPT, TPC>(carry, active && has_carry, b1, d1, q, p.Z, cyn);
             }
-            float gw[DPT];
-            float V[DPT], d[DPT], f[DPT], u[DPT];
-            int vi[DPT];
-            // this thread's edges: the sign parity, its largest phi term and their sum
-            unsigned par = 0;
-            float fmax = -1.0f;
-            int im = -1;
-#pragma unroll
-            for (int i = 0; i < DPT; ++i) {
-                const int j = q + TPC * i;
-                gw[i] = V[i] = d[i] = f[i] = u[i] = 0.0f;
-                vi[i] = 0;
-                if (TPC * i < deg && active && j < deg) {  // the first test is warp-uniform
-                    vi[i] = vn_of(s_vb[b0 + j], z, p.Z);
-                    d[i] = __fsub_rn(s_app[off + vi[i]], ckc[i]);
-                    V[i] = w_t ? __fmul_rn(w_t[b0 + j], d[i]) : d[i];
-                    f[i] = dec::phi_fast(fminf(fmaxf(fabsf(V[i]), lo), hi));
-                    par ^= V[i] < 0.0f ? 1u : 0u;
-                    if (f[i] > fmax) {
-                        fmax = f[i];
-                        im = i;
+            // the row body for NS edge slots per lane (the row's own count: one for a degree of at most TPC), so
+            // that no slot the row does not use is issued; the same operations in the same order for any NS
+            auto row_body = [&](auto ns_tag) {
+                constexpr int NS = decltype(ns_tag)::value;
+                float gw[NS];
+                float V[NS], d[NS], f[NS], u[NS];
+                int vi[NS];
+                // this thread's edges: the sign parity, its largest phi term and their sum
+                unsigned par = 0;
+                float fmax = -1.0f;
+                int im = -1;
+    #pragma unroll
+                for (int i = 0; i < NS; ++i) {
+                    const int j = q + TPC * i;
+                    gw[i] = V[i] = d[i] = f[i] = u[i] = 0.0f;
+                    vi[i] = 0;
+                    if (TPC * i < deg && active && j < deg) {  // the first test is warp-uniform
+                        vi[i] = vn_of(s_vb[b0 + j], z, p.Z);
+                        d[i] = __fsub_rn(s_app[off + vi[i]], ckc[i]);
+                        V[i] = w_t ? __fmul_rn(w_t[b0 + j], d[i]) : d[i];
+                        f[i] = dec::phi_fast(fminf(fmaxf(fabsf(V[i]), lo), hi));
+                        par ^= V[i] < 0.0f ? 1u : 0u;
+                        if (f[i] > fmax) {
+                            fmax = f[i];
+                            im = i;
+                        }
                     }
                 }
-            }
-            // the row's largest term (ties: the lowest edge index) leaves the running sum, as in the forward
-            float rmax = fmax;
-            int jmax = im >= 0 ? q + TPC * im : DMAX;
-#pragma unroll
-            for (int o = 1; o < TPC; o <<= 1) {
-                const float om = __shfl_xor_sync(0xFFFFFFFFu, rmax, o);
-                const int oj = __shfl_xor_sync(0xFFFFFFFFu, jmax, o);
-                if (om > rmax || (om == rmax && oj < jmax)) {
-                    rmax = om;
-                    jmax = oj;
-                }
-            }
-#pragma unroll
-            for (int o = 1; o < TPC; o <<= 1) par ^= __shfl_xor_sync(0xFFFFFFFFu, par, o);
-            float part = 0.0f;
-#pragma unroll
-            for (int i = 0; i < DPT; ++i)
-                if (q + TPC * i < deg && q + TPC * i != jmax) part += f[i];
-            const float s_rest = group_sum<TPC>(part);
-            const float s_all = s_rest + rmax;
-            // u_e = gC_e s_e phi'(x_e) [lo < S_e < hi]
-            float usum = 0.0f;
-#pragma unroll
-            for (int i = 0; i < DPT; ++i) {
-                const int j = q + TPC * i;
-                if (TPC * i < deg && active && j < deg) {  // the first test is warp-uniform
-                    const float S = j == jmax ? s_rest : s_all - f[i];
-                    const float gC = gin[off + vi[i]] + cyc[i];
-                    const float sg = (par ^ (V[i] < 0.0f ? 1u : 0u)) ? -1.0f : 1.0f;
-                    u[i] = (S > lo && S < hi) ? gC * sg * dphi_fast(S) : 0.0f;
-                    usum += u[i];
-                }
-            }
-            const float U_all = group_sum<TPC>(usum);
-            // gV_e = phi'(a_e) sgn(V_e) [lo <= |V_e| <= hi] sum_{e' != e} u_e'
-#pragma unroll
-            for (int i = 0; i < DPT; ++i) {
-                const int j = q + TPC * i;
-                if (TPC * i < deg && active && j < deg) {  // the first test is warp-uniform
-                    const float U = U_all - u[i];
-                    const float a = fabsf(V[i]);
-                    const bool inside = a >= lo && a <= hi;
-                    const float gV = inside ? dphi_fast(a) * (V[i] < 0.0f ? -1.0f : 1.0f) * U : 0.0f;
-                    const float w = w_t ? w_t[b0 + j] : 1.0f;
-                    gw[i] = gV * d[i];
-                    gout[off + vi[i]] += w * gV;
-                    carry[(size_t)(b0 + j) * p.Z] = -w * gV;
-                }
-            }
-            // weight gradient: the lanes of a warp with the same q are at the same blocks b0 + q + TPC i
-            if (p.grad_w) {
-#pragma unroll
-                for (int i = 0; i < DPT; ++i) {
-                    if (TPC * i < deg) {  // warp-uniform: some lane of the warp has an edge in slot i
-                        float x = gw[i];
-#pragma unroll
-                        for (int o = TPC; o < 32; o <<= 1) x += __shfl_xor_sync(0xFFFFFFFFu, x, o);
-                        const int j = q + TPC * i;
-                        if ((threadIdx.x & 31) < TPC && j < deg && x != 0.0f) atomicAdd(&s_gw[b0 + j], x);
+                // the row's largest term (ties: the lowest edge index) leaves the running sum, as in the forward
+                float rmax = fmax;
+                int jmax = im >= 0 ? q + TPC * im : DMAX;
+    #pragma unroll
+                for (int o = 1; o < TPC; o <<= 1) {
+                    const float om = __shfl_xor_sync(0xFFFFFFFFu, rmax, o);
+                    const int oj = __shfl_xor_sync(0xFFFFFFFFu, jmax, o);
+                    if (om > rmax || (om == rmax && oj < jmax)) {
+                        rmax = om;
+                        jmax = oj;
                     }
                 }
+    #pragma unroll
+                for (int o = 1; o < TPC; o <<= 1) par ^= __shfl_xor_sync(0xFFFFFFFFu, par, o);
+                float part = 0.0f;
+    #pragma unroll
+                for (int i = 0; i < NS; ++i)
+                    if (q + TPC * i < deg && q + TPC * i != jmax) part += f[i];
+                const float s_rest = group_sum<TPC>(part);
+                const float s_all = s_rest + rmax;
+                // u_e = gC_e s_e phi'(x_e) [lo < S_e < hi]
+                float usum = 0.0f;
+    #pragma unroll
+                for (int i = 0; i < NS; ++i) {
+                    const int j = q + TPC * i;
+                    if (TPC * i < deg && active && j < deg) {  // the first test is warp-uniform
+                        const float S = j == jmax ? s_rest : s_all - f[i];
+                        const float gC = gin[off + vi[i]] + cyc[i];
+                        const float sg = (par ^ (V[i] < 0.0f ? 1u : 0u)) ? -1.0f : 1.0f;
+                        u[i] = (S > lo && S < hi) ? gC * sg * dphi_fast(S) : 0.0f;
+                        usum += u[i];
+                    }
+                }
+                const float U_all = group_sum<TPC>(usum);
+                // gV_e = phi'(a_e) sgn(V_e) [lo <= |V_e| <= hi] sum_{e' != e} u_e'
+    #pragma unroll
+                for (int i = 0; i < NS; ++i) {
+                    const int j = q + TPC * i;
+                    if (TPC * i < deg && active && j < deg) {  // the first test is warp-uniform
+                        const float U = U_all - u[i];
+                        const float a = fabsf(V[i]);
+                        const bool inside = a >= lo && a <= hi;
+                        const float gV = inside ? dphi_fast(a) * (V[i] < 0.0f ? -1.0f : 1.0f) * U : 0.0f;
+                        const float w = w_t ? w_t[b0 + j] : 1.0f;
+                        gw[i] = gV * d[i];
+                        gout[off + vi[i]] += w * gV;
+                        carry[(size_t)(b0 + j) * p.Z] = -w * gV;
+                    }
+                }
+                // weight gradient: the lanes of a warp with the same q are at the same blocks b0 + q + TPC i
+                if (p.grad_w) {
+    #pragma unroll
+                    for (int i = 0; i < NS; ++i) {
+                        if (TPC * i < deg) {  // warp-uniform: some lane of the warp has an edge in slot i
+                            float x = gw[i];
+    #pragma unroll
+                            for (int o = TPC; o < 32; o <<= 1) x += __shfl_xor_sync(0xFFFFFFFFu, x, o);
+                            const int j = q + TPC * i;
+                            if ((threadIdx.x & 31) < TPC && j < deg && x != 0.0f) atomicAdd(&s_gw[b0 + j], x);
+                        }
+                    }
+                }
+            };
+            const int ns = (deg + TPC - 1) / TPC;
+            if constexpr (DPT >= 2) {
+                if (ns == 1) row_body(std::integral_constant<int, 1>{});
+                else if (ns == 2) row_body(std::integral_constant<int, 2>{});
+                else row_body(std::integral_constant<int, DPT>{});
+            } else {
+                row_body(std::integral_constant<int, DPT>{});
             }
             __syncthreads();  // rows add into gA^t in ascending order
         }
