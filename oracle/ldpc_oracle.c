@@ -46,8 +46,9 @@
 /* generators" (OOPSLA 2014): a Weyl sequence with increment 0x9E3779B97F4A7C15 */
 /* followed by the 64-bit finaliser with constants 0xBF58476D1CE4E5B9 and     */
 /* 0x94D049BB133111EB and shifts 30, 27, 31.                                  */
-/* Parity unpinned against an external known-answer vector (none is in the   */
-/* container); the codes it seeds are pinned structurally.                    */
+/* Pinned by the first outputs of the reference implementation from state 0 */
+/* (tests/test_oracle_random.py); the codes it seeds are also pinned         */
+/* structurally.                                                              */
 /* ------------------------------------------------------------------------- */
 static uint64_t sm64_next(uint64_t *state)
 {

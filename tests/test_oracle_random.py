@@ -2,7 +2,8 @@
 
 Philox is pinned against an independent implementation (Triton's
 ``tl.philox``, run by Triton's CPU interpreter in a subprocess). The noise
-is pinned by its distribution (Kolmogorov-Smirnov against N(0,1), moments).
+is pinned by its distribution (Kolmogorov-Smirnov against N(0,1), moments). splitmix64,
+which seeds the codes, is pinned by known-answer outputs of its reference implementation.
 """
 import json
 import os
@@ -111,3 +112,17 @@ def test_box_muller_pair_values(orc):
     g0, g1 = orc.gauss_pair(0x80000000 - 128, 0x40000000)
     assert g0 == pytest.approx(0.0, abs=1e-12)
     assert g1 == pytest.approx(np.sqrt(-2 * np.log(u1)), rel=1e-15)
+
+
+def test_splitmix64_known_answer():
+    """The oracle's splitmix64 (it seeds the base matrices' shifts and block placement) against the first
+    outputs of the algorithm's reference implementation (S. Vigna, splitmix64.c, which accompanies the
+    xoshiro generators) started from state 0."""
+    import ctypes as C
+
+    import oracle
+    L = oracle.lib()
+    st = C.c_uint64(0)
+    got = [L.orc_splitmix64_next(C.byref(st)) for _ in range(3)]
+    assert got == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
+    assert st.value == (3 * 0x9E3779B97F4A7C15) % (1 << 64)  # the Weyl sequence's state after three draws
