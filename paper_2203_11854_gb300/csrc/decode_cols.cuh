@@ -41,26 +41,42 @@ struct GZWalk {
 
 // The blocks of each column in block order (= ascending row: blocks are
 // numbered row by row): s_cp[c] .. s_cp[c + 1] index s_cb, whose entries are
-// b << 16 | shift. blk: the code's block table (col << 16 | shift). Ends with a
-// block barrier.
+// b << 16 | shift. blk: the code's block table (col << 16 | shift). With at
+// most one column per thread, thread c scans the table for column c; with
+// more columns, one thread places the blocks by a counting sort (stable, so
+// ascending block order within a column): O(nnz + cols) instead of
+// O(cols nnz / threads). Ends with a block barrier.
 __device__ __forceinline__ void build_col_lists(const uint32_t *blk, int nnz, int cols, int32_t *s_cp,
                                                 uint32_t *s_cb) {
-    for (int c = threadIdx.x; c < cols; c += blockDim.x) {
+    if (cols <= (int)blockDim.x) {
+        const int c = threadIdx.x;
         int cnt = 0;
-        for (int b = 0; b < nnz; ++b) cnt += (int)(blk[b] >> 16) == c ? 1 : 0;
-        s_cp[c + 1] = cnt;
-    }
-    if (threadIdx.x == 0) s_cp[0] = 0;
-    __syncthreads();
-    if (threadIdx.x == 0)
-        for (int c = 0; c < cols; ++c) s_cp[c + 1] += s_cp[c];
-    __syncthreads();
-    for (int c = threadIdx.x; c < cols; c += blockDim.x) {
-        int e = s_cp[c];
+        if (c < cols)
+            for (int b = 0; b < nnz; ++b) cnt += (int)(blk[b] >> 16) == c ? 1 : 0;
+        if (c < cols) s_cp[c + 1] = cnt;
+        if (threadIdx.x == 0) s_cp[0] = 0;
+        __syncthreads();
+        if (threadIdx.x == 0)
+            for (int k = 0; k < cols; ++k) s_cp[k + 1] += s_cp[k];
+        __syncthreads();
+        if (c < cols) {
+            int e = s_cp[c];
+            for (int b = 0; b < nnz; ++b) {
+                const uint32_t bk = blk[b];
+                if ((int)(bk >> 16) == c) s_cb[e++] = (uint32_t)b << 16 | (bk & 0xFFFFu);
+            }
+        }
+    } else if (threadIdx.x == 0) {
+        for (int k = 0; k <= cols; ++k) s_cp[k] = 0;
+        for (int b = 0; b < nnz; ++b) ++s_cp[(blk[b] >> 16) + 1];
+        for (int k = 0; k < cols; ++k) s_cp[k + 1] += s_cp[k];
+        // place with s_cp[c] as column c's cursor, then shift the pointers back by one column
         for (int b = 0; b < nnz; ++b) {
             const uint32_t bk = blk[b];
-            if ((int)(bk >> 16) == c) s_cb[e++] = (uint32_t)b << 16 | (bk & 0xFFFFu);
+            s_cb[s_cp[bk >> 16]++] = (uint32_t)b << 16 | (bk & 0xFFFFu);
         }
+        for (int k = cols; k > 0; --k) s_cp[k] = s_cp[k - 1];
+        s_cp[0] = 0;
     }
     __syncthreads();
 }

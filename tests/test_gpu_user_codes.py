@@ -128,3 +128,26 @@ def test_unencodable_code_decodes(lx, orc):
     llr, _, _ = lx.ldpc_bp_decode(code, cuda(L), iters=4, llr_out=True)
     app, _, _ = orc.decode(orc.Graph(S, 8), L.astype(np.float64), algo=0, schedule=0, iters=4, prec=1, store=0)
     assert np.array_equal(llr.cpu().numpy(), app.astype(np.float32))
+
+
+def test_flooding_more_columns_than_threads(lx, orc):
+    """Flooding on a base matrix with more columns than a CTA has threads (600 columns of Z = 2, rows of degree
+    6): a CTA builds its column lists by the counting sort instead of one column per thread; min-sum
+    bit-exact against the oracle's FP32 replay, FP32 and FP16 messages, with early stop."""
+    g = inputs.rng(61)
+    R, C, Z = 300, 600, 2
+    S = -np.ones((R, C), dtype=np.int16)
+    for r in range(R):
+        for c in g.choice(C, size=6, replace=False):
+            S[r, c] = g.integers(Z)
+    code = lx.qc_ldpc_build_base(S, Z, C - R)
+    B = 9
+    L = inputs.gaussian_llrs(np.zeros((B, C * Z), np.uint8), 4.0, 62)
+    for prec in (0, 1):
+        llr, bits, its = lx.ldpc_bp_decode(code, cuda(L), algo=lx.FLOOD_MINSUM, iters=6, msg_prec=prec,
+                                           early_stop=True, llr_out=True)
+        app, hard, oits = orc.decode(orc.Graph(S, Z), L.astype(np.float64), algo=0, schedule=1, iters=6, prec=1,
+                                     store=prec, early_stop=True)
+        assert np.array_equal(llr.cpu().numpy(), app.astype(np.float32))
+        assert np.array_equal(unpack(bits.cpu().numpy(), code.k), hard[:, :code.k])
+        assert np.array_equal(its.cpu().numpy(), oits)
